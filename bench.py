@@ -1,0 +1,416 @@
+"""Benchmark of the plain-LRSTV ADMM iteration (arXiv 2204.12879, Algorithm 1)
+on GB300.
+
+One step = one full ADMM iteration (steps 1-7: L/T_z stencil, 3-D DFT
+Z-solve, fused F/S/multiplier update, t-SVT of the three gradient tensors)
+of the 200x200x80 Pavia-shaped synthetic cube (6 endmembers, 40 Voronoi
+cells, mixed Gaussian / impulse / stripe / dead-line noise), whose denoise is
+50 iterations.  Every 50 iterations the plan is re-initialised (lrstv_init,
+inside the timed region), so the timed iterations follow the real penalty
+schedule.  value = ADMM iterations per second over all ranks; cubes/s =
+value / 50.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun as independent replicas (one cube per rank, no
+collective on the data path); only the timing barrier and the max over ranks
+cross ranks.  --impl reference times the FP64 CPU oracle on the host cores
+(a bounded number of the same iterations).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "c1": {"recipe": "c1", "seed": 1, "iters": 20,
+           "desc": "32x32x16 synthetic cube, 4 endmembers, 12 Voronoi cells, Gaussian 0.1 + 10% impulse, 20 ADMM iterations"},
+    "c2": {"recipe": "c2", "seed": 2, "iters": 50,
+           "desc": "200x200x80 Pavia-shaped synthetic cube, 6 endmembers, 40 Voronoi cells, mixed noise (Gaussian U[0.1,0.2] per band, 20% impulse, stripes on 30% and dead lines on 10% of bands), 50 ADMM iterations"},
+    "c3": {"recipe": "c3", "seed": 3, "iters": 60,
+           "desc": "256x256x191 Washington-DC-shaped synthetic cube, 8 endmembers, mixed noise, 60 ADMM iterations"},
+}
+METRIC = "ADMM iterations/s (plain LRSTV, FP32, 1e-4 max-abs vs FP64 oracle)"
+UNIT = "iter/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+# ------------------------------------------------------------ multi-rank ---
+def dist_env():
+    """(rank, world, local_rank) from the torchrun environment."""
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Each rank denoises its own cube: a distinct seed per rank."""
+    return base_seed + 1000 * rank
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- clocks ---
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons while the
+    timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.rows = []
+        self.proc = None
+        self.gpu = gpu_index
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms",
+                 "200", "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        return self.summary()
+
+    def summary(self):
+        if not self.rows:
+            return None
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[1]) for r in self.rows]
+        mx = [num(r[2]) for r in self.rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "samples": len(self.rows), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ roofline ---
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def kernel_work(name, shape):
+    """Algorithmic work of one launch of each kernel: ('hbm', bytes) or
+    ('alu', flops); FP32 cubes are 4N bytes, half spectra 8 h n1 n2 bytes."""
+    n1, n2, n3 = shape
+    N = n1 * n2 * n3
+    P = n1 * n2
+    h = n3 // 2 + 1
+    nr, nc = max(n1, n2), min(n1, n2)
+    spec = 8 * h * P
+    if name == "l_tz":      # reads Y S Z G1 G2 F[3] G3[3], writes L T_z
+        return "hbm", 13 * 4 * N
+    if name == "fs_dual":   # reads Y L Z S G1 G2 E[3] G3[3] G4[3] ... writes F[3] S G1 G2 G3[3]
+        return "hbm", 23 * 4 * N
+    if name == "r2c_z":
+        return "hbm", 4 * N + spec
+    if name == "c2r_z":
+        return "hbm", spec + 4 * N
+    if name == "r2c_e":
+        return "hbm", 6 * 4 * N + 3 * spec
+    if name == "c2r_e":
+        return "hbm", 3 * spec + 12 * 4 * N
+    if name == "cgemm_z":   # average of the 4 spatial passes: 8 flops per complex MAC
+        return "alu", 8 * P * h * (n1 + n2) // 2
+    if name == "cgemm_e":
+        return "alu", 8 * nr * nc * nc * 3 * h
+    return None, 0
+
+
+def jacobi_flops(prof, shape):
+    """Algorithmic FP32 flops of the Jacobi launches: 16 nr per examined
+    column pair (|w_p|^2, |w_q|^2, w_p^H w_q) and 18 (nr + nc) per rotated pair
+    (phase, two complex scaled sums on W's and V's rows)."""
+    n1, n2, _ = shape
+    nr, nc = max(n1, n2), min(n1, n2)
+    return 16.0 * nr * prof.jacobi_pairs + 18.0 * (nr + nc) * prof.jacobi_rotations
+
+
+def traffic_for(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the
+    current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(workload, {}).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2204_12879_gb300", "csrc", rec["source"])
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return rec["dram_bytes_per_launch"] if digest == rec["source_sha256"] else None
+
+
+# ---------------------------------------------------------------- arms ---
+def make_input(wl, rank):
+    import numpy as np
+    from synthetic import RECIPES, make_cube
+    r = RECIPES[wl["recipe"]]
+    clean, noisy = make_cube(r, replica_seed(wl["seed"], rank))
+    return r.shape, clean, noisy.astype(np.float32)
+
+
+def run_ours(args, wl_name):
+    import numpy as np
+    import torch
+
+    from paper_2204_12879_gb300 import builder, lrstv
+    from synthetic import flat, mpsnr
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        builder.build()
+    barrier(world)
+    lrstv.load()
+
+    wl = WORKLOADS[wl_name]
+    shape, clean, Y = make_input(wl, rank)
+    n1, n2, n3 = shape
+    iters = wl["iters"]
+    params = lrstv.Params.make(n1, n2, max_iter=iters)
+    plan = lrstv.Plan(n1, n2, n3, params)
+    y_dev = torch.from_numpy(flat(Y)).cuda()
+    stream = torch.cuda.current_stream()
+
+    def step():
+        if plan.mu[1] >= iters:
+            plan.init(y_dev)
+        plan.iterate(1)
+
+    plan.init(y_dev)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit()
+                          else local)
+    clocks.start()
+    plan.profile_enable(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = t0.elapsed_time(t1)
+    clk = clocks.stop()
+    prof = plan.profile_read()
+    plan.profile_enable(False)
+    stats = plan.stats()
+    ms_max = max_over_ranks(ms, world, device=torch.device("cuda", local))
+
+    # end to end through the host-buffer call: H2D of Y, `iters` iterations,
+    # D2H of X and S, one full denoise per call
+    yh = torch.from_numpy(flat(Y)).pin_memory()
+    xh = torch.empty_like(yh).pin_memory()
+    sh = torch.empty_like(yh).pin_memory()
+    plan.run_host(yh, xh, sh)  # untimed warm-up call
+    e2e_ms = []
+    for _ in range(2):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.run_host(yh, xh, sh)
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e = max_over_ranks(min(e2e_ms), world, device=torch.device("cuda", local))
+    X = xh.numpy().astype(np.float64).reshape(shape, order="F")
+    quality = {"mpsnr_db": round(mpsnr(X, clean), 3),
+               "noisy_mpsnr_db": round(mpsnr(Y, clean), 3)}
+    plan.close()
+
+    if rank != 0:
+        return None
+    pk, pk_kind = peaks()
+    kernels = {}
+    for k in range(9):
+        if prof.launches[k]:
+            kernels[lrstv.kernel_name(k)] = {"launches": prof.launches[k],
+                                             "ms_per_launch": prof.ms[k] / prof.launches[k],
+                                             "share": prof.ms[k] / max(sum(prof.ms), 1e-9)}
+    dom = max(kernels, key=lambda n: kernels[n]["ms_per_launch"] * kernels[n]["launches"])
+    avg_s = kernels[dom]["ms_per_launch"] / 1e3
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    if dom == "jacobi":
+        flops = jacobi_flops(prof, shape) / prof.launches[6]
+        roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": fp32_peak,
+                "unit": "TFLOP/s"}
+    else:
+        bound, work = kernel_work(dom, shape)
+        if bound == "hbm":
+            roof = {"bound": "hbm", "achieved": work / avg_s / 1e9, "peak": pk["hbm_gbs"],
+                    "unit": "GB/s"}
+        else:
+            roof = {"bound": "alu", "achieved": work / avg_s / 1e12, "peak": fp32_peak,
+                    "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = dom
+    roof["peak_source"] = (("measured hbm_gbs" if roof["bound"] == "hbm" else
+                            "FP32 FMA: 152 SMs x 128 lanes x 2 x sm_max_mhz") + f" ({pk_kind})")
+    roof["traffic"] = traffic_for(dom, wl_name)
+    value = world * args.steps / (ms_max / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["desc"], "shape": list(shape), "iters_per_cube": iters,
+                   "cubes_per_s": value / iters, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "working set (18 state cubes + spectra, ~330 MB) exceeds the 129 MB L2"},
+        "roofline": roof,
+        "kernels": kernels,
+        "gpu_launches": int(sum(prof.launches)),
+        "jacobi": {"max_sweeps_last": stats.jacobi_max_sweeps,
+                   "unconverged_last": stats.jacobi_unconverged,
+                   "pairs": prof.jacobi_pairs, "rotations": prof.jacobi_rotations},
+        "e2e": {"value": world * iters / (e2e / 1e3), "unit": UNIT, "ms_per_cube": e2e,
+                "h2d_bytes_per_step": 4 * n1 * n2 * n3, "d2h_bytes_per_step": 8 * n1 * n2 * n3,
+                "step": f"one lrstv_plan_run_host call: copy Y in, {iters} iterations, copy X and S out"},
+        "quality": quality,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_baseline(wl, Y, budget_s=args.cpu_budget)
+    return line
+
+
+def oracle_baseline(wl, Y, budget_s=25.0, max_iters=None):
+    """Times the FP64 oracle (as it stands) on the same cube: whole ADMM
+    iterations from the initial state until the time budget is spent."""
+    import numpy as np
+
+    import oracle
+    r = Y.shape
+    st = oracle.State(Y.astype(np.float64), oracle.Params(n1=r[0], n2=r[1]))
+    done, t = 0, 0.0
+    while (t < budget_s or done == 0) and (max_iters is None or done < max_iters):
+        a = time.perf_counter()
+        st.iterate(1)
+        t += time.perf_counter() - a
+        done += 1
+    return {"value": done / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{done} ADMM iteration(s) of the {r[0]}x{r[1]}x{r[2]} cube from its initial state ({t:.1f} s)"}
+
+
+def run_reference(args, wl_name):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    wl = WORKLOADS[wl_name]
+    shape, clean, Y = make_input(wl, 0)
+    cb = oracle_baseline(wl, Y, budget_s=args.cpu_budget * 4, max_iters=max(args.steps, 1))
+    steps_run = int(cb["sample"].split()[0])
+    return {
+        "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 / cb["value"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["desc"], "shape": list(shape), "iters_per_cube": wl["iters"],
+                   "steps_timed": steps_run,
+                   "note": "FP64 CPU oracle on the host cores; a bounded number of the requested steps"},
+        "cpu_baseline": cb,
+        "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
+    ap.add_argument("--cpu-budget", type=float, default=20.0,
+                    help="seconds of oracle time for the cpu_baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be >= 3")
+    line = (run_reference if args.impl == "reference" else run_ours)(args, args.workload)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    _, world, _ = dist_env()
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

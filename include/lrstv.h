@@ -1,0 +1,219 @@
+/*
+ * lrstv.h -- C ABI of the GB300 (sm_103a) plain-LRSTV hyperspectral denoiser.
+ *
+ * Method: arXiv 2204.12879, "Low-rank Meets Sparseness: An Integrated
+ * Spatial-Spectral Total Variation Approach to Hyperspectral Denoising".
+ * The library runs the ADMM iteration of Section III-C (Algorithm 1) for the
+ * model min ||L||_LRSTV + lambda ||S||_1 s.t. Y = L + S (eq. TDLRSTV without
+ * the Tucker constraint, i.e. full Tucker ranks, so the HOOI step of the
+ * L-update is the identity).
+ *
+ * Conventions (every entry point):
+ *  - Cubes are FP32, n1 x n2 x n3, element (i, j, k) at i + n1*(j + n2*k)
+ *    (mode 1 fastest, frontal slices contiguous).  N = n1*n2*n3.
+ *  - Unless a name ends in _host, array arguments are DEVICE pointers owned
+ *    by the caller; the library never frees them.  Gradient-shaped arrays
+ *    (g, F, E, Gamma3, Gamma4) hold the three modes back to back: 3N floats.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is stream-ordered and asynchronous unless stated.
+ *  - Every call returns an lrstv_status.  No call aborts, traps or prints.
+ *  - A plan owns all of its device memory (one allocation made by
+ *    lrstv_plan_create); no other call of a plan allocates.
+ */
+#ifndef LRSTV_H
+#define LRSTV_H
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lrstv_status {
+  LRSTV_OK = 0,
+  LRSTV_ERR_ARG = 1,            /* null pointer, bad flag, bad scalar          */
+  LRSTV_ERR_SHAPE = 2,          /* size outside what the kernels support       */
+  LRSTV_ERR_CUDA = 3,           /* a CUDA runtime call or launch failed        */
+  LRSTV_ERR_ALLOC = 4,          /* device memory could not be allocated        */
+  LRSTV_ERR_NOT_CONVERGED = 5,  /* a Jacobi SVD hit its sweep cap              */
+  LRSTV_ERR_NONFINITE = 6       /* a residual is NaN or Inf                    */
+} lrstv_status;
+
+/* Flags (lrstv_params.flags). */
+#define LRSTV_FLAG_F_THRESH_EXACT 1u /* F threshold tau/(2 mu), the exact minimiser of the
+                                        F-subproblem, instead of the printed tau/mu (eq. F_solution) */
+#define LRSTV_FLAG_NO_GAMMA4 2u      /* keep Gamma4 = 0 (the paper lists only Gamma1..3 updates) */
+#define LRSTV_FLAG_GRAPH 4u          /* lrstv_plan_run replays its iterations as one CUDA graph */
+#define LRSTV_FLAG_STRICT 8u         /* stats report NOT_CONVERGED / NONFINITE as the return status */
+
+/* Scalars of Algorithm 1 (Section III-C; parameter roles in Section IV-D).
+ *  tau     weight of ||D_w L||_1 (gradient sparsity)
+ *  alpha   weight of the tensor nuclear norm of the gradient maps
+ *  lambda  weight of ||S||_1 (the paper suggests C / sqrt(n1 n2))
+ *  w[3]    weights of D_w = [w1 D1; w2 D2; w3 D3]
+ *  mu0, rho, mu_max   penalty schedule mu := min(rho mu, mu_max) (step 7)
+ *  eps     stopping tolerance of the convergence check (reported only; the
+ *          iteration count is max_iter)
+ *  max_iter iterations run by lrstv_plan_run / lrstv_denoise (>= 0) */
+typedef struct lrstv_params {
+  float tau, alpha, lambda;
+  float w[3];
+  float mu0, rho, mu_max, eps;
+  int max_iter;
+  unsigned flags;
+} lrstv_params;
+
+/* Filled after a synchronising call (lrstv_get_stats, lrstv_plan_run*). */
+typedef struct lrstv_stats {
+  int iters;                 /* iterations run since lrstv_init                  */
+  float res_inf[2];          /* ||Y-L-S||_inf and ||L-Z||_inf after the last one */
+  float mu;                  /* penalty for the next iteration                   */
+  int jacobi_unconverged;    /* Fourier slices whose SVD hit the sweep cap (last E-step) */
+  int jacobi_max_sweeps;     /* largest sweep count of the last E-step           */
+} lrstv_stats;
+
+/* State blocks for lrstv_state_get / lrstv_state_set.  Blocks of 3N floats
+ * are marked [3]. */
+typedef enum lrstv_block {
+  LRSTV_Y = 0, LRSTV_L = 1, LRSTV_Z = 2, LRSTV_S = 3, LRSTV_GAMMA1 = 4, LRSTV_GAMMA2 = 5,
+  LRSTV_F = 6 /*[3]*/, LRSTV_E = 7 /*[3]*/, LRSTV_GAMMA3 = 8 /*[3]*/, LRSTV_GAMMA4 = 9 /*[3]*/,
+  LRSTV_TZ = 10 /* right-hand side T_z of the last Z-step */
+} lrstv_block;
+
+typedef struct lrstv_plan lrstv_plan;
+
+/* ---------------------------------------------------------------- status */
+const char *lrstv_status_string(int status);
+/* Largest n1, n2 supported by the SVT kernels (min(n1, n2) and max(n1, n2)
+ * bound the Jacobi working matrix). */
+int lrstv_max_spatial(void);
+
+/* ------------------------------------------------------------- profiling */
+/* Kernels a plan launches (lrstv_profile indices). */
+typedef enum lrstv_kernel {
+  LRSTV_K_L_TZ = 0,     /* step 1 + T_z                                   */
+  LRSTV_K_R2C_Z = 1,    /* mode-3 DFT of T_z                              */
+  LRSTV_K_CGEMM_Z = 2,  /* spatial DFTs + spectral division (4 per Z-step) */
+  LRSTV_K_C2R_Z = 3,    /* inverse mode-3 DFT -> Z                        */
+  LRSTV_K_FS_DUAL = 4,  /* steps 3, 5, 6                                  */
+  LRSTV_K_R2C_E = 5,    /* mode-3 DFT of F - Gamma4/mu                    */
+  LRSTV_K_JACOBI = 6,   /* one-sided Jacobi + singular-value threshold    */
+  LRSTV_K_CGEMM_E = 7,  /* SVT reconstruction W (V diag g)^H              */
+  LRSTV_K_C2R_E = 8,    /* inverse mode-3 DFT -> E, Gamma4 update         */
+  LRSTV_NKERNEL = 9
+} lrstv_kernel;
+
+typedef struct lrstv_profile {
+  int launches[16];                     /* per lrstv_kernel                        */
+  double ms[16];                        /* summed device time (CUDA events)       */
+  unsigned long long jacobi_pairs;      /* column pairs examined by Jacobi sweeps  */
+  unsigned long long jacobi_rotations;  /* pairs that were rotated                 */
+} lrstv_profile;
+
+const char *lrstv_kernel_name(int kernel);
+/* on != 0: clears the counters and brackets every later kernel launch of the
+ * plan with CUDA events (none while a stream is being captured; at most 4096
+ * launches are recorded).  on == 0: stops recording. */
+int lrstv_profile_enable(lrstv_plan *plan, int on);
+/* Synchronises the recorded launches and sums their times and the Jacobi
+ * work counters since the last enable. */
+int lrstv_profile_read(lrstv_plan *plan, lrstv_profile *out);
+
+/* ------------------------------------------------------------------ plan */
+/* Allocates and initialises every device buffer for an n1 x n2 x n3 cube:
+ * the 18 state cubes of Algorithm 1, the half spectrum (n3/2 + 1 complex
+ * frontal slices) for the Z-solve and the t-SVT, the per-slice Jacobi
+ * matrices, and DFT tables.  Errors: ERR_ARG (null, n < 1), ERR_SHAPE (n1 or
+ * n2 above lrstv_max_spatial()), ERR_ALLOC, ERR_CUDA.  Uses the current
+ * device; the plan must be used with that device current. */
+int lrstv_plan_create(int n1, int n2, int n3, const lrstv_params *params, lrstv_plan **plan);
+int lrstv_plan_destroy(lrstv_plan *plan);
+/* Bytes of device memory the plan holds. */
+int lrstv_plan_bytes(const lrstv_plan *plan, size_t *bytes);
+/* Replaces the scalars (tau, alpha, lambda, w, mu0, rho, mu_max, eps,
+ * max_iter, flags); takes effect at the next step. */
+int lrstv_plan_set_params(lrstv_plan *plan, const lrstv_params *params);
+
+/* Initialisation of Algorithm 1 (left empty by the paper; this library's
+ * reading): L = Z = Y, S = F = E = 0, all multipliers 0, mu = mu0, iteration
+ * counter 0.  Y: device, N floats. */
+int lrstv_init(lrstv_plan *plan, const float *Y, void *stream);
+
+/* ------------------------------------------------------- per-step calls */
+/* Step 1 (eq. X_solution, full ranks): L = (Y - S + Z + (Gamma1 - Gamma2)/mu)/2,
+ * fused with the right-hand side of the Z-system (eq. Z_solution):
+ * T_z = mu L + Gamma2 + D_w^*(mu F - Gamma3). */
+int lrstv_step_l_tz(lrstv_plan *plan, void *stream);
+/* Step 2 (eq. Z_solution): Z = ifftn(fftn(T_z) / (mu (1 + P_z))). */
+int lrstv_step_z(lrstv_plan *plan, void *stream);
+/* Steps 3, 5 and 6 fused (eq. F_solution, S_solution, Multipliers):
+ * F_n = R_{tau/mu}((w_n D_n Z + Gamma3_n/mu + E_n + Gamma4_n/mu)/2),
+ * S = R_{lambda/mu}(Y - L + Gamma1/mu), Gamma1 += mu (Y - L - S),
+ * Gamma2 += mu (L - Z), Gamma3_n += mu (w_n D_n Z - F_n).  F reads the E of
+ * the previous iteration (Algorithm 1's order); S and Gamma1..3 do not read E,
+ * so fusing them before step 4 keeps the order's results. */
+int lrstv_step_fs_dual(lrstv_plan *plan, void *stream);
+/* Step 4 (eq. E_solution): E_n = t-SVT(F_n - Gamma4_n/mu, alpha/mu) for the
+ * three gradient tensors, then Gamma4_n += mu (E_n - F_n) (unless
+ * LRSTV_FLAG_NO_GAMMA4). */
+int lrstv_step_e(lrstv_plan *plan, void *stream);
+/* Step 7: mu := min(rho mu, mu_max), and the iteration counter advances. */
+int lrstv_step_mu(lrstv_plan *plan);
+/* `iters` full iterations (steps 1-7), stream-ordered, no host sync. */
+int lrstv_iterate(lrstv_plan *plan, int iters, void *stream);
+
+/* Synchronises `stream` and reports residuals, mu and Jacobi status. */
+int lrstv_get_stats(lrstv_plan *plan, lrstv_stats *stats, void *stream);
+/* Copies a state block to / from caller device memory (N or 3N floats,
+ * device-to-device, stream-ordered).  With lrstv_get_mu / lrstv_set_mu this
+ * checkpoints and resumes an ADMM run. */
+int lrstv_state_get(const lrstv_plan *plan, int block, float *dst, void *stream);
+int lrstv_state_set(lrstv_plan *plan, int block, const float *src, void *stream);
+int lrstv_get_mu(const lrstv_plan *plan, float *mu, int *iters);
+int lrstv_set_mu(lrstv_plan *plan, float mu, int iters);
+
+/* ----------------------------------------------------------- whole runs */
+/* The problem statement Y -> (X = L, S) of eq. TDLRSTV (plain form):
+ * lrstv_init, params.max_iter iterations, X := L and S copied out.  Device
+ * buffers of N floats.  Returns after enqueueing, except that stats (if not
+ * NULL) forces a synchronisation. */
+int lrstv_plan_run(lrstv_plan *plan, const float *Y, float *X, float *S, lrstv_stats *stats,
+                   void *stream);
+/* Same with HOST buffers: copies Y in, runs, copies X and S out, and
+ * synchronises `stream` before returning.  Pinned host memory gives
+ * asynchronous copies; pageable memory works too. */
+int lrstv_plan_run_host(lrstv_plan *plan, const float *Y_host, float *X_host, float *S_host,
+                        lrstv_stats *stats, void *stream);
+/* One-shot form: creates a plan, runs it, destroys it (synchronises). */
+int lrstv_denoise(const float *Y, int n1, int n2, int n3, const lrstv_params *params, float *X,
+                  float *S, lrstv_stats *stats, void *stream);
+
+/* ---------------------------------------------------- standalone operators */
+/* g_n = w_n D_n x, circular forward differences D_n x(v) = x(v + e_n) - x(v)
+ * along mode n (Section III-A).  x: N floats, g: 3N floats. */
+int lrstv_diff(const float *x, int n1, int n2, int n3, const float w[3], float *g, void *stream);
+/* x = D_w^* g = sum_n w_n D_n^T g_n, D_n^T g(v) = g(v - e_n) - g(v). */
+int lrstv_diff_adjoint(const float *g, int n1, int n2, int n3, const float w[3], float *x,
+                       void *stream);
+/* y = R_d(x) = sign(x) max(|x| - d, 0) elementwise (Section III-C, step 3;
+ * the printed second case is read as x < -d).  In place allowed. */
+int lrstv_soft_threshold(const float *x, size_t n, float d, float *y, void *stream);
+
+/* Scratch the standalone Z-solve and t-SVT need, in bytes (caller-owned,
+ * device memory, 256-byte aligned). */
+int lrstv_zsolve_workspace_size(int n1, int n2, int n3, size_t *bytes);
+int lrstv_tsvt_workspace_size(int n1, int n2, int n3, size_t *bytes);
+/* Z = ifftn(fftn(T) / (mu (1 + P_z))), P_z = sum_n w_n^2 |fftn(D_n)|^2
+ * (eq. Z_solution).  ERR_ARG if the workspace is too small. */
+int lrstv_zsolve(const float *T, int n1, int n2, int n3, const float w[3], float mu, float *Z,
+                 void *workspace, size_t workspace_bytes, void *stream);
+/* t-SVT of a real cube (eq. E_solution with Theorem 4.2's t-SVD): DFT along
+ * mode 3, singular values of every Fourier frontal slice soft-thresholded by
+ * t, inverse DFT.  `sweeps_host` (may be NULL) receives the largest Jacobi
+ * sweep count, negative if a slice hit the cap; passing it synchronises. */
+int lrstv_tsvt(const float *A, int n1, int n2, int n3, float t, float *out, void *workspace,
+               size_t workspace_bytes, int *sweeps_host, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,761 @@
+// api.cu -- the C ABI of include/lrstv.h: plans, the ADMM iteration of
+// arXiv 2204.12879 (Algorithm 1 with the full-rank L-update) as a sequence of
+// stream-ordered kernel launches, optional CUDA-graph replay of whole runs,
+// state import/export, and the standalone operators.
+#include <math.h>
+#include <new>
+#include <string.h>
+
+#include "lrstv.h"
+#include "lrstv_internal.cuh"
+
+namespace lrstv {
+
+Dims make_dims(int n1, int n2, int n3) {
+  Dims d;
+  d.n1 = n1;
+  d.n2 = n2;
+  d.n3 = n3;
+  d.P = (size_t)n1 * n2;
+  d.N = d.P * n3;
+  d.h = n3 / 2 + 1;
+  d.trans = n1 < n2 ? 1 : 0;
+  d.nr = n1 >= n2 ? n1 : n2;
+  d.nc = n1 >= n2 ? n2 : n1;
+  return d;
+}
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kResRing = 4096;     // per-iteration residual history
+constexpr int kMaxSweeps = 30;     // Jacobi sweep cap per slice and E-step
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Hands out 256-byte-aligned pieces of one allocation (or counts the bytes
+// when base is null).
+struct Carver {
+  char *base;
+  size_t off = 0;
+  explicit Carver(void *b) : base((char *)b) {}
+  template <class T>
+  T *take(size_t count) {
+    T *p = base ? (T *)(base + off) : nullptr;
+    off = align_up(off + sizeof(T) * count);
+    return p;
+  }
+};
+
+struct Tables {
+  float2 *tw3, *F1, *G1, *F2, *G2;
+  float *lam1, *lam2, *lam3;
+};
+
+void carve_tables(Carver &c, const Dims &d, Tables &t) {
+  t.tw3 = c.take<float2>(d.n3);
+  t.F1 = c.take<float2>((size_t)d.n1 * d.n1);
+  t.G1 = c.take<float2>((size_t)d.n1 * d.n1);
+  t.F2 = c.take<float2>((size_t)d.n2 * d.n2);
+  t.G2 = c.take<float2>((size_t)d.n2 * d.n2);
+  t.lam1 = c.take<float>(d.n1);
+  t.lam2 = c.take<float>(d.n2);
+  t.lam3 = c.take<float>(d.n3);
+}
+
+int check_shape(int n1, int n2, int n3) {
+  if (n1 < 1 || n2 < 1 || n3 < 1) return LRSTV_ERR_ARG;
+  if (n1 > kMaxSpatial || n2 > kMaxSpatial) return LRSTV_ERR_SHAPE;
+  if (n3 > kMaxBands) return LRSTV_ERR_SHAPE;  // mode-3 twiddles are staged in shared memory
+  if ((double)n1 * n2 * n3 * 3.0 > 2.0e9) return LRSTV_ERR_SHAPE;  // 3N fits a 32-bit grid walk
+  return LRSTV_OK;
+}
+
+int check_params(const lrstv_params *p) {
+  if (!p) return LRSTV_ERR_ARG;
+  const float v[] = {p->tau, p->alpha, p->lambda, p->w[0], p->w[1], p->w[2], p->mu0, p->rho,
+                     p->mu_max};
+  for (float x : v)
+    if (!isfinite(x) || x < 0.0f) return LRSTV_ERR_ARG;
+  if (!(p->mu0 > 0.0f) || !(p->mu_max >= p->mu0) || p->max_iter < 0) return LRSTV_ERR_ARG;
+  if (p->flags & ~(unsigned)(LRSTV_FLAG_F_THRESH_EXACT | LRSTV_FLAG_NO_GAMMA4 | LRSTV_FLAG_GRAPH |
+                             LRSTV_FLAG_STRICT))
+    return LRSTV_ERR_ARG;
+  return LRSTV_OK;
+}
+
+// Per-launch CUDA-event bracketing for lrstv_profile_* (off unless enabled).
+struct Prof {
+  static constexpr int kCap = 4096;
+  int on = 0;
+  int n = 0;
+  cudaEvent_t *ev = nullptr;  // 2 kCap events, created on first enable
+  unsigned char cls[kCap];
+  unsigned long long *d_work = nullptr;  // Jacobi [pairs, rotations], in the plan arena
+};
+
+// Records a begin event now and an end event when it goes out of scope,
+// around exactly one launch; skipped while `st` is being captured.
+struct Span {
+  Prof *p = nullptr;
+  int idx = -1;
+  cudaStream_t st;
+  Span(Prof *prof, int cls, cudaStream_t s) : st(s) {
+    if (!prof || !prof->on || prof->n >= Prof::kCap) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+      cudaGetLastError();
+      return;
+    }
+    p = prof;
+    idx = p->n++;
+    p->cls[idx] = (unsigned char)cls;
+    cudaEventRecord(p->ev[2 * idx], s);
+  }
+  ~Span() {
+    if (p) cudaEventRecord(p->ev[2 * idx + 1], st);
+  }
+};
+
+cudaError_t gemm_z(const CGemm &g, cudaStream_t st, Prof *prof) {
+  Span sp(prof, LRSTV_K_CGEMM_Z, st);
+  return launch_cgemm(g, st);
+}
+
+// Z-solve on h half-spectrum slices: specA <- fftn(T) / (mu (1 + P_z)) ->
+// ifftn -> Z.  specA, specB: h P complex each.
+cudaError_t zsolve_core(const Dims &d, const Tables &tb, const float *T, float mu, float *Z,
+                        float2 *specA, float2 *specB, cudaStream_t st, Prof *prof = nullptr) {
+  cudaError_t e;
+  {
+    Span sp(prof, LRSTV_K_R2C_Z, st);
+    e = launch_r2c3(d, 1, T, nullptr, 0.0f, specA, 0, tb.tw3, st);
+  }
+  if (e != cudaSuccess) return e;
+  CGemm g{};
+  g.M = d.n1;
+  g.N = d.n2;
+  g.batch = d.h;
+  g.lda = d.n1;
+  g.ldc = d.n1;
+  g.sC = (long long)d.P;
+  // mode 1: specB_k = F1 specA_k
+  g.A = tb.F1; g.sA = 0; g.B = specA; g.sB = (long long)d.P; g.ldb = d.n1; g.K = d.n1;
+  g.C = specB; g.opB = 0; g.epi = 0;
+  if ((e = gemm_z(g, st, prof)) != cudaSuccess) return e;
+  // mode 2 + spectral division: specA_k = (specB_k F2) / (mu (1 + P_z)) / (n1 n2)
+  g.A = specB; g.sA = (long long)d.P; g.B = tb.F2; g.sB = 0; g.ldb = d.n2; g.K = d.n2;
+  g.C = specA; g.epi = 1; g.lam1 = tb.lam1; g.lam2 = tb.lam2; g.lam3 = tb.lam3; g.mu = mu;
+  g.scale = (float)(1.0 / ((double)d.n1 * (double)d.n2));
+  if ((e = gemm_z(g, st, prof)) != cudaSuccess) return e;
+  // inverse mode 1 and mode 2
+  g.epi = 0;
+  g.A = tb.G1; g.sA = 0; g.B = specA; g.sB = (long long)d.P; g.ldb = d.n1; g.K = d.n1; g.C = specB;
+  if ((e = gemm_z(g, st, prof)) != cudaSuccess) return e;
+  g.A = specB; g.sA = (long long)d.P; g.B = tb.G2; g.sB = 0; g.ldb = d.n2; g.K = d.n2; g.C = specA;
+  if ((e = gemm_z(g, st, prof)) != cudaSuccess) return e;
+  Span sp(prof, LRSTV_K_C2R_Z, st);
+  return launch_c2r3(d, 1, specA, 0, tb.tw3, Z, 0, nullptr, nullptr, 0.0f, 0, st);
+}
+
+// t-SVT of nb cubes x_b - ycoef y_b with threshold t: DFT along mode 3 into
+// the working orientation, Jacobi + g-scaling, W V^H, inverse DFT.
+cudaError_t tsvt_core(const Dims &d, int nb, const float *x, const float *y, float ycoef, float t,
+                      float *out, int mode, float *G4, const float *F, float mu, int gamma4,
+                      const float2 *tw3, float2 *specA, float2 *specB, float2 *V, int *sweeps,
+                      cudaStream_t st, Prof *prof = nullptr) {
+  cudaError_t e;
+  {
+    Span sp(prof, LRSTV_K_R2C_E, st);
+    e = launch_r2c3(d, nb, x, y, ycoef, specA, 1, tw3, st);
+  }
+  if (e != cudaSuccess) return e;
+  const int ns = nb * d.h;
+  {
+    Span sp(prof, LRSTV_K_JACOBI, st);
+    e = launch_jacobi(d, ns, specA, V, t, kMaxSweeps, sweeps, prof ? prof->d_work : nullptr, st);
+  }
+  if (e != cudaSuccess) return e;
+  CGemm g{};
+  g.A = specA; g.sA = (long long)d.P; g.lda = d.nr;
+  g.B = V; g.sB = (long long)d.nc * d.nc; g.ldb = d.nc; g.opB = 1;
+  g.C = specB; g.sC = (long long)d.P; g.ldc = d.nr;
+  g.M = d.nr; g.N = d.nc; g.K = d.nc; g.batch = ns; g.epi = 0;
+  {
+    Span sp(prof, LRSTV_K_CGEMM_E, st);
+    e = launch_cgemm(g, st);
+  }
+  if (e != cudaSuccess) return e;
+  Span sp(prof, LRSTV_K_C2R_E, st);
+  return launch_c2r3(d, nb, specB, 1, tw3, out, mode, G4, F, mu, gamma4, st);
+}
+
+}  // namespace
+}  // namespace lrstv
+
+using namespace lrstv;
+
+struct lrstv_plan {
+  Dims d;
+  lrstv_params prm;
+  double mu;
+  int iter;
+  void *arena;
+  size_t arena_bytes;
+  float *Y, *L, *Z, *S, *G1, *G2, *F, *E, *G3, *G4, *T;
+  float2 *specA, *specB, *V;
+  Tables tb;
+  unsigned *res;  // kResRing x 2 residual maxima (float bits)
+  int *sweeps;    // 3h
+  // graph cache for lrstv_plan_run
+  cudaGraphExec_t gexec;
+  const void *gY;
+  void *gX, *gS;
+  int giters;
+  cudaStream_t cap_stream;
+  Prof prof;
+};
+
+#define CK(x)                                   \
+  do {                                          \
+    if ((x) != cudaSuccess) return LRSTV_ERR_CUDA; \
+  } while (0)
+
+namespace {
+
+size_t plan_layout(lrstv_plan *pl, void *base) {
+  const Dims &d = pl->d;
+  Carver c(base);
+  pl->Y = c.take<float>(d.N);
+  pl->L = c.take<float>(d.N);
+  pl->Z = c.take<float>(d.N);
+  pl->S = c.take<float>(d.N);
+  pl->G1 = c.take<float>(d.N);
+  pl->G2 = c.take<float>(d.N);
+  pl->F = c.take<float>(3 * d.N);
+  pl->E = c.take<float>(3 * d.N);
+  pl->G3 = c.take<float>(3 * d.N);
+  pl->G4 = c.take<float>(3 * d.N);
+  pl->T = c.take<float>(d.N);
+  pl->specA = c.take<float2>(3 * (size_t)d.h * d.P);
+  pl->specB = c.take<float2>(3 * (size_t)d.h * d.P);
+  pl->V = c.take<float2>(3 * (size_t)d.h * d.nc * d.nc);
+  carve_tables(c, d, pl->tb);
+  pl->res = c.take<unsigned>(2 * (size_t)kResRing);
+  pl->sweeps = c.take<int>(3 * (size_t)d.h);
+  pl->prof.d_work = c.take<unsigned long long>(2);
+  return c.off;
+}
+
+float *block_ptr(const lrstv_plan *pl, int block, size_t *count) {
+  const size_t N = pl->d.N;
+  *count = N;
+  switch (block) {
+    case LRSTV_Y: return pl->Y;
+    case LRSTV_L: return pl->L;
+    case LRSTV_Z: return pl->Z;
+    case LRSTV_S: return pl->S;
+    case LRSTV_GAMMA1: return pl->G1;
+    case LRSTV_GAMMA2: return pl->G2;
+    case LRSTV_TZ: return pl->T;
+    case LRSTV_F: *count = 3 * N; return pl->F;
+    case LRSTV_E: *count = 3 * N; return pl->E;
+    case LRSTV_GAMMA3: *count = 3 * N; return pl->G3;
+    case LRSTV_GAMMA4: *count = 3 * N; return pl->G4;
+    default: return nullptr;
+  }
+}
+
+void drop_graph(lrstv_plan *pl) {
+  if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
+  pl->gexec = nullptr;
+  pl->gY = nullptr;
+  pl->gX = pl->gS = nullptr;
+  pl->giters = -1;
+}
+
+int init_async(lrstv_plan *pl, const float *Y, cudaStream_t st) {
+  const size_t bytes = sizeof(float) * pl->d.N;
+  if (Y != pl->Y) CK(cudaMemcpyAsync(pl->Y, Y, bytes, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(pl->L, pl->Y, bytes, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(pl->Z, pl->Y, bytes, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(pl->S, 0, bytes, st));
+  CK(cudaMemsetAsync(pl->G1, 0, bytes, st));
+  CK(cudaMemsetAsync(pl->G2, 0, bytes, st));
+  CK(cudaMemsetAsync(pl->F, 0, 3 * bytes, st));
+  CK(cudaMemsetAsync(pl->E, 0, 3 * bytes, st));
+  CK(cudaMemsetAsync(pl->G3, 0, 3 * bytes, st));
+  CK(cudaMemsetAsync(pl->G4, 0, 3 * bytes, st));
+  CK(cudaMemsetAsync(pl->res, 0, sizeof(unsigned) * 2 * kResRing, st));
+  CK(cudaMemsetAsync(pl->sweeps, 0, sizeof(int) * 3 * pl->d.h, st));
+  pl->mu = pl->prm.mu0;
+  pl->iter = 0;
+  return LRSTV_OK;
+}
+
+int iterate_async(lrstv_plan *pl, int iters, cudaStream_t st) {
+  for (int it = 0; it < iters; ++it) {
+    int rc;
+    if ((rc = lrstv_step_l_tz(pl, st)) != LRSTV_OK) return rc;
+    if ((rc = lrstv_step_z(pl, st)) != LRSTV_OK) return rc;
+    if ((rc = lrstv_step_fs_dual(pl, st)) != LRSTV_OK) return rc;
+    if ((rc = lrstv_step_e(pl, st)) != LRSTV_OK) return rc;
+    if ((rc = lrstv_step_mu(pl)) != LRSTV_OK) return rc;
+  }
+  return LRSTV_OK;
+}
+
+int copy_out(lrstv_plan *pl, float *X, float *S, cudaMemcpyKind kind, cudaStream_t st) {
+  const size_t bytes = sizeof(float) * pl->d.N;
+  if (X) CK(cudaMemcpyAsync(X, pl->L, bytes, kind, st));
+  if (S) CK(cudaMemcpyAsync(S, pl->S, bytes, kind, st));
+  return LRSTV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lrstv_status_string(int s) {
+  switch (s) {
+    case LRSTV_OK: return "ok";
+    case LRSTV_ERR_ARG: return "invalid argument";
+    case LRSTV_ERR_SHAPE: return "unsupported cube shape";
+    case LRSTV_ERR_CUDA: return "CUDA runtime error";
+    case LRSTV_ERR_ALLOC: return "device allocation failed";
+    case LRSTV_ERR_NOT_CONVERGED: return "Jacobi SVD reached its sweep cap";
+    case LRSTV_ERR_NONFINITE: return "non-finite residual";
+    default: return "unknown status";
+  }
+}
+
+int lrstv_max_spatial(void) { return kMaxSpatial; }
+
+const char *lrstv_kernel_name(int k) {
+  static const char *names[LRSTV_NKERNEL] = {"l_tz", "r2c_z", "cgemm_z", "c2r_z", "fs_dual",
+                                             "r2c_e", "jacobi", "cgemm_e", "c2r_e"};
+  return (k >= 0 && k < LRSTV_NKERNEL) ? names[k] : "unknown";
+}
+
+int lrstv_profile_enable(lrstv_plan *pl, int on) {
+  if (!pl) return LRSTV_ERR_ARG;
+  Prof &p = pl->prof;
+  if (on && !p.ev) {
+    p.ev = new (std::nothrow) cudaEvent_t[2 * Prof::kCap];
+    if (!p.ev) return LRSTV_ERR_ALLOC;
+    for (int i = 0; i < 2 * Prof::kCap; ++i) {
+      if (cudaEventCreate(&p.ev[i]) != cudaSuccess) {
+        for (int j = 0; j < i; ++j) cudaEventDestroy(p.ev[j]);
+        delete[] p.ev;
+        p.ev = nullptr;
+        return LRSTV_ERR_CUDA;
+      }
+    }
+  }
+  if (on) {
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemset(p.d_work, 0, 2 * sizeof(unsigned long long)));
+    p.n = 0;
+  }
+  p.on = on ? 1 : 0;
+  return LRSTV_OK;
+}
+
+int lrstv_profile_read(lrstv_plan *pl, lrstv_profile *out) {
+  if (!pl || !out) return LRSTV_ERR_ARG;
+  memset(out, 0, sizeof(*out));
+  Prof &p = pl->prof;
+  for (int i = 0; i < p.n; ++i) {
+    CK(cudaEventSynchronize(p.ev[2 * i + 1]));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, p.ev[2 * i], p.ev[2 * i + 1]));
+    out->launches[p.cls[i]] += 1;
+    out->ms[p.cls[i]] += ms;
+  }
+  unsigned long long w[2];
+  CK(cudaMemcpy(w, p.d_work, sizeof(w), cudaMemcpyDeviceToHost));
+  out->jacobi_pairs = w[0];
+  out->jacobi_rotations = w[1];
+  return LRSTV_OK;
+}
+
+int lrstv_plan_create(int n1, int n2, int n3, const lrstv_params *params, lrstv_plan **plan) {
+  if (!plan) return LRSTV_ERR_ARG;
+  *plan = nullptr;
+  int rc = check_shape(n1, n2, n3);
+  if (rc) return rc;
+  if ((rc = check_params(params))) return rc;
+  lrstv_plan *pl = new (std::nothrow) lrstv_plan();
+  if (!pl) return LRSTV_ERR_ALLOC;
+  pl->d = make_dims(n1, n2, n3);
+  pl->prm = *params;
+  pl->giters = -1;
+  pl->arena_bytes = plan_layout(pl, nullptr);
+  if (cudaMalloc(&pl->arena, pl->arena_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete pl;
+    return LRSTV_ERR_ALLOC;
+  }
+  plan_layout(pl, pl->arena);
+  if (cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMemsetAsync(pl->arena, 0, pl->arena_bytes, pl->cap_stream) != cudaSuccess ||
+      launch_tables(pl->d, pl->prm.w, pl->tb.tw3, pl->tb.F1, pl->tb.G1, pl->tb.F2, pl->tb.G2,
+                    pl->tb.lam1, pl->tb.lam2, pl->tb.lam3, pl->cap_stream) != cudaSuccess ||
+      cudaStreamSynchronize(pl->cap_stream) != cudaSuccess) {
+    cudaGetLastError();
+    if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+    cudaFree(pl->arena);
+    delete pl;
+    return LRSTV_ERR_CUDA;
+  }
+  pl->mu = pl->prm.mu0;
+  *plan = pl;
+  return LRSTV_OK;
+}
+
+int lrstv_plan_destroy(lrstv_plan *pl) {
+  if (!pl) return LRSTV_ERR_ARG;
+  drop_graph(pl);
+  int rc = LRSTV_OK;
+  if (pl->prof.ev) {
+    for (int i = 0; i < 2 * Prof::kCap; ++i) cudaEventDestroy(pl->prof.ev[i]);
+    delete[] pl->prof.ev;
+  }
+  if (cudaStreamDestroy(pl->cap_stream) != cudaSuccess) rc = LRSTV_ERR_CUDA;
+  if (cudaFree(pl->arena) != cudaSuccess) rc = LRSTV_ERR_CUDA;
+  delete pl;
+  return rc;
+}
+
+int lrstv_plan_bytes(const lrstv_plan *pl, size_t *bytes) {
+  if (!pl || !bytes) return LRSTV_ERR_ARG;
+  *bytes = pl->arena_bytes;
+  return LRSTV_OK;
+}
+
+int lrstv_plan_set_params(lrstv_plan *pl, const lrstv_params *params) {
+  if (!pl) return LRSTV_ERR_ARG;
+  int rc = check_params(params);
+  if (rc) return rc;
+  const bool wchg = memcmp(pl->prm.w, params->w, sizeof(params->w)) != 0;
+  pl->prm = *params;
+  drop_graph(pl);
+  if (wchg) {
+    const Tables &t = pl->tb;
+    if (launch_tables(pl->d, pl->prm.w, t.tw3, t.F1, t.G1, t.F2, t.G2, t.lam1, t.lam2, t.lam3,
+                      pl->cap_stream) != cudaSuccess ||
+        cudaStreamSynchronize(pl->cap_stream) != cudaSuccess)
+      return LRSTV_ERR_CUDA;
+  }
+  return LRSTV_OK;
+}
+
+int lrstv_init(lrstv_plan *pl, const float *Y, void *stream) {
+  if (!pl || !Y) return LRSTV_ERR_ARG;
+  return init_async(pl, Y, (cudaStream_t)stream);
+}
+
+int lrstv_step_l_tz(lrstv_plan *pl, void *stream) {
+  if (!pl) return LRSTV_ERR_ARG;
+  Span sp(&pl->prof, LRSTV_K_L_TZ, (cudaStream_t)stream);
+  CK(launch_l_tz(pl->d, pl->Y, pl->S, pl->Z, pl->G1, pl->G2, pl->F, pl->G3, (float)pl->mu,
+                 pl->prm.w, pl->L, pl->T, (cudaStream_t)stream));
+  return LRSTV_OK;
+}
+
+int lrstv_step_z(lrstv_plan *pl, void *stream) {
+  if (!pl) return LRSTV_ERR_ARG;
+  CK(zsolve_core(pl->d, pl->tb, pl->T, (float)pl->mu, pl->Z, pl->specA, pl->specB,
+                 (cudaStream_t)stream, &pl->prof));
+  return LRSTV_OK;
+}
+
+int lrstv_step_fs_dual(lrstv_plan *pl, void *stream) {
+  if (!pl) return LRSTV_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const double mu = pl->mu;
+  const double thr_f = (pl->prm.flags & LRSTV_FLAG_F_THRESH_EXACT) ? pl->prm.tau / (2.0 * mu)
+                                                                     : pl->prm.tau / mu;
+  const double thr_s = pl->prm.lambda / mu;
+  unsigned *slot = pl->res + 2 * (size_t)(pl->iter % kResRing);
+  CK(cudaMemsetAsync(slot, 0, 2 * sizeof(unsigned), st));
+  Span sp(&pl->prof, LRSTV_K_FS_DUAL, st);
+  CK(launch_fs_dual(pl->d, pl->Y, pl->L, pl->Z, pl->S, pl->G1, pl->G2, pl->F, pl->E, pl->G3,
+                    pl->G4, (float)mu, (float)thr_f, (float)thr_s, pl->prm.w, slot, st));
+  return LRSTV_OK;
+}
+
+int lrstv_step_e(lrstv_plan *pl, void *stream) {
+  if (!pl) return LRSTV_ERR_ARG;
+  const double mu = pl->mu;
+  const int gamma4 = (pl->prm.flags & LRSTV_FLAG_NO_GAMMA4) ? 0 : 1;
+  CK(tsvt_core(pl->d, 3, pl->F, pl->G4, (float)(1.0 / mu), (float)(pl->prm.alpha / mu), pl->E, 1,
+               pl->G4, pl->F, (float)mu, gamma4, pl->tb.tw3, pl->specA, pl->specB, pl->V,
+               pl->sweeps, (cudaStream_t)stream, &pl->prof));
+  return LRSTV_OK;
+}
+
+int lrstv_step_mu(lrstv_plan *pl) {
+  if (!pl) return LRSTV_ERR_ARG;
+  const double m = (double)pl->prm.rho * pl->mu;
+  pl->mu = m < (double)pl->prm.mu_max ? m : (double)pl->prm.mu_max;
+  pl->iter += 1;
+  return LRSTV_OK;
+}
+
+int lrstv_iterate(lrstv_plan *pl, int iters, void *stream) {
+  if (!pl || iters < 0) return LRSTV_ERR_ARG;
+  return iterate_async(pl, iters, (cudaStream_t)stream);
+}
+
+int lrstv_get_stats(lrstv_plan *pl, lrstv_stats *stats, void *stream) {
+  if (!pl || !stats) return LRSTV_ERR_ARG;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  memset(stats, 0, sizeof(*stats));
+  stats->iters = pl->iter;
+  stats->mu = (float)pl->mu;
+  if (pl->iter > 0) {
+    unsigned r[2];
+    CK(cudaMemcpy(r, pl->res + 2 * (size_t)((pl->iter - 1) % kResRing), sizeof(r),
+                  cudaMemcpyDeviceToHost));
+    memcpy(&stats->res_inf[0], &r[0], sizeof(float));
+    memcpy(&stats->res_inf[1], &r[1], sizeof(float));
+  }
+  const int ns = 3 * pl->d.h;
+  int *sw = new (std::nothrow) int[ns];
+  if (!sw) return LRSTV_ERR_ALLOC;
+  if (cudaMemcpy(sw, pl->sweeps, sizeof(int) * ns, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    delete[] sw;
+    return LRSTV_ERR_CUDA;
+  }
+  for (int s = 0; s < ns; ++s) {
+    if (sw[s] < 0) stats->jacobi_unconverged += 1;
+    const int a = sw[s] < 0 ? -sw[s] : sw[s];
+    if (a > stats->jacobi_max_sweeps) stats->jacobi_max_sweeps = a;
+  }
+  delete[] sw;
+  if (pl->prm.flags & LRSTV_FLAG_STRICT) {
+    if (!isfinite(stats->res_inf[0]) || !isfinite(stats->res_inf[1])) return LRSTV_ERR_NONFINITE;
+    if (stats->jacobi_unconverged) return LRSTV_ERR_NOT_CONVERGED;
+  }
+  return LRSTV_OK;
+}
+
+int lrstv_state_get(const lrstv_plan *pl, int block, float *dst, void *stream) {
+  if (!pl || !dst) return LRSTV_ERR_ARG;
+  size_t n;
+  float *src = block_ptr(pl, block, &n);
+  if (!src) return LRSTV_ERR_ARG;
+  CK(cudaMemcpyAsync(dst, src, sizeof(float) * n, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return LRSTV_OK;
+}
+
+int lrstv_state_set(lrstv_plan *pl, int block, const float *src, void *stream) {
+  if (!pl || !src) return LRSTV_ERR_ARG;
+  size_t n;
+  float *dst = block_ptr(pl, block, &n);
+  if (!dst) return LRSTV_ERR_ARG;
+  CK(cudaMemcpyAsync(dst, src, sizeof(float) * n, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return LRSTV_OK;
+}
+
+int lrstv_get_mu(const lrstv_plan *pl, float *mu, int *iters) {
+  if (!pl) return LRSTV_ERR_ARG;
+  if (mu) *mu = (float)pl->mu;
+  if (iters) *iters = pl->iter;
+  return LRSTV_OK;
+}
+
+int lrstv_set_mu(lrstv_plan *pl, float mu, int iters) {
+  if (!pl || !(mu > 0.0f) || !isfinite(mu) || iters < 0) return LRSTV_ERR_ARG;
+  pl->mu = mu;
+  pl->iter = iters;
+  return LRSTV_OK;
+}
+
+int lrstv_plan_run(lrstv_plan *pl, const float *Y, float *X, float *S, lrstv_stats *stats,
+                   void *stream) {
+  if (!pl || !Y) return LRSTV_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int iters = pl->prm.max_iter;
+  int rc;
+  if (pl->prm.flags & LRSTV_FLAG_GRAPH) {
+    if (!pl->gexec || pl->gY != Y || pl->gX != X || pl->gS != S || pl->giters != iters) {
+      drop_graph(pl);
+      cudaGraph_t graph = nullptr;
+      CK(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal));
+      rc = init_async(pl, Y, pl->cap_stream);
+      if (rc == LRSTV_OK) rc = iterate_async(pl, iters, pl->cap_stream);
+      if (rc == LRSTV_OK) rc = copy_out(pl, X, S, cudaMemcpyDeviceToDevice, pl->cap_stream);
+      cudaError_t ce = cudaStreamEndCapture(pl->cap_stream, &graph);
+      if (rc != LRSTV_OK || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc != LRSTV_OK ? rc : LRSTV_ERR_CUDA;
+      }
+      ce = cudaGraphInstantiate(&pl->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) {
+        pl->gexec = nullptr;
+        return LRSTV_ERR_CUDA;
+      }
+      pl->gY = Y;
+      pl->gX = X;
+      pl->gS = S;
+      pl->giters = iters;
+    }
+    CK(cudaGraphLaunch(pl->gexec, st));
+    // host-side scalars as after an eager run
+    pl->mu = pl->prm.mu0;
+    pl->iter = 0;
+    for (int it = 0; it < iters; ++it) lrstv_step_mu(pl);
+  } else {
+    if ((rc = init_async(pl, Y, st)) != LRSTV_OK) return rc;
+    if ((rc = iterate_async(pl, iters, st)) != LRSTV_OK) return rc;
+    if ((rc = copy_out(pl, X, S, cudaMemcpyDeviceToDevice, st)) != LRSTV_OK) return rc;
+  }
+  if (stats) return lrstv_get_stats(pl, stats, stream);
+  return LRSTV_OK;
+}
+
+int lrstv_plan_run_host(lrstv_plan *pl, const float *Y_host, float *X_host, float *S_host,
+                        lrstv_stats *stats, void *stream) {
+  if (!pl || !Y_host) return LRSTV_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(pl->Y, Y_host, sizeof(float) * pl->d.N, cudaMemcpyHostToDevice, st));
+  int rc = lrstv_plan_run(pl, pl->Y, nullptr, nullptr, nullptr, stream);
+  if (rc != LRSTV_OK) return rc;
+  if ((rc = copy_out(pl, X_host, S_host, cudaMemcpyDeviceToHost, st)) != LRSTV_OK) return rc;
+  if (stats) return lrstv_get_stats(pl, stats, stream);
+  CK(cudaStreamSynchronize(st));
+  return LRSTV_OK;
+}
+
+int lrstv_denoise(const float *Y, int n1, int n2, int n3, const lrstv_params *params, float *X,
+                  float *S, lrstv_stats *stats, void *stream) {
+  if (!Y) return LRSTV_ERR_ARG;
+  lrstv_plan *pl = nullptr;
+  int rc = lrstv_plan_create(n1, n2, n3, params, &pl);
+  if (rc != LRSTV_OK) return rc;
+  lrstv_stats local;
+  rc = lrstv_plan_run(pl, Y, X, S, stats ? stats : &local, stream);
+  int rc2 = lrstv_plan_destroy(pl);
+  return rc != LRSTV_OK ? rc : rc2;
+}
+
+int lrstv_diff(const float *x, int n1, int n2, int n3, const float w[3], float *g, void *stream) {
+  if (!x || !w || !g) return LRSTV_ERR_ARG;
+  int rc = check_shape(n1, n2, n3);
+  if (rc) return rc;
+  CK(launch_diff(make_dims(n1, n2, n3), x, w, g, (cudaStream_t)stream));
+  return LRSTV_OK;
+}
+
+int lrstv_diff_adjoint(const float *g, int n1, int n2, int n3, const float w[3], float *x,
+                       void *stream) {
+  if (!x || !w || !g) return LRSTV_ERR_ARG;
+  int rc = check_shape(n1, n2, n3);
+  if (rc) return rc;
+  CK(launch_diff_adjoint(make_dims(n1, n2, n3), g, w, x, (cudaStream_t)stream));
+  return LRSTV_OK;
+}
+
+int lrstv_soft_threshold(const float *x, size_t n, float d, float *y, void *stream) {
+  if ((!x || !y) && n) return LRSTV_ERR_ARG;
+  if (!isfinite(d) || d < 0.0f) return LRSTV_ERR_ARG;
+  CK(launch_soft(x, n, d, y, (cudaStream_t)stream));
+  return LRSTV_OK;
+}
+
+static size_t zsolve_ws(const Dims &d, Tables *tb, float2 **A, float2 **B, void *base) {
+  Carver c(base);
+  *A = c.take<float2>((size_t)d.h * d.P);
+  *B = c.take<float2>((size_t)d.h * d.P);
+  carve_tables(c, d, *tb);
+  return c.off;
+}
+
+static size_t tsvt_ws(const Dims &d, float2 **tw, float2 **A, float2 **B, float2 **V, int **sw,
+                      void *base) {
+  Carver c(base);
+  *A = c.take<float2>((size_t)d.h * d.P);
+  *B = c.take<float2>((size_t)d.h * d.P);
+  *V = c.take<float2>((size_t)d.h * d.nc * d.nc);
+  *tw = c.take<float2>(d.n3);
+  *sw = c.take<int>(d.h);
+  return c.off;
+}
+
+int lrstv_zsolve_workspace_size(int n1, int n2, int n3, size_t *bytes) {
+  if (!bytes) return LRSTV_ERR_ARG;
+  int rc = check_shape(n1, n2, n3);
+  if (rc) return rc;
+  Tables tb;
+  float2 *a, *b;
+  *bytes = zsolve_ws(make_dims(n1, n2, n3), &tb, &a, &b, nullptr);
+  return LRSTV_OK;
+}
+
+int lrstv_tsvt_workspace_size(int n1, int n2, int n3, size_t *bytes) {
+  if (!bytes) return LRSTV_ERR_ARG;
+  int rc = check_shape(n1, n2, n3);
+  if (rc) return rc;
+  float2 *tw, *a, *b, *v;
+  int *sw;
+  *bytes = tsvt_ws(make_dims(n1, n2, n3), &tw, &a, &b, &v, &sw, nullptr);
+  return LRSTV_OK;
+}
+
+int lrstv_zsolve(const float *T, int n1, int n2, int n3, const float w[3], float mu, float *Z,
+                 void *workspace, size_t workspace_bytes, void *stream) {
+  if (!T || !w || !Z || !workspace) return LRSTV_ERR_ARG;
+  int rc = check_shape(n1, n2, n3);
+  if (rc) return rc;
+  if (!(mu > 0.0f) || !isfinite(mu) || ((size_t)workspace % kAlign)) return LRSTV_ERR_ARG;
+  const Dims d = make_dims(n1, n2, n3);
+  Tables tb;
+  float2 *A, *B;
+  if (zsolve_ws(d, &tb, &A, &B, nullptr) > workspace_bytes) return LRSTV_ERR_ARG;
+  zsolve_ws(d, &tb, &A, &B, workspace);
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(launch_tables(d, w, tb.tw3, tb.F1, tb.G1, tb.F2, tb.G2, tb.lam1, tb.lam2, tb.lam3, st));
+  CK(zsolve_core(d, tb, T, mu, Z, A, B, st));
+  return LRSTV_OK;
+}
+
+int lrstv_tsvt(const float *Ain, int n1, int n2, int n3, float t, float *out, void *workspace,
+               size_t workspace_bytes, int *sweeps_host, void *stream) {
+  if (!Ain || !out || !workspace) return LRSTV_ERR_ARG;
+  int rc = check_shape(n1, n2, n3);
+  if (rc) return rc;
+  if (!isfinite(t) || t < 0.0f || ((size_t)workspace % kAlign)) return LRSTV_ERR_ARG;
+  const Dims d = make_dims(n1, n2, n3);
+  float2 *tw, *A, *B, *V;
+  int *sw;
+  if (tsvt_ws(d, &tw, &A, &B, &V, &sw, nullptr) > workspace_bytes) return LRSTV_ERR_ARG;
+  tsvt_ws(d, &tw, &A, &B, &V, &sw, workspace);
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(launch_tw3(d.n3, tw, st));
+  CK(tsvt_core(d, 1, Ain, nullptr, 0.0f, t, out, 0, nullptr, nullptr, 0.0f, 0, tw, A, B, V, sw,
+               st));
+  if (sweeps_host) {
+    int *h = new (std::nothrow) int[d.h];
+    if (!h) return LRSTV_ERR_ALLOC;
+    if (cudaMemcpyAsync(h, sw, sizeof(int) * d.h, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      delete[] h;
+      return LRSTV_ERR_CUDA;
+    }
+    // the largest count, or the cap (negative) if any slice hit it
+    int worst = 0, capped = 0;
+    for (int k = 0; k < d.h; ++k) {
+      if (h[k] < 0) capped = h[k];
+      else if (h[k] > worst) worst = h[k];
+    }
+    *sweeps_host = capped ? capped : worst;
+    delete[] h;
+  }
+  return LRSTV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,290 @@
+// dft.cu -- discrete Fourier transforms of the LRSTV iteration
+// (arXiv 2204.12879, eq. Z_solution and eq. E_solution):
+//  - mode-3 (spectral) real <-> half-complex DFTs, with the t-SVT prologue
+//    (F - Gamma4/mu) and epilogue (E, Gamma4 update) fused in;
+//  - a batched complex GEMM that applies the spatial DFT matrices of modes 1
+//    and 2 (and the SVT reconstruction W V^H), with the Z-solve's spectral
+//    division fused into its epilogue.
+// Non-power-of-two lengths (31, 80, 145, 191, 200, 220 ...) are handled by
+// direct sums: every transform is a dense product with a table of twiddles
+// built in FP64 (sincospi) and rounded once to FP32.
+#include "lrstv_internal.cuh"
+
+namespace lrstv {
+
+namespace {
+
+// ------------------------------------------------------------------ tables
+__global__ void k_dft_matrix(int n, float2 *__restrict__ F, float2 *__restrict__ G) {
+  const size_t total = (size_t)n * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t a = e % n, t = e / n;
+    const size_t m = (a * t) % (size_t)n;
+    double s, c;
+    sincospi(2.0 * (double)m / (double)n, &s, &c);
+    F[e] = make_float2((float)c, (float)-s);  // exp(-2 pi i a t / n)
+    G[e] = make_float2((float)c, (float)s);   // exp(+2 pi i a t / n)
+  }
+}
+
+__global__ void k_tw3(int n3, float2 *__restrict__ tw) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n3; m += gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi(2.0 * (double)m / (double)n3, &s, &c);
+    tw[m] = make_float2((float)c, (float)-s);
+  }
+}
+
+// lam[a] = w^2 |exp(2 pi i a / n) - 1|^2 = w^2 4 sin^2(pi a / n): the DFT
+// eigenvalues of w^2 D^T D for a circular forward difference of length n.
+__global__ void k_lam(int n, double w, float *__restrict__ lam) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
+    const double s = sinpi((double)a / (double)n);
+    lam[a] = (float)(w * w * 4.0 * s * s);
+  }
+}
+
+// --------------------------------------------------------- mode-3 DFTs
+constexpr int kPix = 128;  // pixels per block
+constexpr int kKF = 16;    // frequencies (or bands) per thread
+
+// X_k(p) = sum_c (x(p, c) - ycoef y(p, c)) exp(-2 pi i k c / n3), k < h.
+__global__ void __launch_bounds__(kPix)
+    k_r2c3(int n1, int n2, int n3, int h, size_t N, size_t P, const float *__restrict__ x,
+           const float *__restrict__ y, float ycoef, float2 *__restrict__ out, int trans,
+           const float2 *__restrict__ tw3) {
+  extern __shared__ float2 s_tw[];
+  for (int m = threadIdx.x; m < n3; m += blockDim.x) s_tw[m] = tw3[m];
+  __syncthreads();
+  const size_t p = blockIdx.x * (size_t)kPix + threadIdx.x;
+  if (p >= P) return;
+  const int kbase = blockIdx.y * kKF;
+  const int b = blockIdx.z;
+  const float *xb = x + (size_t)b * N;
+  const float *yb = y ? y + (size_t)b * N : nullptr;
+  float2 acc[kKF];
+  int idx[kKF], step[kKF];
+#pragma unroll
+  for (int f = 0; f < kKF; ++f) {
+    acc[f] = make_float2(0.f, 0.f);
+    idx[f] = 0;
+    step[f] = (kbase + f) % n3;
+  }
+  for (int c = 0; c < n3; ++c) {
+    float v = xb[p + P * c];
+    if (yb) v -= ycoef * yb[p + P * c];
+#pragma unroll
+    for (int f = 0; f < kKF; ++f) {
+      const float2 t = s_tw[idx[f]];
+      acc[f].x = fmaf(v, t.x, acc[f].x);
+      acc[f].y = fmaf(v, t.y, acc[f].y);
+      idx[f] += step[f];  // (k c) mod n3, advanced by k each band
+      if (idx[f] >= n3) idx[f] -= n3;
+    }
+  }
+  size_t pos = p;
+  if (trans) {
+    const size_t i = p % n1, j = p / n1;
+    pos = j + (size_t)n2 * i;
+  }
+  float2 *ob = out + (size_t)b * h * P;
+#pragma unroll
+  for (int f = 0; f < kKF; ++f) {
+    const int k = kbase + f;
+    if (k < h) ob[(size_t)k * P + pos] = trans ? make_float2(acc[f].x, -acc[f].y) : acc[f];
+  }
+}
+
+// x(p, c) = (1/n3) [X_0 + 2 sum_{0<k<n3/2} Re(X_k e^{2 pi i k c/n3}) + X_{n3/2} (-1)^c],
+// the Nyquist term present for even n3 only.
+__global__ void __launch_bounds__(kPix)
+    k_c2r3(int n1, int n2, int n3, int h, size_t N, size_t P, const float2 *__restrict__ spec,
+           int trans, const float2 *__restrict__ tw3, float *__restrict__ out, int mode,
+           float *__restrict__ G4, const float *__restrict__ F, float mu, int gamma4) {
+  extern __shared__ float2 s_tw[];
+  for (int m = threadIdx.x; m < n3; m += blockDim.x) s_tw[m] = tw3[m];
+  __syncthreads();
+  const size_t p = blockIdx.x * (size_t)kPix + threadIdx.x;
+  if (p >= P) return;
+  const int cbase = blockIdx.y * kKF;
+  const int b = blockIdx.z;
+  size_t pos = p;
+  if (trans) {
+    const size_t i = p % n1, j = p / n1;
+    pos = j + (size_t)n2 * i;
+  }
+  const float2 *sb = spec + (size_t)b * h * P + pos;
+  float acc[kKF];
+  int idx[kKF], step[kKF];
+#pragma unroll
+  for (int f = 0; f < kKF; ++f) {
+    acc[f] = 0.f;
+    idx[f] = 0;
+    step[f] = (cbase + f) % n3;
+  }
+  for (int k = 0; k < h; ++k) {
+    float2 X = sb[(size_t)k * P];
+    if (trans) X.y = -X.y;
+    const float wk = (k == 0 || 2 * k == n3) ? 1.0f : 2.0f;
+    X.x *= wk;
+    X.y *= wk;
+#pragma unroll
+    for (int f = 0; f < kKF; ++f) {
+      const float2 t = s_tw[idx[f]];  // (cos, -sin) of 2 pi k c / n3
+      acc[f] = fmaf(X.x, t.x, acc[f]);
+      acc[f] = fmaf(X.y, t.y, acc[f]);
+      idx[f] += step[f];
+      if (idx[f] >= n3) idx[f] -= n3;
+    }
+  }
+  const float inv = 1.0f / (float)n3;
+  float *ob = out + (size_t)b * N;
+#pragma unroll
+  for (int f = 0; f < kKF; ++f) {
+    const int c = cbase + f;
+    if (c >= n3) break;
+    const size_t v = p + P * c;
+    const float r = acc[f] * inv;
+    ob[v] = r;
+    if (mode == 1 && gamma4) {
+      const size_t vb = (size_t)b * N + v;
+      G4[vb] = G4[vb] + mu * (r - F[vb]);
+    }
+  }
+}
+
+// ------------------------------------------------------------- complex GEMM
+constexpr int BM = 64, BN = 64, BK = 16, GT = 256;
+
+template <int OPB, int EPI>
+__global__ void __launch_bounds__(GT) k_cgemm(CGemm g) {
+  __shared__ float2 As[BK][BM];
+  __shared__ float2 Bs[BK][BN];
+  const int b = blockIdx.z;
+  const float2 *A = g.A + (size_t)b * g.sA;
+  const float2 *B = g.B + (size_t)b * g.sB;
+  float2 *C = g.C + (size_t)b * g.sC;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  float2 acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int s = 0; s < 4; ++s) acc[r][s] = make_float2(0.f, 0.f);
+
+  for (int k0 = 0; k0 < g.K; k0 += BK) {
+#pragma unroll
+    for (int r = 0; r < (BM * BK) / GT; ++r) {
+      const int e = tid + GT * r;
+      const int m = e % BM, k = e / BM;
+      const int gm = m0 + m, gk = k0 + k;
+      As[k][m] = (gm < g.M && gk < g.K) ? A[gm + (size_t)g.lda * gk] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int r = 0; r < (BK * BN) / GT; ++r) {
+      const int e = tid + GT * r;
+      if (OPB == 0) {
+        const int k = e % BK, n = e / BK;
+        const int gk = k0 + k, gn = n0 + n;
+        Bs[k][n] = (gk < g.K && gn < g.N) ? B[gk + (size_t)g.ldb * gn] : make_float2(0.f, 0.f);
+      } else {
+        // op(B)(k, n) = conj(B(n, k)), B stored N x K column-major
+        const int n = e % BN, k = e / BN;
+        const int gk = k0 + k, gn = n0 + n;
+        float2 v = (gk < g.K && gn < g.N) ? B[gn + (size_t)g.ldb * gk] : make_float2(0.f, 0.f);
+        v.y = -v.y;
+        Bs[k][n] = v;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float2 a[4], bb[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][tx + 16 * r];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) bb[s] = Bs[kk][ty + 16 * s];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          acc[r][s].x = fmaf(a[r].x, bb[s].x, acc[r][s].x);
+          acc[r][s].x = fmaf(-a[r].y, bb[s].y, acc[r][s].x);
+          acc[r][s].y = fmaf(a[r].x, bb[s].y, acc[r][s].y);
+          acc[r][s].y = fmaf(a[r].y, bb[s].x, acc[r][s].y);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int m = m0 + tx + 16 * r;
+    if (m >= g.M) continue;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int n = n0 + ty + 16 * s;
+      if (n >= g.N) continue;
+      float2 v = acc[r][s];
+      if (EPI == 1) {
+        const float den = g.mu * (1.0f + g.lam1[m] + g.lam2[n] + g.lam3[b]);
+        const float q = g.scale / den;
+        v.x *= q;
+        v.y *= q;
+      }
+      C[m + (size_t)g.ldc * n] = v;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_tw3(int n3, float2 *tw3, cudaStream_t st) {
+  k_tw3<<<(n3 + 255) / 256, 256, 0, st>>>(n3, tw3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tables(const Dims &d, const float w[3], float2 *tw3, float2 *F1, float2 *G1,
+                          float2 *F2, float2 *G2, float *lam1, float *lam2, float *lam3,
+                          cudaStream_t st) {
+  cudaError_t e = launch_tw3(d.n3, tw3, st);
+  if (e != cudaSuccess) return e;
+  auto blocks = [](size_t n) { return (unsigned)((n + 255) / 256 > 1024 ? 1024 : (n + 255) / 256); };
+  k_dft_matrix<<<blocks((size_t)d.n1 * d.n1), 256, 0, st>>>(d.n1, F1, G1);
+  k_dft_matrix<<<blocks((size_t)d.n2 * d.n2), 256, 0, st>>>(d.n2, F2, G2);
+  k_lam<<<blocks(d.n1), 256, 0, st>>>(d.n1, (double)w[0], lam1);
+  k_lam<<<blocks(d.n2), 256, 0, st>>>(d.n2, (double)w[1], lam2);
+  k_lam<<<blocks(d.n3), 256, 0, st>>>(d.n3, (double)w[2], lam3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_r2c3(const Dims &d, int nb, const float *x, const float *y, float ycoef,
+                        float2 *out, int work_orient, const float2 *tw3, cudaStream_t st) {
+  dim3 grid((unsigned)((d.P + kPix - 1) / kPix), (unsigned)((d.h + kKF - 1) / kKF), nb);
+  const size_t smem = sizeof(float2) * d.n3;
+  k_r2c3<<<grid, kPix, smem, st>>>(d.n1, d.n2, d.n3, d.h, d.N, d.P, x, y, ycoef, out,
+                                   work_orient && d.trans, tw3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_c2r3(const Dims &d, int nb, const float2 *spec, int work_orient,
+                        const float2 *tw3, float *out, int mode, float *G4, const float *F,
+                        float mu, int gamma4, cudaStream_t st) {
+  dim3 grid((unsigned)((d.P + kPix - 1) / kPix), (unsigned)((d.n3 + kKF - 1) / kKF), nb);
+  const size_t smem = sizeof(float2) * d.n3;
+  k_c2r3<<<grid, kPix, smem, st>>>(d.n1, d.n2, d.n3, d.h, d.N, d.P, spec, work_orient && d.trans,
+                                   tw3, out, mode, G4, F, mu, gamma4);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cgemm(const CGemm &g, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+  dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, g.batch);
+  if (g.opB == 0 && g.epi == 0) k_cgemm<0, 0><<<grid, GT, 0, st>>>(g);
+  else if (g.opB == 0 && g.epi == 1) k_cgemm<0, 1><<<grid, GT, 0, st>>>(g);
+  else if (g.opB == 1 && g.epi == 0) k_cgemm<1, 0><<<grid, GT, 0, st>>>(g);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+}  // namespace lrstv

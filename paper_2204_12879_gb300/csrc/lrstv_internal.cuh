@@ -1,0 +1,82 @@
+// lrstv_internal.cuh -- launchers shared between the translation units of
+// liblrstv.so.  Every launcher enqueues on `st` and returns the launch's
+// cudaError_t (cudaGetLastError right after the launch).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace lrstv {
+
+struct Dims {
+  int n1, n2, n3;
+  size_t N;   // n1 n2 n3
+  size_t P;   // n1 n2 (pixels of one frontal slice)
+  int h;      // n3/2 + 1 non-redundant Fourier frontal slices
+  int nr, nc; // Jacobi working matrix: nr = max(n1, n2) rows, nc = min(n1, n2) columns
+  int trans;  // 1 when n1 < n2: the working matrix of a slice A is A^H
+};
+
+Dims make_dims(int n1, int n2, int n3);
+
+// Largest n1, n2 the Jacobi kernel handles (rows of the working matrix per lane x 32).
+constexpr int kMaxSpatial = 512;
+// Largest n3: the mode-3 DFT kernels stage n3 twiddles in shared memory.
+constexpr int kMaxBands = 4096;
+
+// ---------------------------------------------------------------- stencil.cu
+// Step 1 + T_z: L = (Y - S + Z + (G1 - G2)/mu)/2, T = mu L + G2 + D_w^*(mu F - G3).
+cudaError_t launch_l_tz(const Dims &d, const float *Y, const float *S, const float *Z,
+                        const float *G1, const float *G2, const float *F, const float *G3,
+                        float mu, const float w[3], float *L, float *T, cudaStream_t st);
+// Steps 3, 5, 6: F, S, Gamma1..3; res2 receives atomic maxima of |Y-L-S|, |L-Z|
+// as float bits (may be null).
+cudaError_t launch_fs_dual(const Dims &d, const float *Y, const float *L, const float *Z,
+                           float *S, float *G1, float *G2, float *F, const float *E, float *G3,
+                           const float *G4, float mu, float thr_f, float thr_s, const float w[3],
+                           unsigned *res2, cudaStream_t st);
+cudaError_t launch_diff(const Dims &d, const float *x, const float w[3], float *g, cudaStream_t st);
+cudaError_t launch_diff_adjoint(const Dims &d, const float *g, const float w[3], float *x,
+                                cudaStream_t st);
+cudaError_t launch_soft(const float *x, size_t n, float thr, float *y, cudaStream_t st);
+
+// -------------------------------------------------------------------- dft.cu
+// Tables: tw3[m] = exp(-2 pi i m / n3); Fn = exp(-2 pi i a t / n) (n x n,
+// column-major), Gn its conjugate; lam_n[a] = w_n^2 4 sin^2(pi a / n).
+cudaError_t launch_tables(const Dims &d, const float w[3], float2 *tw3, float2 *F1, float2 *G1,
+                          float2 *F2, float2 *G2, float *lam1, float *lam2, float *lam3,
+                          cudaStream_t st);
+cudaError_t launch_tw3(int n3, float2 *tw3, cudaStream_t st);
+// Mode-3 real-to-half-complex DFT of `nb` cubes x_b - ycoef * y_b (y may be
+// null), written as slices b*h + k of `out` (P complex each), in the working
+// orientation (A^H when d.trans and `work_orient`).
+cudaError_t launch_r2c3(const Dims &d, int nb, const float *x, const float *y, float ycoef,
+                        float2 *out, int work_orient, const float2 *tw3, cudaStream_t st);
+// Inverse mode-3 DFT (half-complex to real, 1/n3 included) of `nb` spectra.
+// mode 0: out_b = result.  mode 1 (E-step epilogue): E_b = result and
+// G4_b += mu (E_b - F_b) when `gamma4` (F, G4 given).
+cudaError_t launch_c2r3(const Dims &d, int nb, const float2 *spec, int work_orient,
+                        const float2 *tw3, float *out, int mode, float *G4, const float *F,
+                        float mu, int gamma4, cudaStream_t st);
+// Batched complex GEMM, column-major: C_b = A_b * op(B_b), op(B) = B or B^H.
+// epi 1: C(a, b) *= scale / (mu (1 + lam1[a] + lam2[b] + lam3[batch])).
+struct CGemm {
+  const float2 *A; long long sA; int lda;
+  const float2 *B; long long sB; int ldb; int opB;  // 0: N, 1: conjugate transpose
+  float2 *C; long long sC; int ldc;
+  int M, N, K, batch;
+  int epi; const float *lam1, *lam2, *lam3; float mu, scale;
+};
+cudaError_t launch_cgemm(const CGemm &g, cudaStream_t st);
+
+// -------------------------------------------------------------------- svt.cu
+// One-sided Jacobi on `nslices` working matrices W_s (nr x nc, column-major,
+// slice stride P), accumulating V_s (nc x nc).  On exit W_s = A_s V_s and the
+// columns of V_s are scaled by g_i = max(1 - t / sigma_i, 0), sigma_i = |w_i|,
+// so that SVT_t(A_s) = W_s V_s^H.  sweeps[s] = sweeps used, -cap if the cap hit.
+// work (may be null) accumulates [pairs examined, pairs rotated].
+cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, float t,
+                          int max_sweeps, int *sweeps, unsigned long long *work,
+                          cudaStream_t st);
+
+}  // namespace lrstv

@@ -1,0 +1,384 @@
+"""Thin ctypes binding of liblrstv.so (include/lrstv.h).
+
+Argument marshalling only: every step of the denoiser runs in the library's
+CUDA kernels.  torch supplies device memory and streams.  There is no CPU
+fallback: without the compiled library (or without a CUDA device) every call
+raises.
+
+Cubes are torch float32 CUDA tensors of N = n1*n2*n3 elements in the order
+i + n1*(j + n2*k) (mode 1 fastest).  A tensor of shape (n3, n2, n1) in the
+default C order has exactly that layout; flat tensors work too.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import builder as _build
+
+__all__ = [
+    "Params", "Stats", "Profile", "Plan", "load", "status_string", "kernel_name", "LrstvError",
+    "lrstv_diff", "lrstv_diff_adjoint", "lrstv_soft_threshold", "lrstv_zsolve", "lrstv_tsvt",
+    "lrstv_denoise", "BLOCK", "FLAG_F_THRESH_EXACT", "FLAG_NO_GAMMA4", "FLAG_GRAPH",
+    "FLAG_STRICT", "EXPORTED",
+]
+
+FLAG_F_THRESH_EXACT = 1
+FLAG_NO_GAMMA4 = 2
+FLAG_GRAPH = 4
+FLAG_STRICT = 8
+
+BLOCK = {"Y": 0, "L": 1, "Z": 2, "S": 3, "G1": 4, "G2": 5, "F": 6, "E": 7, "G3": 8, "G4": 9,
+         "TZ": 10}
+_TRIPLE = {"F", "E", "G3", "G4"}
+
+
+class LrstvError(RuntimeError):
+    def __init__(self, fn, code):
+        super().__init__(f"{fn}: {status_string(code)} (status {code})")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    """lrstv_params: tau, alpha, lambda, w[3], mu0, rho, mu_max, eps, max_iter, flags."""
+    _fields_ = [("tau", ctypes.c_float), ("alpha", ctypes.c_float), ("lam", ctypes.c_float),
+                ("w", ctypes.c_float * 3), ("mu0", ctypes.c_float), ("rho", ctypes.c_float),
+                ("mu_max", ctypes.c_float), ("eps", ctypes.c_float), ("max_iter", ctypes.c_int),
+                ("flags", ctypes.c_uint)]
+
+    @classmethod
+    def make(cls, n1, n2, tau=0.001, alpha=0.2, lam=None, C=1.0, w=(1.0, 1.0, 1.0), mu0=1e-2,
+             rho=1.5, mu_max=1e6, eps=1e-6, max_iter=20, flags=0):
+        """Defaults of this library: lambda = C / sqrt(n1 n2) (Section IV-D)."""
+        if lam is None:
+            lam = C / (float(n1 * n2) ** 0.5)
+        p = cls()
+        p.tau, p.alpha, p.lam = tau, alpha, lam
+        p.w[0], p.w[1], p.w[2] = w
+        p.mu0, p.rho, p.mu_max, p.eps = mu0, rho, mu_max, eps
+        p.max_iter, p.flags = int(max_iter), int(flags)
+        return p
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("res_inf", ctypes.c_float * 2), ("mu", ctypes.c_float),
+                ("jacobi_unconverged", ctypes.c_int), ("jacobi_max_sweeps", ctypes.c_int)]
+
+    def as_dict(self):
+        return {"iters": self.iters, "res_inf": [self.res_inf[0], self.res_inf[1]], "mu": self.mu,
+                "jacobi_unconverged": self.jacobi_unconverged,
+                "jacobi_max_sweeps": self.jacobi_max_sweeps}
+
+
+class Profile(ctypes.Structure):
+    """lrstv_profile: per-kernel launches and summed CUDA-event milliseconds,
+    and the Jacobi work counters."""
+    _fields_ = [("launches", ctypes.c_int * 16), ("ms", ctypes.c_double * 16),
+                ("jacobi_pairs", ctypes.c_ulonglong), ("jacobi_rotations", ctypes.c_ulonglong)]
+
+    def as_dict(self):
+        out = {}
+        for k in range(9):
+            if self.launches[k]:
+                out[kernel_name(k)] = {"launches": self.launches[k], "ms": self.ms[k]}
+        return out
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_F = ctypes.c_float
+_SZ = ctypes.c_size_t
+# name -> argtypes (every entry point returns int status unless listed in _RESTYPE)
+_SIGS = {
+    "lrstv_status_string": [_I],
+    "lrstv_max_spatial": [],
+    "lrstv_plan_create": [_I, _I, _I, ctypes.POINTER(Params), ctypes.POINTER(_P)],
+    "lrstv_plan_destroy": [_P],
+    "lrstv_plan_bytes": [_P, ctypes.POINTER(_SZ)],
+    "lrstv_plan_set_params": [_P, ctypes.POINTER(Params)],
+    "lrstv_init": [_P, _P, _P],
+    "lrstv_step_l_tz": [_P, _P],
+    "lrstv_step_z": [_P, _P],
+    "lrstv_step_fs_dual": [_P, _P],
+    "lrstv_step_e": [_P, _P],
+    "lrstv_step_mu": [_P],
+    "lrstv_iterate": [_P, _I, _P],
+    "lrstv_get_stats": [_P, ctypes.POINTER(Stats), _P],
+    "lrstv_state_get": [_P, _I, _P, _P],
+    "lrstv_state_set": [_P, _I, _P, _P],
+    "lrstv_get_mu": [_P, ctypes.POINTER(_F), ctypes.POINTER(_I)],
+    "lrstv_set_mu": [_P, _F, _I],
+    "lrstv_plan_run": [_P, _P, _P, _P, ctypes.POINTER(Stats), _P],
+    "lrstv_plan_run_host": [_P, _P, _P, _P, ctypes.POINTER(Stats), _P],
+    "lrstv_denoise": [_P, _I, _I, _I, ctypes.POINTER(Params), _P, _P, ctypes.POINTER(Stats), _P],
+    "lrstv_diff": [_P, _I, _I, _I, ctypes.POINTER(_F), _P, _P],
+    "lrstv_diff_adjoint": [_P, _I, _I, _I, ctypes.POINTER(_F), _P, _P],
+    "lrstv_soft_threshold": [_P, _SZ, _F, _P, _P],
+    "lrstv_zsolve_workspace_size": [_I, _I, _I, ctypes.POINTER(_SZ)],
+    "lrstv_tsvt_workspace_size": [_I, _I, _I, ctypes.POINTER(_SZ)],
+    "lrstv_zsolve": [_P, _I, _I, _I, ctypes.POINTER(_F), _F, _P, _P, _SZ, _P],
+    "lrstv_tsvt": [_P, _I, _I, _I, _F, _P, _P, _SZ, ctypes.POINTER(_I), _P],
+    "lrstv_kernel_name": [_I],
+    "lrstv_profile_enable": [_P, _I],
+    "lrstv_profile_read": [_P, ctypes.POINTER(Profile)],
+}
+_RESTYPE = {"lrstv_status_string": ctypes.c_char_p, "lrstv_kernel_name": ctypes.c_char_p}
+EXPORTED = sorted(_SIGS)
+
+_lib = None
+
+
+def load(build_if_missing: bool = True):
+    """Loads liblrstv.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if build_if_missing and not _build.up_to_date():
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("liblrstv.so is not built; run paper_2204_12879_gb300.build()")
+        L = ctypes.CDLL(path)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = _RESTYPE.get(name, ctypes.c_int)
+        _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return load().lrstv_status_string(int(code)).decode()
+
+
+def kernel_name(k: int) -> str:
+    return load().lrstv_kernel_name(int(k)).decode()
+
+
+def _call(name, *args):
+    rc = getattr(load(), name)(*args)
+    if rc != 0:
+        raise LrstvError(name, rc)
+    return rc
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("liblrstv needs a CUDA device; there is no CPU path")
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, n=None):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 \
+            or not t.is_contiguous():
+        raise TypeError("expected a contiguous float32 CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"expected {n} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _w(w):
+    return (ctypes.c_float * 3)(*[float(x) for x in w])
+
+
+def _empty(n, device=None):
+    torch = _torch()
+    return torch.empty(int(n), dtype=torch.float32, device=device or "cuda")
+
+
+class Plan:
+    """An lrstv_plan: device state of one n1 x n2 x n3 ADMM run."""
+
+    def __init__(self, n1, n2, n3, params: Params):
+        _torch()
+        self.shape = (int(n1), int(n2), int(n3))
+        self.N = n1 * n2 * n3
+        self.params = params
+        h = ctypes.c_void_p()
+        _call("lrstv_plan_create", int(n1), int(n2), int(n3), ctypes.byref(params), ctypes.byref(h))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lrstv_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def nbytes(self):
+        b = ctypes.c_size_t()
+        _call("lrstv_plan_bytes", self._h, ctypes.byref(b))
+        return b.value
+
+    def set_params(self, params: Params):
+        _call("lrstv_plan_set_params", self._h, ctypes.byref(params))
+        self.params = params
+
+    def init(self, Y, stream=None):
+        _call("lrstv_init", self._h, _dev(Y, self.N), _stream(stream))
+
+    def step_l_tz(self, stream=None):
+        _call("lrstv_step_l_tz", self._h, _stream(stream))
+
+    def step_z(self, stream=None):
+        _call("lrstv_step_z", self._h, _stream(stream))
+
+    def step_fs_dual(self, stream=None):
+        _call("lrstv_step_fs_dual", self._h, _stream(stream))
+
+    def step_e(self, stream=None):
+        _call("lrstv_step_e", self._h, _stream(stream))
+
+    def step_mu(self):
+        _call("lrstv_step_mu", self._h)
+
+    def iterate(self, iters, stream=None):
+        _call("lrstv_iterate", self._h, int(iters), _stream(stream))
+
+    def stats(self, stream=None) -> Stats:
+        s = Stats()
+        _call("lrstv_get_stats", self._h, ctypes.byref(s), _stream(stream))
+        return s
+
+    def get(self, name, stream=None):
+        n = 3 * self.N if name in _TRIPLE else self.N
+        out = _empty(n)
+        _call("lrstv_state_get", self._h, BLOCK[name], _dev(out), _stream(stream))
+        return out
+
+    def set(self, name, value, stream=None):
+        n = 3 * self.N if name in _TRIPLE else self.N
+        _call("lrstv_state_set", self._h, BLOCK[name], _dev(value, n), _stream(stream))
+
+    @property
+    def mu(self):
+        m, it = ctypes.c_float(), ctypes.c_int()
+        _call("lrstv_get_mu", self._h, ctypes.byref(m), ctypes.byref(it))
+        return m.value, it.value
+
+    def set_mu(self, mu, iters):
+        _call("lrstv_set_mu", self._h, float(mu), int(iters))
+
+    def profile_enable(self, on=True):
+        _call("lrstv_profile_enable", self._h, 1 if on else 0)
+
+    def profile_read(self) -> Profile:
+        p = Profile()
+        _call("lrstv_profile_read", self._h, ctypes.byref(p))
+        return p
+
+    def run(self, Y, X=None, S=None, stats=False, stream=None):
+        """lrstv_plan_run on device tensors; returns (X, S[, Stats])."""
+        X = _empty(self.N) if X is None else X
+        S = _empty(self.N) if S is None else S
+        st = Stats()
+        _call("lrstv_plan_run", self._h, _dev(Y, self.N), _dev(X, self.N), _dev(S, self.N),
+              ctypes.byref(st) if stats else None, _stream(stream))
+        return (X, S, st) if stats else (X, S)
+
+    def run_host(self, Y, X, S, stats=False, stream=None):
+        """lrstv_plan_run_host on host float32 buffers (numpy arrays or pinned
+        CPU tensors, N contiguous elements each); synchronises."""
+        st = Stats()
+        _call("lrstv_plan_run_host", self._h, _host_ptr(Y, self.N), _host_ptr(X, self.N),
+              _host_ptr(S, self.N), ctypes.byref(st) if stats else None, _stream(stream))
+        return st
+
+
+def _host_ptr(a, n):
+    import numpy as np
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda or a.dtype != torch.float32 or not a.is_contiguous() or a.numel() != n:
+                raise TypeError("expected a contiguous float32 CPU tensor of N elements")
+            return ctypes.c_void_p(a.data_ptr())
+    except ImportError:
+        pass
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+            and a.size == n):
+        raise TypeError("expected a contiguous float32 host array of N elements")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def lrstv_diff(x, shape, w=(1.0, 1.0, 1.0), out=None, stream=None):
+    """w_n D_n x for n = 1..3 (3N floats)."""
+    n1, n2, n3 = shape
+    out = _empty(3 * x.numel()) if out is None else out
+    _call("lrstv_diff", _dev(x, n1 * n2 * n3), n1, n2, n3, _w(w), _dev(out, 3 * x.numel()),
+          _stream(stream))
+    return out
+
+
+def lrstv_diff_adjoint(g, shape, w=(1.0, 1.0, 1.0), out=None, stream=None):
+    n1, n2, n3 = shape
+    N = n1 * n2 * n3
+    out = _empty(N) if out is None else out
+    _call("lrstv_diff_adjoint", _dev(g, 3 * N), n1, n2, n3, _w(w), _dev(out, N), _stream(stream))
+    return out
+
+
+def lrstv_soft_threshold(x, d, out=None, stream=None):
+    out = _empty(x.numel()) if out is None else out
+    _call("lrstv_soft_threshold", _dev(x), x.numel(), float(d), _dev(out, x.numel()),
+          _stream(stream))
+    return out
+
+
+def _workspace(fn, shape):
+    b = ctypes.c_size_t()
+    _call(fn, *shape, ctypes.byref(b))
+    torch = _torch()
+    return torch.empty(max(int(b.value), 1), dtype=torch.uint8, device="cuda"), b.value
+
+
+def lrstv_zsolve(T, shape, mu, w=(1.0, 1.0, 1.0), out=None, workspace=None, stream=None):
+    """Z = ifftn(fftn(T) / (mu (1 + P_z)))."""
+    n1, n2, n3 = shape
+    N = n1 * n2 * n3
+    out = _empty(N) if out is None else out
+    ws, nb = workspace if workspace is not None else _workspace("lrstv_zsolve_workspace_size", shape)
+    _call("lrstv_zsolve", _dev(T, N), n1, n2, n3, _w(w), float(mu), _dev(out, N),
+          ctypes.c_void_p(ws.data_ptr()), nb, _stream(stream))
+    return out
+
+
+def lrstv_tsvt(A, shape, t, out=None, workspace=None, sweeps=False, stream=None):
+    """t-SVT with threshold t on each Fourier frontal slice; returns out (and
+    the worst Jacobi sweep count when sweeps=True)."""
+    n1, n2, n3 = shape
+    N = n1 * n2 * n3
+    out = _empty(N) if out is None else out
+    ws, nb = workspace if workspace is not None else _workspace("lrstv_tsvt_workspace_size", shape)
+    sw = ctypes.c_int(0)
+    _call("lrstv_tsvt", _dev(A, N), n1, n2, n3, float(t), _dev(out, N),
+          ctypes.c_void_p(ws.data_ptr()), nb, ctypes.byref(sw) if sweeps else None, _stream(stream))
+    return (out, sw.value) if sweeps else out
+
+
+def lrstv_denoise(Y, shape, params: Params, stream=None):
+    """One-shot lrstv_denoise: returns (X, S, Stats)."""
+    n1, n2, n3 = shape
+    N = n1 * n2 * n3
+    X, S, st = _empty(N), _empty(N), Stats()
+    _call("lrstv_denoise", _dev(Y, N), n1, n2, n3, ctypes.byref(params), _dev(X, N), _dev(S, N),
+          ctypes.byref(st), _stream(stream))
+    return X, S, st

@@ -1,0 +1,308 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances: single operators are compared relative to the data's scale at
+FP32 rounding level (1e-5 of the largest magnitude for the DFT-based
+operators, whose sums run over up to a few hundred terms); whole iterations
+use the 1e-4 max-abs / 0.01 dB MPSNR bound on [0, 1]-scaled cubes.
+"""
+import numpy as np
+import pytest
+
+from tests.gpu_util import dev, dev3, f32, host, host3, load_oracle_state, maxabs
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(32, 32, 16), (37, 29, 11), (29, 37, 10), (8, 8, 4), (1, 7, 5), (6, 1, 1), (3, 5, 1),
+          (70, 65, 9)]
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2204_12879_gb300 import lrstv
+    lrstv.load()
+    return lrstv
+
+
+def rnd(shape, seed, scale=1.0):
+    return f32(np.random.default_rng(seed).standard_normal(shape) * scale)
+
+
+# ------------------------------------------------------------ operators ---
+@pytest.mark.parametrize("shape", SHAPES)
+def test_diff_and_adjoint(L, orc, shape):
+    x = rnd(shape, 1)
+    g = rnd((3,) + shape, 2)
+    w = (0.7, 1.3, 0.4)
+    out = host3(L.lrstv_diff(dev(x), shape, w), shape)
+    assert maxabs(out, orc.diff(x, w)) <= 2e-6 * max(1.0, np.abs(x).max())
+    adj = host(L.lrstv_diff_adjoint(dev3(g), shape, w), shape)
+    assert maxabs(adj, orc.diff_adjoint(g, w)) <= 4e-6 * max(1.0, np.abs(g).max())
+
+
+def test_soft_threshold(L, orc):
+    x = rnd((1000,), 3)
+    x[:5] = [0.1, -0.1, 0.0, 0.1000001, -0.0999999]
+    y = L.lrstv_soft_threshold(dev(x), 0.1).cpu().numpy()
+    ref = orc.soft(x, float(np.float32(0.1)))
+    assert maxabs(y, ref) <= 1e-7
+    assert np.all(y[np.abs(x) <= np.float32(0.1)] == 0)
+    assert L.lrstv_soft_threshold(dev(np.zeros(0)), 0.1).numel() == 0
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_zsolve(L, orc, shape):
+    T = rnd(shape, 4)
+    w = (1.0, 0.6, 1.4)
+    for mu in (0.01, 3.7, 1e6):
+        Z = host(L.lrstv_zsolve(dev(T), shape, mu, w), shape)
+        ref = orc.zsolve(T, mu, w)
+        assert maxabs(Z, ref) <= 1e-5 * np.abs(ref).max(), mu
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_tsvt(L, orc, shape):
+    A = rnd(shape, 5)
+    from tests.test_oracle_pins import bcirc
+    sig = np.linalg.svd(bcirc(A), compute_uv=False) if A.size <= 40000 else None
+    ts = [0.0, 1.0, 5.0] if sig is None else [0.0, float(np.percentile(sig, 30)),
+                                               float(np.percentile(sig, 90)), float(sig.max() * 1.01)]
+    for t in ts:
+        out, sw = L.lrstv_tsvt(dev(A), shape, t, sweeps=True)
+        ref, _ = orc.tsvt(A, t)
+        assert sw > 0, "Jacobi hit its sweep cap"
+        assert maxabs(host(out, shape), ref) <= 2e-5 * np.abs(A).max(), t
+
+
+def test_tsvt_low_rank_and_large(L, orc):
+    """A gradient-like cube whose Fourier slices are rank deficient, and a
+    slice height above 256 (the widest Jacobi register tile)."""
+    rng = np.random.default_rng(6)
+    U = rng.standard_normal((40, 3, 6))
+    V = rng.standard_normal((3, 24, 6))
+    A = f32(np.einsum("irk,rjk->ijk", U, V))
+    out = host(L.lrstv_tsvt(dev(A), A.shape, 0.5), A.shape)
+    ref, _ = orc.tsvt(A, 0.5)
+    assert maxabs(out, ref) <= 2e-5 * np.abs(A).max()
+    B = rnd((300, 20, 3), 7)
+    out = host(L.lrstv_tsvt(dev(B), B.shape, 2.0), B.shape)
+    ref, _ = orc.tsvt(B, 2.0)
+    assert maxabs(out, ref) <= 2e-5 * np.abs(B).max()
+
+
+# ------------------------------------------------------------ ADMM steps ---
+def _noisy(shape, seed):
+    from synthetic import Recipe, make_cube
+    n1, n2, n3 = shape
+    clean, noisy = make_cube(Recipe(n1, n2, n3, 4, 12, (0.1, 0.1), 0.1), seed)
+    return clean, f32(noisy)
+
+
+@pytest.fixture(scope="module")
+def mid_state(orc):
+    """An oracle state after 4 iterations on a 32x32x16 cube (rounded to f32)."""
+    shape = (32, 32, 16)
+    _, Y = _noisy(shape, 11)
+    st = orc.State(Y, orc.Params(n1=32, n2=32))
+    st.iterate(4)
+    return shape, st
+
+
+def _plan(L, shape, **kw):
+    n1, n2, n3 = shape
+    return L.Plan(n1, n2, n3, L.Params.make(n1, n2, **kw))
+
+
+def test_step_l_tz(L, orc, mid_state):
+    shape, st = mid_state
+    with _plan(L, shape) as pl:
+        s = load_oracle_state(pl, st)
+        pl.step_l_tz()
+        s.step_l()
+        assert maxabs(host(pl.get("L"), shape), s.get("L")) <= 1e-6
+        # T_z of the oracle, written out from its definition (eq. Z_solution)
+        w = tuple(s.p[3:6])
+        F = np.stack([s.get("F", n) for n in range(3)])
+        G3 = np.stack([s.get("G3", n) for n in range(3)])
+        T = s.mu * s.get("L") + s.mu * orc.diff_adjoint(F, w) + s.get("G2") - orc.diff_adjoint(G3, w)
+        assert maxabs(host(pl.get("TZ"), shape), T) <= 2e-6 * max(1.0, np.abs(T).max())
+
+
+def test_step_z(L, orc, mid_state):
+    shape, st = mid_state
+    with _plan(L, shape) as pl:
+        s = load_oracle_state(pl, st)
+        pl.step_l_tz()
+        pl.step_z()
+        s.step_l()
+        s.step_z()
+        assert maxabs(host(pl.get("Z"), shape), s.get("Z")) <= 2e-5
+
+
+def test_step_fs_dual(L, orc, mid_state):
+    shape, st = mid_state
+    with _plan(L, shape) as pl:
+        s = load_oracle_state(pl, st)
+        pl.step_fs_dual()
+        s.step_f()
+        s.step_s()
+        s.step_dual()
+        # the multipliers carry a factor mu; compare them relative to mu
+        for name, tol in (("S", 1e-6), ("G1", 2e-6 * s.mu), ("G2", 2e-6 * s.mu)):
+            assert maxabs(host(pl.get(name), shape), s.get(name)) <= tol, name
+        for name, tol in (("F", 1e-6), ("G3", 2e-6 * s.mu)):
+            got = host3(pl.get(name), shape)
+            for n in range(3):
+                assert maxabs(got[n], s.get(name, n)) <= tol, name
+
+
+def test_step_e(L, orc, mid_state):
+    shape, st = mid_state
+    with _plan(L, shape) as pl:
+        s = load_oracle_state(pl, st)
+        pl.step_e()
+        s.step_e()
+        # the oracle's Gamma4 update belongs to its dual step
+        G4 = [s.get("G4", n) + s.mu * (s.get("E", n) - s.get("F", n)) for n in range(3)]
+        E = host3(pl.get("E"), shape)
+        G = host3(pl.get("G4"), shape)
+        for n in range(3):
+            assert maxabs(E[n], s.get("E", n)) <= 1e-5
+            assert maxabs(G[n], G4[n]) <= 1e-5 * s.mu
+        st_ = pl.stats()
+        assert st_.jacobi_unconverged == 0 and st_.jacobi_max_sweeps > 0
+
+
+def test_step_mu(L):
+    with _plan(L, (8, 8, 4), mu0=0.5, rho=3.0, mu_max=4.0) as pl:
+        pl.init(dev(np.zeros((8, 8, 4))))
+        assert pl.mu == (0.5, 0)
+        pl.step_mu()
+        assert pl.mu == (1.5, 1)
+        pl.step_mu()
+        assert pl.mu == (4.0, 2)
+
+
+# ------------------------------------------------------- whole iterations ---
+def _run_both(L, orc, shape, iters, seed, flags=0, **kw):
+    clean, Y = _noisy(shape, seed)
+    n1, n2, n3 = shape
+    P = L.Params.make(n1, n2, max_iter=iters, flags=flags, **kw)
+    with L.Plan(n1, n2, n3, P) as pl:
+        X, S, stats = pl.run(dev(Y), stats=True)
+        X, S = host(X, shape), host(S, shape)
+    op = orc.Params(n1=n1, n2=n2, **{k: v for k, v in kw.items() if k in ("tau", "alpha", "lam")})
+    ost = orc.State(Y, op, flags=flags & 3)
+    ost.iterate(iters)
+    return clean, X, S, stats, ost
+
+
+def test_end_to_end_config1(L, orc):
+    """32x32x16 synthetic cube, 20 iterations: 1e-4 max-abs, 0.01 dB MPSNR."""
+    from synthetic import mpsnr
+    clean, X, S, stats, ost = _run_both(L, orc, (32, 32, 16), 20, 1)
+    assert maxabs(X, ost.X) <= 1e-4
+    assert maxabs(S, ost.get("S")) <= 1e-4
+    assert abs(mpsnr(X, clean) - mpsnr(ost.X, clean)) <= 0.01
+    assert mpsnr(X, clean) > 25.0
+    assert stats.iters == 20 and stats.jacobi_unconverged == 0
+    assert abs(stats.mu - ost.mu) <= 1e-6 * ost.mu
+
+
+@pytest.mark.parametrize("flags", [1, 2])
+def test_end_to_end_reading_flags(L, orc, flags):
+    clean, X, S, stats, ost = _run_both(L, orc, (24, 20, 9), 12, 5, flags=flags)
+    assert maxabs(X, ost.X) <= 1e-4
+
+
+def test_end_to_end_ragged(L, orc):
+    clean, X, S, stats, ost = _run_both(L, orc, (37, 29, 11), 15, 3)
+    assert maxabs(X, ost.X) <= 1e-4
+
+
+def test_graph_replay_matches_eager(L):
+    import torch
+    shape = (32, 32, 16)
+    _, Y = _noisy(shape, 2)
+    outs = []
+    for flags in (0, L.FLAG_GRAPH):
+        with _plan(L, shape, max_iter=6, flags=flags) as pl:
+            X, S = pl.run(dev(Y))
+            X2, S2 = pl.run(dev(Y))  # graph replay (cached) or a second eager run
+            torch.cuda.synchronize()
+            assert torch.equal(X, X2) and torch.equal(S, S2)
+            outs.append(X.cpu())
+    assert torch.equal(outs[0], outs[1])
+
+
+def test_run_host_matches_device(L):
+    import torch
+    shape = (20, 24, 7)
+    _, Y = _noisy(shape, 4)
+    y = np.ascontiguousarray(Y.reshape(-1, order="F").astype(np.float32))
+    with _plan(L, shape, max_iter=5) as pl:
+        X, S = pl.run(dev(Y))
+        Xh = np.empty_like(y)
+        Sh = np.empty_like(y)
+        st = pl.run_host(y, Xh, Sh, stats=True)
+        assert st.iters == 5
+        assert np.array_equal(X.cpu().numpy(), Xh) and np.array_equal(S.cpu().numpy(), Sh)
+        # pinned host tensors take the same path
+        yp = torch.from_numpy(y).pin_memory()
+        xp = torch.empty_like(yp).pin_memory()
+        sp = torch.empty_like(yp).pin_memory()
+        pl.run_host(yp, xp, sp)
+        assert np.array_equal(xp.numpy(), Xh)
+
+
+def test_checkpoint_resume(L):
+    """Exporting the state and mu after k iterations and importing it into a
+    fresh plan continues the run exactly."""
+    import torch
+    shape = (16, 12, 6)
+    _, Y = _noisy(shape, 8)
+    with _plan(L, shape) as a, _plan(L, shape) as b:
+        a.init(dev(Y))
+        a.iterate(3)
+        saved = {n: a.get(n) for n in ("Y", "L", "Z", "S", "G1", "G2", "F", "E", "G3", "G4")}
+        mu, it = a.mu
+        a.iterate(2)
+        for n, v in saved.items():
+            b.set(n, v)
+        b.set_mu(mu, it)
+        b.iterate(2)
+        torch.cuda.synchronize()
+        assert torch.equal(a.get("L"), b.get("L"))
+        assert a.mu == b.mu
+
+
+def test_constant_cube_is_fixed_point(L):
+    shape = (10, 9, 5)
+    Y = np.full(shape, 0.37)
+    with _plan(L, shape, max_iter=5) as pl:
+        X, S = pl.run(dev(Y))
+        assert maxabs(host(X, shape), Y) <= 1e-6
+        assert float(S.abs().max()) == 0.0
+
+
+def test_nonfinite_input_is_reported(L):
+    shape = (8, 8, 4)
+    Y = np.zeros(shape)
+    Y[1, 2, 3] = np.nan
+    with _plan(L, shape, max_iter=2, flags=L.FLAG_STRICT) as pl:
+        with pytest.raises(L.LrstvError) as e:
+            pl.run(dev(Y), stats=True)
+        assert e.value.code == 6
+
+
+def test_denoise_one_shot(L, orc):
+    shape = (16, 16, 8)
+    _, Y = _noisy(shape, 9)
+    X, S, st = L.lrstv_denoise(dev(Y), shape, L.Params.make(16, 16, max_iter=4))
+    ost = orc.State(Y, orc.Params(n1=16, n2=16))
+    ost.iterate(4)
+    assert maxabs(host(X, shape), ost.X) <= 1e-4
+    assert st.iters == 4
