@@ -165,11 +165,12 @@ int lrstv_iterate(lrstv_plan *plan, int iters, void *stream);
 int lrstv_get_stats(lrstv_plan *plan, lrstv_stats *stats, void *stream);
 /* Copies a state block to / from caller device memory (N or 3N floats,
  * device-to-device, stream-ordered).  With lrstv_get_mu / lrstv_set_mu this
- * checkpoints and resumes an ADMM run. */
+ * checkpoints and resumes an ADMM run (mu is kept in double precision, so a
+ * resumed run repeats the uninterrupted one bit for bit). */
 int lrstv_state_get(const lrstv_plan *plan, int block, float *dst, void *stream);
 int lrstv_state_set(lrstv_plan *plan, int block, const float *src, void *stream);
-int lrstv_get_mu(const lrstv_plan *plan, float *mu, int *iters);
-int lrstv_set_mu(lrstv_plan *plan, float mu, int iters);
+int lrstv_get_mu(const lrstv_plan *plan, double *mu, int *iters);
+int lrstv_set_mu(lrstv_plan *plan, double mu, int iters);
 
 /* ----------------------------------------------------------- whole runs */
 /* The problem statement Y -> (X = L, S) of eq. TDLRSTV (plain form):

@@ -191,6 +191,7 @@ cudaError_t tsvt_core(const Dims &d, int nb, const float *x, const float *y, flo
 }
 
 }  // namespace
+
 }  // namespace lrstv
 
 using namespace lrstv;
@@ -559,15 +560,15 @@ int lrstv_state_set(lrstv_plan *pl, int block, const float *src, void *stream) {
   return LRSTV_OK;
 }
 
-int lrstv_get_mu(const lrstv_plan *pl, float *mu, int *iters) {
+int lrstv_get_mu(const lrstv_plan *pl, double *mu, int *iters) {
   if (!pl) return LRSTV_ERR_ARG;
-  if (mu) *mu = (float)pl->mu;
+  if (mu) *mu = pl->mu;
   if (iters) *iters = pl->iter;
   return LRSTV_OK;
 }
 
-int lrstv_set_mu(lrstv_plan *pl, float mu, int iters) {
-  if (!pl || !(mu > 0.0f) || !isfinite(mu) || iters < 0) return LRSTV_ERR_ARG;
+int lrstv_set_mu(lrstv_plan *pl, double mu, int iters) {
+  if (!pl || !(mu > 0.0) || !isfinite(mu) || iters < 0) return LRSTV_ERR_ARG;
   pl->mu = mu;
   pl->iter = iters;
   return LRSTV_OK;

@@ -106,8 +106,8 @@ _SIGS = {
     "lrstv_get_stats": [_P, ctypes.POINTER(Stats), _P],
     "lrstv_state_get": [_P, _I, _P, _P],
     "lrstv_state_set": [_P, _I, _P, _P],
-    "lrstv_get_mu": [_P, ctypes.POINTER(_F), ctypes.POINTER(_I)],
-    "lrstv_set_mu": [_P, _F, _I],
+    "lrstv_get_mu": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)],
+    "lrstv_set_mu": [_P, ctypes.c_double, _I],
     "lrstv_plan_run": [_P, _P, _P, _P, ctypes.POINTER(Stats), _P],
     "lrstv_plan_run_host": [_P, _P, _P, _P, ctypes.POINTER(Stats), _P],
     "lrstv_denoise": [_P, _I, _I, _I, ctypes.POINTER(Params), _P, _P, ctypes.POINTER(Stats), _P],
@@ -270,7 +270,7 @@ class Plan:
 
     @property
     def mu(self):
-        m, it = ctypes.c_float(), ctypes.c_int()
+        m, it = ctypes.c_double(), ctypes.c_int()
         _call("lrstv_get_mu", self._h, ctypes.byref(m), ctypes.byref(it))
         return m.value, it.value
 

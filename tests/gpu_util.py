@@ -51,6 +51,5 @@ def load_oracle_state(plan, st):
             plan.set(name, dev3([st32.get(name, n) for n in range(3)]))
         else:
             plan.set(name, dev(st32.get(name)))
-    st32.mu = float(np.float32(st.mu))
     plan.set_mu(st32.mu, st.iters)
     return st32
