@@ -214,6 +214,35 @@ int lrstv_zsolve(const float *T, int n1, int n2, int n3, const float w[3], float
 int lrstv_tsvt(const float *A, int n1, int n2, int n3, float t, float *out, void *workspace,
                size_t workspace_bytes, int *sweeps_host, void *stream);
 
+/* ------------------------------------------------- allocation-free t-SVT */
+/* The paper has no counterpart to this call: it serves callers that cannot
+ * allocate device memory when they call the library (a plug-in whose host
+ * application owns the device memory pool, a process that reserves all of its
+ * device memory up front, a loop that must never reach the allocator).
+ *
+ * lrstv_tsvt_noalloc computes the same t-SVT as lrstv_tsvt, but takes its
+ * scratch from one fixed device array of LRSTV_NOALLOC_SCRATCH_BYTES (16 MiB)
+ * that is part of the library: every GPU that loads liblrstv.so holds that
+ * array until the process exits.  The call allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine).  The caller passes A and out
+ * (device, N floats each) as for lrstv_tsvt.
+ *  - Size limit: 2*h*n1*n2*8 + h*min(n1,n2)^2*8 + n3*8 + h*4 bytes (h =
+ *    n3/2 + 1, each term rounded up to 256) must not exceed the array;
+ *    larger cubes return LRSTV_ERR_SHAPE without touching the GPU.  Examples
+ *    that fit: 64x64x31, 128x128x31, 100x100x80.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call on a device shares the one array and leaves the last call's
+ *    contents in it; each call writes every scratch byte before reading it,
+ *    so nothing has to start at zero.  Calls that overlap on the GPU (on two
+ *    streams, or from two host threads) race on the array and give wrong
+ *    results: order them on one stream.
+ *  - sweeps_host as in lrstv_tsvt (passing it synchronises `stream`). */
+#define LRSTV_NOALLOC_SCRATCH_BYTES (16u << 20)
+int lrstv_tsvt_noalloc(const float *A, int n1, int n2, int n3, float t, float *out,
+                       int *sweeps_host, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

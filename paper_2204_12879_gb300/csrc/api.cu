@@ -192,6 +192,16 @@ cudaError_t tsvt_core(const Dims &d, int nb, const float *x, const float *y, flo
 
 }  // namespace
 
+// Standalone t-SVT on caller-provided scratch pieces (no profiling, cold
+// Jacobi start): used by the allocation-free entry point.
+cudaError_t tsvt_plain(const Dims &d, const float *A, float t, float *out, float2 *tw3,
+                       float2 *specA, float2 *specB, float2 *V, int *sweeps, cudaStream_t st) {
+  cudaError_t e = launch_tw3(d.n3, tw3, st);
+  if (e != cudaSuccess) return e;
+  return tsvt_core(d, 1, A, nullptr, 0.0f, t, out, 0, nullptr, nullptr, 0.0f, 0, tw3, specA,
+                   specB, V, sweeps, st, nullptr);
+}
+
 }  // namespace lrstv
 
 using namespace lrstv;

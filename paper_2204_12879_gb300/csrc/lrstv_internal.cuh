@@ -79,4 +79,11 @@ cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, floa
                           int max_sweeps, int *sweeps, unsigned long long *work,
                           cudaStream_t st);
 
+// ------------------------------------------------------------------- api.cu
+// t-SVT of one cube with threshold t on caller-provided scratch: tw3 (n3),
+// specA and specB (h P each), V (h nc^2), sweeps (h); every piece is written
+// before it is read.
+cudaError_t tsvt_plain(const Dims &d, const float *A, float t, float *out, float2 *tw3,
+                       float2 *specA, float2 *specB, float2 *V, int *sweeps, cudaStream_t st);
+
 }  // namespace lrstv

@@ -19,6 +19,7 @@ from . import builder as _build
 __all__ = [
     "Params", "Stats", "Profile", "Plan", "load", "status_string", "kernel_name", "LrstvError",
     "lrstv_diff", "lrstv_diff_adjoint", "lrstv_soft_threshold", "lrstv_zsolve", "lrstv_tsvt",
+    "lrstv_tsvt_noalloc",
     "lrstv_denoise", "BLOCK", "FLAG_F_THRESH_EXACT", "FLAG_NO_GAMMA4", "FLAG_GRAPH",
     "FLAG_STRICT", "EXPORTED",
 ]
@@ -118,6 +119,7 @@ _SIGS = {
     "lrstv_tsvt_workspace_size": [_I, _I, _I, ctypes.POINTER(_SZ)],
     "lrstv_zsolve": [_P, _I, _I, _I, ctypes.POINTER(_F), _F, _P, _P, _SZ, _P],
     "lrstv_tsvt": [_P, _I, _I, _I, _F, _P, _P, _SZ, ctypes.POINTER(_I), _P],
+    "lrstv_tsvt_noalloc": [_P, _I, _I, _I, _F, _P, ctypes.POINTER(_I), _P],
     "lrstv_kernel_name": [_I],
     "lrstv_profile_enable": [_P, _I],
     "lrstv_profile_read": [_P, ctypes.POINTER(Profile)],
@@ -371,6 +373,18 @@ def lrstv_tsvt(A, shape, t, out=None, workspace=None, sweeps=False, stream=None)
     sw = ctypes.c_int(0)
     _call("lrstv_tsvt", _dev(A, N), n1, n2, n3, float(t), _dev(out, N),
           ctypes.c_void_p(ws.data_ptr()), nb, ctypes.byref(sw) if sweeps else None, _stream(stream))
+    return (out, sw.value) if sweeps else out
+
+
+def lrstv_tsvt_noalloc(A, shape, t, out, sweeps=False, stream=None):
+    """lrstv_tsvt_noalloc: the t-SVT with the library's fixed device scratch
+    array instead of a workspace (for callers that cannot allocate).  `out`
+    must be given; nothing is allocated."""
+    n1, n2, n3 = shape
+    N = n1 * n2 * n3
+    sw = ctypes.c_int(0)
+    _call("lrstv_tsvt_noalloc", _dev(A, N), n1, n2, n3, float(t), _dev(out, N),
+          ctypes.byref(sw) if sweeps else None, _stream(stream))
     return (out, sw.value) if sweeps else out
 
 
