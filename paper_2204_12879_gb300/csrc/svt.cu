@@ -7,15 +7,17 @@
 // |w_p^H w_q| <= tol |w_p| |w_q|.  The rotations accumulate in V, so W = A V
 // has orthogonal columns sigma_i u_i and SVT_t(A) = W diag(g) V^H with
 // g_i = max(1 - t / sigma_i, 0).  U is never formed; the reconstruction
-// W (V diag g)^H is a batched complex GEMM (dft.cu).
+// W (V diag g)^H is a batched complex GEMM (dft.cu).  One CTA per slice; the
+// sweep loop is capped and a slice that reaches the cap reports it.
 //
-// One CTA per slice.  A sweep visits all nc(nc-1)/2 pairs in np-1 rounds of
-// np/2 disjoint pairs (round-robin "circle" ordering, np = nc rounded up to
-// even; an odd nc gets a phantom column).  Each warp owns one pair of a
-// round at a time and keeps both columns in registers (R rows per lane) for
-// the dot products and the rotation.  Columns live in global memory (the
-// slices are L2-resident between rounds); __syncthreads separates rounds.
-// The sweep loop is capped; a slice that reaches the cap reports it.
+// Three kernels share the rotation formula and differ in how columns move:
+//  - k_jacobi_pk (nr <= 224, the common case): 32-column panels staged in
+//    shared memory, a panel's W and V columns held in registers while later
+//    panels stream past, one column pair per half-warp, paired FP32
+//    instructions (__ffma2_rn) on a split row-pair layout;
+//  - k_jacobi_panel (nr <= 256): the same panel order with full warps;
+//  - k_jacobi (any nr up to 512): round-robin over all columns in global
+//    memory (L2-resident), one pair per warp.
 #include <float.h>
 
 #include "lrstv_internal.cuh"
@@ -418,16 +420,7 @@ __global__ void __launch_bounds__(kPWarps * 32, 1)
   }
 }
 
-// ---------------------------------------------------------------------------
-// Half-warp kernel (nr <= 208).  The panel scheme above with one column pair
-// per half-warp (16 lanes, R2 rows per lane), so each warp instruction works on
-// two independent pairs, reductions take four shuffle levels, and the 32
-// columns of panel a map to the 32 half-warps.  Panels are staged in shared
-// memory with rows padded to 16 R2 (zeros, which rotations keep at zero), so
-// no row needs a bounds check.  A half-warp whose pair is phantom, negligible
-// or already orthogonal applies the identity rotation (c = 1, s = 0, e = 1),
-// which leaves its columns bit-for-bit unchanged.
-constexpr int kHW = 16;  // warps per CTA (32 half-warps)
+constexpr int kHW = 16;  // warps per CTA of the packed kernel (32 half-warps)
 
 __device__ __forceinline__ float half_sum(float v) {
 #pragma unroll
@@ -435,89 +428,163 @@ __device__ __forceinline__ float half_sum(float v) {
   return v;
 }
 
-template <int R2>
-__device__ __forceinline__ void hw_dots(const float2 (&a)[R2], const float2 (&b)[R2], float &al,
+// ---------------------------------------------------------------------------
+// Packed kernel (nr <= 224): the half-warp panel scheme with Blackwell's
+// paired FP32 instructions (__ffma2_rn / __fmul2_rn: two FP32 FMAs per lane
+// per instruction).  Staged columns use a split row-pair layout: row pair m is
+// one float4 (re_2m, re_2m+1, im_2m, im_2m+1), so a 128-bit load gives the two
+// packed operands (re, re) and (im, im) directly and complex arithmetic needs
+// no register shuffles: a dot-product step costs 4 paired instructions per two
+// rows and a rotation 12 (against 16 and 24 scalar FMAs).  Panel a's W columns
+// live in registers (one per half-warp); V columns of panel a and of the
+// streamed panel b stay in shared memory.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 dup(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
+
+// A rotation as broadcast pairs: a' = c a - (s e) b, b' = s a + (c e) b.
+struct PRot {
+  float2 C, S, NSEX, SEY, NSEY, CEX, CEY, NCEY;
+};
+
+__device__ __forceinline__ PRot packed(const Rot &r) {
+  const float sex = r.s * r.er, sey = r.s * r.ei, cex = r.c * r.er, cey = r.c * r.ei;
+  PRot q;
+  q.C = dup(r.c);
+  q.S = dup(r.s);
+  q.NSEX = dup(-sex);
+  q.SEY = dup(sey);
+  q.NSEY = dup(-sey);
+  q.CEX = dup(cex);
+  q.CEY = dup(cey);
+  q.NCEY = dup(-cey);
+  return q;
+}
+
+__device__ __forceinline__ void pk_rot(float4 &a, float4 &b, const PRot &q) {
+  const float2 Ra = lo2(a), Ia = hi2(a), Rb = lo2(b), Ib = hi2(b);
+  const float2 aR = fma2(q.SEY, Ib, fma2(q.NSEX, Rb, mul2(q.C, Ra)));
+  const float2 aI = fma2(q.NSEY, Rb, fma2(q.NSEX, Ib, mul2(q.C, Ia)));
+  const float2 bR = fma2(q.NCEY, Ib, fma2(q.CEX, Rb, mul2(q.S, Ra)));
+  const float2 bI = fma2(q.CEY, Rb, fma2(q.CEX, Ib, mul2(q.S, Ia)));
+  a = make_float4(aR.x, aR.y, aI.x, aI.y);
+  b = make_float4(bR.x, bR.y, bI.x, bI.y);
+}
+
+// lane partial sums of |a|^2, |b|^2, re(a^H b), im(a^H b) over K row pairs
+template <int K>
+__device__ __forceinline__ void pk_dots(const float4 (&a)[K], const float4 (&b)[K], float &al,
                                         float &be, float &gr, float &gi) {
-  al = be = gr = gi = 0.f;
+  float2 aa = make_float2(0.f, 0.f), bb = aa, rr = aa, i1 = aa, i2 = aa;
 #pragma unroll
-  for (int k = 0; k < R2; ++k) {
-    al = fmaf(a[k].x, a[k].x, fmaf(a[k].y, a[k].y, al));
-    be = fmaf(b[k].x, b[k].x, fmaf(b[k].y, b[k].y, be));
-    gr = fmaf(a[k].x, b[k].x, fmaf(a[k].y, b[k].y, gr));
-    gi = fmaf(a[k].x, b[k].y, fmaf(-a[k].y, b[k].x, gi));
+  for (int k = 0; k < K; ++k) {
+    const float2 Ra = lo2(a[k]), Ia = hi2(a[k]), Rb = lo2(b[k]), Ib = hi2(b[k]);
+    aa = fma2(Ia, Ia, fma2(Ra, Ra, aa));
+    bb = fma2(Ib, Ib, fma2(Rb, Rb, bb));
+    rr = fma2(Ia, Ib, fma2(Ra, Rb, rr));
+    i1 = fma2(Ra, Ib, i1);
+    i2 = fma2(Ia, Rb, i2);
   }
-  al = half_sum(al);
-  be = half_sum(be);
-  gr = half_sum(gr);
-  gi = half_sum(gi);
+  al = aa.x + aa.y;
+  be = bb.x + bb.y;
+  gr = rr.x + rr.y;
+  gi = (i1.x + i1.y) - (i2.x + i2.y);
 }
 
-template <int R2>
-__device__ __forceinline__ void hw_load(float2 (&x)[R2], const float2 *col, int ul) {
+// rotates two shared-memory columns (row-pair layout), lane stride `step`
+template <int K, int STEP>
+__device__ __forceinline__ void pk_rot_smem(float4 *ca, float4 *cb, const PRot &q, int l) {
 #pragma unroll
-  for (int k = 0; k < R2; ++k) x[k] = col[ul + kHW * k];
-}
-
-template <int R2>
-__device__ __forceinline__ void hw_store(const float2 (&x)[R2], float2 *col, int ul) {
-#pragma unroll
-  for (int k = 0; k < R2; ++k) col[ul + kHW * k] = x[k];
-}
-
-// Rotates the register column a against the shared-memory column col,
-// streaming col through registers C rows at a time (keeps few registers live).
-template <int R2, int C>
-__device__ __forceinline__ void hw_rot_stream(float2 (&a)[R2], float2 *col, const Rot &r, int ul) {
-#pragma unroll
-  for (int k0 = 0; k0 < R2; k0 += C) {
-    float2 b[C];
-#pragma unroll
-    for (int k = 0; k < C; ++k)
-      if (k0 + k < R2) b[k] = col[ul + kHW * (k0 + k)];
-#pragma unroll
-    for (int k = 0; k < C; ++k) {
-      if (k0 + k < R2) {
-        const float2 bb = make_float2(r.er * b[k].x - r.ei * b[k].y, r.er * b[k].y + r.ei * b[k].x);
-        const float2 x = a[k0 + k];
-        a[k0 + k] = make_float2(r.c * x.x - r.s * bb.x, r.c * x.y - r.s * bb.y);
-        b[k] = make_float2(r.s * x.x + r.c * bb.x, r.s * x.y + r.c * bb.y);
-      }
+  for (int k = 0; k < K; k += 2) {
+    float4 x0 = ca[l + STEP * k], y0 = cb[l + STEP * k];
+    float4 x1, y1;
+    if (k + 1 < K) {
+      x1 = ca[l + STEP * (k + 1)];
+      y1 = cb[l + STEP * (k + 1)];
     }
+    pk_rot(x0, y0, q);
+    ca[l + STEP * k] = x0;
+    cb[l + STEP * k] = y0;
+    if (k + 1 < K) {
+      pk_rot(x1, y1, q);
+      ca[l + STEP * (k + 1)] = x1;
+      cb[l + STEP * (k + 1)] = y1;
+    }
+  }
+}
+
+// rotates the register column a against shared-memory column col (row-pair
+// layout, half-warp lane stride), two row pairs at a time
+template <int K>
+__device__ __forceinline__ void pk_rot_stream(float4 (&a)[K], float4 *col, const PRot &q, int ul) {
 #pragma unroll
-    for (int k = 0; k < C; ++k)
-      if (k0 + k < R2) col[ul + kHW * (k0 + k)] = b[k];
+  for (int k = 0; k < K; k += 2) {
+    float4 y0 = col[ul + 16 * k], y1;
+    if (k + 1 < K) y1 = col[ul + 16 * (k + 1)];
+    pk_rot(a[k], y0, q);
+    col[ul + 16 * k] = y0;
+    if (k + 1 < K) {
+      pk_rot(a[k + 1], y1, q);
+      col[ul + 16 * (k + 1)] = y1;
+    }
   }
 }
 
-// shared panel (ld rows per column, zero padded) <- wcols columns of n rows
-__device__ __forceinline__ void stage_in(float2 *dst, int ld, const float2 *src, int n, int wcols) {
-  const float2 z = make_float2(0.f, 0.f);
-  for (int e = threadIdx.x; e < kPW * ld; e += blockDim.x) {
-    const int c = e / ld, r = e - c * ld;
-    dst[e] = (c < wcols && r < n) ? src[(size_t)n * c + r] : z;
+// shared panel (ld2 row pairs per column, split layout, zero padded) <-
+// wcols interleaved columns of n rows; warp w copies columns w, w + 16, ...
+__device__ __forceinline__ void pk_stage_in(float4 *dst, int ld2, const float2 *src, int n,
+                                            int wcols) {
+  const int lane = threadIdx.x & 31;
+  for (int c = threadIdx.x >> 5; c < kPW; c += kHW) {
+    const float2 *s = src + (size_t)n * c;
+    float4 *d = dst + ld2 * c;
+    const bool real = c < wcols;
+    for (int m = lane; m < ld2; m += 32) {
+      const int r0 = 2 * m, r1 = 2 * m + 1;
+      const float2 x0 = (real && r0 < n) ? s[r0] : make_float2(0.f, 0.f);
+      const float2 x1 = (real && r1 < n) ? s[r1] : make_float2(0.f, 0.f);
+      d[m] = make_float4(x0.x, x1.x, x0.y, x1.y);
+    }
   }
 }
 
-__device__ __forceinline__ void stage_out(float2 *dst, const float2 *src, int ld, int n, int wcols) {
-  for (int e = threadIdx.x; e < wcols * n; e += blockDim.x) {
-    const int c = e / n, r = e - c * n;
-    dst[e] = src[c * ld + r];
+__device__ __forceinline__ void pk_stage_out(float2 *dst, const float4 *src, int ld2, int n,
+                                             int wcols) {
+  const int lane = threadIdx.x & 31;
+  for (int c = threadIdx.x >> 5; c < wcols; c += kHW) {
+    float2 *d = dst + (size_t)n * c;
+    const float4 *s = src + ld2 * c;
+    for (int m = lane; 2 * m < n; m += 32) {
+      const float4 v = s[m];
+      d[2 * m] = make_float2(v.x, v.z);
+      if (2 * m + 1 < n) d[2 * m + 1] = make_float2(v.y, v.w);
+    }
   }
 }
 
-template <int R2>
+template <int KP>
+struct PkShape {
+  static constexpr int KPF = (KP + 1) / 2;  // row pairs per lane, full warp
+  static constexpr int LD2 = (16 * KP > 32 * KPF) ? 16 * KP : 32 * KPF;  // row pairs per column
+};
+
+template <int KP>
 __global__ void __launch_bounds__(kHW * 32, 1)
-    k_jacobi_hw(int nr, int nc, size_t wstride, size_t vstride, float2 *W_all, float2 *V_all,
+    k_jacobi_pk(int nr, int nc, size_t wstride, size_t vstride, float2 *W_all, float2 *V_all,
                 float t, int max_sweeps, float tol, float negl_rel, int *__restrict__ sweeps_out,
                 unsigned long long *__restrict__ work) {
-  constexpr int LD = kHW * R2;  // padded rows of a staged column
+  constexpr int KPF = PkShape<KP>::KPF;
+  constexpr int LD2 = PkShape<KP>::LD2;
   extern __shared__ float4 smem_f4[];
-  float2 *sW = reinterpret_cast<float2 *>(smem_f4);  // kPW x LD
-  float2 *sV = sW + kPW * LD;                          // kPW x LD
+  float4 *sW = smem_f4;            // panel a (own pairs), then panel b: W
+  float4 *sVa = sW + kPW * LD2;    // panel a: V
+  float4 *sVb = sVa + kPW * LD2;   // panel b: V
   float2 *W = W_all + (size_t)blockIdx.x * wstride;
   float2 *V = V_all + (size_t)blockIdx.x * vstride;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int unit = tid >> 4, ul = tid & 15;  // half-warp and its lane
+  const int unit = tid >> 4, ul = tid & 15;
   __shared__ float s_red[32];
   __shared__ int s_rot;
 
@@ -540,76 +607,96 @@ __global__ void __launch_bounds__(kHW * 32, 1)
   const float negl = negl_rel * s_red[0];
 
   const int npan = (nc + kPW - 1) / kPW;
-  unsigned long long n_pairs = 0, n_rot = 0;  // counted by lane 0 of each half-warp
+  unsigned n_pairs = 0, n_rot = 0;  // lane 0 (own pairs) and ul 0 (cross pairs) count
   int sweeps = (nc < 2) ? 1 : 0;
   bool converged = (nc < 2);
-  float2 aW[R2], aV[R2], bW[R2];
+  float4 aW[KP], aV[KP], bW[KP];
   for (int sweep = 1; sweep <= max_sweeps && !converged; ++sweep) {
     if (tid == 0) s_rot = 0;
     int rotated = 0;
     for (int a = 0; a < npan; ++a) {
       const int ca = a * kPW, wa = min(kPW, nc - ca);
       __syncthreads();
-      stage_in(sW, LD, W + (size_t)nr * ca, nr, wa);
-      stage_in(sV, LD, V + (size_t)nc * ca, nc, wa);
+      pk_stage_in(sW, LD2, W + (size_t)nr * ca, nr, wa);
+      pk_stage_in(sVa, LD2, V + (size_t)nc * ca, nc, wa);
       __syncthreads();
-      // pairs inside panel a: 16 disjoint pairs per round on half-warps 0..15
+      // pairs inside panel a: 16 disjoint pairs per round, one per warp
       for (int r = 0; r < kPW - 1; ++r) {
-        if (unit < kPW / 2) {
-          int p, q;
-          pair_of(r, unit, kPW, p, q);
-          const bool real = p < wa && q < wa;
-          hw_load<R2>(aW, sW + LD * p, ul);
-          hw_load<R2>(bW, sW + LD * q, ul);
+        int p, q;
+        pair_of(r, warp, kPW, p, q);
+        if (p < wa && q < wa) {
+          float4 xa[KPF], xb[KPF];
+#pragma unroll
+          for (int k = 0; k < KPF; ++k) {
+            xa[k] = sW[LD2 * p + lane + 32 * k];
+            xb[k] = sW[LD2 * q + lane + 32 * k];
+          }
           float al, be, gr, gi;
-          hw_dots<R2>(aW, bW, al, be, gr, gi);
+          pk_dots<KPF>(xa, xb, al, be, gr, gi);
+          al = warp_sum(al);
+          be = warp_sum(be);
+          gr = warp_sum(gr);
+          gi = warp_sum(gi);
+          if (lane == 0) n_pairs += 1;
           Rot rt;
-          const bool go = real && make_rot(al, be, gr, gi, tol, negl, rt);
-          if (ul == 0 && real) n_pairs += 1;
-          if (go) {
-            pair_apply<R2>(aW, bW, rt);
-            hw_store<R2>(aW, sW + LD * p, ul);
-            hw_store<R2>(bW, sW + LD * q, ul);
-            hw_load<R2>(aV, sV + LD * p, ul);
-            hw_rot_stream<R2, 4>(aV, sV + LD * q, rt, ul);
-            hw_store<R2>(aV, sV + LD * p, ul);
-            if (ul == 0) n_rot += 1;
+          if (make_rot(al, be, gr, gi, tol, negl, rt)) {
+            const PRot pq = packed(rt);
+#pragma unroll
+            for (int k = 0; k < KPF; ++k) {
+              pk_rot(xa[k], xb[k], pq);
+              sW[LD2 * p + lane + 32 * k] = xa[k];
+              sW[LD2 * q + lane + 32 * k] = xb[k];
+            }
+            pk_rot_smem<KPF, 32>(sVa + LD2 * p, sVa + LD2 * q, pq, lane);
+            if (lane == 0) n_rot += 1;
             rotated = 1;
           }
         }
         __syncthreads();
       }
-      // panel a's column `unit` moves to registers
+      // panel a's W column `unit` moves to registers
       const bool mine = unit < wa;
-      hw_load<R2>(aW, sW + LD * unit, ul);
-      hw_load<R2>(aV, sV + LD * unit, ul);
+#pragma unroll
+      for (int k = 0; k < KP; ++k) {
+        aW[k] = sW[LD2 * unit + ul + 16 * k];
+        aV[k] = sVa[LD2 * unit + ul + 16 * k];
+      }
       for (int b = a + 1; b < npan; ++b) {
         const int cb = b * kPW, wb = min(kPW, nc - cb);
         __syncthreads();
-        stage_in(sW, LD, W + (size_t)nr * cb, nr, wb);
-        stage_in(sV, LD, V + (size_t)nc * cb, nc, wb);
+        pk_stage_in(sW, LD2, W + (size_t)nr * cb, nr, wb);
+        pk_stage_in(sVb, LD2, V + (size_t)nc * cb, nc, wb);
         __syncthreads();
         for (int r = 0; r < kPW; ++r) {
           const int j = (unit + r) & (kPW - 1);
           const bool real = mine && j < wb;
-          hw_load<R2>(bW, sW + LD * j, ul);
+#pragma unroll
+          for (int k = 0; k < KP; ++k) bW[k] = sW[LD2 * j + ul + 16 * k];
           float al, be, gr, gi;
-          hw_dots<R2>(aW, bW, al, be, gr, gi);
+          pk_dots<KP>(aW, bW, al, be, gr, gi);
+          al = half_sum(al);
+          be = half_sum(be);
+          gr = half_sum(gr);
+          gi = half_sum(gi);
           Rot rt;
           const bool go = real && make_rot(al, be, gr, gi, tol, negl, rt);
           if (ul == 0 && real) n_pairs += 1;
           if (__any_sync(0xffffffffu, go)) {
-            // the other half-warp of this warp may rotate: this half applies
-            // the identity, which rewrites its columns unchanged
+            // the other half-warp may rotate: this half applies the identity,
+            // which rewrites its columns unchanged
             if (!go) {
               rt.c = 1.0f;
               rt.s = 0.0f;
               rt.er = 1.0f;
               rt.ei = 0.0f;
             }
-            pair_apply<R2>(aW, bW, rt);
-            hw_store<R2>(bW, sW + LD * j, ul);
-            hw_rot_stream<R2, 4>(aV, sV + LD * j, rt, ul);
+            const PRot pq = packed(rt);
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+              pk_rot(aW[k], bW[k], pq);
+              sW[LD2 * j + ul + 16 * k] = bW[k];
+            }
+            pk_rot_stream<KP>(aV, sVb + LD2 * j, pq, ul);
             if (go) {
               if (ul == 0) n_rot += 1;
               rotated = 1;
@@ -617,19 +704,22 @@ __global__ void __launch_bounds__(kHW * 32, 1)
           }
           __syncthreads();
         }
-        stage_out(W + (size_t)nr * cb, sW, LD, nr, wb);
-        stage_out(V + (size_t)nc * cb, sV, LD, nc, wb);
+        pk_stage_out(W + (size_t)nr * cb, sW, LD2, nr, wb);
+        pk_stage_out(V + (size_t)nc * cb, sVb, LD2, nc, wb);
       }
+#pragma unroll
+      for (int k = 0; k < KP; ++k) sVa[LD2 * unit + ul + 16 * k] = aV[k];
+      __syncthreads();
       if (mine) {
         float2 *wcol = W + (size_t)nr * (ca + unit);
-        float2 *vcol = V + (size_t)nc * (ca + unit);
 #pragma unroll
-        for (int k = 0; k < R2; ++k) {
-          const int row = ul + kHW * k;
-          if (row < nr) wcol[row] = aW[k];
-          if (row < nc) vcol[row] = aV[k];
+        for (int k = 0; k < KP; ++k) {
+          const int m = ul + 16 * k;
+          if (2 * m < nr) wcol[2 * m] = make_float2(aW[k].x, aW[k].z);
+          if (2 * m + 1 < nr) wcol[2 * m + 1] = make_float2(aW[k].y, aW[k].w);
         }
       }
+      pk_stage_out(V + (size_t)nc * ca, sVa, LD2, nc, wa);
     }
     if (rotated) s_rot = 1;
     __syncthreads();
@@ -650,20 +740,20 @@ __global__ void __launch_bounds__(kHW * 32, 1)
   }
   if (tid == 0) sweeps_out[blockIdx.x] = converged ? sweeps : -max_sweeps;
   if (work && ul == 0) {
-    atomicAdd(work + 0, n_pairs);
-    atomicAdd(work + 1, n_rot);
+    atomicAdd(work + 0, (unsigned long long)n_pairs);
+    atomicAdd(work + 1, (unsigned long long)n_rot);
   }
 }
 
-template <int R2>
-cudaError_t launch_hw(int nslices, int nr, int nc, size_t ws, size_t vs, float2 *W, float2 *V,
+template <int KP>
+cudaError_t launch_pk(int nslices, int nr, int nc, size_t ws, size_t vs, float2 *W, float2 *V,
                       float t, int max_sweeps, float tol, float negl, int *sweeps,
                       unsigned long long *work, cudaStream_t st) {
-  const size_t smem = sizeof(float2) * 2 * (size_t)kPW * kHW * R2;
-  cudaError_t e = cudaFuncSetAttribute(k_jacobi_hw<R2>,
+  const size_t smem = sizeof(float4) * 3 * (size_t)kPW * PkShape<KP>::LD2;
+  cudaError_t e = cudaFuncSetAttribute(k_jacobi_pk<KP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_jacobi_hw<R2><<<nslices, kHW * 32, smem, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl,
+  k_jacobi_pk<KP><<<nslices, kHW * 32, smem, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl,
                                                    sweeps, work);
   return cudaGetLastError();
 }
@@ -699,12 +789,12 @@ cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, floa
   const float tol = 8.0f * sqrtf((float)nr) * eps;
   const float negl = ((float)nr * eps) * ((float)nr * eps);
   const size_t ws = d.P, vs = (size_t)nc * nc;
-  if (nr <= 208 && nc >= 2) {
-    const int R2 = (nr + 15) / 16;
-    if (R2 <= 2) return launch_hw<2>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
-    if (R2 <= 4) return launch_hw<4>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
-    if (R2 <= 8) return launch_hw<8>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
-    return launch_hw<13>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
+  if (nr <= 224 && nc >= 2) {
+    const int KP = (nr + 31) / 32;  // row pairs per lane of a half-warp
+    if (KP <= 1) return launch_pk<1>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
+    if (KP <= 2) return launch_pk<2>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
+    if (KP <= 4) return launch_pk<4>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
+    return launch_pk<7>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
   }
   if (R <= 8 && nc >= 2) {
     if (R <= 1) return launch_panel<1>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
