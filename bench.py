@@ -390,6 +390,30 @@ def run_reference(args, wl_name):
     }
 
 
+def run_micro(args):
+    """One standalone operator, for kernel captures: `tsvt` runs lrstv_tsvt on
+    a seeded random cube of --shape three times and prints its last time."""
+    import numpy as np
+    import torch
+
+    from paper_2204_12879_gb300 import builder, lrstv
+    builder.build()
+    shape = tuple(int(x) for x in args.shape.split(","))
+    N = shape[0] * shape[1] * shape[2]
+    A = torch.from_numpy(np.random.default_rng(0).standard_normal(N).astype(np.float32)).cuda()
+    sweeps, ms = 0, 0.0
+    for _ in range(3):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        out = lrstv.lrstv_tsvt(A, shape, 1.0)
+        e.record()
+        torch.cuda.synchronize()
+        ms = s.elapsed_time(e)
+    _, sweeps = lrstv.lrstv_tsvt(A, shape, 1.0, out=out, sweeps=True)
+    print(json.dumps({"micro": "tsvt", "shape": list(shape), "t": 1.0, "ms": ms,
+                      "sweeps": sweeps, "slices": shape[2] // 2 + 1}))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -400,7 +424,13 @@ def main(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of oracle time for the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--micro", choices=["tsvt"], default=None,
+                    help="time one standalone operator instead of the iteration")
+    ap.add_argument("--shape", default="200,200,16", help="n1,n2,n3 for --micro")
     args = ap.parse_args(argv)
+    if args.micro:
+        run_micro(args)
+        return
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")
     line = (run_reference if args.impl == "reference" else run_ours)(args, args.workload)

@@ -190,19 +190,32 @@ struct Rot {
 
 // Rotation of the 2x2 Hermitian [[al, g], [conj g, be]], or false when the
 // pair is orthogonal to tolerance or a column is negligible.
+// 1/sqrt(x) to about an ulp: the MUFU estimate refined by one Newton step.
+__device__ __forceinline__ float rsqrt_nr(float x) {
+  const float y = rsqrtf(x);
+  return y * fmaf(-0.5f * x * y, y, 1.5f);
+}
+
+// Rotation of the 2x2 Hermitian [[al, g], [conj g, be]], or false when the
+// pair is orthogonal to tolerance (|g|^2 <= tol^2 al be) or a column is
+// negligible.  Unitarity rests on c = 1/sqrt(1 + t^2), s = c t and |e| = 1,
+// which take the Newton-refined reciprocal square root; the angle itself
+// (zeta, t) may carry a few ulps of error without affecting unitarity.
 __device__ __forceinline__ bool make_rot(float al, float be, float gr, float gi, float tol,
                                          float negl, Rot &r) {
   if (!(al > negl && be > negl)) return false;
-  const float ag = hypotf(gr, gi);
-  if (!(ag > tol * sqrtf(al) * sqrtf(be))) return false;
-  const float zeta = (be - al) / (2.0f * ag);
+  const float g2 = fmaf(gr, gr, gi * gi);
+  if (!(g2 > (tol * tol) * (al * be))) return false;
+  const float inv_ag = rsqrt_nr(g2);
+  const float zeta = 0.5f * (be - al) * inv_ag;
   const float az = fabsf(zeta);
-  const float tn = (az > 1e18f ? 0.5f / az : 1.0f / (az + sqrtf(fmaf(az, az, 1.0f))));
+  const float q = fmaf(az, az, 1.0f);
+  const float tn = az > 1e18f ? __fdividef(0.5f, az) : __fdividef(1.0f, az + q * rsqrtf(q));
   const float tt = zeta >= 0.0f ? tn : -tn;
-  r.c = 1.0f / sqrtf(fmaf(tt, tt, 1.0f));
+  r.c = rsqrt_nr(fmaf(tt, tt, 1.0f));
   r.s = r.c * tt;
-  r.er = gr / ag;
-  r.ei = -gi / ag;
+  r.er = gr * inv_ag;
+  r.ei = -gi * inv_ag;
   return true;
 }
 
@@ -473,24 +486,27 @@ __device__ __forceinline__ void pk_rot(float4 &a, float4 &b, const PRot &q) {
   b = make_float4(bR.x, bR.y, bI.x, bI.y);
 }
 
-// lane partial sums of |a|^2, |b|^2, re(a^H b), im(a^H b) over K row pairs
+// lane partial sums of |a|^2, |b|^2, re(a^H b), im(a^H b) over K row pairs,
+// in two interleaved chains (even / odd k) to halve the dependent FMA depth
 template <int K>
 __device__ __forceinline__ void pk_dots(const float4 (&a)[K], const float4 (&b)[K], float &al,
                                         float &be, float &gr, float &gi) {
-  float2 aa = make_float2(0.f, 0.f), bb = aa, rr = aa, i1 = aa, i2 = aa;
+  const float2 z = make_float2(0.f, 0.f);
+  float2 aa[2] = {z, z}, bb[2] = {z, z}, rr[2] = {z, z}, i1[2] = {z, z}, i2[2] = {z, z};
 #pragma unroll
   for (int k = 0; k < K; ++k) {
+    const int c = k & 1;
     const float2 Ra = lo2(a[k]), Ia = hi2(a[k]), Rb = lo2(b[k]), Ib = hi2(b[k]);
-    aa = fma2(Ia, Ia, fma2(Ra, Ra, aa));
-    bb = fma2(Ib, Ib, fma2(Rb, Rb, bb));
-    rr = fma2(Ia, Ib, fma2(Ra, Rb, rr));
-    i1 = fma2(Ra, Ib, i1);
-    i2 = fma2(Ia, Rb, i2);
+    aa[c] = fma2(Ia, Ia, fma2(Ra, Ra, aa[c]));
+    bb[c] = fma2(Ib, Ib, fma2(Rb, Rb, bb[c]));
+    rr[c] = fma2(Ia, Ib, fma2(Ra, Rb, rr[c]));
+    i1[c] = fma2(Ra, Ib, i1[c]);
+    i2[c] = fma2(Ia, Rb, i2[c]);
   }
-  al = aa.x + aa.y;
-  be = bb.x + bb.y;
-  gr = rr.x + rr.y;
-  gi = (i1.x + i1.y) - (i2.x + i2.y);
+  al = (aa[0].x + aa[1].x) + (aa[0].y + aa[1].y);
+  be = (bb[0].x + bb[1].x) + (bb[0].y + bb[1].y);
+  gr = (rr[0].x + rr[1].x) + (rr[0].y + rr[1].y);
+  gi = ((i1[0].x + i1[1].x) + (i1[0].y + i1[1].y)) - ((i2[0].x + i2[1].x) + (i2[0].y + i2[1].y));
 }
 
 // rotates two shared-memory columns (row-pair layout), lane stride `step`
@@ -519,16 +535,15 @@ __device__ __forceinline__ void pk_rot_smem(float4 *ca, float4 *cb, const PRot &
 // layout, half-warp lane stride), two row pairs at a time
 template <int K>
 __device__ __forceinline__ void pk_rot_stream(float4 (&a)[K], float4 *col, const PRot &q, int ul) {
+  // loads run one row pair ahead of the rotate-and-store
+  float4 y = col[ul];
 #pragma unroll
-  for (int k = 0; k < K; k += 2) {
-    float4 y0 = col[ul + 16 * k], y1;
-    if (k + 1 < K) y1 = col[ul + 16 * (k + 1)];
-    pk_rot(a[k], y0, q);
-    col[ul + 16 * k] = y0;
-    if (k + 1 < K) {
-      pk_rot(a[k + 1], y1, q);
-      col[ul + 16 * (k + 1)] = y1;
-    }
+  for (int k = 0; k < K; ++k) {
+    float4 ynext;
+    if (k + 1 < K) ynext = col[ul + 16 * (k + 1)];
+    pk_rot(a[k], y, q);
+    col[ul + 16 * k] = y;
+    if (k + 1 < K) y = ynext;
   }
 }
 
