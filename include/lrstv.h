@@ -188,6 +188,39 @@ int lrstv_plan_run_host(lrstv_plan *plan, const float *Y_host, float *X_host, fl
 int lrstv_denoise(const float *Y, int n1, int n2, int n3, const lrstv_params *params, float *X,
                   float *S, lrstv_stats *stats, void *stream);
 
+/* ------------------------------------------------------------ batches */
+/* A batch of independent cubes of possibly different shapes, run in
+ * lockstep.  Each ADMM step launches the cheap per-cube kernels for every cube
+ * and ONE persistent Jacobi launch that works through the Fourier slices of
+ * all cubes (largest first) from a shared work list, so an uneven batch keeps
+ * every SM busy.  Each cube follows Algorithm 1 exactly as a single plan does
+ * (bit-identical results); the paper treats one cube at a time, and batching
+ * is this library's serving form.
+ *  dims    3*ncubes ints: n1, n2, n3 of each cube.
+ *  params  ncubes structs; mu0, rho, mu_max, max_iter and flags must agree
+ *          (the cubes share one penalty schedule), tau, alpha, lambda and w
+ *          may differ.  Parameters are fixed when the batch is created.
+ * The batch owns one plan per cube (lrstv_batch_plan lends it for stats and
+ * state export; do not destroy it or change its parameters) and one small
+ * allocation for the work list.  Slices taller than 224 rows (max(n1, n2))
+ * take a separate per-cube Jacobi launch.  The persistent launch is recorded
+ * in cube 0's profile (lrstv_profile_*). */
+typedef struct lrstv_batch lrstv_batch;
+int lrstv_batch_create(int ncubes, const int *dims, const lrstv_params *params,
+                       lrstv_batch **batch);
+int lrstv_batch_destroy(lrstv_batch *batch);
+int lrstv_batch_size(const lrstv_batch *batch, int *ncubes);
+int lrstv_batch_plan(const lrstv_batch *batch, int i, lrstv_plan **plan);
+/* Y: host array of ncubes device pointers (N_i floats each). */
+int lrstv_batch_init(lrstv_batch *batch, const float *const *Y, void *stream);
+int lrstv_batch_iterate(lrstv_batch *batch, int iters, void *stream);
+/* lrstv_batch_init, max_iter iterations, X_i := L_i and S_i copied out (host
+ * arrays of device pointers; X or S may be NULL).  With LRSTV_FLAG_GRAPH the
+ * whole run is captured into one CUDA graph on first use and replayed while
+ * the pointers and max_iter stay the same. */
+int lrstv_batch_run(lrstv_batch *batch, const float *const *Y, float *const *X, float *const *S,
+                    void *stream);
+
 /* ---------------------------------------------------- standalone operators */
 /* g_n = w_n D_n x, circular forward differences D_n x(v) = x(v + e_n) - x(v)
  * along mode n (Section III-A).  x: N floats, g: 3N floats. */

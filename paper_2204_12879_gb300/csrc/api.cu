@@ -4,6 +4,7 @@
 // state import/export, and the standalone operators.
 #include <math.h>
 #include <new>
+#include <stdlib.h>
 #include <string.h>
 
 #include "lrstv.h"
@@ -158,29 +159,32 @@ cudaError_t zsolve_core(const Dims &d, const Tables &tb, const float *T, float m
   return launch_c2r3(d, 1, specA, 0, tb.tw3, Z, 0, nullptr, nullptr, 0.0f, 0, st);
 }
 
-// t-SVT of nb cubes x_b - ycoef y_b with threshold t: DFT along mode 3 into
-// the working orientation, Jacobi + g-scaling, W V^H, inverse DFT.
-cudaError_t tsvt_core(const Dims &d, int nb, const float *x, const float *y, float ycoef, float t,
-                      float *out, int mode, float *G4, const float *F, float mu, int gamma4,
-                      const float2 *tw3, float2 *specA, float2 *specB, float2 *V, int *sweeps,
-                      cudaStream_t st, Prof *prof = nullptr) {
-  cudaError_t e;
-  {
-    Span sp(prof, LRSTV_K_R2C_E, st);
-    e = launch_r2c3(d, nb, x, y, ycoef, specA, 1, tw3, st);
-  }
-  if (e != cudaSuccess) return e;
+// t-SVT of nb cubes x_b - ycoef y_b with threshold t, in three phases:
+// DFT along mode 3 into the working orientation (tsvt_pre), Jacobi + g-scaling
+// (tsvt_jac), W V^H and the inverse DFT (tsvt_post).
+cudaError_t tsvt_pre(const Dims &d, int nb, const float *x, const float *y, float ycoef,
+                     const float2 *tw3, float2 *specA, cudaStream_t st, Prof *prof) {
+  Span sp(prof, LRSTV_K_R2C_E, st);
+  return launch_r2c3(d, nb, x, y, ycoef, specA, 1, tw3, st);
+}
+
+cudaError_t tsvt_jac(const Dims &d, int nb, float t, float2 *specA, float2 *V, int *sweeps,
+                     cudaStream_t st, Prof *prof) {
+  Span sp(prof, LRSTV_K_JACOBI, st);
+  return launch_jacobi(d, nb * d.h, specA, V, t, kMaxSweeps, sweeps, prof ? prof->d_work : nullptr,
+                       st);
+}
+
+cudaError_t tsvt_post(const Dims &d, int nb, float *out, int mode, float *G4, const float *F,
+                      float mu, int gamma4, const float2 *tw3, float2 *specA, float2 *specB,
+                      float2 *V, cudaStream_t st, Prof *prof) {
   const int ns = nb * d.h;
-  {
-    Span sp(prof, LRSTV_K_JACOBI, st);
-    e = launch_jacobi(d, ns, specA, V, t, kMaxSweeps, sweeps, prof ? prof->d_work : nullptr, st);
-  }
-  if (e != cudaSuccess) return e;
   CGemm g{};
   g.A = specA; g.sA = (long long)d.P; g.lda = d.nr;
   g.B = V; g.sB = (long long)d.nc * d.nc; g.ldb = d.nc; g.opB = 1;
   g.C = specB; g.sC = (long long)d.P; g.ldc = d.nr;
   g.M = d.nr; g.N = d.nc; g.K = d.nc; g.batch = ns; g.epi = 0;
+  cudaError_t e;
   {
     Span sp(prof, LRSTV_K_CGEMM_E, st);
     e = launch_cgemm(g, st);
@@ -188,6 +192,16 @@ cudaError_t tsvt_core(const Dims &d, int nb, const float *x, const float *y, flo
   if (e != cudaSuccess) return e;
   Span sp(prof, LRSTV_K_C2R_E, st);
   return launch_c2r3(d, nb, specB, 1, tw3, out, mode, G4, F, mu, gamma4, st);
+}
+
+cudaError_t tsvt_core(const Dims &d, int nb, const float *x, const float *y, float ycoef, float t,
+                      float *out, int mode, float *G4, const float *F, float mu, int gamma4,
+                      const float2 *tw3, float2 *specA, float2 *specB, float2 *V, int *sweeps,
+                      cudaStream_t st, Prof *prof = nullptr) {
+  cudaError_t e = tsvt_pre(d, nb, x, y, ycoef, tw3, specA, st, prof);
+  if (e != cudaSuccess) return e;
+  if ((e = tsvt_jac(d, nb, t, specA, V, sweeps, st, prof)) != cudaSuccess) return e;
+  return tsvt_post(d, nb, out, mode, G4, F, mu, gamma4, tw3, specA, specB, V, st, prof);
 }
 
 }  // namespace
@@ -652,6 +666,299 @@ int lrstv_denoise(const float *Y, int n1, int n2, int n3, const lrstv_params *pa
   rc = lrstv_plan_run(pl, Y, X, S, stats ? stats : &local, stream);
   int rc2 = lrstv_plan_destroy(pl);
   return rc != LRSTV_OK ? rc : rc2;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+struct lrstv_batch {
+  int n;
+  lrstv_plan **plans;
+  void *arena;           // the slice work list and its counter
+  SliceTask *d_tasks;
+  int ntasks;
+  int *d_counter;
+  int grid;
+  size_t smem;
+  int *big;              // cubes whose slices take their own Jacobi launch
+  int nbig;
+  cudaStream_t cap_stream;
+  cudaGraphExec_t gexec;
+  const float **gY;
+  float **gX, **gS;
+  int giters;
+};
+
+namespace {
+
+void batch_drop_graph(lrstv_batch *b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  b->gexec = nullptr;
+  b->giters = -1;
+}
+
+void batch_free(lrstv_batch *b) {
+  if (!b) return;
+  batch_drop_graph(b);
+  if (b->plans)
+    for (int i = 0; i < b->n; ++i)
+      if (b->plans[i]) lrstv_plan_destroy(b->plans[i]);
+  delete[] b->plans;
+  delete[] b->big;
+  delete[] b->gY;
+  delete[] b->gX;
+  delete[] b->gS;
+  if (b->arena) cudaFree(b->arena);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+}
+
+int task_cmp(const void *x, const void *y) {
+  const SliceTask *a = (const SliceTask *)x, *b = (const SliceTask *)y;
+  const double ca = (double)a->nr * a->nc * a->nc, cb = (double)b->nr * b->nc * b->nc;
+  if (ca != cb) return ca > cb ? -1 : 1;
+  return a->W < b->W ? -1 : (a->W > b->W ? 1 : 0);  // a fixed order among equals
+}
+
+int batch_e_step(lrstv_batch *b, cudaStream_t st) {
+  const double mu = b->plans[0]->mu;
+  for (int i = 0; i < b->n; ++i) {
+    lrstv_plan *pl = b->plans[i];
+    CK(tsvt_pre(pl->d, 3, pl->F, pl->G4, (float)(1.0 / pl->mu), pl->tb.tw3, pl->specA, st,
+                &pl->prof));
+  }
+  if (b->ntasks > 0) {
+    CK(cudaMemsetAsync(b->d_counter, 0, sizeof(int), st));
+    Prof *prof = &b->plans[0]->prof;
+    Span sp(prof, LRSTV_K_JACOBI, st);
+    CK(launch_jacobi_batch(b->d_tasks, b->ntasks, b->d_counter, mu, kMaxSweeps,
+                           prof->on ? prof->d_work : nullptr, b->grid, b->smem, st));
+  }
+  for (int k = 0; k < b->nbig; ++k) {
+    lrstv_plan *pl = b->plans[b->big[k]];
+    CK(tsvt_jac(pl->d, 3, (float)(pl->prm.alpha / pl->mu), pl->specA, pl->V, pl->sweeps, st,
+                &pl->prof));
+  }
+  for (int i = 0; i < b->n; ++i) {
+    lrstv_plan *pl = b->plans[i];
+    const int gamma4 = (pl->prm.flags & LRSTV_FLAG_NO_GAMMA4) ? 0 : 1;
+    CK(tsvt_post(pl->d, 3, pl->E, 1, pl->G4, pl->F, (float)pl->mu, gamma4, pl->tb.tw3, pl->specA,
+                 pl->specB, pl->V, st, &pl->prof));
+  }
+  return LRSTV_OK;
+}
+
+int batch_iterate_async(lrstv_batch *b, int iters, cudaStream_t st) {
+  for (int it = 0; it < iters; ++it) {
+    int rc;
+    for (int i = 0; i < b->n; ++i) {
+      if ((rc = lrstv_step_l_tz(b->plans[i], st)) != LRSTV_OK) return rc;
+      if ((rc = lrstv_step_z(b->plans[i], st)) != LRSTV_OK) return rc;
+      if ((rc = lrstv_step_fs_dual(b->plans[i], st)) != LRSTV_OK) return rc;
+    }
+    if ((rc = batch_e_step(b, st)) != LRSTV_OK) return rc;
+    for (int i = 0; i < b->n; ++i)
+      if ((rc = lrstv_step_mu(b->plans[i])) != LRSTV_OK) return rc;
+  }
+  return LRSTV_OK;
+}
+
+int batch_init_async(lrstv_batch *b, const float *const *Y, cudaStream_t st) {
+  for (int i = 0; i < b->n; ++i) {
+    if (!Y[i]) return LRSTV_ERR_ARG;
+    int rc = init_async(b->plans[i], Y[i], st);
+    if (rc != LRSTV_OK) return rc;
+  }
+  return LRSTV_OK;
+}
+
+int batch_copy_out(lrstv_batch *b, float *const *X, float *const *S, cudaStream_t st) {
+  for (int i = 0; i < b->n; ++i) {
+    int rc = copy_out(b->plans[i], X ? X[i] : nullptr, S ? S[i] : nullptr,
+                      cudaMemcpyDeviceToDevice, st);
+    if (rc != LRSTV_OK) return rc;
+  }
+  return LRSTV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lrstv_batch_create(int ncubes, const int *dims, const lrstv_params *params,
+                       lrstv_batch **batch) {
+  if (!batch || !dims || !params || ncubes < 1) return LRSTV_ERR_ARG;
+  *batch = nullptr;
+  for (int i = 0; i < ncubes; ++i) {
+    int rc = check_shape(dims[3 * i], dims[3 * i + 1], dims[3 * i + 2]);
+    if (rc) return rc;
+    if ((rc = check_params(&params[i]))) return rc;
+    if (params[i].mu0 != params[0].mu0 || params[i].rho != params[0].rho ||
+        params[i].mu_max != params[0].mu_max || params[i].max_iter != params[0].max_iter ||
+        params[i].flags != params[0].flags)
+      return LRSTV_ERR_ARG;
+  }
+  lrstv_batch *b = new (std::nothrow) lrstv_batch();
+  if (!b) return LRSTV_ERR_ALLOC;
+  b->giters = -1;
+  b->n = ncubes;
+  b->plans = new (std::nothrow) lrstv_plan *[ncubes]();
+  b->big = new (std::nothrow) int[ncubes];
+  b->gY = new (std::nothrow) const float *[ncubes]();
+  b->gX = new (std::nothrow) float *[ncubes]();
+  b->gS = new (std::nothrow) float *[ncubes]();
+  if (!b->plans || !b->big || !b->gY || !b->gX || !b->gS) {
+    batch_free(b);
+    return LRSTV_ERR_ALLOC;
+  }
+  int ntasks = 0, maxnr = 1;
+  for (int i = 0; i < ncubes; ++i) {
+    int rc = lrstv_plan_create(dims[3 * i], dims[3 * i + 1], dims[3 * i + 2], &params[i],
+                               &b->plans[i]);
+    if (rc != LRSTV_OK) {
+      batch_free(b);
+      return rc;
+    }
+    const Dims &d = b->plans[i]->d;
+    if (d.nr <= kBatchMaxNr) {
+      ntasks += 3 * d.h;
+      if (d.nr > maxnr) maxnr = d.nr;
+    } else {
+      b->big[b->nbig++] = i;
+    }
+  }
+  b->ntasks = ntasks;
+  if (ntasks > 0) {
+    SliceTask *h = new (std::nothrow) SliceTask[ntasks];
+    if (!h) {
+      batch_free(b);
+      return LRSTV_ERR_ALLOC;
+    }
+    int k = 0;
+    for (int i = 0; i < ncubes; ++i) {
+      lrstv_plan *pl = b->plans[i];
+      const Dims &d = pl->d;
+      if (d.nr > kBatchMaxNr) continue;
+      for (int s = 0; s < 3 * d.h; ++s) {
+        h[k].W = pl->specA + (size_t)s * d.P;
+        h[k].V = pl->V + (size_t)s * d.nc * d.nc;
+        h[k].sweeps = pl->sweeps + s;
+        h[k].alpha = pl->prm.alpha;
+        h[k].nr = d.nr;
+        h[k].nc = d.nc;
+        ++k;
+      }
+    }
+    qsort(h, (size_t)ntasks, sizeof(SliceTask), task_cmp);
+    const size_t tbytes = align_up(sizeof(SliceTask) * (size_t)ntasks);
+    int dev = 0, sms = 1;
+    if (cudaMalloc(&b->arena, tbytes + kAlign) != cudaSuccess) {
+      cudaGetLastError();
+      delete[] h;
+      batch_free(b);
+      return LRSTV_ERR_ALLOC;
+    }
+    b->d_tasks = (SliceTask *)b->arena;
+    b->d_counter = (int *)((char *)b->arena + tbytes);
+    const bool ok = cudaMemcpy(b->d_tasks, h, sizeof(SliceTask) * (size_t)ntasks,
+                               cudaMemcpyHostToDevice) == cudaSuccess &&
+                    cudaGetDevice(&dev) == cudaSuccess &&
+                    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
+    delete[] h;
+    if (!ok) {
+      cudaGetLastError();
+      batch_free(b);
+      return LRSTV_ERR_CUDA;
+    }
+    b->grid = ntasks < sms ? ntasks : sms;  // one 512-thread CTA fills an SM's registers
+    b->smem = jacobi_batch_smem(maxnr);
+  }
+  if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    batch_free(b);
+    return LRSTV_ERR_CUDA;
+  }
+  *batch = b;
+  return LRSTV_OK;
+}
+
+int lrstv_batch_destroy(lrstv_batch *b) {
+  if (!b) return LRSTV_ERR_ARG;
+  batch_free(b);
+  return LRSTV_OK;
+}
+
+int lrstv_batch_size(const lrstv_batch *b, int *ncubes) {
+  if (!b || !ncubes) return LRSTV_ERR_ARG;
+  *ncubes = b->n;
+  return LRSTV_OK;
+}
+
+int lrstv_batch_plan(const lrstv_batch *b, int i, lrstv_plan **plan) {
+  if (!b || !plan || i < 0 || i >= b->n) return LRSTV_ERR_ARG;
+  *plan = b->plans[i];
+  return LRSTV_OK;
+}
+
+int lrstv_batch_init(lrstv_batch *b, const float *const *Y, void *stream) {
+  if (!b || !Y) return LRSTV_ERR_ARG;
+  return batch_init_async(b, Y, (cudaStream_t)stream);
+}
+
+int lrstv_batch_iterate(lrstv_batch *b, int iters, void *stream) {
+  if (!b || iters < 0) return LRSTV_ERR_ARG;
+  return batch_iterate_async(b, iters, (cudaStream_t)stream);
+}
+
+int lrstv_batch_run(lrstv_batch *b, const float *const *Y, float *const *X, float *const *S,
+                    void *stream) {
+  if (!b || !Y) return LRSTV_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int iters = b->plans[0]->prm.max_iter;
+  int rc;
+  if (b->plans[0]->prm.flags & LRSTV_FLAG_GRAPH) {
+    bool same = b->gexec && b->giters == iters;
+    for (int i = 0; same && i < b->n; ++i)
+      same = b->gY[i] == Y[i] && b->gX[i] == (X ? X[i] : nullptr) &&
+             b->gS[i] == (S ? S[i] : nullptr);
+    if (!same) {
+      batch_drop_graph(b);
+      cudaGraph_t graph = nullptr;
+      CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+      rc = batch_init_async(b, Y, b->cap_stream);
+      if (rc == LRSTV_OK) rc = batch_iterate_async(b, iters, b->cap_stream);
+      if (rc == LRSTV_OK) rc = batch_copy_out(b, X, S, b->cap_stream);
+      cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &graph);
+      if (rc != LRSTV_OK || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc != LRSTV_OK ? rc : LRSTV_ERR_CUDA;
+      }
+      ce = cudaGraphInstantiate(&b->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) {
+        b->gexec = nullptr;
+        return LRSTV_ERR_CUDA;
+      }
+      for (int i = 0; i < b->n; ++i) {
+        b->gY[i] = Y[i];
+        b->gX[i] = X ? X[i] : nullptr;
+        b->gS[i] = S ? S[i] : nullptr;
+      }
+      b->giters = iters;
+    }
+    CK(cudaGraphLaunch(b->gexec, st));
+    for (int i = 0; i < b->n; ++i) {
+      lrstv_plan *pl = b->plans[i];
+      pl->mu = pl->prm.mu0;
+      pl->iter = 0;
+      for (int it = 0; it < iters; ++it) lrstv_step_mu(pl);
+    }
+    return LRSTV_OK;
+  }
+  if ((rc = batch_init_async(b, Y, st)) != LRSTV_OK) return rc;
+  if ((rc = batch_iterate_async(b, iters, st)) != LRSTV_OK) return rc;
+  return batch_copy_out(b, X, S, st);
 }
 
 int lrstv_diff(const float *x, int n1, int n2, int n3, const float w[3], float *g, void *stream) {

@@ -79,6 +79,22 @@ cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, floa
                           int max_sweeps, int *sweeps, unsigned long long *work,
                           cudaStream_t st);
 
+// One slice of a batched Jacobi launch (working matrix W, V, sweep slot, the
+// cube's alpha; threshold alpha / mu formed on the device).
+struct SliceTask {
+  float2 *W, *V;
+  int *sweeps;
+  float alpha;
+  int nr, nc;
+};
+// Largest slice height the persistent batch kernel takes.
+constexpr int kBatchMaxNr = 224;
+size_t jacobi_batch_smem(int max_nr);
+// Persistent work-list Jacobi over `ntasks` slices; *counter must be 0.
+cudaError_t launch_jacobi_batch(const SliceTask *tasks, int ntasks, int *counter, double mu,
+                                int max_sweeps, unsigned long long *work, int grid, size_t smem,
+                                cudaStream_t st);
+
 // ------------------------------------------------------------------- api.cu
 // t-SVT of one cube with threshold t on caller-provided scratch: tw3 (n3),
 // specA and specB (h P each), V (h nc^2), sweeps (h); every piece is written

@@ -585,19 +585,21 @@ struct PkShape {
   static constexpr int LD2 = (16 * KP > 32 * KPF) ? 16 * KP : 32 * KPF;  // row pairs per column
 };
 
+// The packed Jacobi SVT of one slice by the whole CTA (kHW warps): W (nr x nc)
+// and V (nc x nc) in global memory, `smem` the CTA's dynamic shared memory
+// (3 kPW LD2 float4).  Writes the sweep count (negative at the cap) to
+// *sweeps_slot.  Shared by the one-slice-per-CTA kernel and the persistent
+// batch kernel, so both compute bit-identical results.
 template <int KP>
-__global__ void __launch_bounds__(kHW * 32, 1)
-    k_jacobi_pk(int nr, int nc, size_t wstride, size_t vstride, float2 *W_all, float2 *V_all,
-                float t, int max_sweeps, float tol, float negl_rel, int *__restrict__ sweeps_out,
-                unsigned long long *__restrict__ work) {
+__device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float2 *V, float t,
+                                                int max_sweeps, float tol, float negl_rel,
+                                                int *sweeps_slot, unsigned long long *work,
+                                                float4 *smem) {
   constexpr int KPF = PkShape<KP>::KPF;
   constexpr int LD2 = PkShape<KP>::LD2;
-  extern __shared__ float4 smem_f4[];
-  float4 *sW = smem_f4;            // panel a (own pairs), then panel b: W
+  float4 *sW = smem;               // panel a (own pairs), then panel b: W
   float4 *sVa = sW + kPW * LD2;    // panel a: V
   float4 *sVb = sVa + kPW * LD2;   // panel b: V
-  float2 *W = W_all + (size_t)blockIdx.x * wstride;
-  float2 *V = V_all + (size_t)blockIdx.x * vstride;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int unit = tid >> 4, ul = tid & 15;
   __shared__ float s_red[32];
@@ -753,10 +755,54 @@ __global__ void __launch_bounds__(kHW * 32, 1)
     float2 *vi = V + (size_t)nc * i;
     for (int row = lane; row < nc; row += 32) vi[row] = make_float2(vi[row].x * g, vi[row].y * g);
   }
-  if (tid == 0) sweeps_out[blockIdx.x] = converged ? sweeps : -max_sweeps;
+  if (tid == 0) *sweeps_slot = converged ? sweeps : -max_sweeps;
   if (work && ul == 0) {
     atomicAdd(work + 0, (unsigned long long)n_pairs);
     atomicAdd(work + 1, (unsigned long long)n_rot);
+  }
+}
+
+template <int KP>
+__global__ void __launch_bounds__(kHW * 32, 1)
+    k_jacobi_pk(int nr, int nc, size_t wstride, size_t vstride, float2 *W_all, float2 *V_all,
+                float t, int max_sweeps, float tol, float negl_rel, int *__restrict__ sweeps_out,
+                unsigned long long *__restrict__ work) {
+  extern __shared__ float4 smem_f4[];
+  jacobi_pk_slice<KP>(nr, nc, W_all + (size_t)blockIdx.x * wstride,
+                      V_all + (size_t)blockIdx.x * vstride, t, max_sweeps, tol, negl_rel,
+                      sweeps_out + blockIdx.x, work, smem_f4);
+}
+
+// Persistent kernel for a batch of cubes: each CTA takes the next slice from
+// an atomic counter (tasks sorted largest first) until the list is empty, and
+// runs the same jacobi_pk_slice as the one-slice kernel on it.  Threshold and
+// tolerances are formed exactly as the per-cube launch forms them, so the two
+// paths agree bit for bit.
+__global__ void __launch_bounds__(kHW * 32, 1)
+    k_jacobi_batch(const SliceTask *__restrict__ tasks, int ntasks, int *counter, double mu,
+                   int max_sweeps, unsigned long long *work) {
+  extern __shared__ float4 smem_f4[];
+  __shared__ int s_item;
+  const float eps = FLT_EPSILON * 0.5f;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= ntasks) return;
+    const SliceTask tk = tasks[item];
+    const float t = (float)((double)tk.alpha / mu);
+    const float tol = 8.0f * sqrtf((float)tk.nr) * eps;
+    const float negl = ((float)tk.nr * eps) * ((float)tk.nr * eps);
+    const int KP = (tk.nr + 31) / 32;
+    if (KP <= 1)
+      jacobi_pk_slice<1>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4);
+    else if (KP <= 2)
+      jacobi_pk_slice<2>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4);
+    else if (KP <= 4)
+      jacobi_pk_slice<4>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4);
+    else
+      jacobi_pk_slice<7>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4);
   }
 }
 
@@ -787,6 +833,24 @@ cudaError_t launch_panel(int nslices, int nr, int nc, size_t ws, size_t vs, floa
 }
 
 }  // namespace
+
+size_t jacobi_batch_smem(int max_nr) {
+  const int KP = (max_nr + 31) / 32;
+  const int LD2 = KP <= 1 ? PkShape<1>::LD2 : KP <= 2 ? PkShape<2>::LD2 : KP <= 4 ? PkShape<4>::LD2
+                                                                               : PkShape<7>::LD2;
+  return sizeof(float4) * 3 * (size_t)kPW * LD2;
+}
+
+cudaError_t launch_jacobi_batch(const SliceTask *tasks, int ntasks, int *counter, double mu,
+                                int max_sweeps, unsigned long long *work, int grid, size_t smem,
+                                cudaStream_t st) {
+  if (ntasks <= 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_jacobi_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_jacobi_batch<<<grid, kHW * 32, smem, st>>>(tasks, ntasks, counter, mu, max_sweeps, work);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, float t,
                           int max_sweeps, int *sweeps, unsigned long long *work,

@@ -17,7 +17,7 @@ import os
 from . import builder as _build
 
 __all__ = [
-    "Params", "Stats", "Profile", "Plan", "load", "status_string", "kernel_name", "LrstvError",
+    "Params", "Stats", "Profile", "Plan", "Batch", "load", "status_string", "kernel_name", "LrstvError",
     "lrstv_diff", "lrstv_diff_adjoint", "lrstv_soft_threshold", "lrstv_zsolve", "lrstv_tsvt",
     "lrstv_tsvt_noalloc",
     "lrstv_denoise", "BLOCK", "FLAG_F_THRESH_EXACT", "FLAG_NO_GAMMA4", "FLAG_GRAPH",
@@ -120,6 +120,13 @@ _SIGS = {
     "lrstv_zsolve": [_P, _I, _I, _I, ctypes.POINTER(_F), _F, _P, _P, _SZ, _P],
     "lrstv_tsvt": [_P, _I, _I, _I, _F, _P, _P, _SZ, ctypes.POINTER(_I), _P],
     "lrstv_tsvt_noalloc": [_P, _I, _I, _I, _F, _P, ctypes.POINTER(_I), _P],
+    "lrstv_batch_create": [_I, ctypes.POINTER(_I), ctypes.POINTER(Params), ctypes.POINTER(_P)],
+    "lrstv_batch_destroy": [_P],
+    "lrstv_batch_size": [_P, ctypes.POINTER(_I)],
+    "lrstv_batch_plan": [_P, _I, ctypes.POINTER(_P)],
+    "lrstv_batch_init": [_P, ctypes.POINTER(_P), _P],
+    "lrstv_batch_iterate": [_P, _I, _P],
+    "lrstv_batch_run": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
     "lrstv_kernel_name": [_I],
     "lrstv_profile_enable": [_P, _I],
     "lrstv_profile_read": [_P, ctypes.POINTER(Profile)],
@@ -303,6 +310,85 @@ class Plan:
         _call("lrstv_plan_run_host", self._h, _host_ptr(Y, self.N), _host_ptr(X, self.N),
               _host_ptr(S, self.N), ctypes.byref(st) if stats else None, _stream(stream))
         return st
+
+
+class _BorrowedPlan(Plan):
+    """A plan owned by a batch: usable for stats and state export, never freed here."""
+
+    def __init__(self, handle, shape, params):
+        self.shape = tuple(shape)
+        self.N = shape[0] * shape[1] * shape[2]
+        self.params = params
+        self._borrowed = handle
+
+    @property
+    def _h(self):
+        return self._borrowed
+
+    def close(self):
+        pass
+
+
+class Batch:
+    """An lrstv_batch: independent cubes of uneven shapes run in lockstep with
+    one persistent Jacobi launch per E-step."""
+
+    def __init__(self, shapes, params):
+        _torch()
+        self.shapes = [tuple(int(x) for x in sh) for sh in shapes]
+        n = len(self.shapes)
+        if isinstance(params, Params):
+            params = [params] * n
+        self.params = list(params)
+        dims = (ctypes.c_int * (3 * n))(*[x for sh in self.shapes for x in sh])
+        parr = (Params * n)(*self.params)
+        h = ctypes.c_void_p()
+        _call("lrstv_batch_create", n, dims, parr, ctypes.byref(h))
+        self._h = h
+        self.n = n
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lrstv_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def plan(self, i) -> Plan:
+        h = ctypes.c_void_p()
+        _call("lrstv_batch_plan", self._h, int(i), ctypes.byref(h))
+        return _BorrowedPlan(h, self.shapes[i], self.params[i])
+
+    @staticmethod
+    def _ptrs(ts, shapes):
+        arr = (ctypes.c_void_p * len(ts))()
+        for i, (t, sh) in enumerate(zip(ts, shapes)):
+            arr[i] = _dev(t, sh[0] * sh[1] * sh[2]).value
+        return arr
+
+    def init(self, Ys, stream=None):
+        _call("lrstv_batch_init", self._h, self._ptrs(Ys, self.shapes), _stream(stream))
+
+    def iterate(self, iters, stream=None):
+        _call("lrstv_batch_iterate", self._h, int(iters), _stream(stream))
+
+    def run(self, Ys, Xs=None, Ss=None, stream=None):
+        """lrstv_batch_run; returns (Xs, Ss) lists of device tensors."""
+        Xs = [_empty(sh[0] * sh[1] * sh[2]) for sh in self.shapes] if Xs is None else Xs
+        Ss = [_empty(sh[0] * sh[1] * sh[2]) for sh in self.shapes] if Ss is None else Ss
+        _call("lrstv_batch_run", self._h, self._ptrs(Ys, self.shapes),
+              self._ptrs(Xs, self.shapes), self._ptrs(Ss, self.shapes), _stream(stream))
+        return Xs, Ss
 
 
 def _host_ptr(a, n):
