@@ -42,6 +42,8 @@ WORKLOADS = {
     "c3": {"recipe": "c3", "seed": 3, "iters": 60,
            "desc": "256x256x191 Washington-DC-shaped synthetic cube, 8 endmembers, mixed noise, 60 ADMM iterations"},
 }
+BATCH = {"count": 64, "seed": 4, "iters": 50,
+         "desc": "batch of 64 uneven synthetic cubes drawn by seed from 64x64x31, 128x128x64, 145x145x220 (Indian Pines shape) and 200x200x80, each with Gaussian U[0.05,0.2] and impulse U[0,0.3] noise, 50 ADMM iterations, one persistent Jacobi launch per step"}
 METRIC = "ADMM iterations/s (plain LRSTV, FP32, 1e-4 max-abs vs FP64 oracle)"
 UNIT = "iter/s"
 SM_COUNT = 152
@@ -350,6 +352,82 @@ def run_ours(args, wl_name):
     return line
 
 
+def run_batch(args):
+    """The batched form: all cubes advance one ADMM iteration per step (one
+    persistent Jacobi launch over every Fourier slice of every cube); value =
+    cube-iterations per second.  The same cubes run one plan at a time for a
+    few iterations give the unbatched comparison."""
+    import numpy as np
+    import torch
+
+    from paper_2204_12879_gb300 import builder, lrstv
+    from synthetic import batch_recipes, flat, make_cube
+
+    builder.build()
+    recs = batch_recipes(BATCH["count"], BATCH["seed"])
+    shapes = [r.shape for r in recs]
+    Ys = [torch.from_numpy(flat(make_cube(r, 5000 + i)[1])).cuda() for i, r in enumerate(recs)]
+    params = [lrstv.Params.make(sh[0], sh[1], max_iter=BATCH["iters"]) for sh in shapes]
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    with lrstv.Batch(shapes, params) as b:
+        b.init(Ys)
+        done = 0
+        for _ in range(args.warmup):
+            b.iterate(1)
+            done += 1
+        torch.cuda.synchronize()
+        clocks = ClockSampler(0)
+        clocks.start()
+        p0 = b.plan(0)
+        p0.profile_enable(True)
+        t0, t1 = ev(), ev()
+        t0.record(stream)
+        for _ in range(args.steps):
+            if done >= BATCH["iters"]:
+                b.init(Ys)
+                done = 0
+            b.iterate(1)
+            done += 1
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        clk = clocks.stop()
+        prof = p0.profile_read()
+        p0.profile_enable(False)
+        unconv = sum(b.plan(i).stats().jacobi_unconverged for i in range(len(shapes)))
+    # unbatched comparison: the same cubes, one plan after another
+    single_ms = 0.0
+    k_single = 2
+    for i, sh in enumerate(shapes):
+        with lrstv.Plan(*sh, params[i]) as pl:
+            pl.init(Ys[i])
+            a, c = ev(), ev()
+            a.record(stream)
+            pl.iterate(k_single)
+            c.record(stream)
+            torch.cuda.synchronize()
+            single_ms += a.elapsed_time(c) / k_single
+    n = len(shapes)
+    value = n * args.steps / (ms / 1e3)
+    slices = sum(3 * (sh[2] // 2 + 1) for sh in shapes)
+    return {
+        "metric": "cube-ADMM-iterations/s (batched plain LRSTV, FP32)", "value": value,
+        "unit": "cube-iter/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": BATCH["desc"], "cubes": n,
+                   "shapes": {f"{a}x{b_}x{c}": shapes.count((a, b_, c)) for (a, b_, c) in sorted(set(shapes))},
+                   "fourier_slices_per_step": slices, "cubes_per_s": value / BATCH["iters"]},
+        "jacobi_persistent": {"launches": prof.launches[6],
+                              "ms_per_launch": prof.ms[6] / max(prof.launches[6], 1),
+                              "share_of_step": prof.ms[6] / max(ms, 1e-9),
+                              "unconverged_slices": unconv},
+        "unbatched": {"ms_per_step": single_ms, "speedup_of_batch": single_ms / (ms / args.steps)},
+        "clocks": clk,
+    }
+
+
 def oracle_baseline(wl, Y, budget_s=25.0, max_iters=None):
     """Times the FP64 oracle (as it stands) on the same cube: whole ADMM
     iterations from the initial state until the time budget is spent."""
@@ -420,7 +498,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["c4"], default="c2",
+                    help="c4 = the batch of 64 uneven cubes")
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of oracle time for the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -430,6 +509,9 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.micro:
         run_micro(args)
+        return
+    if args.workload == "c4" and args.impl == "ours":
+        print(json.dumps(run_batch(args)), flush=True)
         return
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")

@@ -29,7 +29,8 @@ import math
 
 import numpy as np
 
-__all__ = ["Stream", "Recipe", "RECIPES", "make_cube", "mpsnr", "flat", "unflat"]
+__all__ = ["Stream", "Recipe", "RECIPES", "BATCH_SHAPES", "batch_recipes", "make_cube", "mpsnr",
+           "flat", "unflat"]
 
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
@@ -112,6 +113,21 @@ RECIPES = {
     # 64x64x31 pairs for the unrolled form
     "c5": Recipe(64, 64, 31, 4, 12, (0.1, 0.1), 0.10),
 }
+
+
+BATCH_SHAPES = ((64, 64, 31), (128, 128, 64), (145, 145, 220), (200, 200, 80))
+
+
+def batch_recipes(count: int, seed: int):
+    """`count` recipes for a batch of uneven cubes: shapes drawn by seed from
+    the Indian-Pines, Pavia and smaller shapes above, each cube with its own
+    Gaussian level U[0.05, 0.2] and impulse fraction U[0, 0.3]."""
+    st = Stream(seed, "batch")
+    pick = st.integers(count, 0, len(BATCH_SHAPES))
+    sig = st.uniform(count, 0.05, 0.2)
+    imp = st.uniform(count, 0.0, 0.3)
+    return [Recipe(*BATCH_SHAPES[int(k)], 6, 24, (float(s_), float(s_)), float(p_))
+            for k, s_, p_ in zip(pick, sig, imp)]
 
 
 def make_cube(recipe: Recipe, seed: int):
