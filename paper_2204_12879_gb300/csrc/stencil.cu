@@ -7,6 +7,8 @@
 // the thread keeps the mode-3 neighbour in a register, so each cube is read
 // once; the mode-1 / mode-2 neighbours come from L1 (the same block read
 // them).  Chunks of k are sized so the grid fills all SMs several times.
+#include <initializer_list>
+
 #include "lrstv_internal.cuh"
 
 namespace lrstv {
@@ -206,11 +208,184 @@ __global__ void k_soft(const float *__restrict__ x, size_t n, float thr, float *
     y[e] = soft_thr(x[e], thr);
 }
 
+// ---------------------------------------------------------------------------
+// Vector forms (n1 % 4 == 0, 16-byte aligned cubes): one thread per four
+// consecutive voxels along mode 1, no loop, so every load of a thread is
+// independent and in flight at once.  The mode-1 neighbours outside the
+// float4 are single floats (v - 1 for the adjoint, v + 4 for the forward
+// difference); the mode-2 and mode-3 neighbours are whole float4s.
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+
+struct Vox4 {
+  size_t v, vm2, vm3, vp2, vp3;  // v and its mode-2 / mode-3 neighbours (backward, forward)
+  size_t im1, ip4;               // the single neighbours along mode 1
+};
+
+__device__ __forceinline__ bool vox4(int n1, int n2, int n3, size_t q, Vox4 &o) {
+  const int n1q = n1 >> 2;
+  const size_t P = (size_t)n1 * n2;
+  const int iq = (int)(q % n1q);
+  const size_t r = q / n1q;
+  const int j = (int)(r % n2);
+  const int k = (int)(r / n2);
+  if (k >= n3) return false;
+  const int i = 4 * iq;
+  const size_t col = (size_t)n1 * j;
+  const size_t plane = P * k;
+  o.v = plane + col + i;
+  o.vm2 = plane + (j == 0 ? (size_t)n1 * (n2 - 1) : col - n1) + i;
+  o.vp2 = plane + (j == n2 - 1 ? 0 : col + n1) + i;
+  o.vm3 = (k == 0 ? P * (n3 - 1) : plane - P) + col + i;
+  o.vp3 = (k == n3 - 1 ? 0 : plane + P) + col + i;
+  o.im1 = plane + col + (i == 0 ? n1 - 1 : i - 1);
+  o.ip4 = plane + col + (i + 4 == n1 ? 0 : i + 4);
+  return true;
+}
+
+__global__ void __launch_bounds__(256)
+    k_l_tz4(int n1, int n2, int n3, size_t N, const float *__restrict__ Y,
+            const float *__restrict__ S, const float *__restrict__ Z, const float *__restrict__ G1,
+            const float *__restrict__ G2, const float *__restrict__ F, const float *__restrict__ G3,
+            float mu, float w0, float w1, float w2, float *__restrict__ L, float *__restrict__ T) {
+  Vox4 o;
+  if (!vox4(n1, n2, n3, blockIdx.x * (size_t)blockDim.x + threadIdx.x, o)) return;
+  const float *F1 = F, *F2 = F + N, *F3 = F + 2 * N;
+  const float *H1 = G3, *H2 = G3 + N, *H3 = G3 + 2 * N;
+  const float4 y = ld4(Y + o.v), s = ld4(S + o.v), z = ld4(Z + o.v), g1 = ld4(G1 + o.v),
+               g2 = ld4(G2 + o.v);
+  const float4 f1 = ld4(F1 + o.v), h1 = ld4(H1 + o.v), f2 = ld4(F2 + o.v), h2 = ld4(H2 + o.v),
+               f3 = ld4(F3 + o.v), h3 = ld4(H3 + o.v);
+  const float4 f2m = ld4(F2 + o.vm2), h2m = ld4(H2 + o.vm2), f3m = ld4(F3 + o.vm3),
+               h3m = ld4(H3 + o.vm3);
+  const float f1m = F1[o.im1], h1m = H1[o.im1];
+  // q_n = mu F_n - Gamma3_n; D_n^T q(v) = q(v - e_n) - q(v)
+  const float q1[5] = {mu * f1m - h1m, mu * f1.x - h1.x, mu * f1.y - h1.y, mu * f1.z - h1.z,
+                       mu * f1.w - h1.w};
+  const float yy[4] = {y.x, y.y, y.z, y.w}, ss[4] = {s.x, s.y, s.z, s.w},
+              zz[4] = {z.x, z.y, z.z, z.w}, a1[4] = {g1.x, g1.y, g1.z, g1.w},
+              a2[4] = {g2.x, g2.y, g2.z, g2.w};
+  const float F2c[4] = {f2.x, f2.y, f2.z, f2.w}, H2c[4] = {h2.x, h2.y, h2.z, h2.w},
+              F2m[4] = {f2m.x, f2m.y, f2m.z, f2m.w}, H2m[4] = {h2m.x, h2m.y, h2m.z, h2m.w},
+              F3c[4] = {f3.x, f3.y, f3.z, f3.w}, H3c[4] = {h3.x, h3.y, h3.z, h3.w},
+              F3m[4] = {f3m.x, f3m.y, f3m.z, f3m.w}, H3m[4] = {h3m.x, h3m.y, h3m.z, h3m.w};
+  float lo[4], to[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float q2 = mu * F2c[e] - H2c[e], q2m = mu * F2m[e] - H2m[e];
+    const float q3 = mu * F3c[e] - H3c[e], q3m = mu * F3m[e] - H3m[e];
+    const float adj = w0 * (q1[e] - q1[e + 1]) + w1 * (q2m - q2) + w2 * (q3m - q3);
+    const float l = 0.5f * (yy[e] - ss[e] + zz[e] + (a1[e] - a2[e]) / mu);
+    lo[e] = l;
+    to[e] = mu * l + a2[e] + adj;
+  }
+  st4(L + o.v, make_float4(lo[0], lo[1], lo[2], lo[3]));
+  st4(T + o.v, make_float4(to[0], to[1], to[2], to[3]));
+}
+
+__global__ void __launch_bounds__(256)
+    k_fs_dual4(int n1, int n2, int n3, size_t N, const float *__restrict__ Y,
+               const float *__restrict__ L, const float *__restrict__ Z, float *__restrict__ S,
+               float *__restrict__ G1, float *__restrict__ G2, float *__restrict__ F,
+               const float *__restrict__ E, float *__restrict__ G3, const float *__restrict__ G4,
+               float mu, float thr_f, float thr_s, float w0, float w1, float w2,
+               unsigned *__restrict__ res2) {
+  float r1max = 0.0f, r2max = 0.0f;
+  Vox4 o;
+  if (vox4(n1, n2, n3, blockIdx.x * (size_t)blockDim.x + threadIdx.x, o)) {
+    const float4 z = ld4(Z + o.v), zp2 = ld4(Z + o.vp2), zp3 = ld4(Z + o.vp3);
+    const float zp1 = Z[o.ip4];
+    const float zc[4] = {z.x, z.y, z.z, z.w};
+    const float z1[4] = {z.y, z.z, z.w, zp1};  // z(v + e1)
+    const float z2[4] = {zp2.x, zp2.y, zp2.z, zp2.w}, z3[4] = {zp3.x, zp3.y, zp3.z, zp3.w};
+    float g[3][4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      g[0][e] = w0 * (z1[e] - zc[e]);
+      g[1][e] = w1 * (z2[e] - zc[e]);
+      g[2][e] = w2 * (z3[e] - zc[e]);
+    }
+#pragma unroll
+    for (int n = 0; n < 3; ++n) {
+      const size_t vn = o.v + (size_t)n * N;
+      const float4 h3 = ld4(G3 + vn), ev = ld4(E + vn), h4 = ld4(G4 + vn);
+      const float H[4] = {h3.x, h3.y, h3.z, h3.w}, EE[4] = {ev.x, ev.y, ev.z, ev.w},
+                  H4[4] = {h4.x, h4.y, h4.z, h4.w};
+      float fo[4], ho[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float t1 = g[n][e] + H[e] / mu;
+        const float t2 = EE[e] + H4[e] / mu;
+        const float f = soft_thr(0.5f * (t1 + t2), thr_f);
+        fo[e] = f;
+        ho[e] = H[e] + mu * (g[n][e] - f);
+      }
+      st4(F + vn, make_float4(fo[0], fo[1], fo[2], fo[3]));
+      st4(G3 + vn, make_float4(ho[0], ho[1], ho[2], ho[3]));
+    }
+    const float4 y4 = ld4(Y + o.v), l4 = ld4(L + o.v), a4 = ld4(G1 + o.v), b4 = ld4(G2 + o.v);
+    const float yy[4] = {y4.x, y4.y, y4.z, y4.w}, ll[4] = {l4.x, l4.y, l4.z, l4.w},
+                a1[4] = {a4.x, a4.y, a4.z, a4.w}, a2[4] = {b4.x, b4.y, b4.z, b4.w};
+    float so[4], g1o[4], g2o[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float sv = soft_thr(yy[e] - ll[e] + a1[e] / mu, thr_s);
+      so[e] = sv;
+      const float r1 = yy[e] - ll[e] - sv;
+      const float r2 = ll[e] - zc[e];
+      g1o[e] = a1[e] + mu * r1;
+      g2o[e] = a2[e] + mu * r2;
+      r1max = nanmax(r1max, fabsf(r1));
+      r2max = nanmax(r2max, fabsf(r2));
+    }
+    st4(S + o.v, make_float4(so[0], so[1], so[2], so[3]));
+    st4(G1 + o.v, make_float4(g1o[0], g1o[1], g1o[2], g1o[3]));
+    st4(G2 + o.v, make_float4(g2o[0], g2o[1], g2o[2], g2o[3]));
+  }
+  if (res2 == nullptr) return;
+#pragma unroll
+  for (int o2 = 16; o2 > 0; o2 >>= 1) {
+    r1max = nanmax(r1max, __shfl_xor_sync(0xffffffffu, r1max, o2));
+    r2max = nanmax(r2max, __shfl_xor_sync(0xffffffffu, r2max, o2));
+  }
+  __shared__ float s1[8], s2[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { s1[wid] = r1max; s2[wid] = r2max; }
+  __syncthreads();
+  if (wid == 0) {
+    r1max = lane < 8 ? s1[lane] : 0.0f;
+    r2max = lane < 8 ? s2[lane] : 0.0f;
+#pragma unroll
+    for (int o2 = 4; o2 > 0; o2 >>= 1) {
+      r1max = nanmax(r1max, __shfl_xor_sync(0xffffffffu, r1max, o2));
+      r2max = nanmax(r2max, __shfl_xor_sync(0xffffffffu, r2max, o2));
+    }
+    if (lane == 0) {
+      atomicMax(res2 + 0, __float_as_uint(r1max));
+      atomicMax(res2 + 1, __float_as_uint(r2max));
+    }
+  }
+}
+
+bool vec4_ok(const Dims &d, std::initializer_list<const void *> ptrs) {
+  if (d.n1 % 4 != 0) return false;
+  for (const void *p : ptrs)
+    if (((uintptr_t)p & 15u) != 0) return false;
+  return true;
+}
+
+unsigned vec4_blocks(const Dims &d) { return (unsigned)((d.N / 4 + 255) / 256); }
+
 }  // namespace
 
 cudaError_t launch_l_tz(const Dims &d, const float *Y, const float *S, const float *Z,
                         const float *G1, const float *G2, const float *F, const float *G3,
                         float mu, const float w[3], float *L, float *T, cudaStream_t st) {
+  if (vec4_ok(d, {Y, S, Z, G1, G2, F, G3, L, T})) {
+    k_l_tz4<<<vec4_blocks(d), 256, 0, st>>>(d.n1, d.n2, d.n3, d.N, Y, S, Z, G1, G2, F, G3, mu, w[0],
+                                             w[1], w[2], L, T);
+    return cudaGetLastError();
+  }
   Chunking c = chunking(d);
   k_l_tz<<<c.grid, dim3(kBX, kBY), 0, st>>>(d.n1, d.n2, d.n3, d.N, c.kchunk, Y, S, Z, G1, G2, F,
                                             G3, mu, w[0], w[1], w[2], L, T);
@@ -221,6 +396,11 @@ cudaError_t launch_fs_dual(const Dims &d, const float *Y, const float *L, const 
                            float *S, float *G1, float *G2, float *F, const float *E, float *G3,
                            const float *G4, float mu, float thr_f, float thr_s, const float w[3],
                            unsigned *res2, cudaStream_t st) {
+  if (vec4_ok(d, {Y, L, Z, S, G1, G2, F, E, G3, G4})) {
+    k_fs_dual4<<<vec4_blocks(d), 256, 0, st>>>(d.n1, d.n2, d.n3, d.N, Y, L, Z, S, G1, G2, F, E, G3,
+                                                G4, mu, thr_f, thr_s, w[0], w[1], w[2], res2);
+    return cudaGetLastError();
+  }
   Chunking c = chunking(d);
   k_fs_dual<<<c.grid, dim3(kBX, kBY), 0, st>>>(d.n1, d.n2, d.n3, d.N, c.kchunk, Y, L, Z, S, G1,
                                                G2, F, E, G3, G4, mu, thr_f, thr_s, w[0], w[1],
