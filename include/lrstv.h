@@ -44,6 +44,8 @@ typedef enum lrstv_status {
 #define LRSTV_FLAG_NO_GAMMA4 2u      /* keep Gamma4 = 0 (the paper lists only Gamma1..3 updates) */
 #define LRSTV_FLAG_GRAPH 4u          /* lrstv_plan_run replays its iterations as one CUDA graph */
 #define LRSTV_FLAG_STRICT 8u         /* stats report NOT_CONVERGED / NONFINITE as the return status */
+#define LRSTV_FLAG_SIMT_GEMM 16u     /* spatial DFT and SVT-reconstruction GEMMs on the FP32 SIMT
+                                        path instead of the tensor cores (tcgen05, 3xTF32) */
 
 /* Scalars of Algorithm 1 (Section III-C; parameter roles in Section IV-D).
  *  tau     weight of ||D_w L||_1 (gradient sparsity)
@@ -69,6 +71,7 @@ typedef struct lrstv_stats {
   float mu;                  /* penalty for the next iteration                   */
   int jacobi_unconverged;    /* Fourier slices whose SVD hit the sweep cap (last E-step) */
   int jacobi_max_sweeps;     /* largest sweep count of the last E-step           */
+  int gemm_errors;           /* tensor-core GEMM tiles whose bounded wait ran out (0) */
 } lrstv_stats;
 
 /* State blocks for lrstv_state_get / lrstv_state_set.  Blocks of 3N floats

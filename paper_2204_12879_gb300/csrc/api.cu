@@ -80,7 +80,7 @@ int check_params(const lrstv_params *p) {
     if (!isfinite(x) || x < 0.0f) return LRSTV_ERR_ARG;
   if (!(p->mu0 > 0.0f) || !(p->mu_max >= p->mu0) || p->max_iter < 0) return LRSTV_ERR_ARG;
   if (p->flags & ~(unsigned)(LRSTV_FLAG_F_THRESH_EXACT | LRSTV_FLAG_NO_GAMMA4 | LRSTV_FLAG_GRAPH |
-                             LRSTV_FLAG_STRICT))
+                             LRSTV_FLAG_STRICT | LRSTV_FLAG_SIMT_GEMM))
     return LRSTV_ERR_ARG;
   return LRSTV_OK;
 }
@@ -118,15 +118,28 @@ struct Span {
   }
 };
 
-cudaError_t gemm_z(const CGemm &g, cudaStream_t st, Prof *prof) {
+// Which GEMM implementation a call uses: the tensor cores (with an error
+// slot for bounded-wait timeouts) or the FP32 SIMT kernel.
+struct GemmSel {
+  bool tc;
+  int *err;
+};
+constexpr GemmSel kSimt = {false, nullptr};
+
+cudaError_t gemm(const CGemm &g, GemmSel gs, cudaStream_t st) {
+  return gs.tc ? launch_cgemm_tc(g, gs.err, st) : launch_cgemm(g, st);
+}
+
+cudaError_t gemm_z(const CGemm &g, cudaStream_t st, Prof *prof, GemmSel gs) {
   Span sp(prof, LRSTV_K_CGEMM_Z, st);
-  return launch_cgemm(g, st);
+  return gemm(g, gs, st);
 }
 
 // Z-solve on h half-spectrum slices: specA <- fftn(T) / (mu (1 + P_z)) ->
 // ifftn -> Z.  specA, specB: h P complex each.
 cudaError_t zsolve_core(const Dims &d, const Tables &tb, const float *T, float mu, float *Z,
-                        float2 *specA, float2 *specB, cudaStream_t st, Prof *prof = nullptr) {
+                        float2 *specA, float2 *specB, cudaStream_t st, Prof *prof = nullptr,
+                        GemmSel gs = kSimt) {
   cudaError_t e;
   {
     Span sp(prof, LRSTV_K_R2C_Z, st);
@@ -143,18 +156,18 @@ cudaError_t zsolve_core(const Dims &d, const Tables &tb, const float *T, float m
   // mode 1: specB_k = F1 specA_k
   g.A = tb.F1; g.sA = 0; g.B = specA; g.sB = (long long)d.P; g.ldb = d.n1; g.K = d.n1;
   g.C = specB; g.opB = 0; g.epi = 0;
-  if ((e = gemm_z(g, st, prof)) != cudaSuccess) return e;
+  if ((e = gemm_z(g, st, prof, gs)) != cudaSuccess) return e;
   // mode 2 + spectral division: specA_k = (specB_k F2) / (mu (1 + P_z)) / (n1 n2)
   g.A = specB; g.sA = (long long)d.P; g.B = tb.F2; g.sB = 0; g.ldb = d.n2; g.K = d.n2;
   g.C = specA; g.epi = 1; g.lam1 = tb.lam1; g.lam2 = tb.lam2; g.lam3 = tb.lam3; g.mu = mu;
   g.scale = (float)(1.0 / ((double)d.n1 * (double)d.n2));
-  if ((e = gemm_z(g, st, prof)) != cudaSuccess) return e;
+  if ((e = gemm_z(g, st, prof, gs)) != cudaSuccess) return e;
   // inverse mode 1 and mode 2
   g.epi = 0;
   g.A = tb.G1; g.sA = 0; g.B = specA; g.sB = (long long)d.P; g.ldb = d.n1; g.K = d.n1; g.C = specB;
-  if ((e = gemm_z(g, st, prof)) != cudaSuccess) return e;
+  if ((e = gemm_z(g, st, prof, gs)) != cudaSuccess) return e;
   g.A = specB; g.sA = (long long)d.P; g.B = tb.G2; g.sB = 0; g.ldb = d.n2; g.K = d.n2; g.C = specA;
-  if ((e = gemm_z(g, st, prof)) != cudaSuccess) return e;
+  if ((e = gemm_z(g, st, prof, gs)) != cudaSuccess) return e;
   Span sp(prof, LRSTV_K_C2R_Z, st);
   return launch_c2r3(d, 1, specA, 0, tb.tw3, Z, 0, nullptr, nullptr, 0.0f, 0, st);
 }
@@ -177,7 +190,7 @@ cudaError_t tsvt_jac(const Dims &d, int nb, float t, float2 *specA, float2 *V, i
 
 cudaError_t tsvt_post(const Dims &d, int nb, float *out, int mode, float *G4, const float *F,
                       float mu, int gamma4, const float2 *tw3, float2 *specA, float2 *specB,
-                      float2 *V, cudaStream_t st, Prof *prof) {
+                      float2 *V, cudaStream_t st, Prof *prof, GemmSel gs = kSimt) {
   const int ns = nb * d.h;
   CGemm g{};
   g.A = specA; g.sA = (long long)d.P; g.lda = d.nr;
@@ -187,7 +200,7 @@ cudaError_t tsvt_post(const Dims &d, int nb, float *out, int mode, float *G4, co
   cudaError_t e;
   {
     Span sp(prof, LRSTV_K_CGEMM_E, st);
-    e = launch_cgemm(g, st);
+    e = gemm(g, gs, st);
   }
   if (e != cudaSuccess) return e;
   Span sp(prof, LRSTV_K_C2R_E, st);
@@ -197,11 +210,11 @@ cudaError_t tsvt_post(const Dims &d, int nb, float *out, int mode, float *G4, co
 cudaError_t tsvt_core(const Dims &d, int nb, const float *x, const float *y, float ycoef, float t,
                       float *out, int mode, float *G4, const float *F, float mu, int gamma4,
                       const float2 *tw3, float2 *specA, float2 *specB, float2 *V, int *sweeps,
-                      cudaStream_t st, Prof *prof = nullptr) {
+                      cudaStream_t st, Prof *prof = nullptr, GemmSel gs = kSimt) {
   cudaError_t e = tsvt_pre(d, nb, x, y, ycoef, tw3, specA, st, prof);
   if (e != cudaSuccess) return e;
   if ((e = tsvt_jac(d, nb, t, specA, V, sweeps, st, prof)) != cudaSuccess) return e;
-  return tsvt_post(d, nb, out, mode, G4, F, mu, gamma4, tw3, specA, specB, V, st, prof);
+  return tsvt_post(d, nb, out, mode, G4, F, mu, gamma4, tw3, specA, specB, V, st, prof, gs);
 }
 
 }  // namespace
@@ -232,6 +245,7 @@ struct lrstv_plan {
   Tables tb;
   unsigned *res;  // kResRing x 2 residual maxima (float bits)
   int *sweeps;    // 3h
+  int *gemm_err;  // tensor-core GEMM wait timeouts
   // graph cache for lrstv_plan_run
   cudaGraphExec_t gexec;
   const void *gY;
@@ -247,6 +261,11 @@ struct lrstv_plan {
   } while (0)
 
 namespace {
+
+GemmSel plan_gemm(const lrstv_plan *pl) {
+  if (pl->prm.flags & LRSTV_FLAG_SIMT_GEMM) return kSimt;
+  return GemmSel{true, pl->gemm_err};
+}
 
 size_t plan_layout(lrstv_plan *pl, void *base) {
   const Dims &d = pl->d;
@@ -268,6 +287,7 @@ size_t plan_layout(lrstv_plan *pl, void *base) {
   carve_tables(c, d, pl->tb);
   pl->res = c.take<unsigned>(2 * (size_t)kResRing);
   pl->sweeps = c.take<int>(3 * (size_t)d.h);
+  pl->gemm_err = c.take<int>(1);
   pl->prof.d_work = c.take<unsigned long long>(2);
   return c.off;
 }
@@ -491,7 +511,7 @@ int lrstv_step_l_tz(lrstv_plan *pl, void *stream) {
 int lrstv_step_z(lrstv_plan *pl, void *stream) {
   if (!pl) return LRSTV_ERR_ARG;
   CK(zsolve_core(pl->d, pl->tb, pl->T, (float)pl->mu, pl->Z, pl->specA, pl->specB,
-                 (cudaStream_t)stream, &pl->prof));
+                 (cudaStream_t)stream, &pl->prof, plan_gemm(pl)));
   return LRSTV_OK;
 }
 
@@ -516,7 +536,7 @@ int lrstv_step_e(lrstv_plan *pl, void *stream) {
   const int gamma4 = (pl->prm.flags & LRSTV_FLAG_NO_GAMMA4) ? 0 : 1;
   CK(tsvt_core(pl->d, 3, pl->F, pl->G4, (float)(1.0 / mu), (float)(pl->prm.alpha / mu), pl->E, 1,
                pl->G4, pl->F, (float)mu, gamma4, pl->tb.tw3, pl->specA, pl->specB, pl->V,
-               pl->sweeps, (cudaStream_t)stream, &pl->prof));
+               pl->sweeps, (cudaStream_t)stream, &pl->prof, plan_gemm(pl)));
   return LRSTV_OK;
 }
 
@@ -553,12 +573,21 @@ int lrstv_get_stats(lrstv_plan *pl, lrstv_stats *stats, void *stream) {
     delete[] sw;
     return LRSTV_ERR_CUDA;
   }
+  {
+    int ge = 0;
+    if (cudaMemcpy(&ge, pl->gemm_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      delete[] sw;
+      return LRSTV_ERR_CUDA;
+    }
+    stats->gemm_errors = ge;
+  }
   for (int s = 0; s < ns; ++s) {
     if (sw[s] < 0) stats->jacobi_unconverged += 1;
     const int a = sw[s] < 0 ? -sw[s] : sw[s];
     if (a > stats->jacobi_max_sweeps) stats->jacobi_max_sweeps = a;
   }
   delete[] sw;
+  if (stats->gemm_errors) return LRSTV_ERR_CUDA;
   if (pl->prm.flags & LRSTV_FLAG_STRICT) {
     if (!isfinite(stats->res_inf[0]) || !isfinite(stats->res_inf[1])) return LRSTV_ERR_NONFINITE;
     if (stats->jacobi_unconverged) return LRSTV_ERR_NOT_CONVERGED;
@@ -743,7 +772,7 @@ int batch_e_step(lrstv_batch *b, cudaStream_t st) {
     lrstv_plan *pl = b->plans[i];
     const int gamma4 = (pl->prm.flags & LRSTV_FLAG_NO_GAMMA4) ? 0 : 1;
     CK(tsvt_post(pl->d, 3, pl->E, 1, pl->G4, pl->F, (float)pl->mu, gamma4, pl->tb.tw3, pl->specA,
-                 pl->specB, pl->V, st, &pl->prof));
+                 pl->specB, pl->V, st, &pl->prof, plan_gemm(pl)));
   }
   return LRSTV_OK;
 }

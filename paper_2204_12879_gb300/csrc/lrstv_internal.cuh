@@ -69,6 +69,12 @@ struct CGemm {
 };
 cudaError_t launch_cgemm(const CGemm &g, cudaStream_t st);
 
+// ---------------------------------------------------------------- tcgemm.cu
+// The same GEMM on the tensor cores (tcgen05, 3xTF32 split precision); *err
+// (may be null) is set to 1 if a CTA's wait for its MMAs runs out.
+cudaError_t launch_cgemm_tc(const CGemm &g, int *err, cudaStream_t st);
+size_t cgemm_tc_smem();
+
 // -------------------------------------------------------------------- svt.cu
 // One-sided Jacobi on `nslices` working matrices W_s (nr x nc, column-major,
 // slice stride P), accumulating V_s (nc x nc).  On exit W_s = A_s V_s and the

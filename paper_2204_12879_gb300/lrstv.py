@@ -21,13 +21,14 @@ __all__ = [
     "lrstv_diff", "lrstv_diff_adjoint", "lrstv_soft_threshold", "lrstv_zsolve", "lrstv_tsvt",
     "lrstv_tsvt_noalloc",
     "lrstv_denoise", "BLOCK", "FLAG_F_THRESH_EXACT", "FLAG_NO_GAMMA4", "FLAG_GRAPH",
-    "FLAG_STRICT", "EXPORTED",
+    "FLAG_STRICT", "FLAG_SIMT_GEMM", "EXPORTED",
 ]
 
 FLAG_F_THRESH_EXACT = 1
 FLAG_NO_GAMMA4 = 2
 FLAG_GRAPH = 4
 FLAG_STRICT = 8
+FLAG_SIMT_GEMM = 16
 
 BLOCK = {"Y": 0, "L": 1, "Z": 2, "S": 3, "G1": 4, "G2": 5, "F": 6, "E": 7, "G3": 8, "G4": 9,
          "TZ": 10}
@@ -63,12 +64,13 @@ class Params(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("res_inf", ctypes.c_float * 2), ("mu", ctypes.c_float),
-                ("jacobi_unconverged", ctypes.c_int), ("jacobi_max_sweeps", ctypes.c_int)]
+                ("jacobi_unconverged", ctypes.c_int), ("jacobi_max_sweeps", ctypes.c_int),
+                ("gemm_errors", ctypes.c_int)]
 
     def as_dict(self):
         return {"iters": self.iters, "res_inf": [self.res_inf[0], self.res_inf[1]], "mu": self.mu,
                 "jacobi_unconverged": self.jacobi_unconverged,
-                "jacobi_max_sweeps": self.jacobi_max_sweeps}
+                "jacobi_max_sweeps": self.jacobi_max_sweeps, "gemm_errors": self.gemm_errors}
 
 
 class Profile(ctypes.Structure):

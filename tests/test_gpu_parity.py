@@ -308,3 +308,42 @@ def test_denoise_one_shot(L, orc):
     ost.iterate(4)
     assert maxabs(host(X, shape), ost.X) <= 1e-4
     assert st.iters == 4
+
+
+def test_tensor_core_gemm_matches_simt(L, orc, mid_state):
+    """The spatial DFT and SVT-reconstruction GEMMs on the tensor cores
+    (tcgen05, 3xTF32) against the FP32 SIMT kernel, on the same state."""
+    shape, st = mid_state
+    outs = {}
+    for flags in (0, L.FLAG_SIMT_GEMM):
+        with _plan(L, shape, flags=flags) as pl:
+            load_oracle_state(pl, st)
+            pl.step_l_tz()
+            pl.step_z()
+            pl.step_fs_dual()
+            pl.step_e()
+            s = pl.stats()
+            assert s.gemm_errors == 0
+            outs[flags] = (host(pl.get("Z"), shape), host3(pl.get("E"), shape))
+    z_tc, e_tc = outs[0]
+    z_si, e_si = outs[L.FLAG_SIMT_GEMM]
+    # 3xTF32 carries ~2^-21 per product; FP32 sums on both sides
+    assert maxabs(z_tc, z_si) <= 2e-6 * max(1.0, np.abs(z_si).max())
+    assert maxabs(e_tc, e_si) <= 2e-6 * max(1.0, np.abs(e_si).max())
+
+
+@pytest.mark.parametrize("shape", [(200, 200, 4), (130, 70, 5), (37, 29, 11)])
+def test_tensor_core_zsolve_shapes(L, orc, shape):
+    """Tile edges of the tensor-core GEMM (128-row and 64-column tiles, ragged
+    K) through a plan's Z-step, against the oracle's solve of the same T_z."""
+    n1, n2, n3 = shape
+    rng = np.random.default_rng(21)
+    with _plan(L, shape) as pl:
+        pl.init(dev(np.zeros(shape)))
+        T = f32(rng.standard_normal(shape))
+        pl.set("TZ", dev(T))
+        pl.step_z()
+        mu, _ = pl.mu
+        ref = orc.zsolve(T, mu)
+        assert maxabs(host(pl.get("Z"), shape), ref) <= 1e-5 * np.abs(ref).max()
+        assert pl.stats().gemm_errors == 0
