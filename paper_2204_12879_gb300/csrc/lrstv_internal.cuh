@@ -94,7 +94,7 @@ struct SliceTask {
   int nr, nc;
 };
 // Largest slice height the persistent batch kernel takes.
-constexpr int kBatchMaxNr = 224;
+constexpr int kBatchMaxNr = 224;  // keeps the persistent kernel free of spills
 size_t jacobi_batch_smem(int max_nr);
 // Persistent work-list Jacobi over `ntasks` slices; *counter must be 0.
 cudaError_t launch_jacobi_batch(const SliceTask *tasks, int ntasks, int *counter, double mu,

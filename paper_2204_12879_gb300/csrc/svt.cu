@@ -11,11 +11,12 @@
 // sweep loop is capped and a slice that reaches the cap reports it.
 //
 // Three kernels share the rotation formula and differ in how columns move:
-//  - k_jacobi_pk (nr <= 224, the common case): 32-column panels staged in
+//  - k_jacobi_pk (nr <= 256, the common case): 32-column panels staged in
 //    shared memory, a panel's W and V columns held in registers while later
 //    panels stream past, one column pair per half-warp, paired FP32
 //    instructions (__ffma2_rn) on a split row-pair layout;
-//  - k_jacobi_panel (nr <= 256): the same panel order with full warps;
+//  - k_jacobi_panel: the same panel order with full warps (kept for reference
+//    shapes; no longer dispatched);
 //  - k_jacobi (any nr up to 512): round-robin over all columns in global
 //    memory (L2-resident), one pair per warp.
 #include <float.h>
@@ -836,8 +837,11 @@ cudaError_t launch_panel(int nslices, int nr, int nc, size_t ws, size_t vs, floa
 
 size_t jacobi_batch_smem(int max_nr) {
   const int KP = (max_nr + 31) / 32;
-  const int LD2 = KP <= 1 ? PkShape<1>::LD2 : KP <= 2 ? PkShape<2>::LD2 : KP <= 4 ? PkShape<4>::LD2
-                                                                               : PkShape<7>::LD2;
+  const int LD2 = KP <= 1 ? PkShape<1>::LD2
+                  : KP <= 2 ? PkShape<2>::LD2
+                  : KP <= 4 ? PkShape<4>::LD2
+                  : KP <= 7 ? PkShape<7>::LD2
+                            : PkShape<8>::LD2;
   return sizeof(float4) * 3 * (size_t)kPW * LD2;
 }
 
@@ -868,12 +872,13 @@ cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, floa
   const float tol = 8.0f * sqrtf((float)nr) * eps;
   const float negl = ((float)nr * eps) * ((float)nr * eps);
   const size_t ws = d.P, vs = (size_t)nc * nc;
-  if (nr <= 224 && nc >= 2) {
+  if (nr <= 256 && nc >= 2) {
     const int KP = (nr + 31) / 32;  // row pairs per lane of a half-warp
     if (KP <= 1) return launch_pk<1>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
     if (KP <= 2) return launch_pk<2>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
     if (KP <= 4) return launch_pk<4>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
-    return launch_pk<7>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
+    if (KP <= 7) return launch_pk<7>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
+    return launch_pk<8>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
   }
   if (R <= 8 && nc >= 2) {
     if (R <= 1) return launch_panel<1>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);

@@ -13,7 +13,7 @@ from tests.gpu_util import dev, f32, host, maxabs
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(24, 20, 9), (20, 24, 8), (32, 32, 16), (16, 16, 5), (70, 40, 6), (230, 16, 3)]
+SHAPES = [(24, 20, 9), (20, 24, 8), (32, 32, 16), (16, 16, 5), (70, 40, 6), (230, 16, 3), (260, 12, 3)]
 
 
 @pytest.fixture(scope="module")
