@@ -685,8 +685,13 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
         pk_stage_in(sW, LD2, W + (size_t)nr * cb, nr, wb);
         pk_stage_in(sVb, LD2, V + (size_t)nc * cb, nc, wb);
         __syncthreads();
+        // 16 double rounds: warp w owns streamed columns 2c, 2c+1 (c = (w + R) mod 16); its
+        // half-warps rotate them in swapped order, so only the warp synchronises between the
+        // two sub-steps and the block once per double round
         for (int r = 0; r < kPW; ++r) {
-          const int j = (unit + r) & (kPW - 1);
+          const int sub = r & 1;
+          const int cpi = (warp + (r >> 1)) & (kPW / 2 - 1);
+          const int j = 2 * cpi + ((unit & 1) ^ sub);
           const bool real = mine && j < wb;
 #pragma unroll
           for (int k = 0; k < KP; ++k) bW[k] = sW[LD2 * j + ul + 16 * k];
@@ -720,7 +725,10 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
               rotated = 1;
             }
           }
-          __syncthreads();
+          if (sub == 0)
+            __syncwarp();
+          else
+            __syncthreads();
         }
         pk_stage_out(W + (size_t)nr * cb, sW, LD2, nr, wb);
         pk_stage_out(V + (size_t)nc * cb, sVb, LD2, nc, wb);
