@@ -277,6 +277,21 @@ class State:
         lib().orc_residual(_p(self.buf), *self.shape, _p(r))
         return r
 
+    def step_theta(self, tau, alpha, lam, mu):
+        """One iteration of Algorithm 1 with explicit scalars (tau, alpha,
+        lambda, mu) for this iteration and no penalty update: the iteration
+        of an unrolled solver whose per-iteration scalars are free."""
+        self.p[0], self.p[1], self.p[2] = float(tau), float(alpha), float(lam)
+        self.mu = float(mu)
+        self.step_l()
+        self.step_z()
+        self.step_f()
+        sw = self.step_e()
+        self.step_s()
+        self.step_dual()
+        self.iters += 1
+        return sw
+
     def iterate(self, iters):
         """Runs `iters` iterations; returns (residuals (iters, 2), sweeps)."""
         res = np.zeros(2 * max(iters, 1))
