@@ -428,6 +428,89 @@ def run_batch(args):
     }
 
 
+UNROLL = {"batch": 8, "iters": 10, "pool": 64, "seed": 5,
+          "desc": "unrolled plain LRSTV, 10 iterations with 40 learnable scalars (tau, alpha, lambda, mu per iteration), batch 8 of 64x64x31 synthetic pairs (4 endmembers, 12 Voronoi cells, Gaussian 0.1 + 10% impulse), MSE to the clean cube, Adam on the log-scalars"}
+
+
+def run_unroll(args):
+    """The differentiable unrolled form: one step = forward (10 iterations,
+    iterates and SVD factors kept) + backward (hand-written adjoint) + an Adam
+    update of the 40 log-scalars, on the next batch of 8 pairs from a pool
+    resident in HBM.  value = training steps per second."""
+    import numpy as np
+    import torch
+
+    from paper_2204_12879_gb300 import builder
+    from paper_2204_12879_gb300.unrolled import UnrolledLRSTV
+    from synthetic import RECIPES, make_cube
+
+    builder.build()
+    rec = RECIPES["c5"]
+    n1, n2, n3 = rec.shape
+    B, K = UNROLL["batch"], UNROLL["iters"]
+    pairs = [make_cube(rec, 70000 + i) for i in range(UNROLL["pool"])]
+    to_dev = lambda cubes: torch.from_numpy(np.ascontiguousarray(
+        np.stack([c.astype(np.float32).transpose(2, 1, 0) for c in cubes]))).cuda()
+    clean = to_dev([c for c, _ in pairs])
+    noisy = to_dev([y for _, y in pairs])
+    nb = UNROLL["pool"] // B
+    model = UnrolledLRSTV(n1, n2, n3, batch=B, iters=K)
+    opt = torch.optim.Adam(model.parameters(), lr=0.02)
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def step(i, marks=None):
+        sl = slice((i % nb) * B, (i % nb + 1) * B)
+        opt.zero_grad(set_to_none=True)
+        X = model(noisy[sl])
+        loss = ((X - clean[sl]) ** 2).mean()
+        if marks is not None:
+            marks[0].record(stream)
+        loss.backward()
+        opt.step()
+        return loss
+
+    losses = []
+    for i in range(args.warmup):
+        losses.append(float(step(i)))
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    t0, t1 = ev(), ev()
+    mids = [ev() for _ in range(args.steps)]
+    starts = [ev() for _ in range(args.steps)]
+    ends = [ev() for _ in range(args.steps)]
+    t0.record(stream)
+    last = None
+    for i in range(args.steps):
+        starts[i].record(stream)
+        last = step(args.warmup + i, marks=[mids[i]])
+        ends[i].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    clk = clocks.stop()
+    fwd = sum(starts[i].elapsed_time(mids[i]) for i in range(args.steps)) / args.steps
+    bwd = sum(mids[i].elapsed_time(ends[i]) for i in range(args.steps)) / args.steps
+    unconv, gerr = model.handle.stats()
+    value = args.steps / (ms / 1e3)
+    return {
+        "metric": "unrolled-LRSTV training steps/s (forward + backward + update, FP32)",
+        "value": value, "unit": "step/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": UNROLL["desc"], "shape": [n1, n2, n3], "batch": B,
+                   "unrolled_iters": K, "learnable_scalars": 4 * K,
+                   "pool": f"{UNROLL['pool']} pairs resident in HBM, cycled",
+                   "cubes_per_s": value * B, "cube_iterations_per_s": value * B * K},
+        "phases": {"forward_ms": fwd, "backward_and_update_ms": bwd,
+                   "arena_bytes": model.handle.nbytes},
+        "loss": {"first_warmup": losses[0] if losses else None, "last": float(last)},
+        "unconverged_slices": unconv, "gemm_errors": gerr,
+        "clocks": clk,
+    }
+
+
 def oracle_baseline(wl, Y, budget_s=25.0, max_iters=None):
     """Times the FP64 oracle (as it stands) on the same cube: whole ADMM
     iterations from the initial state until the time budget is spent."""
@@ -498,8 +581,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["c4"], default="c2",
-                    help="c4 = the batch of 64 uneven cubes")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["c4", "c5"], default="c2",
+                    help="c4 = the batch of 64 uneven cubes, c5 = the unrolled, "
+                         "differentiable form (training steps)")
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of oracle time for the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -512,6 +596,9 @@ def main(argv=None):
         return
     if args.workload == "c4" and args.impl == "ours":
         print(json.dumps(run_batch(args)), flush=True)
+        return
+    if args.workload == "c5" and args.impl == "ours":
+        print(json.dumps(run_unroll(args)), flush=True)
         return
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")

@@ -35,7 +35,9 @@ typedef enum lrstv_status {
   LRSTV_ERR_CUDA = 3,           /* a CUDA runtime call or launch failed        */
   LRSTV_ERR_ALLOC = 4,          /* device memory could not be allocated        */
   LRSTV_ERR_NOT_CONVERGED = 5,  /* a Jacobi SVD hit its sweep cap              */
-  LRSTV_ERR_NONFINITE = 6       /* a residual is NaN or Inf                    */
+  LRSTV_ERR_NONFINITE = 6,      /* a residual is NaN or Inf                    */
+  LRSTV_ERR_STATE = 7           /* call out of order (a backward pass with no
+                                   forward pass before it)                     */
 } lrstv_status;
 
 /* Flags (lrstv_params.flags). */
@@ -278,6 +280,47 @@ int lrstv_tsvt(const float *A, int n1, int n2, int n3, float t, float *out, void
 #define LRSTV_NOALLOC_SCRATCH_BYTES (16u << 20)
 int lrstv_tsvt_noalloc(const float *A, int n1, int n2, int n3, float t, float *out,
                        int *sweeps_host, void *stream);
+
+/* ------------------------------------ unrolled, differentiable iteration */
+/* K iterations of Algorithm 1 (Section III-C, printed F threshold tau/mu,
+ * Gamma4 updated) on a batch of B cubes of one shape, with free scalars per
+ * iteration, and the exact gradient of a loss on the final L with respect to
+ * those scalars and to Y.  The paper runs the iteration with fixed tau,
+ * alpha, lambda and a geometric mu; here theta_k = (tau_k, alpha_k,
+ * lambda_k, mu_k) for k = 0..K-1 are inputs (an unrolled solver whose scalars
+ * are learned), and iteration k runs with mu = mu_k and no penalty update.
+ * The start is the plan's: L = Z = Y, everything else zero.
+ *
+ * lrstv_unroll_create   allocates one device arena holding every iterate
+ *   (K + 1 states of 17 B N floats), the SVD factors of every Fourier slice
+ *   of every E-update (K x 3 B (n3/2+1) slices) and the scratch of both
+ *   passes; lrstv_unroll_bytes reports its size.  w: weights of D_w (NULL =
+ *   1, 1, 1).  flags: 0 or LRSTV_FLAG_SIMT_GEMM.  iters in 1..4096.
+ * lrstv_unroll_forward  Y: device, B cubes back to back (B N floats).
+ *   theta: HOST array of K x 4 doubles (tau, alpha, lambda, mu per
+ *   iteration; all finite and >= 0, mu > 0), copied during the call.
+ *   X: device, B N floats (may be NULL): L after the K iterations.
+ * lrstv_unroll_backward dX: device, B N floats: dLoss/dX.  dtheta: DEVICE
+ *   array of K x 4 doubles, overwritten with dLoss/dtheta (same order as
+ *   theta).  dY: device, B N floats (may be NULL): dLoss/dY.  Uses the last
+ *   forward's theta and iterates; LRSTV_ERR_STATE before any forward.
+ *   The soft-threshold masks are taken where the forward took them, and a
+ *   voxel exactly on a threshold counts as cut.
+ * lrstv_unroll_stats    (synchronises `stream`) unconverged: Fourier slices
+ *   of the last forward whose Jacobi SVD hit its sweep cap; gemm_errors: 1 if
+ *   a tensor-core GEMM's bounded wait ran out (either pointer may be NULL).
+ * A forward or backward pass of one handle must not overlap another call of
+ * that handle on the GPU. */
+typedef struct lrstv_unroll lrstv_unroll;
+int lrstv_unroll_create(int n1, int n2, int n3, int batch, int iters, const float w[3],
+                        unsigned flags, lrstv_unroll **unroll);
+int lrstv_unroll_destroy(lrstv_unroll *unroll);
+int lrstv_unroll_bytes(const lrstv_unroll *unroll, size_t *bytes);
+int lrstv_unroll_forward(lrstv_unroll *unroll, const float *Y, const double *theta, float *X,
+                         void *stream);
+int lrstv_unroll_backward(lrstv_unroll *unroll, const float *dX, double *dtheta, float *dY,
+                          void *stream);
+int lrstv_unroll_stats(lrstv_unroll *unroll, int *unconverged, int *gemm_errors, void *stream);
 
 #ifdef __cplusplus
 }

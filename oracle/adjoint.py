@@ -30,8 +30,8 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["forward_iteration", "backward_iteration", "svt", "svt_backward", "tsvt",
-           "tsvt_backward", "diff", "diff_adjoint", "zsolve", "soft", "unrolled_loss_grad",
-           "initial_state"]
+           "tsvt_backward", "diff", "diff_adjoint", "zsolve", "soft", "unrolled_forward",
+           "unrolled_backward", "unrolled_loss_grad", "initial_state"]
 
 
 # ------------------------------------------------------------ operators ---
@@ -246,22 +246,33 @@ def backward_iteration(st, inter, theta, adj, w=(1.0, 1.0, 1.0)):
     return out, np.array([dtau, dalpha, dlam, dmu])
 
 
-def unrolled_loss_grad(Y, clean, thetas, w=(1.0, 1.0, 1.0)):
-    """Loss = mean((L_K - clean)^2) after K = len(thetas) iterations from the
-    initial state; returns (loss, dLoss/dthetas (K x 4), dLoss/dY)."""
+def unrolled_forward(Y, thetas, w=(1.0, 1.0, 1.0)):
+    """K = len(thetas) iterations from the initial state; returns (L_K, tape)."""
     st = initial_state(Y)
     tape = []
     for th in thetas:
         new, inter = forward_iteration(st, th, w)
         tape.append((st, inter, th))
         st = new
-    diffL = st["L"] - clean
-    loss = float(np.mean(diffL ** 2))
-    adj = {"L": 2.0 * diffL / diffL.size}
-    grads = np.zeros((len(thetas), 4))
-    for k in range(len(thetas) - 1, -1, -1):
+    return st["L"], tape
+
+
+def unrolled_backward(tape, dX, w=(1.0, 1.0, 1.0)):
+    """Given dLoss/dL_K, returns (dLoss/dthetas (K x 4), dLoss/dY)."""
+    adj = {"L": np.asarray(dX, np.float64)}
+    grads = np.zeros((len(tape), 4))
+    for k in range(len(tape) - 1, -1, -1):
         s0, inter, th = tape[k]
         adj, grads[k] = backward_iteration(s0, inter, th, adj, w)
     # the initial state is L = Z = Y, so Y also feeds through Z and L
-    dY = adj["Y"] + adj["Z"] + adj["L"]
+    return grads, adj["Y"] + adj["Z"] + adj["L"]
+
+
+def unrolled_loss_grad(Y, clean, thetas, w=(1.0, 1.0, 1.0)):
+    """Loss = mean((L_K - clean)^2) after K = len(thetas) iterations from the
+    initial state; returns (loss, dLoss/dthetas (K x 4), dLoss/dY)."""
+    X, tape = unrolled_forward(Y, thetas, w)
+    diffL = X - clean
+    loss = float(np.mean(diffL ** 2))
+    grads, dY = unrolled_backward(tape, 2.0 * diffL / diffL.size, w)
     return loss, grads, dY

@@ -26,33 +26,6 @@ Dims make_dims(int n1, int n2, int n3) {
   return d;
 }
 
-namespace {
-
-constexpr size_t kAlign = 256;
-constexpr int kResRing = 4096;     // per-iteration residual history
-constexpr int kMaxSweeps = 30;     // Jacobi sweep cap per slice and E-step
-
-size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
-
-// Hands out 256-byte-aligned pieces of one allocation (or counts the bytes
-// when base is null).
-struct Carver {
-  char *base;
-  size_t off = 0;
-  explicit Carver(void *b) : base((char *)b) {}
-  template <class T>
-  T *take(size_t count) {
-    T *p = base ? (T *)(base + off) : nullptr;
-    off = align_up(off + sizeof(T) * count);
-    return p;
-  }
-};
-
-struct Tables {
-  float2 *tw3, *F1, *G1, *F2, *G2;
-  float *lam1, *lam2, *lam3;
-};
-
 void carve_tables(Carver &c, const Dims &d, Tables &t) {
   t.tw3 = c.take<float2>(d.n3);
   t.F1 = c.take<float2>((size_t)d.n1 * d.n1);
@@ -72,6 +45,10 @@ int check_shape(int n1, int n2, int n3) {
   return LRSTV_OK;
 }
 
+namespace {
+
+constexpr int kResRing = 4096;     // per-iteration residual history
+
 int check_params(const lrstv_params *p) {
   if (!p) return LRSTV_ERR_ARG;
   const float v[] = {p->tau, p->alpha, p->lambda, p->w[0], p->w[1], p->w[2], p->mu0, p->rho,
@@ -84,6 +61,8 @@ int check_params(const lrstv_params *p) {
     return LRSTV_ERR_ARG;
   return LRSTV_OK;
 }
+
+}  // namespace
 
 // Per-launch CUDA-event bracketing for lrstv_profile_* (off unless enabled).
 struct Prof {
@@ -118,38 +97,35 @@ struct Span {
   }
 };
 
-// Which GEMM implementation a call uses: the tensor cores (with an error
-// slot for bounded-wait timeouts) or the FP32 SIMT kernel.
-struct GemmSel {
-  bool tc;
-  int *err;
-};
-constexpr GemmSel kSimt = {false, nullptr};
-
-cudaError_t gemm(const CGemm &g, GemmSel gs, cudaStream_t st) {
-  return gs.tc ? launch_cgemm_tc(g, gs.err, st) : launch_cgemm(g, st);
-}
+namespace {
 
 cudaError_t gemm_z(const CGemm &g, cudaStream_t st, Prof *prof, GemmSel gs) {
   Span sp(prof, LRSTV_K_CGEMM_Z, st);
   return gemm(g, gs, st);
 }
 
-// Z-solve on h half-spectrum slices: specA <- fftn(T) / (mu (1 + P_z)) ->
-// ifftn -> Z.  specA, specB: h P complex each.
-cudaError_t zsolve_core(const Dims &d, const Tables &tb, const float *T, float mu, float *Z,
-                        float2 *specA, float2 *specB, cudaStream_t st, Prof *prof = nullptr,
-                        GemmSel gs = kSimt) {
+}  // namespace
+
+cudaError_t gemm(const CGemm &g, GemmSel gs, cudaStream_t st) {
+  return gs.tc ? launch_cgemm_tc(g, gs.err, st) : launch_cgemm(g, st);
+}
+
+// Z-solve of nb cubes on their h half-spectrum slices each: specA <- fftn(T)
+// / (mu (1 + P_z)) -> ifftn -> Z.  specA, specB: nb h P complex each.
+cudaError_t zsolve_core(const Dims &d, int nb, const Tables &tb, const float *T, float mu,
+                        float *Z, float2 *specA, float2 *specB, cudaStream_t st, Prof *prof,
+                        GemmSel gs) {
   cudaError_t e;
   {
     Span sp(prof, LRSTV_K_R2C_Z, st);
-    e = launch_r2c3(d, 1, T, nullptr, 0.0f, specA, 0, tb.tw3, st);
+    e = launch_r2c3(d, nb, T, nullptr, 0.0f, specA, 0, tb.tw3, st);
   }
   if (e != cudaSuccess) return e;
   CGemm g{};
   g.M = d.n1;
   g.N = d.n2;
-  g.batch = d.h;
+  g.batch = nb * d.h;
+  g.lam3_period = d.h;
   g.lda = d.n1;
   g.ldc = d.n1;
   g.sC = (long long)d.P;
@@ -169,8 +145,10 @@ cudaError_t zsolve_core(const Dims &d, const Tables &tb, const float *T, float m
   g.A = specB; g.sA = (long long)d.P; g.B = tb.G2; g.sB = 0; g.ldb = d.n2; g.K = d.n2; g.C = specA;
   if ((e = gemm_z(g, st, prof, gs)) != cudaSuccess) return e;
   Span sp(prof, LRSTV_K_C2R_Z, st);
-  return launch_c2r3(d, 1, specA, 0, tb.tw3, Z, 0, nullptr, nullptr, 0.0f, 0, st);
+  return launch_c2r3(d, nb, specA, 0, tb.tw3, Z, 0, nullptr, nullptr, 0.0f, 0, st);
 }
+
+namespace {
 
 // t-SVT of nb cubes x_b - ycoef y_b with threshold t, in three phases:
 // DFT along mode 3 into the working orientation (tsvt_pre), Jacobi + g-scaling
@@ -370,6 +348,7 @@ const char *lrstv_status_string(int s) {
     case LRSTV_ERR_ALLOC: return "device allocation failed";
     case LRSTV_ERR_NOT_CONVERGED: return "Jacobi SVD reached its sweep cap";
     case LRSTV_ERR_NONFINITE: return "non-finite residual";
+    case LRSTV_ERR_STATE: return "call out of order";
     default: return "unknown status";
   }
 }
@@ -510,7 +489,7 @@ int lrstv_step_l_tz(lrstv_plan *pl, void *stream) {
 
 int lrstv_step_z(lrstv_plan *pl, void *stream) {
   if (!pl) return LRSTV_ERR_ARG;
-  CK(zsolve_core(pl->d, pl->tb, pl->T, (float)pl->mu, pl->Z, pl->specA, pl->specB,
+  CK(zsolve_core(pl->d, 1, pl->tb, pl->T, (float)pl->mu, pl->Z, pl->specA, pl->specB,
                  (cudaStream_t)stream, &pl->prof, plan_gemm(pl)));
   return LRSTV_OK;
 }
@@ -1066,7 +1045,7 @@ int lrstv_zsolve(const float *T, int n1, int n2, int n3, const float w[3], float
   zsolve_ws(d, &tb, &A, &B, workspace);
   cudaStream_t st = (cudaStream_t)stream;
   CK(launch_tables(d, w, tb.tw3, tb.F1, tb.G1, tb.F2, tb.G2, tb.lam1, tb.lam2, tb.lam3, st));
-  CK(zsolve_core(d, tb, T, mu, Z, A, B, st));
+  CK(zsolve_core(d, 1, tb, T, mu, Z, A, B, st, nullptr, kSimt));
   return LRSTV_OK;
 }
 

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kPix)
 // ------------------------------------------------------------- complex GEMM
 constexpr int BM = 64, BN = 64, BK = 16, GT = 256;
 
-template <int OPB, int EPI>
+template <int OPA, int OPB, int EPI>
 __global__ void __launch_bounds__(GT) k_cgemm(CGemm g) {
   __shared__ float2 As[BK][BM];
   __shared__ float2 Bs[BK][BN];
@@ -177,9 +177,18 @@ __global__ void __launch_bounds__(GT) k_cgemm(CGemm g) {
 #pragma unroll
     for (int r = 0; r < (BM * BK) / GT; ++r) {
       const int e = tid + GT * r;
-      const int m = e % BM, k = e / BM;
-      const int gm = m0 + m, gk = k0 + k;
-      As[k][m] = (gm < g.M && gk < g.K) ? A[gm + (size_t)g.lda * gk] : make_float2(0.f, 0.f);
+      if (OPA == 0) {
+        const int m = e % BM, k = e / BM;
+        const int gm = m0 + m, gk = k0 + k;
+        As[k][m] = (gm < g.M && gk < g.K) ? A[gm + (size_t)g.lda * gk] : make_float2(0.f, 0.f);
+      } else {
+        // op(A)(m, k) = conj(A(k, m)), A stored K x M column-major
+        const int k = e % BK, m = e / BK;
+        const int gm = m0 + m, gk = k0 + k;
+        float2 v = (gm < g.M && gk < g.K) ? A[gk + (size_t)g.lda * gm] : make_float2(0.f, 0.f);
+        v.y = -v.y;
+        As[k][m] = v;
+      }
     }
 #pragma unroll
     for (int r = 0; r < (BK * BN) / GT; ++r) {
@@ -227,10 +236,16 @@ __global__ void __launch_bounds__(GT) k_cgemm(CGemm g) {
       if (n >= g.N) continue;
       float2 v = acc[r][s];
       if (EPI == 1) {
-        const float den = g.mu * (1.0f + g.lam1[m] + g.lam2[n] + g.lam3[b]);
+        const int lb = g.lam3_period > 0 ? b % g.lam3_period : b;
+        const float den = g.mu * (1.0f + g.lam1[m] + g.lam2[n] + g.lam3[lb]);
         const float q = g.scale / den;
         v.x *= q;
         v.y *= q;
+      }
+      if (EPI == 2) {
+        const float2 c = C[m + (size_t)g.ldc * n];
+        v.x += c.x;
+        v.y += c.y;
       }
       C[m + (size_t)g.ldc * n] = v;
     }
@@ -280,9 +295,11 @@ cudaError_t launch_c2r3(const Dims &d, int nb, const float2 *spec, int work_orie
 cudaError_t launch_cgemm(const CGemm &g, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
   dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, g.batch);
-  if (g.opB == 0 && g.epi == 0) k_cgemm<0, 0><<<grid, GT, 0, st>>>(g);
-  else if (g.opB == 0 && g.epi == 1) k_cgemm<0, 1><<<grid, GT, 0, st>>>(g);
-  else if (g.opB == 1 && g.epi == 0) k_cgemm<1, 0><<<grid, GT, 0, st>>>(g);
+  if (g.opA == 0 && g.opB == 0 && g.epi == 0) k_cgemm<0, 0, 0><<<grid, GT, 0, st>>>(g);
+  else if (g.opA == 0 && g.opB == 0 && g.epi == 1) k_cgemm<0, 0, 1><<<grid, GT, 0, st>>>(g);
+  else if (g.opA == 0 && g.opB == 1 && g.epi == 0) k_cgemm<0, 1, 0><<<grid, GT, 0, st>>>(g);
+  else if (g.opA == 1 && g.opB == 0 && g.epi == 0) k_cgemm<1, 0, 0><<<grid, GT, 0, st>>>(g);
+  else if (g.opA == 0 && g.opB == 0 && g.epi == 2) k_cgemm<0, 0, 2><<<grid, GT, 0, st>>>(g);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

@@ -60,12 +60,16 @@ cudaError_t launch_c2r3(const Dims &d, int nb, const float2 *spec, int work_orie
                         float mu, int gamma4, cudaStream_t st);
 // Batched complex GEMM, column-major: C_b = A_b * op(B_b), op(B) = B or B^H.
 // epi 1: C(a, b) *= scale / (mu (1 + lam1[a] + lam2[b] + lam3[batch])).
+// opA 1 (SIMT kernel only): op(A) = A^H, A stored K x M.  epi 2 (SIMT kernel
+// only): C_b += A_b op(B_b).  lam3_period > 0: the epi-1 mode-3 eigenvalue of
+// batch entry b is lam3[b % lam3_period] (several cubes' spectra in one batch).
 struct CGemm {
-  const float2 *A; long long sA; int lda;
+  const float2 *A; long long sA; int lda; int opA;  // 0: N, 1: conjugate transpose
   const float2 *B; long long sB; int ldb; int opB;  // 0: N, 1: conjugate transpose
   float2 *C; long long sC; int ldc;
   int M, N, K, batch;
   int epi; const float *lam1, *lam2, *lam3; float mu, scale;
+  int lam3_period;
 };
 cudaError_t launch_cgemm(const CGemm &g, cudaStream_t st);
 
@@ -79,7 +83,9 @@ size_t cgemm_tc_smem();
 // One-sided Jacobi on `nslices` working matrices W_s (nr x nc, column-major,
 // slice stride P), accumulating V_s (nc x nc).  On exit W_s = A_s V_s and the
 // columns of V_s are scaled by g_i = max(1 - t / sigma_i, 0), sigma_i = |w_i|,
-// so that SVT_t(A_s) = W_s V_s^H.  sweeps[s] = sweeps used, -cap if the cap hit.
+// so that SVT_t(A_s) = W_s V_s^H; with t < 0 V_s is left unscaled (W_s, V_s are
+// then the factors of the SVD A_s = (W_s diag(1/sigma)) diag(sigma) V_s^H).
+// sweeps[s] = sweeps used, -cap if the cap hit.
 // work (may be null) accumulates [pairs examined, pairs rotated].
 cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, float t,
                           int max_sweeps, int *sweeps, unsigned long long *work,
@@ -102,6 +108,52 @@ cudaError_t launch_jacobi_batch(const SliceTask *tasks, int ntasks, int *counter
                                 cudaStream_t st);
 
 // ------------------------------------------------------------------- api.cu
+constexpr size_t kAlign = 256;
+constexpr int kMaxSweeps = 30;  // Jacobi sweep cap per slice and E-step
+
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Hands out 256-byte-aligned pieces of one allocation (or counts the bytes
+// when base is null).
+struct Carver {
+  char *base;
+  size_t off = 0;
+  explicit Carver(void *b) : base((char *)b) {}
+  template <class T>
+  T *take(size_t count) {
+    T *p = base ? (T *)(base + off) : nullptr;
+    off = align_up(off + sizeof(T) * count);
+    return p;
+  }
+};
+
+// DFT tables of one cube shape (launch_tables fills them).
+struct Tables {
+  float2 *tw3, *F1, *G1, *F2, *G2;
+  float *lam1, *lam2, *lam3;
+};
+void carve_tables(Carver &c, const Dims &d, Tables &t);
+// LRSTV_OK or the status a shape outside the kernels' limits gets.
+int check_shape(int n1, int n2, int n3);
+
+struct Prof;  // per-kernel event profiler of a plan; null: not profiled
+
+// Which GEMM implementation a call uses: the tensor cores (with an error
+// slot for bounded-wait timeouts) or the FP32 SIMT kernel.
+struct GemmSel {
+  bool tc;
+  int *err;
+};
+constexpr GemmSel kSimt = {false, nullptr};
+cudaError_t gemm(const CGemm &g, GemmSel gs, cudaStream_t st);
+
+// Z-solve (eq. Z_solution) of nb cubes of shape d stored back to back:
+// Z_b = (mu (I + D_w^* D_w))^{-1} T_b through the 3-D DFT.  specA, specB:
+// nb h P complex scratch each.
+cudaError_t zsolve_core(const Dims &d, int nb, const Tables &tb, const float *T, float mu,
+                        float *Z, float2 *specA, float2 *specB, cudaStream_t st, Prof *prof,
+                        GemmSel gs);
+
 // t-SVT of one cube with threshold t on caller-provided scratch: tw3 (n3),
 // specA and specB (h P each), V (h nc^2), sweeps (h); every piece is written
 // before it is read.

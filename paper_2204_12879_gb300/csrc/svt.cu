@@ -6,7 +6,8 @@
 // by one-sided (Hestenes) Jacobi: column pairs (p, q) are rotated until
 // |w_p^H w_q| <= tol |w_p| |w_q|.  The rotations accumulate in V, so W = A V
 // has orthogonal columns sigma_i u_i and SVT_t(A) = W diag(g) V^H with
-// g_i = max(1 - t / sigma_i, 0).  U is never formed; the reconstruction
+// g_i = max(1 - t / sigma_i, 0) (a negative t leaves V unscaled, so that the
+// factors W and V of the SVD itself are kept).  U is never formed; the reconstruction
 // W (V diag g)^H is a batched complex GEMM (dft.cu).  One CTA per slice; the
 // sweep loop is capped and a slice that reaches the cap reports it.
 //
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(R <= 8 ? 1024 : 512)
     for (int row = lane; row < nr; row += 32) n2 = fmaf(wi[row].x, wi[row].x, fmaf(wi[row].y, wi[row].y, n2));
     n2 = warp_sum(n2);
     const double sigma = sqrt((double)n2);
-    const float g = sigma > (double)t ? (float)(1.0 - (double)t / sigma) : 0.0f;
+    const float g = t < 0.0f ? 1.0f : (sigma > (double)t ? (float)(1.0 - (double)t / sigma) : 0.0f);
     float2 *vi = V + (size_t)nc * i;
     for (int row = lane; row < nc; row += 32) vi[row] = make_float2(vi[row].x * g, vi[row].y * g);
   }
@@ -423,7 +424,7 @@ __global__ void __launch_bounds__(kPWarps * 32, 1)
     for (int row = lane; row < nr; row += 32) n2 = fmaf(wi[row].x, wi[row].x, fmaf(wi[row].y, wi[row].y, n2));
     n2 = warp_sum(n2);
     const double sigma = sqrt((double)n2);
-    const float g = sigma > (double)t ? (float)(1.0 - (double)t / sigma) : 0.0f;
+    const float g = t < 0.0f ? 1.0f : (sigma > (double)t ? (float)(1.0 - (double)t / sigma) : 0.0f);
     float2 *vi = V + (size_t)nc * i;
     for (int row = lane; row < nc; row += 32) vi[row] = make_float2(vi[row].x * g, vi[row].y * g);
   }
@@ -760,7 +761,7 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
     for (int row = lane; row < nr; row += 32) n2 = fmaf(wi[row].x, wi[row].x, fmaf(wi[row].y, wi[row].y, n2));
     n2 = warp_sum(n2);
     const double sigma = sqrt((double)n2);
-    const float g = sigma > (double)t ? (float)(1.0 - (double)t / sigma) : 0.0f;
+    const float g = t < 0.0f ? 1.0f : (sigma > (double)t ? (float)(1.0 - (double)t / sigma) : 0.0f);
     float2 *vi = V + (size_t)nc * i;
     for (int row = lane; row < nc; row += 32) vi[row] = make_float2(vi[row].x * g, vi[row].y * g);
   }
@@ -771,8 +772,9 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
   }
 }
 
+// Slices of up to 64 rows fit in 64 registers a thread: two CTAs share an SM.
 template <int KP>
-__global__ void __launch_bounds__(kHW * 32, 1)
+__global__ void __launch_bounds__(kHW * 32, KP <= 2 ? 2 : 1)
     k_jacobi_pk(int nr, int nc, size_t wstride, size_t vstride, float2 *W_all, float2 *V_all,
                 float t, int max_sweeps, float tol, float negl_rel, int *__restrict__ sweeps_out,
                 unsigned long long *__restrict__ work) {

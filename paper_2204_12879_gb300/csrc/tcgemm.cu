@@ -236,6 +236,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(CGemm g, int *err) {
   } else if (nchunks > 0) {
     // epilogue: thread (warp w, lane l) owns row m0 + 32 w + l of the tile
     const int gm = m0 + row;
+    const int lb = g.lam3_period > 0 ? b % g.lam3_period : b;
     if (gm < g.M) {
 #pragma unroll
       for (int c = 0; c < TN; ++c) {
@@ -243,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(CGemm g, int *err) {
         if (n >= g.N) break;
         float2 v = make_float2(accRe[c], accIm[c]);
         if (EPI == 1) {
-          const float den = g.mu * (1.0f + g.lam1[gm] + g.lam2[n] + g.lam3[b]);
+          const float den = g.mu * (1.0f + g.lam1[gm] + g.lam2[n] + g.lam3[lb]);
           const float q = g.scale / den;
           v.x *= q;
           v.y *= q;
@@ -264,6 +265,7 @@ size_t cgemm_tc_smem() { return sizeof(float) * (2 * (size_t)kTileA + 4 * (size_
 
 cudaError_t launch_cgemm_tc(const CGemm &g, int *err, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+  if (g.opA != 0 || g.epi == 2) return cudaErrorInvalidValue;  // SIMT kernel only
   const size_t smem = cgemm_tc_smem();
   dim3 grid((g.M + TM - 1) / TM, (g.N + TN - 1) / TN, g.batch);
   cudaError_t e;

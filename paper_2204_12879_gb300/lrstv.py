@@ -17,7 +17,7 @@ import os
 from . import builder as _build
 
 __all__ = [
-    "Params", "Stats", "Profile", "Plan", "Batch", "load", "status_string", "kernel_name", "LrstvError",
+    "Params", "Stats", "Profile", "Plan", "Batch", "Unroll", "load", "status_string", "kernel_name", "LrstvError",
     "lrstv_diff", "lrstv_diff_adjoint", "lrstv_soft_threshold", "lrstv_zsolve", "lrstv_tsvt",
     "lrstv_tsvt_noalloc",
     "lrstv_denoise", "BLOCK", "FLAG_F_THRESH_EXACT", "FLAG_NO_GAMMA4", "FLAG_GRAPH",
@@ -129,6 +129,13 @@ _SIGS = {
     "lrstv_batch_init": [_P, ctypes.POINTER(_P), _P],
     "lrstv_batch_iterate": [_P, _I, _P],
     "lrstv_batch_run": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
+    "lrstv_unroll_create": [_I, _I, _I, _I, _I, ctypes.POINTER(_F), ctypes.c_uint,
+                            ctypes.POINTER(_P)],
+    "lrstv_unroll_destroy": [_P],
+    "lrstv_unroll_bytes": [_P, ctypes.POINTER(_SZ)],
+    "lrstv_unroll_forward": [_P, _P, ctypes.POINTER(ctypes.c_double), _P, _P],
+    "lrstv_unroll_backward": [_P, _P, _P, _P, _P],
+    "lrstv_unroll_stats": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), _P],
     "lrstv_kernel_name": [_I],
     "lrstv_profile_enable": [_P, _I],
     "lrstv_profile_read": [_P, ctypes.POINTER(Profile)],
@@ -391,6 +398,77 @@ class Batch:
         _call("lrstv_batch_run", self._h, self._ptrs(Ys, self.shapes),
               self._ptrs(Xs, self.shapes), self._ptrs(Ss, self.shapes), _stream(stream))
         return Xs, Ss
+
+
+class Unroll:
+    """An lrstv_unroll: K iterations of Algorithm 1 with per-iteration scalars
+    theta_k = (tau, alpha, lambda, mu) on B cubes of one shape, and the
+    gradient of a loss on the final L with respect to theta and Y.
+
+    Y and X are B cubes back to back (a (B, n3, n2, n1) tensor in C order).
+    theta is a host (K, 4) float64 array; its gradient comes back as a
+    (K, 4) float64 CUDA tensor.  A backward pass uses the iterates of the
+    handle's last forward pass."""
+
+    def __init__(self, shape, batch, iters, w=(1.0, 1.0, 1.0), flags=0):
+        self.shape = tuple(int(x) for x in shape)
+        self.batch, self.iters = int(batch), int(iters)
+        self.N = self.shape[0] * self.shape[1] * self.shape[2]
+        h = ctypes.c_void_p()
+        _call("lrstv_unroll_create", *self.shape, self.batch, self.iters, _w(w),
+              int(flags), ctypes.byref(h))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lrstv_unroll_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def nbytes(self):
+        b = ctypes.c_size_t()
+        _call("lrstv_unroll_bytes", self._h, ctypes.byref(b))
+        return b.value
+
+    def forward(self, Y, theta, X=None, stream=None):
+        import numpy as np
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+        if th.shape != (self.iters, 4):
+            raise ValueError(f"theta must be ({self.iters}, 4)")
+        n = self.batch * self.N
+        X = _empty(n, Y.device).view(Y.shape) if X is None else X
+        _call("lrstv_unroll_forward", self._h, _dev(Y, n),
+              th.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _dev(X, n), _stream(stream))
+        return X
+
+    def backward(self, dX, want_dY=True, stream=None):
+        """Returns (dtheta (K, 4) float64 CUDA tensor, dY or None)."""
+        torch = _torch()
+        n = self.batch * self.N
+        dth = torch.empty((self.iters, 4), dtype=torch.float64, device=dX.device)
+        dY = _empty(n, dX.device).view(dX.shape) if want_dY else None
+        _call("lrstv_unroll_backward", self._h, _dev(dX, n), ctypes.c_void_p(dth.data_ptr()),
+              _dev(dY, n) if dY is not None else None, _stream(stream))
+        return dth, dY
+
+    def stats(self, stream=None):
+        """(Fourier slices whose Jacobi hit its sweep cap in the last forward,
+        tensor-core GEMM wait timeouts); synchronises."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _call("lrstv_unroll_stats", self._h, ctypes.byref(a), ctypes.byref(b), _stream(stream))
+        return a.value, b.value
 
 
 def _host_ptr(a, n):
