@@ -7,7 +7,9 @@ of the 200x200x80 Pavia-shaped synthetic cube (6 endmembers, 40 Voronoi
 cells, mixed Gaussian / impulse / stripe / dead-line noise), whose denoise is
 50 iterations.  Every 50 iterations the plan is re-initialised (lrstv_init,
 inside the timed region), so the timed iterations follow the real penalty
-schedule.  value = ADMM iterations per second over all ranks; cubes/s =
+schedule.  Each E-step's Jacobi SVDs start from the previous E-step's singular
+vectors (LRSTV_FLAG_WARM_START; --jacobi-start cold starts every one from the
+identity).  value = ADMM iterations per second over all ranks; cubes/s =
 value / 50.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -179,6 +181,9 @@ def kernel_work(name, shape):
         return "alu", 8 * P * h * (n1 + n2) // 2
     if name == "cgemm_e":
         return "alu", 8 * nr * nc * nc * 3 * h
+    if name == "warm_e":    # per E-step: V V^H, (V V^H) V, A V per slice; the NS update and
+        # sigma / V diag g launches are HBM-light; this is the per-launch average over 5 launches
+        return "alu", 8 * 3 * h * (2 * nc ** 3 + nr * nc * nc) // 5
     return None, 0
 
 
@@ -240,7 +245,8 @@ def run_ours(args, wl_name):
     shape, clean, Y = make_input(wl, rank)
     n1, n2, n3 = shape
     iters = wl["iters"]
-    params = lrstv.Params.make(n1, n2, max_iter=iters)
+    flags = lrstv.FLAG_WARM_START if args.jacobi_start == "warm" else 0
+    params = lrstv.Params.make(n1, n2, max_iter=iters, flags=flags)
     plan = lrstv.Plan(n1, n2, n3, params)
     y_dev = torch.from_numpy(flat(Y)).cuda()
     stream = torch.cuda.current_stream()
@@ -302,7 +308,7 @@ def run_ours(args, wl_name):
         return None
     pk, pk_kind = peaks()
     kernels = {}
-    for k in range(9):
+    for k in range(16):
         if prof.launches[k]:
             kernels[lrstv.kernel_name(k)] = {"launches": prof.launches[k],
                                              "ms_per_launch": prof.ms[k] / prof.launches[k],
@@ -334,6 +340,7 @@ def run_ours(args, wl_name):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl["desc"], "shape": list(shape), "iters_per_cube": iters,
                    "cubes_per_s": value / iters, "parallelism": "replicas" if world > 1 else "single",
+                   "jacobi_start": args.jacobi_start,
                    "l2": "working set (18 state cubes + spectra, ~330 MB) exceeds the 129 MB L2"},
         "roofline": roof,
         "kernels": kernels,
@@ -587,6 +594,9 @@ def main(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of oracle time for the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--jacobi-start", choices=["cold", "warm"], default="warm",
+                    help="start each E-step's Jacobi SVDs from the identity or from the "
+                         "previous E-step's singular vectors (LRSTV_FLAG_WARM_START)")
     ap.add_argument("--micro", choices=["tsvt"], default=None,
                     help="time one standalone operator instead of the iteration")
     ap.add_argument("--shape", default="200,200,16", help="n1,n2,n3 for --micro")

@@ -48,6 +48,12 @@ typedef enum lrstv_status {
 #define LRSTV_FLAG_STRICT 8u         /* stats report NOT_CONVERGED / NONFINITE as the return status */
 #define LRSTV_FLAG_SIMT_GEMM 16u     /* spatial DFT and SVT-reconstruction GEMMs on the FP32 SIMT
                                         path instead of the tensor cores (tcgen05, 3xTF32) */
+#define LRSTV_FLAG_WARM_START 32u    /* each E-step's Jacobi SVDs start from the previous E-step's
+                                        right singular vectors (made unitary again by one
+                                        Newton-Schulz step) instead of the identity: the same
+                                        t-SVT to rounding, in fewer sweeps.  The first E-step after
+                                        lrstv_init or lrstv_state_set starts cold.  Not accepted by
+                                        lrstv_batch_create. */
 
 /* Scalars of Algorithm 1 (Section III-C; parameter roles in Section IV-D).
  *  tau     weight of ||D_w L||_1 (gradient sparsity)
@@ -104,7 +110,9 @@ typedef enum lrstv_kernel {
   LRSTV_K_JACOBI = 6,   /* one-sided Jacobi + singular-value threshold    */
   LRSTV_K_CGEMM_E = 7,  /* SVT reconstruction W (V diag g)^H              */
   LRSTV_K_C2R_E = 8,    /* inverse mode-3 DFT -> E, Gamma4 update         */
-  LRSTV_NKERNEL = 9
+  LRSTV_K_WARM_E = 9,   /* warm start: Newton-Schulz step on V, W = A V,
+                           sigma and V diag g (LRSTV_FLAG_WARM_START)     */
+  LRSTV_NKERNEL = 10
 } lrstv_kernel;
 
 typedef struct lrstv_profile {

@@ -57,7 +57,7 @@ int check_params(const lrstv_params *p) {
     if (!isfinite(x) || x < 0.0f) return LRSTV_ERR_ARG;
   if (!(p->mu0 > 0.0f) || !(p->mu_max >= p->mu0) || p->max_iter < 0) return LRSTV_ERR_ARG;
   if (p->flags & ~(unsigned)(LRSTV_FLAG_F_THRESH_EXACT | LRSTV_FLAG_NO_GAMMA4 | LRSTV_FLAG_GRAPH |
-                             LRSTV_FLAG_STRICT | LRSTV_FLAG_SIMT_GEMM))
+                             LRSTV_FLAG_STRICT | LRSTV_FLAG_SIMT_GEMM | LRSTV_FLAG_WARM_START))
     return LRSTV_ERR_ARG;
   return LRSTV_OK;
 }
@@ -220,6 +220,8 @@ struct lrstv_plan {
   size_t arena_bytes;
   float *Y, *L, *Z, *S, *G1, *G2, *F, *E, *G3, *G4, *T;
   float2 *specA, *specB, *V;
+  float2 *Vs;     // V diag g for the reconstruction (warm start keeps V itself)
+  int vwarm;      // V holds the last E-step's right singular vectors
   Tables tb;
   unsigned *res;  // kResRing x 2 residual maxima (float bits)
   int *sweeps;    // 3h
@@ -245,6 +247,77 @@ GemmSel plan_gemm(const lrstv_plan *pl) {
   return GemmSel{true, pl->gemm_err};
 }
 
+// The E-step with a warm-started Jacobi (LRSTV_FLAG_WARM_START).  V keeps the
+// previous E-step's right singular vectors of each Fourier slice; one
+// Newton-Schulz step V := V (3I - V^H V)/2 (two tensor-core GEMMs) removes the
+// rounding drift of its unitarity, W = A V starts the sweeps nearly
+// orthogonal, and the rotations accumulate onto V.  The Jacobi runs with a
+// negative threshold (V kept unscaled) and k_sigma_scale forms V diag g for
+// the reconstruction, exactly as the Jacobi epilogue would.
+cudaError_t tsvt_warm(lrstv_plan *pl, float ycoef, float t, float mu, int gamma4, cudaStream_t st) {
+  const Dims &d = pl->d;
+  const int ns = 3 * d.h;
+  const GemmSel gs = plan_gemm(pl);
+  const long long nc2 = (long long)d.nc * d.nc, P = (long long)d.P;
+  cudaError_t e = tsvt_pre(d, 3, pl->F, pl->G4, ycoef, pl->tb.tw3, pl->specA, st, &pl->prof);
+  if (e != cudaSuccess) return e;
+  float2 *Wm = pl->specA, *R = pl->specB;
+  if (pl->vwarm) {
+    auto warm_gemm = [&](const CGemm &g) {
+      Span sp(&pl->prof, LRSTV_K_WARM_E, st);
+      return gemm(g, gs, st);
+    };
+    CGemm g{};
+    g.batch = ns;
+    // C = V V^H (into Vs)
+    g.A = pl->V; g.sA = nc2; g.lda = d.nc;
+    g.B = pl->V; g.sB = nc2; g.ldb = d.nc; g.opB = 1;
+    g.C = pl->Vs; g.sC = nc2; g.ldc = d.nc;
+    g.M = d.nc; g.N = d.nc; g.K = d.nc;
+    if ((e = warm_gemm(g)) != cudaSuccess) return e;
+    // D = C V (into specB), V := 1.5 V - 0.5 D
+    g.A = pl->Vs; g.B = pl->V; g.opB = 0;
+    g.C = pl->specB; g.sC = P; g.ldc = d.nc;
+    if ((e = warm_gemm(g)) != cudaSuccess) return e;
+    {
+      Span sp(&pl->prof, LRSTV_K_WARM_E, st);
+      if ((e = launch_ns_update(d.nc, ns, (size_t)P, pl->V, pl->specB, st)) != cudaSuccess)
+        return e;
+    }
+    // W = A V (into specB)
+    g.A = pl->specA; g.sA = P; g.lda = d.nr;
+    g.B = pl->V; g.sB = nc2; g.ldb = d.nc; g.opB = 0;
+    g.C = pl->specB; g.sC = P; g.ldc = d.nr;
+    g.M = d.nr; g.N = d.nc; g.K = d.nc;
+    if ((e = warm_gemm(g)) != cudaSuccess) return e;
+    Wm = pl->specB;
+    R = pl->specA;
+  }
+  {
+    Span sp(&pl->prof, LRSTV_K_JACOBI, st);
+    e = launch_jacobi(d, ns, Wm, pl->V, -1.0f, kMaxSweeps, pl->sweeps,
+                      pl->prof.on ? pl->prof.d_work : nullptr, st, pl->vwarm);
+  }
+  if (e != cudaSuccess) return e;
+  {
+    Span sp(&pl->prof, LRSTV_K_WARM_E, st);
+    if ((e = launch_sigma_scale(d, ns, Wm, pl->V, t, nullptr, pl->Vs, st)) != cudaSuccess)
+      return e;
+  }
+  CGemm g{};
+  g.A = Wm; g.sA = P; g.lda = d.nr;
+  g.B = pl->Vs; g.sB = nc2; g.ldb = d.nc; g.opB = 1;
+  g.C = R; g.sC = P; g.ldc = d.nr;
+  g.M = d.nr; g.N = d.nc; g.K = d.nc; g.batch = ns;
+  {
+    Span sp(&pl->prof, LRSTV_K_CGEMM_E, st);
+    if ((e = gemm(g, gs, st)) != cudaSuccess) return e;
+  }
+  pl->vwarm = 1;
+  Span sp(&pl->prof, LRSTV_K_C2R_E, st);
+  return launch_c2r3(d, 3, R, 1, pl->tb.tw3, pl->E, 1, pl->G4, pl->F, mu, gamma4, st);
+}
+
 size_t plan_layout(lrstv_plan *pl, void *base) {
   const Dims &d = pl->d;
   Carver c(base);
@@ -262,6 +335,7 @@ size_t plan_layout(lrstv_plan *pl, void *base) {
   pl->specA = c.take<float2>(3 * (size_t)d.h * d.P);
   pl->specB = c.take<float2>(3 * (size_t)d.h * d.P);
   pl->V = c.take<float2>(3 * (size_t)d.h * d.nc * d.nc);
+  pl->Vs = c.take<float2>(3 * (size_t)d.h * d.nc * d.nc);
   carve_tables(c, d, pl->tb);
   pl->res = c.take<unsigned>(2 * (size_t)kResRing);
   pl->sweeps = c.take<int>(3 * (size_t)d.h);
@@ -313,6 +387,7 @@ int init_async(lrstv_plan *pl, const float *Y, cudaStream_t st) {
   CK(cudaMemsetAsync(pl->sweeps, 0, sizeof(int) * 3 * pl->d.h, st));
   pl->mu = pl->prm.mu0;
   pl->iter = 0;
+  pl->vwarm = 0;
   return LRSTV_OK;
 }
 
@@ -357,7 +432,7 @@ int lrstv_max_spatial(void) { return kMaxSpatial; }
 
 const char *lrstv_kernel_name(int k) {
   static const char *names[LRSTV_NKERNEL] = {"l_tz", "r2c_z", "cgemm_z", "c2r_z", "fs_dual",
-                                             "r2c_e", "jacobi", "cgemm_e", "c2r_e"};
+                                             "r2c_e", "jacobi", "cgemm_e", "c2r_e", "warm_e"};
   return (k >= 0 && k < LRSTV_NKERNEL) ? names[k] : "unknown";
 }
 
@@ -513,6 +588,11 @@ int lrstv_step_e(lrstv_plan *pl, void *stream) {
   if (!pl) return LRSTV_ERR_ARG;
   const double mu = pl->mu;
   const int gamma4 = (pl->prm.flags & LRSTV_FLAG_NO_GAMMA4) ? 0 : 1;
+  if (pl->prm.flags & LRSTV_FLAG_WARM_START) {
+    CK(tsvt_warm(pl, (float)(1.0 / mu), (float)(pl->prm.alpha / mu), (float)mu, gamma4,
+                 (cudaStream_t)stream));
+    return LRSTV_OK;
+  }
   CK(tsvt_core(pl->d, 3, pl->F, pl->G4, (float)(1.0 / mu), (float)(pl->prm.alpha / mu), pl->E, 1,
                pl->G4, pl->F, (float)mu, gamma4, pl->tb.tw3, pl->specA, pl->specB, pl->V,
                pl->sweeps, (cudaStream_t)stream, &pl->prof, plan_gemm(pl)));
@@ -589,6 +669,7 @@ int lrstv_state_set(lrstv_plan *pl, int block, const float *src, void *stream) {
   float *dst = block_ptr(pl, block, &n);
   if (!dst) return LRSTV_ERR_ARG;
   CK(cudaMemcpyAsync(dst, src, sizeof(float) * n, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  pl->vwarm = 0;  // the imported state has no Jacobi history
   return LRSTV_OK;
 }
 
@@ -642,6 +723,7 @@ int lrstv_plan_run(lrstv_plan *pl, const float *Y, float *X, float *S, lrstv_sta
     pl->mu = pl->prm.mu0;
     pl->iter = 0;
     for (int it = 0; it < iters; ++it) lrstv_step_mu(pl);
+    pl->vwarm = (iters > 0 && (pl->prm.flags & LRSTV_FLAG_WARM_START)) ? 1 : 0;
   } else {
     if ((rc = init_async(pl, Y, st)) != LRSTV_OK) return rc;
     if ((rc = iterate_async(pl, iters, st)) != LRSTV_OK) return rc;
@@ -801,6 +883,7 @@ int lrstv_batch_create(int ncubes, const int *dims, const lrstv_params *params,
     int rc = check_shape(dims[3 * i], dims[3 * i + 1], dims[3 * i + 2]);
     if (rc) return rc;
     if ((rc = check_params(&params[i]))) return rc;
+    if (params[i].flags & LRSTV_FLAG_WARM_START) return LRSTV_ERR_ARG;
     if (params[i].mu0 != params[0].mu0 || params[i].rho != params[0].rho ||
         params[i].mu_max != params[0].mu_max || params[i].max_iter != params[0].max_iter ||
         params[i].flags != params[0].flags)

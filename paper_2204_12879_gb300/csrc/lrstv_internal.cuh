@@ -87,9 +87,22 @@ size_t cgemm_tc_smem();
 // then the factors of the SVD A_s = (W_s diag(1/sigma)) diag(sigma) V_s^H).
 // sweeps[s] = sweeps used, -cap if the cap hit.
 // work (may be null) accumulates [pairs examined, pairs rotated].
+// warm = 1: V on entry is the unitary basis W was already multiplied by (the
+// rotations accumulate onto it) instead of the identity.
 cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, float t,
                           int max_sweeps, int *sweeps, unsigned long long *work,
-                          cudaStream_t st);
+                          cudaStream_t st, int warm = 0);
+
+// sigma_i = |w_i| of every working matrix (into sig, nc doubles a slice, may be
+// null) and Vs = V diag(g), g = max(1 - t / sigma, 0): the Jacobi epilogue's
+// arithmetic, for a Jacobi run with t < 0 (V kept unscaled).
+cudaError_t launch_sigma_scale(const Dims &d, int nslices, const float2 *W, const float2 *V,
+                               float t, double *sig, float2 *Vs, cudaStream_t st);
+// V := 1.5 V - 0.5 D for nslices nc x nc matrices (V contiguous, D at slice
+// stride dstride): with D = V V^H V, one Newton-Schulz step towards the nearest
+// unitary matrix.
+cudaError_t launch_ns_update(int nc, int nslices, size_t dstride, float2 *V, const float2 *D,
+                             cudaStream_t st);
 
 // One slice of a batched Jacobi launch (working matrix W, V, sweep slot, the
 // cube's alpha; threshold alpha / mu formed on the device).

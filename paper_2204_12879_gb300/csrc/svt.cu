@@ -48,15 +48,16 @@ template <int R>
 __global__ void __launch_bounds__(R <= 8 ? 1024 : 512)
     k_jacobi(int nr, int nc, size_t wstride, size_t vstride, float2 *W_all, float2 *V_all,
              float t, int max_sweeps, float tol, float negl_rel, int *__restrict__ sweeps_out,
-             unsigned long long *__restrict__ work) {
+             unsigned long long *__restrict__ work, int warm) {
   float2 *W = W_all + (size_t)blockIdx.x * wstride;
   float2 *V = V_all + (size_t)blockIdx.x * vstride;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   __shared__ float s_red[32];
   __shared__ int s_rot;
 
-  for (int e = tid; e < nc * nc; e += blockDim.x)
-    V[e] = make_float2((e % nc) == (e / nc) ? 1.0f : 0.0f, 0.0f);
+  if (!warm)  // warm: V holds the basis W was multiplied by
+    for (int e = tid; e < nc * nc; e += blockDim.x)
+      V[e] = make_float2((e % nc) == (e / nc) ? 1.0f : 0.0f, 0.0f);
 
   // ||W||_F^2: columns whose squared norm is below negl_rel ||W||_F^2 are
   // rounding residue and take part in no rotation.
@@ -596,7 +597,7 @@ template <int KP>
 __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float2 *V, float t,
                                                 int max_sweeps, float tol, float negl_rel,
                                                 int *sweeps_slot, unsigned long long *work,
-                                                float4 *smem) {
+                                                float4 *smem, int warm) {
   constexpr int KPF = PkShape<KP>::KPF;
   constexpr int LD2 = PkShape<KP>::LD2;
   float4 *sW = smem;               // panel a (own pairs), then panel b: W
@@ -607,8 +608,9 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
   __shared__ float s_red[32];
   __shared__ int s_rot;
 
-  for (int e = tid; e < nc * nc; e += blockDim.x)
-    V[e] = make_float2((e % nc) == (e / nc) ? 1.0f : 0.0f, 0.0f);
+  if (!warm)  // warm: V holds the basis W was multiplied by
+    for (int e = tid; e < nc * nc; e += blockDim.x)
+      V[e] = make_float2((e % nc) == (e / nc) ? 1.0f : 0.0f, 0.0f);
   float part = 0.0f;
   for (size_t e = tid; e < (size_t)nr * nc; e += blockDim.x) {
     const float2 x = W[e];
@@ -777,11 +779,11 @@ template <int KP>
 __global__ void __launch_bounds__(kHW * 32, KP <= 2 ? 2 : 1)
     k_jacobi_pk(int nr, int nc, size_t wstride, size_t vstride, float2 *W_all, float2 *V_all,
                 float t, int max_sweeps, float tol, float negl_rel, int *__restrict__ sweeps_out,
-                unsigned long long *__restrict__ work) {
+                unsigned long long *__restrict__ work, int warm) {
   extern __shared__ float4 smem_f4[];
   jacobi_pk_slice<KP>(nr, nc, W_all + (size_t)blockIdx.x * wstride,
                       V_all + (size_t)blockIdx.x * vstride, t, max_sweeps, tol, negl_rel,
-                      sweeps_out + blockIdx.x, work, smem_f4);
+                      sweeps_out + blockIdx.x, work, smem_f4, warm);
 }
 
 // Persistent kernel for a batch of cubes: each CTA takes the next slice from
@@ -807,26 +809,26 @@ __global__ void __launch_bounds__(kHW * 32, 1)
     const float negl = ((float)tk.nr * eps) * ((float)tk.nr * eps);
     const int KP = (tk.nr + 31) / 32;
     if (KP <= 1)
-      jacobi_pk_slice<1>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4);
+      jacobi_pk_slice<1>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, 0);
     else if (KP <= 2)
-      jacobi_pk_slice<2>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4);
+      jacobi_pk_slice<2>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, 0);
     else if (KP <= 4)
-      jacobi_pk_slice<4>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4);
+      jacobi_pk_slice<4>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, 0);
     else
-      jacobi_pk_slice<7>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4);
+      jacobi_pk_slice<7>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, 0);
   }
 }
 
 template <int KP>
 cudaError_t launch_pk(int nslices, int nr, int nc, size_t ws, size_t vs, float2 *W, float2 *V,
                       float t, int max_sweeps, float tol, float negl, int *sweeps,
-                      unsigned long long *work, cudaStream_t st) {
+                      unsigned long long *work, int warm, cudaStream_t st) {
   const size_t smem = sizeof(float4) * 3 * (size_t)kPW * PkShape<KP>::LD2;
   cudaError_t e = cudaFuncSetAttribute(k_jacobi_pk<KP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_jacobi_pk<KP><<<nslices, kHW * 32, smem, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl,
-                                                   sweeps, work);
+                                                   sweeps, work, warm);
   return cudaGetLastError();
 }
 
@@ -843,7 +845,63 @@ cudaError_t launch_panel(int nslices, int nr, int nc, size_t ws, size_t vs, floa
   return cudaGetLastError();
 }
 
+// sigma_i = |w_i| and V_s = V diag(g), g = max(1 - t / sigma, 0), with the same
+// arithmetic and summation order as the Jacobi kernels' epilogue (so a Jacobi
+// run with t < 0 followed by this kernel equals a run with threshold t).
+__global__ void __launch_bounds__(512)
+    k_sigma_scale(int nr, int nc, size_t wstride, const float2 *__restrict__ W,
+                  const float2 *__restrict__ V, float t, double *__restrict__ sig,
+                  float2 *__restrict__ Vs) {
+  const int s = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  const float2 *Ws = W + (size_t)s * wstride;
+  const size_t vs = (size_t)nc * nc;
+  for (int i = warp; i < nc; i += nwarps) {
+    const float2 *wi = Ws + (size_t)nr * i;
+    float n2 = 0.f;
+    for (int row = lane; row < nr; row += 32)
+      n2 = fmaf(wi[row].x, wi[row].x, fmaf(wi[row].y, wi[row].y, n2));
+    n2 = warp_sum(n2);
+    const double sigma = sqrt((double)n2);
+    const float g = sigma > (double)t ? (float)(1.0 - (double)t / sigma) : 0.0f;
+    if (sig && lane == 0) sig[(size_t)s * nc + i] = sigma;
+    const float2 *vi = V + s * vs + (size_t)nc * i;
+    float2 *oi = Vs + s * vs + (size_t)nc * i;
+    for (int row = lane; row < nc; row += 32) oi[row] = make_float2(vi[row].x * g, vi[row].y * g);
+  }
+}
+
+// One Newton-Schulz step towards the nearest unitary matrix:
+// V := V (3 I - V^H V) / 2 = 1.5 V - 0.5 D with D = (V V^H) V given.
+__global__ void k_ns_update(int nc, int nslices, size_t dstride, float2 *__restrict__ V,
+                            const float2 *__restrict__ D) {
+  const size_t per = (size_t)nc * nc, total = per * nslices;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t s = e / per, r = e - s * per;
+    const float2 v = V[e], d = D[s * dstride + r];
+    V[e] = make_float2(1.5f * v.x - 0.5f * d.x, 1.5f * v.y - 0.5f * d.y);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_sigma_scale(const Dims &d, int nslices, const float2 *W, const float2 *V,
+                               float t, double *sig, float2 *Vs, cudaStream_t st) {
+  if (nslices <= 0) return cudaSuccess;
+  k_sigma_scale<<<nslices, 512, 0, st>>>(d.nr, d.nc, d.P, W, V, t, sig, Vs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ns_update(int nc, int nslices, size_t dstride, float2 *V, const float2 *D,
+                             cudaStream_t st) {
+  const size_t total = (size_t)nc * nc * nslices;
+  if (total == 0) return cudaSuccess;
+  size_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_ns_update<<<(unsigned)blocks, 256, 0, st>>>(nc, nslices, dstride, V, D);
+  return cudaGetLastError();
+}
 
 size_t jacobi_batch_smem(int max_nr) {
   const int KP = (max_nr + 31) / 32;
@@ -868,7 +926,7 @@ cudaError_t launch_jacobi_batch(const SliceTask *tasks, int ntasks, int *counter
 
 cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, float t,
                           int max_sweeps, int *sweeps, unsigned long long *work,
-                          cudaStream_t st) {
+                          cudaStream_t st, int warm) {
   const int nr = d.nr, nc = d.nc;
   if (nslices <= 0) return cudaSuccess;
   const int np = nc + (nc & 1);
@@ -884,24 +942,24 @@ cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, floa
   const size_t ws = d.P, vs = (size_t)nc * nc;
   if (nr <= 256 && nc >= 2) {
     const int KP = (nr + 31) / 32;  // row pairs per lane of a half-warp
-    if (KP <= 1) return launch_pk<1>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
-    if (KP <= 2) return launch_pk<2>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
-    if (KP <= 4) return launch_pk<4>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
-    if (KP <= 7) return launch_pk<7>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
-    return launch_pk<8>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
+    if (KP <= 1) return launch_pk<1>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, st);
+    if (KP <= 2) return launch_pk<2>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, st);
+    if (KP <= 4) return launch_pk<4>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, st);
+    if (KP <= 7) return launch_pk<7>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, st);
+    return launch_pk<8>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, st);
   }
-  if (R <= 8 && nc >= 2) {
+  if (R <= 8 && nc >= 2 && !warm) {
     if (R <= 1) return launch_panel<1>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
     if (R <= 2) return launch_panel<2>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
     if (R <= 4) return launch_panel<4>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
     return launch_panel<8>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
   }
   dim3 grid(nslices), block(32 * nw);
-  if (R <= 1) k_jacobi<1><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work);
-  else if (R <= 2) k_jacobi<2><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work);
-  else if (R <= 4) k_jacobi<4><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work);
-  else if (R <= 8) k_jacobi<8><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work);
-  else if (R <= 16) k_jacobi<16><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work);
+  if (R <= 1) k_jacobi<1><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm);
+  else if (R <= 2) k_jacobi<2><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm);
+  else if (R <= 4) k_jacobi<4><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm);
+  else if (R <= 8) k_jacobi<8><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm);
+  else if (R <= 16) k_jacobi<16><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

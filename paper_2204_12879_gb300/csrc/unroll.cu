@@ -50,12 +50,6 @@ constexpr int kT = 256;
 // theta slot indices
 enum { kTau = 0, kAlpha = 1, kLam = 2, kMu = 3 };
 
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 // out[s] += sum_c m[s][c] R_c for the raw sums R_c of a kernel: each block
 // adds its threads' FP32 partials r[c] in FP64 and applies the scalar factors
 // (1/mu^2, tau/mu^2, ...) once, with one atomic per nonzero slot.  Every
@@ -120,31 +114,6 @@ __device__ __forceinline__ bool soft_keep(float x, float d, float &sgn) {
   // R_d(x) = sign(x) max(|x| - d, 0): derivative 1 where x > d or x < -d
   sgn = x > d ? 1.0f : -1.0f;
   return x > d || x < -d;
-}
-
-// sigma_i = |w_i| and V_s = V diag(g), g = max(1 - t / sigma, 0), with the same
-// arithmetic and summation order as the Jacobi kernels' epilogue.
-__global__ void __launch_bounds__(512)
-    k_sigma_scale(int nr, int nc, size_t wstride, const float2 *__restrict__ W,
-                  const float2 *__restrict__ V, float t, double *__restrict__ sig,
-                  float2 *__restrict__ Vs) {
-  const int s = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nwarps = blockDim.x >> 5;
-  const float2 *Ws = W + (size_t)s * wstride;
-  const size_t vs = (size_t)nc * nc;
-  for (int i = warp; i < nc; i += nwarps) {
-    const float2 *wi = Ws + (size_t)nr * i;
-    float n2 = 0.f;
-    for (int row = lane; row < nr; row += 32)
-      n2 = fmaf(wi[row].x, wi[row].x, fmaf(wi[row].y, wi[row].y, n2));
-    n2 = warp_sum_f(n2);
-    const double sigma = sqrt((double)n2);
-    const float g = sigma > (double)t ? (float)(1.0 - (double)t / sigma) : 0.0f;
-    if (lane == 0) sig[(size_t)s * nc + i] = sigma;
-    const float2 *vi = V + s * vs + (size_t)nc * i;
-    float2 *oi = Vs + s * vs + (size_t)nc * i;
-    for (int row = lane; row < nc; row += 32) oi[row] = make_float2(vi[row].x * g, vi[row].y * g);
-  }
 }
 
 struct AdjPtrs {
@@ -507,8 +476,7 @@ int unroll_forward(lrstv_unroll *u, cudaStream_t st) {
     UCK(launch_jacobi(d, (int)ns, Wk, Vk, -1.0f, kMaxSweeps, u->sweeps + (size_t)k * ns, nullptr,
                       st));
     const float t = (float)(alpha / mu);
-    k_sigma_scale<<<(unsigned)ns, 512, 0, st>>>(d.nr, d.nc, d.P, Wk, Vk, t, sk, u->Hs);
-    UCK(cudaGetLastError());
+    UCK(launch_sigma_scale(d, (int)ns, Wk, Vk, t, sk, u->Hs, st));
     CGemm g{};
     g.A = Wk; g.sA = (long long)d.P; g.lda = d.nr;
     g.B = u->Hs; g.sB = (long long)d.nc * d.nc; g.ldb = d.nc; g.opB = 1;

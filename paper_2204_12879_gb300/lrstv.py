@@ -21,7 +21,7 @@ __all__ = [
     "lrstv_diff", "lrstv_diff_adjoint", "lrstv_soft_threshold", "lrstv_zsolve", "lrstv_tsvt",
     "lrstv_tsvt_noalloc",
     "lrstv_denoise", "BLOCK", "FLAG_F_THRESH_EXACT", "FLAG_NO_GAMMA4", "FLAG_GRAPH",
-    "FLAG_STRICT", "FLAG_SIMT_GEMM", "EXPORTED",
+    "FLAG_STRICT", "FLAG_SIMT_GEMM", "FLAG_WARM_START", "EXPORTED",
 ]
 
 FLAG_F_THRESH_EXACT = 1
@@ -29,6 +29,7 @@ FLAG_NO_GAMMA4 = 2
 FLAG_GRAPH = 4
 FLAG_STRICT = 8
 FLAG_SIMT_GEMM = 16
+FLAG_WARM_START = 32
 
 BLOCK = {"Y": 0, "L": 1, "Z": 2, "S": 3, "G1": 4, "G2": 5, "F": 6, "E": 7, "G3": 8, "G4": 9,
          "TZ": 10}
@@ -81,7 +82,7 @@ class Profile(ctypes.Structure):
 
     def as_dict(self):
         out = {}
-        for k in range(9):
+        for k in range(16):
             if self.launches[k]:
                 out[kernel_name(k)] = {"launches": self.launches[k], "ms": self.ms[k]}
         return out
