@@ -52,8 +52,7 @@ typedef enum lrstv_status {
                                         right singular vectors (made unitary again by one
                                         Newton-Schulz step) instead of the identity: the same
                                         t-SVT to rounding, in fewer sweeps.  The first E-step after
-                                        lrstv_init or lrstv_state_set starts cold.  Not accepted by
-                                        lrstv_batch_create. */
+                                        lrstv_init or lrstv_state_set starts cold. */
 
 /* Scalars of Algorithm 1 (Section III-C; parameter roles in Section IV-D).
  *  tau     weight of ||D_w L||_1 (gradient sparsity)
@@ -256,7 +255,8 @@ int lrstv_zsolve(const float *T, int n1, int n2, int n3, const float w[3], float
 /* t-SVT of a real cube (eq. E_solution with Theorem 4.2's t-SVD): DFT along
  * mode 3, singular values of every Fourier frontal slice soft-thresholded by
  * t, inverse DFT.  `sweeps_host` (may be NULL) receives the largest Jacobi
- * sweep count, negative if a slice hit the cap; passing it synchronises. */
+ * sweep count, negative if a slice hit the cap (0 if every slice's Frobenius
+ * norm is at most t, so that no sweep was needed); passing it synchronises. */
 int lrstv_tsvt(const float *A, int n1, int n2, int n3, float t, float *out, void *workspace,
                size_t workspace_bytes, int *sweeps_host, void *stream);
 
@@ -303,7 +303,9 @@ int lrstv_tsvt_noalloc(const float *A, int n1, int n2, int n3, float t, float *o
  *   (K + 1 states of 17 B N floats), the SVD factors of every Fourier slice
  *   of every E-update (K x 3 B (n3/2+1) slices) and the scratch of both
  *   passes; lrstv_unroll_bytes reports its size.  w: weights of D_w (NULL =
- *   1, 1, 1).  flags: 0 or LRSTV_FLAG_SIMT_GEMM.  iters in 1..4096.
+ *   1, 1, 1).  flags: 0, LRSTV_FLAG_SIMT_GEMM, LRSTV_FLAG_WARM_START (iteration
+ *   k > 0 starts its Jacobi SVDs from iteration k-1's singular vectors, as a
+ *   plan does).  iters in 1..4096.
  * lrstv_unroll_forward  Y: device, B cubes back to back (B N floats).
  *   theta: HOST array of K x 4 doubles (tau, alpha, lambda, mu per
  *   iteration; all finite and >= 0, mu > 0), copied during the call.

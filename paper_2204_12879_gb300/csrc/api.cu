@@ -163,7 +163,7 @@ cudaError_t tsvt_jac(const Dims &d, int nb, float t, float2 *specA, float2 *V, i
                      cudaStream_t st, Prof *prof) {
   Span sp(prof, LRSTV_K_JACOBI, st);
   return launch_jacobi(d, nb * d.h, specA, V, t, kMaxSweeps, sweeps, prof ? prof->d_work : nullptr,
-                       st);
+                       st, 0, t);
 }
 
 cudaError_t tsvt_post(const Dims &d, int nb, float *out, int mode, float *G4, const float *F,
@@ -247,6 +247,42 @@ GemmSel plan_gemm(const lrstv_plan *pl) {
   return GemmSel{true, pl->gemm_err};
 }
 
+// Warm start of a plan's E-step: one Newton-Schulz step on V (the previous
+// E-step's right singular vectors): C = V V^H (into Vs), D = C V (into Dscr),
+// V := 1.5 V - 0.5 D; then W = A V into Wout (A, Wout, Dscr: the plan's
+// specA / specB in either role; Dscr may be Wout).
+cudaError_t warm_basis(lrstv_plan *pl, const float2 *A, float2 *Wout, float2 *Dscr,
+                       cudaStream_t st) {
+  const Dims &d = pl->d;
+  const int ns = 3 * d.h;
+  const GemmSel gs = plan_gemm(pl);
+  const long long nc2 = (long long)d.nc * d.nc, P = (long long)d.P;
+  auto run = [&](const CGemm &g) {
+    Span sp(&pl->prof, LRSTV_K_WARM_E, st);
+    return gemm(g, gs, st);
+  };
+  cudaError_t e;
+  CGemm g{};
+  g.batch = ns;
+  g.A = pl->V; g.sA = nc2; g.lda = d.nc;
+  g.B = pl->V; g.sB = nc2; g.ldb = d.nc; g.opB = 1;
+  g.C = pl->Vs; g.sC = nc2; g.ldc = d.nc;
+  g.M = d.nc; g.N = d.nc; g.K = d.nc;
+  if ((e = run(g)) != cudaSuccess) return e;
+  g.A = pl->Vs; g.B = pl->V; g.opB = 0;
+  g.C = Dscr; g.sC = P; g.ldc = d.nc;
+  if ((e = run(g)) != cudaSuccess) return e;
+  {
+    Span sp(&pl->prof, LRSTV_K_WARM_E, st);
+    if ((e = launch_ns_update(d.nc, ns, (size_t)P, pl->V, Dscr, st)) != cudaSuccess) return e;
+  }
+  g.A = A; g.sA = P; g.lda = d.nr;
+  g.B = pl->V; g.sB = nc2; g.ldb = d.nc; g.opB = 0;
+  g.C = Wout; g.sC = P; g.ldc = d.nr;
+  g.M = d.nr; g.N = d.nc; g.K = d.nc;
+  return run(g);
+}
+
 // The E-step with a warm-started Jacobi (LRSTV_FLAG_WARM_START).  V keeps the
 // previous E-step's right singular vectors of each Fourier slice; one
 // Newton-Schulz step V := V (3I - V^H V)/2 (two tensor-core GEMMs) removes the
@@ -263,40 +299,14 @@ cudaError_t tsvt_warm(lrstv_plan *pl, float ycoef, float t, float mu, int gamma4
   if (e != cudaSuccess) return e;
   float2 *Wm = pl->specA, *R = pl->specB;
   if (pl->vwarm) {
-    auto warm_gemm = [&](const CGemm &g) {
-      Span sp(&pl->prof, LRSTV_K_WARM_E, st);
-      return gemm(g, gs, st);
-    };
-    CGemm g{};
-    g.batch = ns;
-    // C = V V^H (into Vs)
-    g.A = pl->V; g.sA = nc2; g.lda = d.nc;
-    g.B = pl->V; g.sB = nc2; g.ldb = d.nc; g.opB = 1;
-    g.C = pl->Vs; g.sC = nc2; g.ldc = d.nc;
-    g.M = d.nc; g.N = d.nc; g.K = d.nc;
-    if ((e = warm_gemm(g)) != cudaSuccess) return e;
-    // D = C V (into specB), V := 1.5 V - 0.5 D
-    g.A = pl->Vs; g.B = pl->V; g.opB = 0;
-    g.C = pl->specB; g.sC = P; g.ldc = d.nc;
-    if ((e = warm_gemm(g)) != cudaSuccess) return e;
-    {
-      Span sp(&pl->prof, LRSTV_K_WARM_E, st);
-      if ((e = launch_ns_update(d.nc, ns, (size_t)P, pl->V, pl->specB, st)) != cudaSuccess)
-        return e;
-    }
-    // W = A V (into specB)
-    g.A = pl->specA; g.sA = P; g.lda = d.nr;
-    g.B = pl->V; g.sB = nc2; g.ldb = d.nc; g.opB = 0;
-    g.C = pl->specB; g.sC = P; g.ldc = d.nr;
-    g.M = d.nr; g.N = d.nc; g.K = d.nc;
-    if ((e = warm_gemm(g)) != cudaSuccess) return e;
+    if ((e = warm_basis(pl, pl->specA, pl->specB, pl->specB, st)) != cudaSuccess) return e;
     Wm = pl->specB;
     R = pl->specA;
   }
   {
     Span sp(&pl->prof, LRSTV_K_JACOBI, st);
     e = launch_jacobi(d, ns, Wm, pl->V, -1.0f, kMaxSweeps, pl->sweeps,
-                      pl->prof.on ? pl->prof.d_work : nullptr, st, pl->vwarm);
+                      pl->prof.on ? pl->prof.d_work : nullptr, st, pl->vwarm, t);
   }
   if (e != cudaSuccess) return e;
   {
@@ -812,28 +822,39 @@ int task_cmp(const void *x, const void *y) {
 
 int batch_e_step(lrstv_batch *b, cudaStream_t st) {
   const double mu = b->plans[0]->mu;
+  const bool wflag = (b->plans[0]->prm.flags & LRSTV_FLAG_WARM_START) != 0;
+  const int warm = wflag && b->plans[0]->vwarm;
+  // the Jacobi always works on specA: a warm start transforms into it from specB
   for (int i = 0; i < b->n; ++i) {
     lrstv_plan *pl = b->plans[i];
-    CK(tsvt_pre(pl->d, 3, pl->F, pl->G4, (float)(1.0 / pl->mu), pl->tb.tw3, pl->specA, st,
-                &pl->prof));
+    CK(tsvt_pre(pl->d, 3, pl->F, pl->G4, (float)(1.0 / pl->mu), pl->tb.tw3,
+                warm ? pl->specB : pl->specA, st, &pl->prof));
+    if (warm) CK(warm_basis(pl, pl->specB, pl->specA, pl->specA, st));
   }
   if (b->ntasks > 0) {
     CK(cudaMemsetAsync(b->d_counter, 0, sizeof(int), st));
     Prof *prof = &b->plans[0]->prof;
     Span sp(prof, LRSTV_K_JACOBI, st);
     CK(launch_jacobi_batch(b->d_tasks, b->ntasks, b->d_counter, mu, kMaxSweeps,
-                           prof->on ? prof->d_work : nullptr, b->grid, b->smem, st));
+                           prof->on ? prof->d_work : nullptr, b->grid, b->smem, st, warm,
+                           wflag ? 1 : 0));
   }
   for (int k = 0; k < b->nbig; ++k) {
     lrstv_plan *pl = b->plans[b->big[k]];
-    CK(tsvt_jac(pl->d, 3, (float)(pl->prm.alpha / pl->mu), pl->specA, pl->V, pl->sweeps, st,
-                &pl->prof));
+    Span sp(&pl->prof, LRSTV_K_JACOBI, st);
+    const float t = (float)(pl->prm.alpha / pl->mu);
+    CK(launch_jacobi(pl->d, 3 * pl->d.h, pl->specA, pl->V, wflag ? -1.0f : t, kMaxSweeps,
+                     pl->sweeps, pl->prof.on ? pl->prof.d_work : nullptr, st, warm, t));
   }
   for (int i = 0; i < b->n; ++i) {
     lrstv_plan *pl = b->plans[i];
     const int gamma4 = (pl->prm.flags & LRSTV_FLAG_NO_GAMMA4) ? 0 : 1;
+    if (wflag)
+      CK(launch_sigma_scale(pl->d, 3 * pl->d.h, pl->specA, pl->V,
+                            (float)(pl->prm.alpha / pl->mu), nullptr, pl->Vs, st));
     CK(tsvt_post(pl->d, 3, pl->E, 1, pl->G4, pl->F, (float)pl->mu, gamma4, pl->tb.tw3, pl->specA,
-                 pl->specB, pl->V, st, &pl->prof, plan_gemm(pl)));
+                 pl->specB, wflag ? pl->Vs : pl->V, st, &pl->prof, plan_gemm(pl)));
+    if (wflag) pl->vwarm = 1;
   }
   return LRSTV_OK;
 }
@@ -883,7 +904,6 @@ int lrstv_batch_create(int ncubes, const int *dims, const lrstv_params *params,
     int rc = check_shape(dims[3 * i], dims[3 * i + 1], dims[3 * i + 2]);
     if (rc) return rc;
     if ((rc = check_params(&params[i]))) return rc;
-    if (params[i].flags & LRSTV_FLAG_WARM_START) return LRSTV_ERR_ARG;
     if (params[i].mu0 != params[0].mu0 || params[i].rho != params[0].rho ||
         params[i].mu_max != params[0].mu_max || params[i].max_iter != params[0].max_iter ||
         params[i].flags != params[0].flags)

@@ -88,10 +88,12 @@ size_t cgemm_tc_smem();
 // sweeps[s] = sweeps used, -cap if the cap hit.
 // work (may be null) accumulates [pairs examined, pairs rotated].
 // warm = 1: V on entry is the unitary basis W was already multiplied by (the
-// rotations accumulate onto it) instead of the identity.
+// rotations accumulate onto it) instead of the identity.  skip_t >= 0: a
+// slice with ||W||_F <= skip_t (so every singular value is at most skip_t)
+// runs no sweep, as its SVT with that threshold is zero (V stays as it came).
 cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, float t,
                           int max_sweeps, int *sweeps, unsigned long long *work,
-                          cudaStream_t st, int warm = 0);
+                          cudaStream_t st, int warm = 0, float skip_t = -1.0f);
 
 // sigma_i = |w_i| of every working matrix (into sig, nc doubles a slice, may be
 // null) and Vs = V diag(g), g = max(1 - t / sigma, 0): the Jacobi epilogue's
@@ -115,10 +117,11 @@ struct SliceTask {
 // Largest slice height the persistent batch kernel takes.
 constexpr int kBatchMaxNr = 224;  // keeps the persistent kernel free of spills
 size_t jacobi_batch_smem(int max_nr);
-// Persistent work-list Jacobi over `ntasks` slices; *counter must be 0.
+// Persistent work-list Jacobi over `ntasks` slices; *counter must be 0.  warm:
+// as launch_jacobi; keep: V left unscaled (threshold taken as negative).
 cudaError_t launch_jacobi_batch(const SliceTask *tasks, int ntasks, int *counter, double mu,
                                 int max_sweeps, unsigned long long *work, int grid, size_t smem,
-                                cudaStream_t st);
+                                cudaStream_t st, int warm = 0, int keep = 0);
 
 // ------------------------------------------------------------------- api.cu
 constexpr size_t kAlign = 256;

@@ -48,7 +48,7 @@ template <int R>
 __global__ void __launch_bounds__(R <= 8 ? 1024 : 512)
     k_jacobi(int nr, int nc, size_t wstride, size_t vstride, float2 *W_all, float2 *V_all,
              float t, int max_sweeps, float tol, float negl_rel, int *__restrict__ sweeps_out,
-             unsigned long long *__restrict__ work, int warm) {
+             unsigned long long *__restrict__ work, int warm, float skip_t) {
   float2 *W = W_all + (size_t)blockIdx.x * wstride;
   float2 *V = V_all + (size_t)blockIdx.x * vstride;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -82,6 +82,12 @@ __global__ void __launch_bounds__(R <= 8 ? 1024 : 512)
   // a slice with fewer than two columns is diagonal already: one empty sweep
   int sweeps = (nc < 2) ? 1 : 0;
   bool converged = (nc < 2);
+  // every singular value is at most ||W||_F: at or below the threshold the SVT
+  // is zero whatever the sweeps would find, so none is run
+  if (skip_t >= 0.0f && s_red[0] <= skip_t * skip_t) {
+    sweeps = 0;
+    converged = true;
+  }
   for (int sweep = 1; sweep <= max_sweeps && !converged; ++sweep) {
     if (tid == 0) s_rot = 0;
     __syncthreads();
@@ -597,7 +603,7 @@ template <int KP>
 __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float2 *V, float t,
                                                 int max_sweeps, float tol, float negl_rel,
                                                 int *sweeps_slot, unsigned long long *work,
-                                                float4 *smem, int warm) {
+                                                float4 *smem, int warm, float skip_t) {
   constexpr int KPF = PkShape<KP>::KPF;
   constexpr int LD2 = PkShape<KP>::LD2;
   float4 *sW = smem;               // panel a (own pairs), then panel b: W
@@ -631,6 +637,12 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
   unsigned n_pairs = 0, n_rot = 0;  // lane 0 (own pairs) and ul 0 (cross pairs) count
   int sweeps = (nc < 2) ? 1 : 0;
   bool converged = (nc < 2);
+  // every singular value is at most ||W||_F: at or below the threshold the SVT
+  // is zero whatever the sweeps would find, so none is run
+  if (skip_t >= 0.0f && s_red[0] <= skip_t * skip_t) {
+    sweeps = 0;
+    converged = true;
+  }
   float4 aW[KP], aV[KP], bW[KP];
   for (int sweep = 1; sweep <= max_sweeps && !converged; ++sweep) {
     if (tid == 0) s_rot = 0;
@@ -779,11 +791,11 @@ template <int KP>
 __global__ void __launch_bounds__(kHW * 32, KP <= 2 ? 2 : 1)
     k_jacobi_pk(int nr, int nc, size_t wstride, size_t vstride, float2 *W_all, float2 *V_all,
                 float t, int max_sweeps, float tol, float negl_rel, int *__restrict__ sweeps_out,
-                unsigned long long *__restrict__ work, int warm) {
+                unsigned long long *__restrict__ work, int warm, float skip_t) {
   extern __shared__ float4 smem_f4[];
   jacobi_pk_slice<KP>(nr, nc, W_all + (size_t)blockIdx.x * wstride,
                       V_all + (size_t)blockIdx.x * vstride, t, max_sweeps, tol, negl_rel,
-                      sweeps_out + blockIdx.x, work, smem_f4, warm);
+                      sweeps_out + blockIdx.x, work, smem_f4, warm, skip_t);
 }
 
 // Persistent kernel for a batch of cubes: each CTA takes the next slice from
@@ -793,7 +805,7 @@ __global__ void __launch_bounds__(kHW * 32, KP <= 2 ? 2 : 1)
 // paths agree bit for bit.
 __global__ void __launch_bounds__(kHW * 32, 1)
     k_jacobi_batch(const SliceTask *__restrict__ tasks, int ntasks, int *counter, double mu,
-                   int max_sweeps, unsigned long long *work) {
+                   int max_sweeps, unsigned long long *work, int warm, int keep) {
   extern __shared__ float4 smem_f4[];
   __shared__ int s_item;
   const float eps = FLT_EPSILON * 0.5f;
@@ -804,31 +816,32 @@ __global__ void __launch_bounds__(kHW * 32, 1)
     __syncthreads();
     if (item >= ntasks) return;
     const SliceTask tk = tasks[item];
-    const float t = (float)((double)tk.alpha / mu);
+    const float tt = (float)((double)tk.alpha / mu);
+    const float t = keep ? -1.0f : tt;
     const float tol = 8.0f * sqrtf((float)tk.nr) * eps;
     const float negl = ((float)tk.nr * eps) * ((float)tk.nr * eps);
     const int KP = (tk.nr + 31) / 32;
     if (KP <= 1)
-      jacobi_pk_slice<1>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, 0);
+      jacobi_pk_slice<1>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt);
     else if (KP <= 2)
-      jacobi_pk_slice<2>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, 0);
+      jacobi_pk_slice<2>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt);
     else if (KP <= 4)
-      jacobi_pk_slice<4>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, 0);
+      jacobi_pk_slice<4>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt);
     else
-      jacobi_pk_slice<7>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, 0);
+      jacobi_pk_slice<7>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt);
   }
 }
 
 template <int KP>
 cudaError_t launch_pk(int nslices, int nr, int nc, size_t ws, size_t vs, float2 *W, float2 *V,
                       float t, int max_sweeps, float tol, float negl, int *sweeps,
-                      unsigned long long *work, int warm, cudaStream_t st) {
+                      unsigned long long *work, int warm, float skip_t, cudaStream_t st) {
   const size_t smem = sizeof(float4) * 3 * (size_t)kPW * PkShape<KP>::LD2;
   cudaError_t e = cudaFuncSetAttribute(k_jacobi_pk<KP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_jacobi_pk<KP><<<nslices, kHW * 32, smem, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl,
-                                                   sweeps, work, warm);
+                                                   sweeps, work, warm, skip_t);
   return cudaGetLastError();
 }
 
@@ -915,18 +928,19 @@ size_t jacobi_batch_smem(int max_nr) {
 
 cudaError_t launch_jacobi_batch(const SliceTask *tasks, int ntasks, int *counter, double mu,
                                 int max_sweeps, unsigned long long *work, int grid, size_t smem,
-                                cudaStream_t st) {
+                                cudaStream_t st, int warm, int keep) {
   if (ntasks <= 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k_jacobi_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_jacobi_batch<<<grid, kHW * 32, smem, st>>>(tasks, ntasks, counter, mu, max_sweeps, work);
+  k_jacobi_batch<<<grid, kHW * 32, smem, st>>>(tasks, ntasks, counter, mu, max_sweeps, work, warm,
+                                                keep);
   return cudaGetLastError();
 }
 
 cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, float t,
                           int max_sweeps, int *sweeps, unsigned long long *work,
-                          cudaStream_t st, int warm) {
+                          cudaStream_t st, int warm, float skip_t) {
   const int nr = d.nr, nc = d.nc;
   if (nslices <= 0) return cudaSuccess;
   const int np = nc + (nc & 1);
@@ -942,11 +956,11 @@ cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, floa
   const size_t ws = d.P, vs = (size_t)nc * nc;
   if (nr <= 256 && nc >= 2) {
     const int KP = (nr + 31) / 32;  // row pairs per lane of a half-warp
-    if (KP <= 1) return launch_pk<1>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, st);
-    if (KP <= 2) return launch_pk<2>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, st);
-    if (KP <= 4) return launch_pk<4>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, st);
-    if (KP <= 7) return launch_pk<7>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, st);
-    return launch_pk<8>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, st);
+    if (KP <= 1) return launch_pk<1>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, skip_t, st);
+    if (KP <= 2) return launch_pk<2>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, skip_t, st);
+    if (KP <= 4) return launch_pk<4>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, skip_t, st);
+    if (KP <= 7) return launch_pk<7>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, skip_t, st);
+    return launch_pk<8>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, skip_t, st);
   }
   if (R <= 8 && nc >= 2 && !warm) {
     if (R <= 1) return launch_panel<1>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
@@ -955,11 +969,11 @@ cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, floa
     return launch_panel<8>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
   }
   dim3 grid(nslices), block(32 * nw);
-  if (R <= 1) k_jacobi<1><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm);
-  else if (R <= 2) k_jacobi<2><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm);
-  else if (R <= 4) k_jacobi<4><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm);
-  else if (R <= 8) k_jacobi<8><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm);
-  else if (R <= 16) k_jacobi<16><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm);
+  if (R <= 1) k_jacobi<1><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, skip_t);
+  else if (R <= 2) k_jacobi<2><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, skip_t);
+  else if (R <= 4) k_jacobi<4><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, skip_t);
+  else if (R <= 8) k_jacobi<8><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, skip_t);
+  else if (R <= 16) k_jacobi<16><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, skip_t);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

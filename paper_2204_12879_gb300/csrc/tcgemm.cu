@@ -141,24 +141,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(CGemm g, int *err) {
   const int nchunks = (g.K + TK - 1) / TK;
   for (int ch = 0; ch < nchunks && ok; ++ch) {
     const int k0 = ch * TK;
-    // A tile: rows m0..m0+127, complex k0..k0+15 -> real kk = k (re), k + 16 (im)
+    // A tile: rows m0..m0+127, complex k0..k0+15 -> real kk = k (re), k + 16 (im).
+    // A warp covers 8 rows x 4 k: its 32 stores hit 32 distinct banks of a core
+    // matrix row group, and its loads are four 64-byte runs of a column.
     for (int e = tid; e < TM * TK; e += kThreads) {
-      const int r = e % TM, kc = e / TM;  // consecutive threads: consecutive rows (coalesced)
+      const int rest = e >> 5;
+      const int r = ((rest % (TM / 8)) << 3) | ((e >> 2) & 7);
+      const int kc = ((rest / (TM / 8)) << 2) | (e & 3);
       const int gm = m0 + r, gk = k0 + kc;
       const float2 v = (gm < g.M && gk < g.K) ? A[gm + (size_t)g.lda * gk] : make_float2(0.f, 0.f);
       put_split(aHi, aLo, koff(r, kc), v.x);
       put_split(aHi, aLo, koff(r, kc + TK), v.y);
     }
     // B tiles for output columns n0..n0+63: row n holds op(B)(k, n) over k
+    // (8 rows n x 4 k per warp, as for A: conflict-free stores; loads are runs
+    // of 4 k (B(k, n) at k + ldb n) or of 8 n (B(n, k) at n + ldb k))
     for (int e = tid; e < TN * TK; e += kThreads) {
-      int n, kc;
-      if (OPB == 0) {  // B(k, n) at k + ldb n: consecutive threads along k
-        kc = e % TK;
-        n = e / TK;
-      } else {         // op(B)(k, n) = conj(B(n, k)), B(n, k) at n + ldb k: along n
-        n = e % TN;
-        kc = e / TN;
-      }
+      const int rest = e >> 5;
+      const int n = ((rest % (TN / 8)) << 3) | ((e >> 2) & 7);
+      const int kc = ((rest / (TN / 8)) << 2) | (e & 3);
       const int gn = n0 + n, gk = k0 + kc;
       float2 v = make_float2(0.f, 0.f);
       if (gn < g.N && gk < g.K) {

@@ -472,10 +472,36 @@ int unroll_forward(lrstv_unroll *u, cudaStream_t st) {
     float2 *Wk = u->W + (size_t)k * ns * d.P;
     float2 *Vk = u->V + (size_t)k * ns * d.nc * d.nc;
     double *sk = u->sig + (size_t)k * ns * d.nc;
-    UCK(launch_r2c3(d, 3 * B, s.F, s.G4, (float)(1.0 / mu), Wk, 1, u->tb.tw3, st));
-    UCK(launch_jacobi(d, (int)ns, Wk, Vk, -1.0f, kMaxSweeps, u->sweeps + (size_t)k * ns, nullptr,
-                      st));
+    const int warm = (u->flags & LRSTV_FLAG_WARM_START) && k > 0;
+    if (warm) {
+      // start from the previous iteration's right singular vectors, made
+      // unitary again by one Newton-Schulz step, exactly as a plan does
+      const long long nc2 = (long long)d.nc * d.nc, P = (long long)d.P;
+      UCK(launch_r2c3(d, 3 * B, s.F, s.G4, (float)(1.0 / mu), u->specA, 1, u->tb.tw3, st));
+      UCK(cudaMemcpyAsync(Vk, Vk - ns * d.nc * d.nc, sizeof(float2) * ns * d.nc * d.nc,
+                          cudaMemcpyDeviceToDevice, st));
+      CGemm g{};
+      g.batch = (int)ns;
+      g.A = Vk; g.sA = nc2; g.lda = d.nc;
+      g.B = Vk; g.sB = nc2; g.ldb = d.nc; g.opB = 1;
+      g.C = u->Hs; g.sC = nc2; g.ldc = d.nc;
+      g.M = d.nc; g.N = d.nc; g.K = d.nc;
+      UCK(gemm(g, gs, st));
+      g.A = u->Hs; g.B = Vk; g.opB = 0;
+      g.C = u->specB; g.sC = P; g.ldc = d.nc;
+      UCK(gemm(g, gs, st));
+      UCK(launch_ns_update(d.nc, (int)ns, (size_t)P, Vk, u->specB, st));
+      g.A = u->specA; g.sA = P; g.lda = d.nr;
+      g.B = Vk; g.sB = nc2; g.ldb = d.nc; g.opB = 0;
+      g.C = Wk; g.sC = P; g.ldc = d.nr;
+      g.M = d.nr; g.N = d.nc; g.K = d.nc;
+      UCK(gemm(g, gs, st));
+    } else {
+      UCK(launch_r2c3(d, 3 * B, s.F, s.G4, (float)(1.0 / mu), Wk, 1, u->tb.tw3, st));
+    }
     const float t = (float)(alpha / mu);
+    UCK(launch_jacobi(d, (int)ns, Wk, Vk, -1.0f, kMaxSweeps, u->sweeps + (size_t)k * ns, nullptr,
+                      st, warm, t));
     UCK(launch_sigma_scale(d, (int)ns, Wk, Vk, t, sk, u->Hs, st));
     CGemm g{};
     g.A = Wk; g.sA = (long long)d.P; g.lda = d.nr;
@@ -590,7 +616,7 @@ int lrstv_unroll_create(int n1, int n2, int n3, int batch, int iters, const floa
   int rc = check_shape(n1, n2, n3);
   if (rc) return rc;
   if (batch < 1 || iters < 1 || iters > 4096) return LRSTV_ERR_ARG;
-  if (flags & ~(unsigned)LRSTV_FLAG_SIMT_GEMM) return LRSTV_ERR_ARG;
+  if (flags & ~(unsigned)(LRSTV_FLAG_SIMT_GEMM | LRSTV_FLAG_WARM_START)) return LRSTV_ERR_ARG;
   float wl[3] = {1.0f, 1.0f, 1.0f};
   if (w)
     for (int n = 0; n < 3; ++n) {

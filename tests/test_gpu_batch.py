@@ -40,11 +40,13 @@ def _params(L, shape, i, iters, flags=0):
                          max_iter=iters, flags=flags)
 
 
-def test_batch_equals_single_plans(L):
+@pytest.mark.parametrize("warm", [False, True])
+def test_batch_equals_single_plans(L, warm):
     import torch
     iters = 6
+    flags = L.FLAG_WARM_START if warm else 0
     Ys = [dev(_cube(sh, 100 + i)) for i, sh in enumerate(SHAPES)]
-    params = [_params(L, sh, i, iters) for i, sh in enumerate(SHAPES)]
+    params = [_params(L, sh, i, iters, flags) for i, sh in enumerate(SHAPES)]
     with L.Batch(SHAPES, params) as b:
         Xs, Ss = b.run(Ys)
         torch.cuda.synchronize()

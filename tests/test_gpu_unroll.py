@@ -73,13 +73,15 @@ def _free_theta(K):
 
 
 @pytest.mark.parametrize("shape", [(24, 20, 9), (20, 24, 8)])
-def test_forward_equals_plan_bitwise(L, shape):
+@pytest.mark.parametrize("warm", [False, True])
+def test_forward_equals_plan_bitwise(L, shape, warm):
     import torch
     K, B = 4, 2
     cubes = _cubes(shape, B, 40)
     Y = _to_dev([c[1] for c in cubes])
-    p = L.Params.make(shape[0], shape[1], max_iter=K)
-    with L.Unroll(shape, B, K) as u:
+    flags = L.FLAG_WARM_START if warm else 0
+    p = L.Params.make(shape[0], shape[1], max_iter=K, flags=flags)
+    with L.Unroll(shape, B, K, flags=flags) as u:
         X = u.forward(Y, _plain_theta(p, K))
         assert u.stats() == (0, 0)
     for b in range(B):
@@ -236,7 +238,7 @@ def test_unroll_training_shape_cube0_matches_oracle(L):
     theta = np.array(default_theta(64, 64, K))  # where a training run starts
     dX0 = f32(2.0 * (cubes[0][1] - cubes[0][0]) / np.prod(shape))
     dXs = [dX0] + [np.zeros(shape, np.float32)] * (B - 1)
-    with L.Unroll(shape, B, K) as u:
+    with L.Unroll(shape, B, K, flags=L.FLAG_WARM_START) as u:
         X = u.forward(Y, theta)
         assert u.stats() == (0, 0)
         dth, dY = u.backward(_to_dev(dXs))

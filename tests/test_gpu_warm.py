@@ -83,10 +83,19 @@ def test_warm_uses_fewer_jacobi_pairs(L):
     assert maxabs(res["warm"][0], res["cold"][0]) <= 1e-4
 
 
-def test_batch_rejects_warm_start(L):
-    import ctypes
-    lib = L.load()
-    p = [L.Params.make(8, 8, flags=L.FLAG_WARM_START)]
-    dims = (ctypes.c_int * 3)(8, 8, 4)
-    h = ctypes.c_void_p()
-    assert lib.lrstv_batch_create(1, dims, (L.Params * 1)(*p), ctypes.byref(h)) == 1
+def test_all_cut_slices_skip_sweeps(L, orc):
+    """A Fourier slice whose Frobenius norm is at most the threshold has every
+    singular value cut: its SVT is zero and the Jacobi runs no sweep on it.
+    A cube whose slices straddle the threshold still matches the oracle."""
+    import torch
+    shape = (24, 20, 6)
+    A = f32(np.random.default_rng(7).standard_normal(shape))
+    norms = np.linalg.norm(np.fft.fft(A, axis=2)[:, :, : shape[2] // 2 + 1], axis=(0, 1))
+    out, sw = L.lrstv_tsvt(dev(A), shape, float(norms.max()) * 1.01, sweeps=True)
+    torch.cuda.synchronize()
+    assert sw == 0 and float(out.abs().max()) == 0.0
+    # a threshold between the slices' norms: some slices skip, the rest rotate
+    t = float(np.median(norms))
+    out = host(L.lrstv_tsvt(dev(A), shape, t), shape)
+    ref, _ = orc.tsvt(A, t)
+    assert maxabs(out, ref) <= 2e-5 * np.max(np.abs(A))
