@@ -251,14 +251,21 @@ def run_ours(args, wl_name):
     y_dev = torch.from_numpy(flat(Y)).cuda()
     stream = torch.cuda.current_stream()
 
-    def step():
-        if plan.mu[1] >= iters:
-            plan.init(y_dev)
-        plan.iterate(1)
+    def run_steps(k):
+        # k iterations, re-initialising every `iters`; each call of iterate
+        # runs up to the end of the current denoise so that the library can
+        # overlap one iteration's L/Z steps with the previous E-step
+        while k > 0:
+            done = plan.mu[1]
+            if done >= iters:
+                plan.init(y_dev)
+                done = 0
+            n = min(k, iters - done)
+            plan.iterate(n)
+            k -= n
 
     plan.init(y_dev)
-    for _ in range(args.warmup):
-        step()
+    run_steps(args.warmup)
     torch.cuda.synchronize()
 
     clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
@@ -271,8 +278,7 @@ def run_ours(args, wl_name):
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    for _ in range(args.steps):
-        step()
+    run_steps(args.steps)
     t1.record(stream)
     torch.cuda.synchronize()
     barrier(world)

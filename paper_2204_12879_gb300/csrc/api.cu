@@ -159,11 +159,21 @@ cudaError_t tsvt_pre(const Dims &d, int nb, const float *x, const float *y, floa
   return launch_r2c3(d, nb, x, y, ycoef, specA, 1, tw3, st);
 }
 
+// ms2 (may be null): nb floats for the tensors' largest mean-square column
+// norms, which then set the threshold-aware tolerance tensor by tensor.
 cudaError_t tsvt_jac(const Dims &d, int nb, float t, float2 *specA, float2 *V, int *sweeps,
-                     cudaStream_t st, Prof *prof) {
+                     cudaStream_t st, Prof *prof, float *ms2 = nullptr) {
+  if (ms2) {
+    cudaError_t e = launch_group_ms2(d, nb * d.h, specA, d.h, ms2, st);
+    if (e != cudaSuccess) return e;
+  }
+  JacOpt o;
+  o.t_svt = t;
+  o.ms2 = ms2;
+  o.group = d.h;
   Span sp(prof, LRSTV_K_JACOBI, st);
   return launch_jacobi(d, nb * d.h, specA, V, t, kMaxSweeps, sweeps, prof ? prof->d_work : nullptr,
-                       st, 0, t);
+                       st, o);
 }
 
 cudaError_t tsvt_post(const Dims &d, int nb, float *out, int mode, float *G4, const float *F,
@@ -188,10 +198,11 @@ cudaError_t tsvt_post(const Dims &d, int nb, float *out, int mode, float *G4, co
 cudaError_t tsvt_core(const Dims &d, int nb, const float *x, const float *y, float ycoef, float t,
                       float *out, int mode, float *G4, const float *F, float mu, int gamma4,
                       const float2 *tw3, float2 *specA, float2 *specB, float2 *V, int *sweeps,
-                      cudaStream_t st, Prof *prof = nullptr, GemmSel gs = kSimt) {
+                      cudaStream_t st, Prof *prof = nullptr, GemmSel gs = kSimt,
+                      float *ms2 = nullptr) {
   cudaError_t e = tsvt_pre(d, nb, x, y, ycoef, tw3, specA, st, prof);
   if (e != cudaSuccess) return e;
-  if ((e = tsvt_jac(d, nb, t, specA, V, sweeps, st, prof)) != cudaSuccess) return e;
+  if ((e = tsvt_jac(d, nb, t, specA, V, sweeps, st, prof, ms2)) != cudaSuccess) return e;
   return tsvt_post(d, nb, out, mode, G4, F, mu, gamma4, tw3, specA, specB, V, st, prof, gs);
 }
 
@@ -221,6 +232,7 @@ struct lrstv_plan {
   float *Y, *L, *Z, *S, *G1, *G2, *F, *E, *G3, *G4, *T;
   float2 *specA, *specB, *V;
   float2 *Vs;     // V diag g for the reconstruction (warm start keeps V itself)
+  float *ms2;     // per gradient tensor: largest mean-square column norm of its slices
   int vwarm;      // V holds the last E-step's right singular vectors
   Tables tb;
   unsigned *res;  // kResRing x 2 residual maxima (float bits)
@@ -232,6 +244,11 @@ struct lrstv_plan {
   void *gX, *gS;
   int giters;
   cudaStream_t cap_stream;
+  // iterate_async runs the next iteration's L/T_z and Z-solve (which do not
+  // read E) on `side` while the current E-step runs: Z-solve scratch of its own
+  cudaStream_t side;
+  cudaEvent_t ev_fs, ev_side;
+  float2 *zA, *zB;
   Prof prof;
 };
 
@@ -303,10 +320,16 @@ cudaError_t tsvt_warm(lrstv_plan *pl, float ycoef, float t, float mu, int gamma4
     Wm = pl->specB;
     R = pl->specA;
   }
+  if ((e = launch_group_ms2(d, ns, Wm, d.h, pl->ms2, st)) != cudaSuccess) return e;
   {
+    JacOpt o;
+    o.warm = pl->vwarm;
+    o.t_svt = t;
+    o.ms2 = pl->ms2;
+    o.group = d.h;
     Span sp(&pl->prof, LRSTV_K_JACOBI, st);
     e = launch_jacobi(d, ns, Wm, pl->V, -1.0f, kMaxSweeps, pl->sweeps,
-                      pl->prof.on ? pl->prof.d_work : nullptr, st, pl->vwarm, t);
+                      pl->prof.on ? pl->prof.d_work : nullptr, st, o);
   }
   if (e != cudaSuccess) return e;
   {
@@ -346,6 +369,9 @@ size_t plan_layout(lrstv_plan *pl, void *base) {
   pl->specB = c.take<float2>(3 * (size_t)d.h * d.P);
   pl->V = c.take<float2>(3 * (size_t)d.h * d.nc * d.nc);
   pl->Vs = c.take<float2>(3 * (size_t)d.h * d.nc * d.nc);
+  pl->ms2 = c.take<float>(3);
+  pl->zA = c.take<float2>((size_t)d.h * d.P);
+  pl->zB = c.take<float2>((size_t)d.h * d.P);
   carve_tables(c, d, pl->tb);
   pl->res = c.take<unsigned>(2 * (size_t)kResRing);
   pl->sweeps = c.take<int>(3 * (size_t)d.h);
@@ -401,12 +427,43 @@ int init_async(lrstv_plan *pl, const float *Y, cudaStream_t st) {
   return LRSTV_OK;
 }
 
+// Steps 1 and 2 with an explicit penalty and Z-solve scratch.
+int step_l_tz_mu(lrstv_plan *pl, double mu, cudaStream_t st) {
+  Span sp(&pl->prof, LRSTV_K_L_TZ, st);
+  CK(launch_l_tz(pl->d, pl->Y, pl->S, pl->Z, pl->G1, pl->G2, pl->F, pl->G3, (float)mu, pl->prm.w,
+                 pl->L, pl->T, st));
+  return LRSTV_OK;
+}
+
+int step_z_mu(lrstv_plan *pl, double mu, float2 *A, float2 *B, cudaStream_t st) {
+  CK(zsolve_core(pl->d, 1, pl->tb, pl->T, (float)mu, pl->Z, A, B, st, &pl->prof, plan_gemm(pl)));
+  return LRSTV_OK;
+}
+
+// `iters` iterations.  Iteration k+1's L/T_z and Z-solve read S, Z, Gamma1..3
+// and F of iteration k (written by its fused F/S/multiplier step) but not E or
+// Gamma4, so they run on the plan's low-priority side stream while iteration
+// k's E-step runs on `st`; the next F/S step waits for both.  The results are
+// those of the steps run one after another, bit for bit.
 int iterate_async(lrstv_plan *pl, int iters, cudaStream_t st) {
+  int rc;
   for (int it = 0; it < iters; ++it) {
-    int rc;
-    if ((rc = lrstv_step_l_tz(pl, st)) != LRSTV_OK) return rc;
-    if ((rc = lrstv_step_z(pl, st)) != LRSTV_OK) return rc;
+    if (it == 0) {
+      if ((rc = step_l_tz_mu(pl, pl->mu, st)) != LRSTV_OK) return rc;
+      if ((rc = step_z_mu(pl, pl->mu, pl->zA, pl->zB, st)) != LRSTV_OK) return rc;
+    } else {
+      CK(cudaStreamWaitEvent(st, pl->ev_side, 0));
+    }
     if ((rc = lrstv_step_fs_dual(pl, st)) != LRSTV_OK) return rc;
+    if (it + 1 < iters) {
+      const double m = (double)pl->prm.rho * pl->mu;
+      const double mu_next = m < (double)pl->prm.mu_max ? m : (double)pl->prm.mu_max;
+      CK(cudaEventRecord(pl->ev_fs, st));
+      CK(cudaStreamWaitEvent(pl->side, pl->ev_fs, 0));
+      if ((rc = step_l_tz_mu(pl, mu_next, pl->side)) != LRSTV_OK) return rc;
+      if ((rc = step_z_mu(pl, mu_next, pl->zA, pl->zB, pl->side)) != LRSTV_OK) return rc;
+      CK(cudaEventRecord(pl->ev_side, pl->side));
+    }
     if ((rc = lrstv_step_e(pl, st)) != LRSTV_OK) return rc;
     if ((rc = lrstv_step_mu(pl)) != LRSTV_OK) return rc;
   }
@@ -506,13 +563,21 @@ int lrstv_plan_create(int n1, int n2, int n3, const lrstv_params *params, lrstv_
     return LRSTV_ERR_ALLOC;
   }
   plan_layout(pl, pl->arena);
+  int lo_prio = 0, hi_prio = 0;
   if (cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&pl->side, cudaStreamNonBlocking, lo_prio) != cudaSuccess ||
+      cudaEventCreateWithFlags(&pl->ev_fs, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&pl->ev_side, cudaEventDisableTiming) != cudaSuccess ||
       cudaMemsetAsync(pl->arena, 0, pl->arena_bytes, pl->cap_stream) != cudaSuccess ||
       launch_tables(pl->d, pl->prm.w, pl->tb.tw3, pl->tb.F1, pl->tb.G1, pl->tb.F2, pl->tb.G2,
                     pl->tb.lam1, pl->tb.lam2, pl->tb.lam3, pl->cap_stream) != cudaSuccess ||
       cudaStreamSynchronize(pl->cap_stream) != cudaSuccess) {
     cudaGetLastError();
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+    if (pl->side) cudaStreamDestroy(pl->side);
+    if (pl->ev_fs) cudaEventDestroy(pl->ev_fs);
+    if (pl->ev_side) cudaEventDestroy(pl->ev_side);
     cudaFree(pl->arena);
     delete pl;
     return LRSTV_ERR_CUDA;
@@ -531,6 +596,9 @@ int lrstv_plan_destroy(lrstv_plan *pl) {
     delete[] pl->prof.ev;
   }
   if (cudaStreamDestroy(pl->cap_stream) != cudaSuccess) rc = LRSTV_ERR_CUDA;
+  if (cudaStreamDestroy(pl->side) != cudaSuccess) rc = LRSTV_ERR_CUDA;
+  if (cudaEventDestroy(pl->ev_fs) != cudaSuccess) rc = LRSTV_ERR_CUDA;
+  if (cudaEventDestroy(pl->ev_side) != cudaSuccess) rc = LRSTV_ERR_CUDA;
   if (cudaFree(pl->arena) != cudaSuccess) rc = LRSTV_ERR_CUDA;
   delete pl;
   return rc;
@@ -566,17 +634,12 @@ int lrstv_init(lrstv_plan *pl, const float *Y, void *stream) {
 
 int lrstv_step_l_tz(lrstv_plan *pl, void *stream) {
   if (!pl) return LRSTV_ERR_ARG;
-  Span sp(&pl->prof, LRSTV_K_L_TZ, (cudaStream_t)stream);
-  CK(launch_l_tz(pl->d, pl->Y, pl->S, pl->Z, pl->G1, pl->G2, pl->F, pl->G3, (float)pl->mu,
-                 pl->prm.w, pl->L, pl->T, (cudaStream_t)stream));
-  return LRSTV_OK;
+  return step_l_tz_mu(pl, pl->mu, (cudaStream_t)stream);
 }
 
 int lrstv_step_z(lrstv_plan *pl, void *stream) {
   if (!pl) return LRSTV_ERR_ARG;
-  CK(zsolve_core(pl->d, 1, pl->tb, pl->T, (float)pl->mu, pl->Z, pl->specA, pl->specB,
-                 (cudaStream_t)stream, &pl->prof, plan_gemm(pl)));
-  return LRSTV_OK;
+  return step_z_mu(pl, pl->mu, pl->specA, pl->specB, (cudaStream_t)stream);
 }
 
 int lrstv_step_fs_dual(lrstv_plan *pl, void *stream) {
@@ -605,7 +668,7 @@ int lrstv_step_e(lrstv_plan *pl, void *stream) {
   }
   CK(tsvt_core(pl->d, 3, pl->F, pl->G4, (float)(1.0 / mu), (float)(pl->prm.alpha / mu), pl->E, 1,
                pl->G4, pl->F, (float)mu, gamma4, pl->tb.tw3, pl->specA, pl->specB, pl->V,
-               pl->sweeps, (cudaStream_t)stream, &pl->prof, plan_gemm(pl)));
+               pl->sweeps, (cudaStream_t)stream, &pl->prof, plan_gemm(pl), pl->ms2));
   return LRSTV_OK;
 }
 
@@ -830,6 +893,7 @@ int batch_e_step(lrstv_batch *b, cudaStream_t st) {
     CK(tsvt_pre(pl->d, 3, pl->F, pl->G4, (float)(1.0 / pl->mu), pl->tb.tw3,
                 warm ? pl->specB : pl->specA, st, &pl->prof));
     if (warm) CK(warm_basis(pl, pl->specB, pl->specA, pl->specA, st));
+    CK(launch_group_ms2(pl->d, 3 * pl->d.h, pl->specA, pl->d.h, pl->ms2, st));
   }
   if (b->ntasks > 0) {
     CK(cudaMemsetAsync(b->d_counter, 0, sizeof(int), st));
@@ -842,9 +906,13 @@ int batch_e_step(lrstv_batch *b, cudaStream_t st) {
   for (int k = 0; k < b->nbig; ++k) {
     lrstv_plan *pl = b->plans[b->big[k]];
     Span sp(&pl->prof, LRSTV_K_JACOBI, st);
-    const float t = (float)(pl->prm.alpha / pl->mu);
-    CK(launch_jacobi(pl->d, 3 * pl->d.h, pl->specA, pl->V, wflag ? -1.0f : t, kMaxSweeps,
-                     pl->sweeps, pl->prof.on ? pl->prof.d_work : nullptr, st, warm, t));
+    JacOpt o;
+    o.warm = warm;
+    o.t_svt = (float)(pl->prm.alpha / pl->mu);
+    o.ms2 = pl->ms2;
+    o.group = pl->d.h;
+    CK(launch_jacobi(pl->d, 3 * pl->d.h, pl->specA, pl->V, wflag ? -1.0f : o.t_svt, kMaxSweeps,
+                     pl->sweeps, pl->prof.on ? pl->prof.d_work : nullptr, st, o));
   }
   for (int i = 0; i < b->n; ++i) {
     lrstv_plan *pl = b->plans[i];
@@ -957,6 +1025,7 @@ int lrstv_batch_create(int ncubes, const int *dims, const lrstv_params *params,
         h[k].alpha = pl->prm.alpha;
         h[k].nr = d.nr;
         h[k].nc = d.nc;
+        h[k].ms2 = pl->ms2 + s / d.h;
         ++k;
       }
     }

@@ -87,13 +87,28 @@ size_t cgemm_tc_smem();
 // then the factors of the SVD A_s = (W_s diag(1/sigma)) diag(sigma) V_s^H).
 // sweeps[s] = sweeps used, -cap if the cap hit.
 // work (may be null) accumulates [pairs examined, pairs rotated].
-// warm = 1: V on entry is the unitary basis W was already multiplied by (the
-// rotations accumulate onto it) instead of the identity.  skip_t >= 0: a
-// slice with ||W||_F <= skip_t (so every singular value is at most skip_t)
-// runs no sweep, as its SVT with that threshold is zero (V stays as it came).
+// Options of a Jacobi launch.
+//  warm: V on entry is the unitary basis W was already multiplied by (the
+//    rotations accumulate onto it) instead of the identity.
+//  t_svt >= 0: the SVT threshold the factors serve.  A slice with
+//    ||W||_F <= t_svt (every singular value at most t_svt) runs no sweep, its
+//    SVT being zero (V stays as it came); and the relative tolerance grows to
+//    tol max(1, rms / t_svt), rms the columns' RMS norm.
+//  ms2 (may be null): per group of `group` consecutive slices (the Fourier
+//    slices of one tensor), the largest mean-square column norm, used as
+//    rms^2 instead of the slice's own (launch_group_ms2).
+struct JacOpt {
+  int warm = 0;
+  float t_svt = -1.0f;
+  const float *ms2 = nullptr;
+  int group = 1;
+};
 cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, float t,
                           int max_sweeps, int *sweeps, unsigned long long *work,
-                          cudaStream_t st, int warm = 0, float skip_t = -1.0f);
+                          cudaStream_t st, const JacOpt &opt = JacOpt());
+// ms2[g] = max over slices s of group g (s / group == g) of ||W_s||_F^2 / nc.
+cudaError_t launch_group_ms2(const Dims &d, int nslices, const float2 *W, int group, float *ms2,
+                             cudaStream_t st);
 
 // sigma_i = |w_i| of every working matrix (into sig, nc doubles a slice, may be
 // null) and Vs = V diag(g), g = max(1 - t / sigma, 0): the Jacobi epilogue's
@@ -113,6 +128,7 @@ struct SliceTask {
   int *sweeps;
   float alpha;
   int nr, nc;
+  const float *ms2;  // the slice's group value of launch_group_ms2 (may be null)
 };
 // Largest slice height the persistent batch kernel takes.
 constexpr int kBatchMaxNr = 224;  // keeps the persistent kernel free of spills

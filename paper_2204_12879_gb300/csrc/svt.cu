@@ -48,7 +48,10 @@ template <int R>
 __global__ void __launch_bounds__(R <= 8 ? 1024 : 512)
     k_jacobi(int nr, int nc, size_t wstride, size_t vstride, float2 *W_all, float2 *V_all,
              float t, int max_sweeps, float tol, float negl_rel, int *__restrict__ sweeps_out,
-             unsigned long long *__restrict__ work, int warm, float skip_t) {
+             unsigned long long *__restrict__ work, JacOpt o) {
+  const int warm = o.warm;
+  const float skip_t = o.t_svt;
+  const float gms2 = o.ms2 ? o.ms2[blockIdx.x / o.group] : -1.0f;
   float2 *W = W_all + (size_t)blockIdx.x * wstride;
   float2 *V = V_all + (size_t)blockIdx.x * vstride;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -87,6 +90,18 @@ __global__ void __launch_bounds__(R <= 8 ? 1024 : 512)
   if (skip_t >= 0.0f && s_red[0] <= skip_t * skip_t) {
     sweeps = 0;
     converged = true;
+  }
+  // A pair left with relative inner product g moves the SVT result by at most
+  // about t g (both values kept: t g s_p / (s_p + s_q); one kept: g s_cut <= t g;
+  // both cut: nothing), so with the threshold t below the columns' RMS norm the
+  // relative tolerance is raised to tol rms / t: the absolute error stays at
+  // the level tol rms that a threshold near the RMS norm already allows.  The
+  // RMS norm is the largest over the slices of one tensor when it is given
+  // (ms2): the inverse DFT mixes the slices, so all of them are resolved to
+  // the same absolute precision.
+  if (skip_t > 0.0f && nc > 0) {
+    const float ms2 = gms2 >= 0.0f ? gms2 : s_red[0] / (float)nc;
+    tol = fmaxf(tol, tol * (sqrtf(ms2) / skip_t));
   }
   for (int sweep = 1; sweep <= max_sweeps && !converged; ++sweep) {
     if (tid == 0) s_rot = 0;
@@ -603,7 +618,8 @@ template <int KP>
 __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float2 *V, float t,
                                                 int max_sweeps, float tol, float negl_rel,
                                                 int *sweeps_slot, unsigned long long *work,
-                                                float4 *smem, int warm, float skip_t) {
+                                                float4 *smem, int warm, float skip_t,
+                                                float gms2) {
   constexpr int KPF = PkShape<KP>::KPF;
   constexpr int LD2 = PkShape<KP>::LD2;
   float4 *sW = smem;               // panel a (own pairs), then panel b: W
@@ -642,6 +658,18 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
   if (skip_t >= 0.0f && s_red[0] <= skip_t * skip_t) {
     sweeps = 0;
     converged = true;
+  }
+  // A pair left with relative inner product g moves the SVT result by at most
+  // about t g (both values kept: t g s_p / (s_p + s_q); one kept: g s_cut <= t g;
+  // both cut: nothing), so with the threshold t below the columns' RMS norm the
+  // relative tolerance is raised to tol rms / t: the absolute error stays at
+  // the level tol rms that a threshold near the RMS norm already allows.  The
+  // RMS norm is the largest over the slices of one tensor when it is given
+  // (ms2): the inverse DFT mixes the slices, so all of them are resolved to
+  // the same absolute precision.
+  if (skip_t > 0.0f && nc > 0) {
+    const float ms2 = gms2 >= 0.0f ? gms2 : s_red[0] / (float)nc;
+    tol = fmaxf(tol, tol * (sqrtf(ms2) / skip_t));
   }
   float4 aW[KP], aV[KP], bW[KP];
   for (int sweep = 1; sweep <= max_sweeps && !converged; ++sweep) {
@@ -791,11 +819,12 @@ template <int KP>
 __global__ void __launch_bounds__(kHW * 32, KP <= 2 ? 2 : 1)
     k_jacobi_pk(int nr, int nc, size_t wstride, size_t vstride, float2 *W_all, float2 *V_all,
                 float t, int max_sweeps, float tol, float negl_rel, int *__restrict__ sweeps_out,
-                unsigned long long *__restrict__ work, int warm, float skip_t) {
+                unsigned long long *__restrict__ work, JacOpt o) {
   extern __shared__ float4 smem_f4[];
   jacobi_pk_slice<KP>(nr, nc, W_all + (size_t)blockIdx.x * wstride,
                       V_all + (size_t)blockIdx.x * vstride, t, max_sweeps, tol, negl_rel,
-                      sweeps_out + blockIdx.x, work, smem_f4, warm, skip_t);
+                      sweeps_out + blockIdx.x, work, smem_f4, o.warm, o.t_svt,
+                      o.ms2 ? o.ms2[blockIdx.x / o.group] : -1.0f);
 }
 
 // Persistent kernel for a batch of cubes: each CTA takes the next slice from
@@ -822,26 +851,26 @@ __global__ void __launch_bounds__(kHW * 32, 1)
     const float negl = ((float)tk.nr * eps) * ((float)tk.nr * eps);
     const int KP = (tk.nr + 31) / 32;
     if (KP <= 1)
-      jacobi_pk_slice<1>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt);
+      jacobi_pk_slice<1>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
     else if (KP <= 2)
-      jacobi_pk_slice<2>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt);
+      jacobi_pk_slice<2>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
     else if (KP <= 4)
-      jacobi_pk_slice<4>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt);
+      jacobi_pk_slice<4>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
     else
-      jacobi_pk_slice<7>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt);
+      jacobi_pk_slice<7>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
   }
 }
 
 template <int KP>
 cudaError_t launch_pk(int nslices, int nr, int nc, size_t ws, size_t vs, float2 *W, float2 *V,
                       float t, int max_sweeps, float tol, float negl, int *sweeps,
-                      unsigned long long *work, int warm, float skip_t, cudaStream_t st) {
+                      unsigned long long *work, const JacOpt &o, cudaStream_t st) {
   const size_t smem = sizeof(float4) * 3 * (size_t)kPW * PkShape<KP>::LD2;
   cudaError_t e = cudaFuncSetAttribute(k_jacobi_pk<KP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_jacobi_pk<KP><<<nslices, kHW * 32, smem, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl,
-                                                   sweeps, work, warm, skip_t);
+                                                   sweeps, work, o);
   return cudaGetLastError();
 }
 
@@ -884,6 +913,29 @@ __global__ void __launch_bounds__(512)
   }
 }
 
+// Mean-square column norm ||W_s||_F^2 / nc of every slice, reduced to the
+// largest over each group of `group` consecutive slices (atomic max on the
+// bits of non-negative floats; the group slots start at zero).
+__global__ void __launch_bounds__(256)
+    k_group_ms2(int nr, int nc, size_t wstride, const float2 *__restrict__ W, int group,
+                unsigned *__restrict__ gmax) {
+  __shared__ float s_red[8];
+  const float2 *Ws = W + (size_t)blockIdx.x * wstride;
+  float part = 0.0f;
+  for (size_t e = threadIdx.x; e < (size_t)nr * nc; e += blockDim.x) {
+    const float2 x = Ws[e];
+    part = fmaf(x.x, x.x, fmaf(x.y, x.y, part));
+  }
+  part = warp_sum(part);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float v = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s_red[w];
+    atomicMax(gmax + blockIdx.x / group, __float_as_uint(v / (float)nc));
+  }
+}
+
 // One Newton-Schulz step towards the nearest unitary matrix:
 // V := V (3 I - V^H V) / 2 = 1.5 V - 0.5 D with D = (V V^H) V given.
 __global__ void k_ns_update(int nc, int nslices, size_t dstride, float2 *__restrict__ V,
@@ -903,6 +955,16 @@ cudaError_t launch_sigma_scale(const Dims &d, int nslices, const float2 *W, cons
                                float t, double *sig, float2 *Vs, cudaStream_t st) {
   if (nslices <= 0) return cudaSuccess;
   k_sigma_scale<<<nslices, 512, 0, st>>>(d.nr, d.nc, d.P, W, V, t, sig, Vs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_ms2(const Dims &d, int nslices, const float2 *W, int group, float *ms2,
+                             cudaStream_t st) {
+  if (nslices <= 0) return cudaSuccess;
+  const int ngroups = (nslices + group - 1) / group;
+  cudaError_t e = cudaMemsetAsync(ms2, 0, sizeof(float) * ngroups, st);
+  if (e != cudaSuccess) return e;
+  k_group_ms2<<<nslices, 256, 0, st>>>(d.nr, d.nc, d.P, W, group, (unsigned *)ms2);
   return cudaGetLastError();
 }
 
@@ -940,7 +1002,8 @@ cudaError_t launch_jacobi_batch(const SliceTask *tasks, int ntasks, int *counter
 
 cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, float t,
                           int max_sweeps, int *sweeps, unsigned long long *work,
-                          cudaStream_t st, int warm, float skip_t) {
+                          cudaStream_t st, const JacOpt &o) {
+  const int warm = o.warm;
   const int nr = d.nr, nc = d.nc;
   if (nslices <= 0) return cudaSuccess;
   const int np = nc + (nc & 1);
@@ -956,11 +1019,11 @@ cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, floa
   const size_t ws = d.P, vs = (size_t)nc * nc;
   if (nr <= 256 && nc >= 2) {
     const int KP = (nr + 31) / 32;  // row pairs per lane of a half-warp
-    if (KP <= 1) return launch_pk<1>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, skip_t, st);
-    if (KP <= 2) return launch_pk<2>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, skip_t, st);
-    if (KP <= 4) return launch_pk<4>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, skip_t, st);
-    if (KP <= 7) return launch_pk<7>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, skip_t, st);
-    return launch_pk<8>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, skip_t, st);
+    if (KP <= 1) return launch_pk<1>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
+    if (KP <= 2) return launch_pk<2>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
+    if (KP <= 4) return launch_pk<4>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
+    if (KP <= 7) return launch_pk<7>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
+    return launch_pk<8>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
   }
   if (R <= 8 && nc >= 2 && !warm) {
     if (R <= 1) return launch_panel<1>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
@@ -969,11 +1032,11 @@ cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, floa
     return launch_panel<8>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
   }
   dim3 grid(nslices), block(32 * nw);
-  if (R <= 1) k_jacobi<1><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, skip_t);
-  else if (R <= 2) k_jacobi<2><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, skip_t);
-  else if (R <= 4) k_jacobi<4><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, skip_t);
-  else if (R <= 8) k_jacobi<8><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, skip_t);
-  else if (R <= 16) k_jacobi<16><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, warm, skip_t);
+  if (R <= 1) k_jacobi<1><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o);
+  else if (R <= 2) k_jacobi<2><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o);
+  else if (R <= 4) k_jacobi<4><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o);
+  else if (R <= 8) k_jacobi<8><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o);
+  else if (R <= 16) k_jacobi<16><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

@@ -382,6 +382,7 @@ struct lrstv_unroll {
   double *sig;         // K x (3 B h) x nc
   float2 *Hs;          // 3 B h nc^2 complex: thresholded V, then H / K'
   int *sweeps;         // K x 3 B h
+  float *ms2;          // 3 B: per gradient tensor, largest mean-square column norm
   int *gemm_err;
   Tables tb;
   double *theta;       // host copy of the last forward's scalars (K x 4)
@@ -426,6 +427,7 @@ size_t unroll_layout(lrstv_unroll *u, void *base) {
   u->sig = c.take<double>((size_t)u->K * ns * d.nc);
   u->Hs = c.take<float2>(ns * d.nc * d.nc);
   u->sweeps = c.take<int>((size_t)u->K * ns);
+  u->ms2 = c.take<float>((size_t)3 * u->B);
   u->gemm_err = c.take<int>(1);
   carve_tables(c, d, u->tb);
   return c.off;
@@ -500,8 +502,14 @@ int unroll_forward(lrstv_unroll *u, cudaStream_t st) {
       UCK(launch_r2c3(d, 3 * B, s.F, s.G4, (float)(1.0 / mu), Wk, 1, u->tb.tw3, st));
     }
     const float t = (float)(alpha / mu);
+    UCK(launch_group_ms2(d, (int)ns, Wk, d.h, u->ms2, st));
+    JacOpt o;
+    o.warm = warm;
+    o.t_svt = t;
+    o.ms2 = u->ms2;
+    o.group = d.h;
     UCK(launch_jacobi(d, (int)ns, Wk, Vk, -1.0f, kMaxSweeps, u->sweeps + (size_t)k * ns, nullptr,
-                      st, warm, t));
+                      st, o));
     UCK(launch_sigma_scale(d, (int)ns, Wk, Vk, t, sk, u->Hs, st));
     CGemm g{};
     g.A = Wk; g.sA = (long long)d.P; g.lda = d.nr;

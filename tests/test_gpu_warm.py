@@ -30,7 +30,8 @@ def _noisy(shape, seed):
     return f32(clean), f32(noisy)
 
 
-@pytest.mark.parametrize("shape,iters", [((32, 32, 16), 20), ((29, 37, 10), 15), ((70, 65, 9), 8)])
+@pytest.mark.parametrize("shape,iters", [((32, 32, 16), 20), ((29, 37, 10), 15), ((70, 65, 9), 8),
+                                         ((64, 64, 31), 50)])
 def test_warm_run_matches_oracle(L, orc, shape, iters):
     from synthetic import mpsnr
     clean, Y = _noisy(shape, 11)
@@ -44,6 +45,25 @@ def test_warm_run_matches_oracle(L, orc, shape, iters):
     ost.iterate(iters)
     assert maxabs(X, ost.X) <= 1e-4
     assert maxabs(S, ost.get("S")) <= 1e-4
+    assert abs(mpsnr(X, clean) - mpsnr(ost.X, clean)) <= 0.01
+    print(shape, iters, "max-abs", maxabs(X, ost.X), "dMPSNR", mpsnr(X, clean) - mpsnr(ost.X, clean))
+
+
+def test_cold_run_50_iterations_matches_oracle(L, orc):
+    """All 50 iterations of a denoise, where the late thresholds t sit far
+    below the slices' RMS column norm (the regime of the threshold-aware
+    Jacobi tolerance)."""
+    from synthetic import mpsnr
+    shape = (64, 64, 31)
+    clean, Y = _noisy(shape, 12)
+    p = L.Params.make(64, 64, max_iter=50)
+    with L.Plan(*shape, p) as pl:
+        X, S = pl.run(dev(Y))
+        X = host(X, shape)
+    ost = orc.State(Y, orc.Params(n1=64, n2=64))
+    ost.iterate(50)
+    print("cold 50 it max-abs", maxabs(X, ost.X), "dMPSNR", mpsnr(X, clean) - mpsnr(ost.X, clean))
+    assert maxabs(X, ost.X) <= 1e-4
     assert abs(mpsnr(X, clean) - mpsnr(ost.X, clean)) <= 0.01
 
 
