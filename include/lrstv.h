@@ -175,6 +175,10 @@ int lrstv_iterate(lrstv_plan *plan, int iters, void *stream);
 
 /* Synchronises `stream` and reports residuals, mu and Jacobi status. */
 int lrstv_get_stats(lrstv_plan *plan, lrstv_stats *stats, void *stream);
+/* Per-slice Jacobi sweep counts of the last E-step (synchronises `stream`):
+ * count must be 3 (n3/2 + 1); entry n (n3/2 + 1) + k is Fourier slice k of
+ * gradient tensor n, negative if it hit the sweep cap, 0 if it needed none. */
+int lrstv_get_slice_sweeps(lrstv_plan *plan, int *sweeps_host, int count, void *stream);
 /* Copies a state block to / from caller device memory (N or 3N floats,
  * device-to-device, stream-ordered).  With lrstv_get_mu / lrstv_set_mu this
  * checkpoints and resumes an ADMM run (mu is kept in double precision, so a

@@ -685,6 +685,13 @@ int lrstv_iterate(lrstv_plan *pl, int iters, void *stream) {
   return iterate_async(pl, iters, (cudaStream_t)stream);
 }
 
+int lrstv_get_slice_sweeps(lrstv_plan *pl, int *sweeps_host, int count, void *stream) {
+  if (!pl || !sweeps_host || count != 3 * pl->d.h) return LRSTV_ERR_ARG;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  CK(cudaMemcpy(sweeps_host, pl->sweeps, sizeof(int) * count, cudaMemcpyDeviceToHost));
+  return LRSTV_OK;
+}
+
 int lrstv_get_stats(lrstv_plan *pl, lrstv_stats *stats, void *stream) {
   if (!pl || !stats) return LRSTV_ERR_ARG;
   CK(cudaStreamSynchronize((cudaStream_t)stream));

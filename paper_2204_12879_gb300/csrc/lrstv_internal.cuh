@@ -131,7 +131,7 @@ struct SliceTask {
   const float *ms2;  // the slice's group value of launch_group_ms2 (may be null)
 };
 // Largest slice height the persistent batch kernel takes.
-constexpr int kBatchMaxNr = 224;  // keeps the persistent kernel free of spills
+constexpr int kBatchMaxNr = 224;  // keeps the persistent kernel to a few bytes of spills
 size_t jacobi_batch_smem(int max_nr);
 // Persistent work-list Jacobi over `ntasks` slices; *counter must be 0.  warm:
 // as launch_jacobi; keep: V left unscaled (threshold taken as negative).

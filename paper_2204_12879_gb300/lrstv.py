@@ -108,6 +108,7 @@ _SIGS = {
     "lrstv_step_mu": [_P],
     "lrstv_iterate": [_P, _I, _P],
     "lrstv_get_stats": [_P, ctypes.POINTER(Stats), _P],
+    "lrstv_get_slice_sweeps": [_P, ctypes.POINTER(_I), _I, _P],
     "lrstv_state_get": [_P, _I, _P, _P],
     "lrstv_state_set": [_P, _I, _P, _P],
     "lrstv_get_mu": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)],
@@ -276,6 +277,15 @@ class Plan:
         s = Stats()
         _call("lrstv_get_stats", self._h, ctypes.byref(s), _stream(stream))
         return s
+
+    def slice_sweeps(self, stream=None):
+        """Per-slice Jacobi sweep counts of the last E-step, shape (3, n3//2 + 1)."""
+        import numpy as np
+        h = self.shape[2] // 2 + 1
+        out = np.zeros(3 * h, dtype=np.int32)
+        _call("lrstv_get_slice_sweeps", self._h, out.ctypes.data_as(ctypes.POINTER(_I)), 3 * h,
+              _stream(stream))
+        return out.reshape(3, h)
 
     def get(self, name, stream=None):
         n = 3 * self.N if name in _TRIPLE else self.N
