@@ -7,7 +7,8 @@ legs of ``bench.py`` may import it; the product path
 (``paper_2204_12879_gb300``) never does.  It shares no code with the CUDA
 path: the arithmetic lives in ``lrstv_oracle.c`` (plain C, FP64, OpenMP),
 loaded here through ctypes, and, for the unrolled iteration and its
-hand-derived adjoint, in ``adjoint.py`` (numpy, FP64).
+hand-derived adjoint, in ``adjoint.py`` (numpy, FP64), and for the Tucker
+(HOOI) L-update of the full TDLRSTV model in ``tucker.py`` (numpy, FP64).
 """
 from .oracle import *  # noqa: F401,F403
 from .oracle import __all__  # noqa: F401
