@@ -53,6 +53,13 @@ typedef enum lrstv_status {
                                         Newton-Schulz step) instead of the identity: the same
                                         t-SVT to rounding, in fewer sweeps.  The first E-step after
                                         lrstv_init or lrstv_state_set starts cold. */
+#define LRSTV_FLAG_ISO_TV 64u        /* isotropic LRSTV (eq. CRSSTV_iso, read with the per-pixel
+                                        2-norm of the isotropic TV of Section II-B and
+                                        tau_n = (tau w_n)^2): the F-update thresholds each voxel's
+                                        3-vector (F_1, F_2, F_3) by its 2-norm,
+                                        F_v = x_v max(1 - thr / |x_v|_2, 0), thr as for the
+                                        anisotropic threshold (tau/mu, or tau/(2 mu) with
+                                        LRSTV_FLAG_F_THRESH_EXACT).  Plans and batches only. */
 
 /* Scalars of Algorithm 1 (Section III-C; parameter roles in Section IV-D).
  *  tau     weight of ||D_w L||_1 (gradient sparsity)
@@ -97,6 +104,26 @@ const char *lrstv_status_string(int status);
  * bound the Jacobi working matrix). */
 int lrstv_max_spatial(void);
 
+/* ------------------------------------------------- full TDLRSTV (Tucker) */
+/* Turns the L-update of a plan into the Tucker projection of the full TDLRSTV
+ * model (eq. TDLRSTV, Section III-C step 1, eq. X_solution with the Tucker-3
+ * model of eq. LRTAmodel): L = X x1 U1 U1^T x2 U2 U2^T x3 U3 U3^T with X =
+ * 1/2 (Y - S + Z + (Gamma1 - Gamma2)/mu) and multilinear ranks
+ * ranks = {r1, r2, r3} (1 <= r_n <= n_n; the paper sets r1 = 0.8 n1,
+ * r2 = 0.8 n2 and tunes r3).  The factors come from one HOOI sweep per ADMM
+ * iteration (U1, U2, U3 in turn), started from the previous iteration's
+ * factors, or from the truncated HOSVD of X in the first iteration after
+ * lrstv_init or lrstv_state_set; with LRSTV_FLAG_WARM_START each mode's
+ * eigen-solve also starts from that mode's previous eigenvectors.  The six
+ * eigen-solves' sweep counts join lrstv_stats (a capped one counts as
+ * unconverged).  ranks NULL or {0, 0, 0}: back to the plain
+ * L-update.  Makes a second device allocation owned by the plan (freed by
+ * lrstv_plan_destroy or by turning the mode off); synchronises the device.
+ * ERR_ARG for ranks out of range, ERR_SHAPE for n3 > lrstv_max_spatial() (each
+ * mode's Gram matrix is diagonalised by the Jacobi kernel), ERR_ALLOC if the
+ * allocation fails. */
+int lrstv_plan_set_tucker(lrstv_plan *plan, const int ranks[3]);
+
 /* ------------------------------------------------------------- profiling */
 /* Kernels a plan launches (lrstv_profile indices). */
 typedef enum lrstv_kernel {
@@ -111,7 +138,9 @@ typedef enum lrstv_kernel {
   LRSTV_K_C2R_E = 8,    /* inverse mode-3 DFT -> E, Gamma4 update         */
   LRSTV_K_WARM_E = 9,   /* warm start: Newton-Schulz step on V, W = A V,
                            sigma and V diag g (LRSTV_FLAG_WARM_START)     */
-  LRSTV_NKERNEL = 10
+  LRSTV_K_TUCKER = 10,  /* Tucker (HOOI) L-update and T_z from the projected L,
+                           one entry per L-update (lrstv_plan_set_tucker) */
+  LRSTV_NKERNEL = 11
 } lrstv_kernel;
 
 typedef struct lrstv_profile {

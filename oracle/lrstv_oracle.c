@@ -375,8 +375,21 @@ void orc_step_z(double *st, int n1, int n2, int n3, const double *p, double mu) 
   free(T);
 }
 
+/* Group soft threshold (the prox of d ||.||_2 on R^m): x scaled by
+ * max(1 - d / ||x||_2, 0), zero when ||x||_2 <= d. */
+void orc_group_soft(double *x, int m, double d) {
+  double s = 0.0;
+  for (int i = 0; i < m; ++i) s += x[i] * x[i];
+  const double nrm = sqrt(s);
+  const double g = nrm > d ? 1.0 - d / nrm : 0.0;
+  for (int i = 0; i < m; ++i) x[i] *= g;
+}
+
 /* Step 3 (eq. F_solution): F = R_{tau/mu}((T1 + T2)/2),
- * T1 = D_w Z + Gamma3/mu, T2 = E + Gamma4/mu. */
+ * T1 = D_w Z + Gamma3/mu, T2 = E + Gamma4/mu.  Isotropic LRSTV (eq. CRSSTV_iso,
+ * with the per-pixel 2-norm of the isotropic TV of Section II-B and
+ * tau_n = (tau w_n)^2): the soft threshold becomes the group threshold of the
+ * 3-vector (F_1, F_2, F_3) at each voxel. */
 void orc_step_f(double *st, int n1, int n2, int n3, const double *p, double mu, int flags) {
   size_t N = vol(n1, n2, n3);
   double *g = (double *)malloc(sizeof(double) * 3 * N);
@@ -384,6 +397,20 @@ void orc_step_f(double *st, int n1, int n2, int n3, const double *p, double mu, 
   double thr = (flags & ORC_FLAG_F_THRESH_EXACT) ? p[ORC_P_TAU] / (2.0 * mu) : p[ORC_P_TAU] / mu;
   double *F = BLK(st, ORC_F);
   const double *E = BLK(st, ORC_E), *G3 = BLK(st, ORC_G3), *G4 = BLK(st, ORC_G4);
+  if (flags & ORC_FLAG_ISO_TV) {
+#pragma omp parallel for schedule(static)
+    for (size_t v = 0; v < N; ++v) {
+      double x[3];
+      for (int n = 0; n < 3; ++n) {
+        const size_t u = v + (size_t)n * N;
+        x[n] = 0.5 * ((g[u] + G3[u] / mu) + (E[u] + G4[u] / mu));
+      }
+      orc_group_soft(x, 3, thr);
+      for (int n = 0; n < 3; ++n) F[v + (size_t)n * N] = x[n];
+    }
+    free(g);
+    return;
+  }
 #pragma omp parallel for schedule(static)
   for (size_t v = 0; v < 3 * N; ++v) {
     double t1 = g[v] + G3[v] / mu, t2 = E[v] + G4[v] / mu;

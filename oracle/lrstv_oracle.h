@@ -42,6 +42,8 @@ enum {
 /* flags */
 #define ORC_FLAG_F_THRESH_EXACT 1 /* F threshold tau/(2 mu) instead of the printed tau/mu */
 #define ORC_FLAG_NO_GAMMA4      2 /* literal multiplier list: Gamma4 never updated      */
+#define ORC_FLAG_ISO_TV         4 /* isotropic LRSTV (eq. CRSSTV_iso): F thresholded per voxel
+                                     as the 3-vector (F_1, F_2, F_3), by its 2-norm          */
 
 /* Circular forward differences g_n = w_n D_n x, n = 1..3; g holds 3N doubles. */
 void orc_diff(const double *x, int n1, int n2, int n3, const double *w, double *g);
@@ -61,6 +63,8 @@ void orc_zsolve(const double *T, int n1, int n2, int n3, const double *w, double
 
 /* Soft threshold R_d(x) = sign(x) max(|x| - d, 0). */
 double orc_soft(double x, double d);
+/* Group soft threshold of x (m entries) in place: x max(1 - d/||x||_2, 0). */
+void orc_group_soft(double *x, int m, double d);
 
 /* SVT of one complex m x n column-major matrix, in place (one-sided Jacobi).
  * Returns the number of sweeps used (negative if the sweep cap was hit). */

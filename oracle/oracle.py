@@ -17,8 +17,9 @@ import numpy as np
 
 __all__ = [
     "build_oracle", "lib", "Params", "diff", "diff_adjoint", "dft_axis", "dft3",
-    "pz", "zsolve", "soft", "svt_matrix", "singular_values", "tsvt",
+    "pz", "zsolve", "soft", "group_soft", "svt_matrix", "singular_values", "tsvt",
     "State", "NSTATE", "BLOCKS", "num_threads", "mpsnr",
+    "FLAG_F_THRESH_EXACT", "FLAG_NO_GAMMA4", "FLAG_ISO_TV",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -29,6 +30,7 @@ _lib = None
 
 FLAG_F_THRESH_EXACT = 1
 FLAG_NO_GAMMA4 = 2
+FLAG_ISO_TV = 4
 
 NSTATE = 18
 BLOCKS = {"Y": 0, "L": 1, "Z": 2, "S": 3, "G1": 4, "G2": 5,
@@ -64,6 +66,7 @@ def load_library(path: str):
             "orc_pz": (None, [i, i, i, D, D]),
             "orc_zsolve": (None, [D, i, i, i, D, d, D]),
             "orc_soft": (d, [d, d]),
+            "orc_group_soft": (None, [D, i, d]),
             "orc_svt_matrix": (i, [D, i, i, d]),
             "orc_singular_values": (i, [D, i, i, D]),
             "orc_tsvt": (i, [D, i, i, i, d, D]),
@@ -186,6 +189,18 @@ def soft(x, d):
     """R_d(x) = sign(x) max(|x| - d, 0) (Section III-C, step 3)."""
     f = lib().orc_soft
     return np.vectorize(lambda t: f(float(t), float(d)))(np.asarray(x, np.float64))
+
+
+def group_soft(x, d):
+    """The prox of d ||.||_2 applied to each row of x (the isotropic
+    F-update's group threshold, eq. CRSSTV_iso)."""
+    x = np.array(x, dtype=np.float64, ndmin=2)
+    out = np.empty_like(x)
+    for k in range(x.shape[0]):
+        row = np.ascontiguousarray(x[k])
+        lib().orc_group_soft(_p(row), row.size, float(d))
+        out[k] = row
+    return out
 
 
 def svt_matrix(A, t):

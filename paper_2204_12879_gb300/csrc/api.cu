@@ -57,7 +57,8 @@ int check_params(const lrstv_params *p) {
     if (!isfinite(x) || x < 0.0f) return LRSTV_ERR_ARG;
   if (!(p->mu0 > 0.0f) || !(p->mu_max >= p->mu0) || p->max_iter < 0) return LRSTV_ERR_ARG;
   if (p->flags & ~(unsigned)(LRSTV_FLAG_F_THRESH_EXACT | LRSTV_FLAG_NO_GAMMA4 | LRSTV_FLAG_GRAPH |
-                             LRSTV_FLAG_STRICT | LRSTV_FLAG_SIMT_GEMM | LRSTV_FLAG_WARM_START))
+                             LRSTV_FLAG_STRICT | LRSTV_FLAG_SIMT_GEMM | LRSTV_FLAG_WARM_START |
+                             LRSTV_FLAG_ISO_TV))
     return LRSTV_ERR_ARG;
   return LRSTV_OK;
 }
@@ -249,6 +250,10 @@ struct lrstv_plan {
   cudaStream_t side;
   cudaEvent_t ev_fs, ev_side;
   float2 *zA, *zB;
+  // Tucker (HOOI) L-update of the full TDLRSTV model (lrstv_plan_set_tucker)
+  int tucker;
+  void *tk_mem;
+  TuckerWs tk;
   Prof prof;
 };
 
@@ -424,14 +429,27 @@ int init_async(lrstv_plan *pl, const float *Y, cudaStream_t st) {
   pl->mu = pl->prm.mu0;
   pl->iter = 0;
   pl->vwarm = 0;
+  pl->tk.valid = 0;
+  pl->tk.vvalid[0] = pl->tk.vvalid[1] = pl->tk.vvalid[2] = 0;
+  if (pl->tucker) CK(cudaMemsetAsync(pl->tk.sweeps, 0, sizeof(int) * kTuckerSweepSlots, st));
   return LRSTV_OK;
 }
 
 // Steps 1 and 2 with an explicit penalty and Z-solve scratch.
 int step_l_tz_mu(lrstv_plan *pl, double mu, cudaStream_t st) {
-  Span sp(&pl->prof, LRSTV_K_L_TZ, st);
-  CK(launch_l_tz(pl->d, pl->Y, pl->S, pl->Z, pl->G1, pl->G2, pl->F, pl->G3, (float)mu, pl->prm.w,
-                 pl->L, pl->T, st));
+  {
+    Span sp(&pl->prof, LRSTV_K_L_TZ, st);
+    CK(launch_l_tz(pl->d, pl->Y, pl->S, pl->Z, pl->G1, pl->G2, pl->F, pl->G3, (float)mu, pl->prm.w,
+                   pl->L, pl->T, st));
+  }
+  if (pl->tucker) {
+    // the target just written to L is replaced by its Tucker projection, and
+    // T_z is formed again from the projected L
+    Span sp(&pl->prof, LRSTV_K_TUCKER, st);
+    pl->tk.warm = (pl->prm.flags & LRSTV_FLAG_WARM_START) != 0;
+    CK(tucker_project(pl->tk, pl->L, st));
+    CK(launch_tz(pl->d, pl->L, pl->G2, pl->F, pl->G3, (float)mu, pl->prm.w, pl->T, st));
+  }
   return LRSTV_OK;
 }
 
@@ -499,7 +517,8 @@ int lrstv_max_spatial(void) { return kMaxSpatial; }
 
 const char *lrstv_kernel_name(int k) {
   static const char *names[LRSTV_NKERNEL] = {"l_tz", "r2c_z", "cgemm_z", "c2r_z", "fs_dual",
-                                             "r2c_e", "jacobi", "cgemm_e", "c2r_e", "warm_e"};
+                                             "r2c_e", "jacobi", "cgemm_e", "c2r_e", "warm_e",
+                                             "tucker"};
   return (k >= 0 && k < LRSTV_NKERNEL) ? names[k] : "unknown";
 }
 
@@ -600,8 +619,36 @@ int lrstv_plan_destroy(lrstv_plan *pl) {
   if (cudaEventDestroy(pl->ev_fs) != cudaSuccess) rc = LRSTV_ERR_CUDA;
   if (cudaEventDestroy(pl->ev_side) != cudaSuccess) rc = LRSTV_ERR_CUDA;
   if (cudaFree(pl->arena) != cudaSuccess) rc = LRSTV_ERR_CUDA;
+  if (pl->tk_mem && cudaFree(pl->tk_mem) != cudaSuccess) rc = LRSTV_ERR_CUDA;
   delete pl;
   return rc;
+}
+
+int lrstv_plan_set_tucker(lrstv_plan *pl, const int ranks[3]) {
+  if (!pl) return LRSTV_ERR_ARG;
+  const bool off = !ranks || (ranks[0] == 0 && ranks[1] == 0 && ranks[2] == 0);
+  const int n[3] = {pl->d.n1, pl->d.n2, pl->d.n3};
+  if (!off) {
+    for (int i = 0; i < 3; ++i)
+      if (ranks[i] < 1 || ranks[i] > n[i]) return LRSTV_ERR_ARG;
+    if (n[2] > kMaxSpatial) return LRSTV_ERR_SHAPE;  // each mode's Gram goes through the Jacobi
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) return LRSTV_ERR_CUDA;
+  drop_graph(pl);
+  if (pl->tk_mem) cudaFree(pl->tk_mem);
+  pl->tk_mem = nullptr;
+  pl->tucker = 0;
+  if (off) return LRSTV_OK;
+  const size_t bytes = tucker_ws_bytes(n[0], n[1], n[2], ranks);
+  if (cudaMalloc(&pl->tk_mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    pl->tk_mem = nullptr;
+    return LRSTV_ERR_ALLOC;
+  }
+  tucker_carve(pl->tk, pl->tk_mem, n[0], n[1], n[2], ranks);
+  if (cudaMemset(pl->tk.sweeps, 0, sizeof(int) * kTuckerSweepSlots) != cudaSuccess) return LRSTV_ERR_CUDA;
+  pl->tucker = 1;
+  return LRSTV_OK;
 }
 
 int lrstv_plan_bytes(const lrstv_plan *pl, size_t *bytes) {
@@ -653,7 +700,8 @@ int lrstv_step_fs_dual(lrstv_plan *pl, void *stream) {
   CK(cudaMemsetAsync(slot, 0, 2 * sizeof(unsigned), st));
   Span sp(&pl->prof, LRSTV_K_FS_DUAL, st);
   CK(launch_fs_dual(pl->d, pl->Y, pl->L, pl->Z, pl->S, pl->G1, pl->G2, pl->F, pl->E, pl->G3,
-                    pl->G4, (float)mu, (float)thr_f, (float)thr_s, pl->prm.w, slot, st));
+                    pl->G4, (float)mu, (float)thr_f, (float)thr_s, pl->prm.w, slot, st,
+                    (pl->prm.flags & LRSTV_FLAG_ISO_TV) ? 1 : 0));
   return LRSTV_OK;
 }
 
@@ -726,6 +774,15 @@ int lrstv_get_stats(lrstv_plan *pl, lrstv_stats *stats, void *stream) {
     if (a > stats->jacobi_max_sweeps) stats->jacobi_max_sweeps = a;
   }
   delete[] sw;
+  if (pl->tucker) {  // the eigen-solves of the Tucker L-update count alongside
+    int tsw[kTuckerSweepSlots];
+    CK(cudaMemcpy(tsw, pl->tk.sweeps, sizeof(tsw), cudaMemcpyDeviceToHost));
+    for (int s = 0; s < kTuckerSweepSlots; ++s) {
+      if (tsw[s] < 0) stats->jacobi_unconverged += 1;
+      const int a = tsw[s] < 0 ? -tsw[s] : tsw[s];
+      if (a > stats->jacobi_max_sweeps) stats->jacobi_max_sweeps = a;
+    }
+  }
   if (stats->gemm_errors) return LRSTV_ERR_CUDA;
   if (pl->prm.flags & LRSTV_FLAG_STRICT) {
     if (!isfinite(stats->res_inf[0]) || !isfinite(stats->res_inf[1])) return LRSTV_ERR_NONFINITE;
@@ -750,6 +807,8 @@ int lrstv_state_set(lrstv_plan *pl, int block, const float *src, void *stream) {
   if (!dst) return LRSTV_ERR_ARG;
   CK(cudaMemcpyAsync(dst, src, sizeof(float) * n, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
   pl->vwarm = 0;  // the imported state has no Jacobi history
+  pl->tk.valid = 0;  // nor Tucker factors
+  pl->tk.vvalid[0] = pl->tk.vvalid[1] = pl->tk.vvalid[2] = 0;
   return LRSTV_OK;
 }
 

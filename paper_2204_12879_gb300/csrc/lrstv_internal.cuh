@@ -30,11 +30,12 @@ cudaError_t launch_l_tz(const Dims &d, const float *Y, const float *S, const flo
                         const float *G1, const float *G2, const float *F, const float *G3,
                         float mu, const float w[3], float *L, float *T, cudaStream_t st);
 // Steps 3, 5, 6: F, S, Gamma1..3; res2 receives atomic maxima of |Y-L-S|, |L-Z|
-// as float bits (may be null).
+// as float bits (may be null).  iso: the F threshold acts on each voxel's
+// 3-vector (F_1, F_2, F_3) by its 2-norm (isotropic LRSTV, eq. CRSSTV_iso).
 cudaError_t launch_fs_dual(const Dims &d, const float *Y, const float *L, const float *Z,
                            float *S, float *G1, float *G2, float *F, const float *E, float *G3,
                            const float *G4, float mu, float thr_f, float thr_s, const float w[3],
-                           unsigned *res2, cudaStream_t st);
+                           unsigned *res2, cudaStream_t st, int iso = 0);
 cudaError_t launch_diff(const Dims &d, const float *x, const float w[3], float *g, cudaStream_t st);
 cudaError_t launch_diff_adjoint(const Dims &d, const float *g, const float w[3], float *x,
                                 cudaStream_t st);
@@ -97,11 +98,18 @@ size_t cgemm_tc_smem();
 //  ms2 (may be null): per group of `group` consecutive slices (the Fourier
 //    slices of one tensor), the largest mean-square column norm, used as
 //    rms^2 instead of the slice's own (launch_group_ms2).
+//  negl_rel >= 0: columns whose squared norm is at or below negl_rel ||W||_F^2
+//    take part in no rotation (default, when negative: (nr eps)^2, the level
+//    of rounding residue).  0 rotates every nonzero column: an exactly
+//    rank-deficient matrix then still has its leading right singular vectors
+//    cleared of null-space components, which rotations against the skipped
+//    residue columns would otherwise never remove.
 struct JacOpt {
   int warm = 0;
   float t_svt = -1.0f;
   const float *ms2 = nullptr;
   int group = 1;
+  float negl_rel = -1.0f;
 };
 cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, float t,
                           int max_sweeps, int *sweeps, unsigned long long *work,
@@ -185,6 +193,32 @@ cudaError_t gemm(const CGemm &g, GemmSel gs, cudaStream_t st);
 cudaError_t zsolve_core(const Dims &d, int nb, const Tables &tb, const float *T, float mu,
                         float *Z, float2 *specA, float2 *specB, cudaStream_t st, Prof *prof,
                         GemmSel gs);
+
+// --------------------------------------------------------------- tucker.cu
+// Workspace and state of the Tucker (HOOI) L-update of one cube: factors U_n
+// (n_n x r_n, column-major), two scratch cubes, the Gram matrix and the
+// Jacobi buffers of its eigen-solve.  valid = 0: the next projection starts
+// from the truncated HOSVD.
+struct TuckerWs {
+  int n[3], r[3];
+  float *U[3];
+  float *s0, *s1, *G;
+  float2 *W, *D;       // the Jacobi's W, a GEMM scratch
+  float *Vr, *Wr;      // real parts of a warm start's basis and of G times it
+  float2 *Vm[3];       // per mode: eigenvectors of the last solve (warm start)
+  int *sweeps;          // Jacobi sweeps (-cap if capped): modes' HOOI solves, then HOSVD's
+  int valid;           // U holds factors (else the next projection starts from the HOSVD)
+  int vvalid[3];       // Vm[n] holds eigenvectors
+  int warm;            // eigen-solves start from Vm[n] when it holds eigenvectors
+};
+constexpr int kTuckerSweepSlots = 6;
+size_t tucker_ws_bytes(int n1, int n2, int n3, const int r[3]);
+void tucker_carve(TuckerWs &t, void *ws, int n1, int n2, int n3, const int r[3]);
+// X (in place) := X x1 U1 U1^T x2 U2 U2^T x3 U3 U3^T after one HOOI sweep.
+cudaError_t tucker_project(TuckerWs &t, float *X, cudaStream_t st);
+// T = mu L + Gamma2 + D_w^*(mu F - Gamma3) for a given L.
+cudaError_t launch_tz(const Dims &d, const float *L, const float *G2, const float *F,
+                      const float *G3, float mu, const float w[3], float *T, cudaStream_t st);
 
 // t-SVT of one cube with threshold t on caller-provided scratch: tw3 (n3),
 // specA and specB (h P each), V (h nc^2), sweeps (h); every piece is written

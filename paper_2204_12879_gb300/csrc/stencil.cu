@@ -27,6 +27,17 @@ __device__ __forceinline__ float soft_thr(float x, float d) {
   return x > d ? x - d : (x < -d ? x + d : 0.0f);
 }
 
+// Group soft threshold of the 3-vector x (the prox of d ||.||_2): the
+// isotropic F-update of eq. CRSSTV_iso, one voxel's three gradient entries
+// scaled together by max(1 - d / ||x||_2, 0).
+__device__ __forceinline__ void group_thr3(float (&x)[3], float d) {
+  const float nrm = sqrtf(fmaf(x[0], x[0], fmaf(x[1], x[1], x[2] * x[2])));
+  const float g = nrm > d ? 1.0f - d / nrm : 0.0f;
+  x[0] *= g;
+  x[1] *= g;
+  x[2] *= g;
+}
+
 struct Chunking {
   dim3 grid;
   int kchunk;
@@ -82,6 +93,7 @@ __global__ void __launch_bounds__(kBX *kBY)
   }
 }
 
+template <int ISO>
 __global__ void __launch_bounds__(kBX *kBY)
     k_fs_dual(int n1, int n2, int n3, size_t N, int kchunk, const float *__restrict__ Y,
               const float *__restrict__ L, const float *__restrict__ Z, float *__restrict__ S,
@@ -106,15 +118,22 @@ __global__ void __launch_bounds__(kBX *kBY)
       const float z3 = Z[col + P * kp];
       const float g[3] = {w0 * (Z[colp1 + P * k] - zc), w1 * (Z[colp2 + P * k] - zc),
                           w2 * (z3 - zc)};
+      float h3[3], x[3];
 #pragma unroll
       for (int n = 0; n < 3; ++n) {
         const size_t vn = v + (size_t)n * N;
-        const float h3 = G3[vn];
-        const float t1 = g[n] + h3 / mu;
+        h3[n] = G3[vn];
+        const float t1 = g[n] + h3[n] / mu;
         const float t2 = E[vn] + G4[vn] / mu;
-        const float f = soft_thr(0.5f * (t1 + t2), thr_f);
+        x[n] = 0.5f * (t1 + t2);
+      }
+      if (ISO) group_thr3(x, thr_f);
+#pragma unroll
+      for (int n = 0; n < 3; ++n) {
+        const size_t vn = v + (size_t)n * N;
+        const float f = ISO ? x[n] : soft_thr(x[n], thr_f);
         F[vn] = f;
-        G3[vn] = h3 + mu * (g[n] - f);
+        G3[vn] = h3[n] + mu * (g[n] - f);
       }
       const float y = Y[v], l = L[v], g1 = G1[v];
       const float s = soft_thr(y - l + g1 / mu, thr_s);
@@ -283,6 +302,7 @@ __global__ void __launch_bounds__(256)
   st4(T + o.v, make_float4(to[0], to[1], to[2], to[3]));
 }
 
+template <int ISO>
 __global__ void __launch_bounds__(256)
     k_fs_dual4(int n1, int n2, int n3, size_t N, const float *__restrict__ Y,
                const float *__restrict__ L, const float *__restrict__ Z, float *__restrict__ S,
@@ -305,20 +325,37 @@ __global__ void __launch_bounds__(256)
       g[1][e] = w1 * (z2[e] - zc[e]);
       g[2][e] = w2 * (z3[e] - zc[e]);
     }
+    float x[3][4], H[3][4];
 #pragma unroll
     for (int n = 0; n < 3; ++n) {
       const size_t vn = o.v + (size_t)n * N;
       const float4 h3 = ld4(G3 + vn), ev = ld4(E + vn), h4 = ld4(G4 + vn);
-      const float H[4] = {h3.x, h3.y, h3.z, h3.w}, EE[4] = {ev.x, ev.y, ev.z, ev.w},
-                  H4[4] = {h4.x, h4.y, h4.z, h4.w};
+      const float EE[4] = {ev.x, ev.y, ev.z, ev.w}, H4[4] = {h4.x, h4.y, h4.z, h4.w};
+      H[n][0] = h3.x; H[n][1] = h3.y; H[n][2] = h3.z; H[n][3] = h3.w;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float t1 = g[n][e] + H[n][e] / mu;
+        const float t2 = EE[e] + H4[e] / mu;
+        x[n][e] = 0.5f * (t1 + t2);
+      }
+    }
+    if (ISO) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float xv[3] = {x[0][e], x[1][e], x[2][e]};
+        group_thr3(xv, thr_f);
+        x[0][e] = xv[0]; x[1][e] = xv[1]; x[2][e] = xv[2];
+      }
+    }
+#pragma unroll
+    for (int n = 0; n < 3; ++n) {
+      const size_t vn = o.v + (size_t)n * N;
       float fo[4], ho[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const float t1 = g[n][e] + H[e] / mu;
-        const float t2 = EE[e] + H4[e] / mu;
-        const float f = soft_thr(0.5f * (t1 + t2), thr_f);
+        const float f = ISO ? x[n][e] : soft_thr(x[n][e], thr_f);
         fo[e] = f;
-        ho[e] = H[e] + mu * (g[n][e] - f);
+        ho[e] = H[n][e] + mu * (g[n][e] - f);
       }
       st4(F + vn, make_float4(fo[0], fo[1], fo[2], fo[3]));
       st4(G3 + vn, make_float4(ho[0], ho[1], ho[2], ho[3]));
@@ -395,16 +432,17 @@ cudaError_t launch_l_tz(const Dims &d, const float *Y, const float *S, const flo
 cudaError_t launch_fs_dual(const Dims &d, const float *Y, const float *L, const float *Z,
                            float *S, float *G1, float *G2, float *F, const float *E, float *G3,
                            const float *G4, float mu, float thr_f, float thr_s, const float w[3],
-                           unsigned *res2, cudaStream_t st) {
+                           unsigned *res2, cudaStream_t st, int iso) {
   if (vec4_ok(d, {Y, L, Z, S, G1, G2, F, E, G3, G4})) {
-    k_fs_dual4<<<vec4_blocks(d), 256, 0, st>>>(d.n1, d.n2, d.n3, d.N, Y, L, Z, S, G1, G2, F, E, G3,
-                                                G4, mu, thr_f, thr_s, w[0], w[1], w[2], res2);
+    auto k = iso ? k_fs_dual4<1> : k_fs_dual4<0>;
+    k<<<vec4_blocks(d), 256, 0, st>>>(d.n1, d.n2, d.n3, d.N, Y, L, Z, S, G1, G2, F, E, G3, G4, mu,
+                                      thr_f, thr_s, w[0], w[1], w[2], res2);
     return cudaGetLastError();
   }
   Chunking c = chunking(d);
-  k_fs_dual<<<c.grid, dim3(kBX, kBY), 0, st>>>(d.n1, d.n2, d.n3, d.N, c.kchunk, Y, L, Z, S, G1,
-                                               G2, F, E, G3, G4, mu, thr_f, thr_s, w[0], w[1],
-                                               w[2], res2);
+  auto k = iso ? k_fs_dual<1> : k_fs_dual<0>;
+  k<<<c.grid, dim3(kBX, kBY), 0, st>>>(d.n1, d.n2, d.n3, d.N, c.kchunk, Y, L, Z, S, G1, G2, F, E,
+                                       G3, G4, mu, thr_f, thr_s, w[0], w[1], w[2], res2);
   return cudaGetLastError();
 }
 

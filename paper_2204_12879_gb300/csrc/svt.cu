@@ -1015,7 +1015,7 @@ cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, floa
   // pairs are rotated only above a few times that.
   const float eps = FLT_EPSILON * 0.5f;
   const float tol = 8.0f * sqrtf((float)nr) * eps;
-  const float negl = ((float)nr * eps) * ((float)nr * eps);
+  const float negl = o.negl_rel >= 0.0f ? o.negl_rel : ((float)nr * eps) * ((float)nr * eps);
   const size_t ws = d.P, vs = (size_t)nc * nc;
   if (nr <= 256 && nc >= 2) {
     const int KP = (nr + 31) / 32;  // row pairs per lane of a half-warp

@@ -21,7 +21,7 @@ __all__ = [
     "lrstv_diff", "lrstv_diff_adjoint", "lrstv_soft_threshold", "lrstv_zsolve", "lrstv_tsvt",
     "lrstv_tsvt_noalloc",
     "lrstv_denoise", "BLOCK", "FLAG_F_THRESH_EXACT", "FLAG_NO_GAMMA4", "FLAG_GRAPH",
-    "FLAG_STRICT", "FLAG_SIMT_GEMM", "FLAG_WARM_START", "EXPORTED",
+    "FLAG_STRICT", "FLAG_SIMT_GEMM", "FLAG_WARM_START", "FLAG_ISO_TV", "EXPORTED",
 ]
 
 FLAG_F_THRESH_EXACT = 1
@@ -30,6 +30,7 @@ FLAG_GRAPH = 4
 FLAG_STRICT = 8
 FLAG_SIMT_GEMM = 16
 FLAG_WARM_START = 32
+FLAG_ISO_TV = 64
 
 BLOCK = {"Y": 0, "L": 1, "Z": 2, "S": 3, "G1": 4, "G2": 5, "F": 6, "E": 7, "G3": 8, "G4": 9,
          "TZ": 10}
@@ -109,6 +110,7 @@ _SIGS = {
     "lrstv_iterate": [_P, _I, _P],
     "lrstv_get_stats": [_P, ctypes.POINTER(Stats), _P],
     "lrstv_get_slice_sweeps": [_P, ctypes.POINTER(_I), _I, _P],
+    "lrstv_plan_set_tucker": [_P, ctypes.POINTER(_I)],
     "lrstv_state_get": [_P, _I, _P, _P],
     "lrstv_state_set": [_P, _I, _P, _P],
     "lrstv_get_mu": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)],
@@ -277,6 +279,12 @@ class Plan:
         s = Stats()
         _call("lrstv_get_stats", self._h, ctypes.byref(s), _stream(stream))
         return s
+
+    def set_tucker(self, ranks):
+        """Full TDLRSTV: Tucker (HOOI) L-update with multilinear ranks
+        (r1, r2, r3); None or (0, 0, 0) restores the plain L-update."""
+        arr = None if ranks is None else (_I * 3)(*[int(r) for r in ranks])
+        _call("lrstv_plan_set_tucker", self._h, arr)
 
     def slice_sweeps(self, stream=None):
         """Per-slice Jacobi sweep counts of the last E-step, shape (3, n3//2 + 1)."""

@@ -261,9 +261,11 @@ def test_tsvt_limits(orc):
 
 
 # ----------------------------------------------------------------- ADMM ---
-def brute_force_iteration(st, shape, p, mu):
+def brute_force_iteration(st, shape, p, mu, fstep=None):
     """One ADMM iteration of Section III-C written with dense matrices,
-    numpy's dense solve and the block-circulant t-SVT; state is a dict."""
+    numpy's dense solve and the block-circulant t-SVT; state is a dict.
+    fstep(v, mu), when given, replaces the F-update's soft threshold of the
+    stacked 3N-vector v."""
     tau, alpha, lam, w = p["tau"], p["alpha"], p["lam"], p["w"]
     D = dense_D(shape)
     Dw = np.vstack([w[n] * D[n] for n in range(3)])
@@ -278,7 +280,7 @@ def brute_force_iteration(st, shape, p, mu):
     Z = np.linalg.solve(mu * (np.eye(N) + Dw.T @ Dw), T)
     DZ = Dw @ Z
     v = 0.5 * ((DZ + G3 / mu) + (E + G4 / mu))
-    F = np.sign(v) * np.maximum(np.abs(v) - tau / mu, 0)
+    F = np.sign(v) * np.maximum(np.abs(v) - tau / mu, 0) if fstep is None else fstep(v, mu)
     E = np.concatenate([vec(tsvt_bcirc(unvec(F[n * N:(n + 1) * N] - G4[n * N:(n + 1) * N] / mu,
                                              shape), alpha / mu)) for n in range(3)])
     u = Y - L + G1 / mu
@@ -314,6 +316,95 @@ def test_admm_iterations_brute_force(orc):
     for name in ("F", "E", "G3", "G4"):
         for n in range(3):
             np.testing.assert_allclose(st.get(name, n), bf[name][n], atol=1e-9, err_msg=name)
+
+
+# ------------------------------------------------- isotropic LRSTV (F) ---
+def _nelder_mead_min(f, x0):
+    from scipy.optimize import minimize
+    best = None
+    for start in (x0, np.zeros_like(x0), 0.5 * x0):
+        r = minimize(f, start, method="Nelder-Mead",
+                     options={"xatol": 1e-13, "fatol": 1e-16, "maxiter": 20000, "maxfev": 40000})
+        if best is None or r.fun < best.fun:
+            best = r
+    return best.x
+
+
+def test_group_soft_is_the_prox_of_the_two_norm(orc):
+    """x = argmin 1/2 |x - v|^2 + d |x|_2, found by a derivative-free minimiser;
+    in one dimension it is the scalar soft threshold; it commutes with
+    rotations; inside the ball |v| <= d it is zero."""
+    rng = np.random.default_rng(31)
+    for m in (1, 2, 3, 4):
+        for _ in range(4):
+            v = rng.standard_normal(m)
+            d = float(rng.uniform(0.1, 1.5))
+            x = orc.group_soft(v, d)[0]
+            ref = _nelder_mead_min(lambda y: 0.5 * np.sum((y - v) ** 2) + d * np.linalg.norm(y), v)
+            assert np.max(np.abs(x - ref)) < 1e-6, (m, v, d)
+            if m == 1:
+                assert abs(x[0] - orc.soft(v, d)[0]) < 1e-15
+    v = rng.standard_normal(3)
+    Q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    np.testing.assert_allclose(orc.group_soft(Q @ v, 0.4)[0], Q @ orc.group_soft(v, 0.4)[0],
+                               atol=1e-14)
+    inside = 0.3 * v / np.linalg.norm(v)
+    assert np.all(orc.group_soft(inside, 0.3 + 1e-12)[0] == 0.0)
+
+
+@pytest.mark.parametrize("exact", [False, True])
+def test_iso_admm_iterations_brute_force(orc, exact):
+    """Isotropic LRSTV (eq. CRSSTV_iso, per-voxel 2-norm): the oracle's F-update
+    against the F-subproblem kappa sum_v |F_v|_2 + mu/2 (|a - F|^2 + |b - F|^2)
+    minimised voxel by voxel with a derivative-free minimiser (kappa = tau for
+    the exact minimiser's reading, 2 tau for the printed tau/mu threshold)."""
+    shape = (6, 5, 4)
+    N = int(np.prod(shape))
+    rng = np.random.default_rng(14)
+    Y = np.clip(rng.uniform(0, 1, shape) + 0.1 * rng.standard_normal(shape), -0.2, 1.2)
+    P = orc.Params(tau=0.05, alpha=0.3, lam=0.05, w=(1.0, 0.8, 1.2), mu0=0.5, rho=1.7)
+    flags = orc.FLAG_ISO_TV | (orc.FLAG_F_THRESH_EXACT if exact else 0)
+    st = orc.State(Y, P, flags=flags)
+    kappa = P.tau if exact else 2 * P.tau
+
+    def fstep(v, mu):
+        # v = (a + b)/2 and |a-F|^2 + |b-F|^2 = 2 |F - v|^2 + const
+        V = v.reshape(3, N).T
+        out = np.empty_like(V)
+        for k in range(N):
+            out[k] = _nelder_mead_min(lambda y: kappa * np.linalg.norm(y) + mu * np.sum((y - V[k]) ** 2),
+                                      V[k])
+        return out.T.reshape(-1)
+
+    bf = {"Y": Y, "L": Y.copy(), "Z": Y.copy(), "S": np.zeros(shape), "G1": np.zeros(shape),
+          "G2": np.zeros(shape), "F": np.zeros((3,) + shape), "E": np.zeros((3,) + shape),
+          "G3": np.zeros((3,) + shape), "G4": np.zeros((3,) + shape)}
+    pd = {"tau": P.tau, "alpha": P.alpha, "lam": P.lam, "w": P.w}
+    mu = P.mu0
+    for _ in range(2):
+        bf = brute_force_iteration(bf, shape, pd, mu, fstep)
+        mu = min(P.rho * mu, P.mu_max)
+    st.iterate(2)
+    for name in ("L", "Z", "S", "G1", "G2"):
+        np.testing.assert_allclose(st.get(name), bf[name], atol=1e-6, err_msg=name)
+    for name in ("F", "E", "G3", "G4"):
+        for n in range(3):
+            np.testing.assert_allclose(st.get(name, n), bf[name][n], atol=1e-6, err_msg=name)
+    # the group threshold zeroes whole voxels: F_1, F_2, F_3 vanish together
+    F = np.stack([st.get("F", n) for n in range(3)])
+    zero = np.all(F == 0.0, axis=0)
+    assert zero.any() and not zero.all()
+
+
+def test_iso_residuals_vanish_and_differ_from_anisotropic(orc):
+    from synthetic import Recipe, make_cube
+    clean, noisy = make_cube(Recipe(16, 16, 8, 3, 6, (0.1, 0.1), 0.1), 3)
+    iso = orc.State(noisy, orc.Params(n1=16, n2=16), flags=orc.FLAG_ISO_TV)
+    res, _ = iso.iterate(60)
+    assert res[-1].max() < 1e-5
+    ani = orc.State(noisy, orc.Params(n1=16, n2=16))
+    ani.iterate(60)
+    assert np.max(np.abs(iso.X - ani.X)) > 1e-4
 
 
 def test_admm_residuals_vanish(orc):
