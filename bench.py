@@ -147,6 +147,14 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ roofline ---
+def gemm_precision(args, wl_name):
+    """Split precision of the tensor-core GEMMs: the mixed-precision workload
+    (256x256x191) runs 3xBF16 unless told otherwise, the others 3xTF32."""
+    if args.precision != "auto":
+        return args.precision
+    return "bf16x3" if wl_name == "c3" else "tf32x3"
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -246,6 +254,9 @@ def run_ours(args, wl_name):
     n1, n2, n3 = shape
     iters = wl["iters"]
     flags = lrstv.FLAG_WARM_START if args.jacobi_start == "warm" else 0
+    precision = gemm_precision(args, wl_name)
+    if precision == "bf16x3":
+        flags |= lrstv.FLAG_BF16X3
     params = lrstv.Params.make(n1, n2, max_iter=iters, flags=flags)
     plan = lrstv.Plan(n1, n2, n3, params)
     ranks = None
@@ -314,6 +325,18 @@ def run_ours(args, wl_name):
     quality = {"mpsnr_db": round(mpsnr(X, clean), 3),
                "noisy_mpsnr_db": round(mpsnr(Y, clean), 3)}
     plan.close()
+    if precision == "bf16x3":
+        # the same denoise with FP32-accurate (3xTF32) GEMMs, the path held to
+        # 1e-4 of the FP64 oracle: the mixed-precision error at full size
+        ref_params = lrstv.Params.make(n1, n2, max_iter=iters, flags=flags & ~lrstv.FLAG_BF16X3)
+        with lrstv.Plan(n1, n2, n3, ref_params) as ref_plan:
+            if ranks:
+                ref_plan.set_tucker(ranks)
+            ref_plan.run_host(yh, xh, sh)
+        Xr = xh.numpy().astype(np.float64).reshape(shape, order="F")
+        quality["vs_tf32x3"] = {"max_abs": float(np.max(np.abs(X - Xr))),
+                                "mpsnr_db": round(mpsnr(Xr, clean), 3),
+                                "d_mpsnr_db": float(mpsnr(X, clean) - mpsnr(Xr, clean))}
 
     if rank != 0:
         return None
@@ -345,13 +368,21 @@ def run_ours(args, wl_name):
                             "FP32 FMA: 152 SMs x 128 lanes x 2 x sm_max_mhz") + f" ({pk_kind})")
     roof["traffic"] = traffic_for(dom, wl_name)
     value = world * args.steps / (ms_max / 1e3)
+    if ranks:
+        metric = "ADMM iterations/s (full TDLRSTV, Tucker L-update, FP32)"
+    elif precision == "bf16x3":
+        metric = "ADMM iterations/s (plain LRSTV, mixed precision: 3xBF16 tensor-core GEMMs)"
+    else:
+        metric = METRIC
     line = {
-        "metric": METRIC if not ranks else "ADMM iterations/s (full TDLRSTV, Tucker L-update, FP32)", "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if precision == "tf32x3" else "f32 (GEMMs 3xbf16)", "data": "synthetic",
         "config": {"workload": wl["desc"], "shape": list(shape), "iters_per_cube": iters,
                    "cubes_per_s": value / iters, "parallelism": "replicas" if world > 1 else "single",
                    "jacobi_start": args.jacobi_start,
+                   "gemm_precision": precision,
                    "l_update": ("Tucker projection, one HOOI sweep per iteration, ranks %s" % (ranks,)
                                 if ranks else "plain (full Tucker ranks)"),
                    "l2": "working set (18 state cubes + spectra, ~330 MB) exceeds the 129 MB L2"},
@@ -619,6 +650,9 @@ def main(argv=None):
                          "previous E-step's singular vectors (LRSTV_FLAG_WARM_START)")
     ap.add_argument("--tucker", type=int, default=0, metavar="R3",
                     help="full TDLRSTV: Tucker L-update with ranks (0.8 n1, 0.8 n2, R3)")
+    ap.add_argument("--precision", choices=["auto", "tf32x3", "bf16x3"], default="auto",
+                    help="tensor-core GEMM split: 3xTF32 (FP32-accurate) or 3xBF16 "
+                         "(LRSTV_FLAG_BF16X3); auto = 3xBF16 for c3 only")
     ap.add_argument("--micro", choices=["tsvt"], default=None,
                     help="time one standalone operator instead of the iteration")
     ap.add_argument("--shape", default="200,200,16", help="n1,n2,n3 for --micro")

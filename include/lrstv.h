@@ -60,6 +60,14 @@ typedef enum lrstv_status {
                                         F_v = x_v max(1 - thr / |x_v|_2, 0), thr as for the
                                         anisotropic threshold (tau/mu, or tau/(2 mu) with
                                         LRSTV_FLAG_F_THRESH_EXACT).  Plans and batches only. */
+#define LRSTV_FLAG_BF16X3 128u       /* mixed precision: the tensor-core GEMMs (spatial DFTs of
+                                        the Z-solve, SVT reconstruction, warm-start products)
+                                        split each FP32 operand into two BF16 halves and form
+                                        hi*hi + hi*lo + lo*hi with FP32 accumulation (about
+                                        2^-17 relative error per term instead of 3xTF32's
+                                        2^-21); storage, the Jacobi and the thresholds stay
+                                        FP32, the sigma-vs-threshold decisions FP64.  Not with
+                                        LRSTV_FLAG_SIMT_GEMM (ERR_ARG). */
 
 /* Scalars of Algorithm 1 (Section III-C; parameter roles in Section IV-D).
  *  tau     weight of ||D_w L||_1 (gradient sparsity)

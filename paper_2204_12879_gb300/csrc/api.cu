@@ -58,8 +58,10 @@ int check_params(const lrstv_params *p) {
   if (!(p->mu0 > 0.0f) || !(p->mu_max >= p->mu0) || p->max_iter < 0) return LRSTV_ERR_ARG;
   if (p->flags & ~(unsigned)(LRSTV_FLAG_F_THRESH_EXACT | LRSTV_FLAG_NO_GAMMA4 | LRSTV_FLAG_GRAPH |
                              LRSTV_FLAG_STRICT | LRSTV_FLAG_SIMT_GEMM | LRSTV_FLAG_WARM_START |
-                             LRSTV_FLAG_ISO_TV))
+                             LRSTV_FLAG_ISO_TV | LRSTV_FLAG_BF16X3))
     return LRSTV_ERR_ARG;
+  // the split-BF16 products exist on the tensor-core path only
+  if ((p->flags & LRSTV_FLAG_BF16X3) && (p->flags & LRSTV_FLAG_SIMT_GEMM)) return LRSTV_ERR_ARG;
   return LRSTV_OK;
 }
 
@@ -108,7 +110,7 @@ cudaError_t gemm_z(const CGemm &g, cudaStream_t st, Prof *prof, GemmSel gs) {
 }  // namespace
 
 cudaError_t gemm(const CGemm &g, GemmSel gs, cudaStream_t st) {
-  return gs.tc ? launch_cgemm_tc(g, gs.err, st) : launch_cgemm(g, st);
+  return gs.tc ? launch_cgemm_tc(g, gs.err, st, gs.prec) : launch_cgemm(g, st);
 }
 
 // Z-solve of nb cubes on their h half-spectrum slices each: specA <- fftn(T)
@@ -266,7 +268,7 @@ namespace {
 
 GemmSel plan_gemm(const lrstv_plan *pl) {
   if (pl->prm.flags & LRSTV_FLAG_SIMT_GEMM) return kSimt;
-  return GemmSel{true, pl->gemm_err};
+  return GemmSel{true, pl->gemm_err, (pl->prm.flags & LRSTV_FLAG_BF16X3) ? 1 : 0};
 }
 
 // Warm start of a plan's E-step: one Newton-Schulz step on V (the previous

@@ -75,9 +75,11 @@ struct CGemm {
 cudaError_t launch_cgemm(const CGemm &g, cudaStream_t st);
 
 // ---------------------------------------------------------------- tcgemm.cu
-// The same GEMM on the tensor cores (tcgen05, 3xTF32 split precision); *err
-// (may be null) is set to 1 if a CTA's wait for its MMAs runs out.
-cudaError_t launch_cgemm_tc(const CGemm &g, int *err, cudaStream_t st);
+// The same GEMM on the tensor cores (tcgen05): prec 0 splits FP32 operands
+// into two TF32 halves (3xTF32, FP32-accurate), prec 1 into two BF16 halves
+// (3xBF16, about 2^-17 relative error per term, the mixed-precision mode).
+// *err (may be null) is set to 1 if a CTA's wait for its MMAs runs out.
+cudaError_t launch_cgemm_tc(const CGemm &g, int *err, cudaStream_t st, int prec = 0);
 size_t cgemm_tc_smem();
 
 // -------------------------------------------------------------------- svt.cu
@@ -183,8 +185,9 @@ struct Prof;  // per-kernel event profiler of a plan; null: not profiled
 struct GemmSel {
   bool tc;
   int *err;
+  int prec;  // tensor-core split precision (launch_cgemm_tc)
 };
-constexpr GemmSel kSimt = {false, nullptr};
+constexpr GemmSel kSimt = {false, nullptr, 0};
 cudaError_t gemm(const CGemm &g, GemmSel gs, cudaStream_t st);
 
 // Z-solve (eq. Z_solution) of nb cubes of shape d stored back to back:

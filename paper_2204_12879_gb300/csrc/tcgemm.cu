@@ -18,14 +18,22 @@
 // Complex arithmetic as real GEMMs with K doubled: for a K chunk,
 //   Re C += [Re A | Im A] . [Re B | -Im B]^T,   Im C += [Re A | Im A] . [Im B | Re B]^T.
 //
+// Mixed precision (prec = 1, "3xBF16"): the same split with bf16 halves,
+// x_hi = bf16(x), x_lo = bf16(x - x_hi), and the three products on the BF16
+// tensor-core path (kind::f16, both operands bf16, FP32 accumulation): about
+// 2^-17 relative error per term, half the shared-memory bytes and half the
+// MMA instructions of 3xTF32 (K = 16 per instruction instead of 8).
+//
 // Tile: 128 rows of C (M = 128 MMA), 64 complex columns (two N = 64 MMAs
-// into 128 TMEM columns), 16 complex K per chunk (four K = 8 MMA steps per
-// product).  Operands are staged by the CTA's threads into shared memory in
-// the canonical K-major layout without swizzle: 8-row x 16-byte core matrices,
-// K-adjacent core matrices 128 B apart (LBO), 8-row groups 1024 B apart (SBO).
+// into 128 TMEM columns), 16 complex K per chunk (four K = 8 TF32 or two
+// K = 16 BF16 MMA steps per product).  Operands are staged by the CTA's
+// threads into shared memory in the canonical K-major layout without swizzle:
+// 8-row x 16-byte core matrices, K-adjacent core matrices 128 B apart (LBO),
+// 8-row groups one chunk row (KR elements) apart (SBO).
 // One thread issues the MMAs and commits them to an mbarrier; every wait on
 // that barrier is bounded and, if it runs out, the CTA records an error flag,
 // skips its epilogue and still frees its tensor memory.
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 #include "lrstv_internal.cuh"
@@ -39,26 +47,42 @@ constexpr int TN = 64;        // complex columns of C per CTA
 constexpr int TK = 16;        // complex K per chunk (32 real K)
 constexpr int KR = 2 * TK;    // real K per chunk
 constexpr int kThreads = 128; // four warps: TMEM lanes 0..127
-constexpr uint32_t kLBO = 128, kSBO = (KR / 4) * 128;  // bytes
-constexpr int kTileA = TM * KR;  // floats per A tile (one split)
-constexpr int kTileB = TN * KR;  // floats per B tile (one split, one of re/im)
+constexpr uint32_t kLBO = 128;  // bytes
 constexpr long long kWaitLimit = 20000000;
+
+// Per precision: element bytes, elements per 16-byte core-matrix row, the
+// 8-row group stride, tile sizes and the instruction descriptor's operand
+// format (kind::tf32: TF32 = 2; kind::f16: BF16 = 1).
+template <int PREC>
+struct Prec {
+  static constexpr int kBytes = PREC ? 2 : 4;
+  static constexpr int kPerCore = 16 / kBytes;                    // along K
+  static constexpr uint32_t kSBO = (KR / kPerCore) * 128;         // bytes
+  static constexpr int kMmaK = PREC ? 16 : 8;                     // K per instruction
+  static constexpr uint32_t kFmt = PREC ? 1u : 2u;
+  static constexpr size_t kTileA = (size_t)TM * KR * kBytes;      // bytes, one split
+  static constexpr size_t kTileB = (size_t)TN * KR * kBytes;      // bytes, one split, re or im
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+template <int PREC>
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
   d |= (uint64_t)((kLBO >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((kSBO >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)((Prec<PREC>::kSBO >> 4) & 0x3FFF) << 32;
   d |= (uint64_t)1 << 46;  // descriptor version of tcgen05; no swizzle, base offset 0
   return d;
 }
 
 // byte offset of element (row r, real k kk) in a K-major no-swizzle tile
+template <int PREC>
 __device__ __forceinline__ int koff(int r, int kk) {
-  return (r >> 3) * (int)kSBO + (kk >> 2) * (int)kLBO + (r & 7) * 16 + (kk & 3) * 4;
+  constexpr int pc = Prec<PREC>::kPerCore;
+  return (r >> 3) * (int)Prec<PREC>::kSBO + (kk / pc) * (int)kLBO + (r & 7) * 16 +
+         (kk % pc) * Prec<PREC>::kBytes;
 }
 
 __device__ __forceinline__ float tf32_hi(float x) {
@@ -67,18 +91,33 @@ __device__ __forceinline__ float tf32_hi(float x) {
   return __uint_as_float(r);
 }
 
-__device__ __forceinline__ void put_split(float *hi, float *lo, int off, float x) {
-  const float h = tf32_hi(x);
-  hi[off >> 2] = h;
-  lo[off >> 2] = x - h;
+// x = hi + lo at byte offset off of the hi and lo tiles
+template <int PREC>
+__device__ __forceinline__ void put_split(char *hi, char *lo, int off, float x) {
+  if (PREC == 0) {
+    const float h = tf32_hi(x);
+    *(float *)(hi + off) = h;
+    *(float *)(lo + off) = x - h;
+  } else {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    *(__nv_bfloat16 *)(hi + off) = h;
+    *(__nv_bfloat16 *)(lo + off) = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+template <int PREC>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t accumulate) {
+  if (PREC == 0)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
@@ -88,17 +127,19 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(bar), "r"(parity));
+        : "r"(bar), "r"(parity)
+        : "memory");
   }
   return done != 0;
 }
 
-template <int OPB, int EPI>
+template <int OPB, int EPI, int PREC>
 __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(CGemm g, int *err) {
-  extern __shared__ __align__(1024) float smem[];
-  float *aHi = smem, *aLo = aHi + kTileA;
-  float *bReHi = aLo + kTileA, *bReLo = bReHi + kTileB;
-  float *bImHi = bReLo + kTileB, *bImLo = bImHi + kTileB;
+  extern __shared__ __align__(1024) char smem[];
+  using P = Prec<PREC>;
+  char *aHi = smem, *aLo = aHi + P::kTileA;
+  char *bReHi = aLo + P::kTileA, *bReLo = bReHi + P::kTileB;
+  char *bImHi = bReLo + P::kTileB, *bImLo = bImHi + P::kTileB;
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tslot;
   __shared__ int s_ok;
@@ -124,8 +165,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(CGemm g, int *err) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tslot;
-  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) |
-                         ((uint32_t)(TM >> 4) << 24);
+  // D format F32, A and B in the precision's format, both K-major, N, M
+  const uint32_t idesc = (1u << 4) | (P::kFmt << 7) | (P::kFmt << 10) |
+                         ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
   const uint32_t bar = smem_u32(&mbar);
 
   uint32_t phase = 0;
@@ -139,37 +181,66 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(CGemm g, int *err) {
     accIm[c] = 0.f;
   }
   const int nchunks = (g.K + TK - 1) / TK;
-  for (int ch = 0; ch < nchunks && ok; ++ch) {
-    const int k0 = ch * TK;
-    // A tile: rows m0..m0+127, complex k0..k0+15 -> real kk = k (re), k + 16 (im).
-    // A warp covers 8 rows x 4 k: its 32 stores hit 32 distinct banks of a core
-    // matrix row group, and its loads are four 64-byte runs of a column.
-    for (int e = tid; e < TM * TK; e += kThreads) {
-      const int rest = e >> 5;
-      const int r = ((rest % (TM / 8)) << 3) | ((e >> 2) & 7);
-      const int kc = ((rest / (TM / 8)) << 2) | (e & 3);
+  // Staging is software-pipelined: chunk ch + 1's operands are loaded from
+  // global memory into registers while chunk ch's MMAs run, then split and
+  // stored to shared memory once those MMAs are done with the tiles.
+  // A tile: rows m0..m0+127, complex k0..k0+15 -> real kk = k (re), k + 16
+  // (im).  Element e of a tile: a warp covers 8 rows x 4 k, so its 32 stores
+  // hit 32 distinct banks of a core-matrix row group and its loads are four
+  // 64-byte runs of a column.  B tiles (output columns n0..n0+63): row n holds
+  // op(B)(k, n) over k, 8 rows n x 4 k per warp (loads are runs of 4 k,
+  // B(k, n) at k + ldb n, or of 8 n, B(n, k) at n + ldb k).
+  constexpr int kPa = TM * TK / kThreads, kPb = TN * TK / kThreads;
+  float2 ra[kPa], rb[kPb];
+  auto a_pos = [&](int i, int &r, int &kc) {
+    const int e = tid + kThreads * i, rest = e >> 5;
+    r = ((rest % (TM / 8)) << 3) | ((e >> 2) & 7);
+    kc = ((rest / (TM / 8)) << 2) | (e & 3);
+  };
+  auto b_pos = [&](int i, int &n, int &kc) {
+    const int e = tid + kThreads * i, rest = e >> 5;
+    n = ((rest % (TN / 8)) << 3) | ((e >> 2) & 7);
+    kc = ((rest / (TN / 8)) << 2) | (e & 3);
+  };
+  auto load_chunk = [&](int k0) {
+#pragma unroll
+    for (int i = 0; i < kPa; ++i) {
+      int r, kc;
+      a_pos(i, r, kc);
       const int gm = m0 + r, gk = k0 + kc;
-      const float2 v = (gm < g.M && gk < g.K) ? A[gm + (size_t)g.lda * gk] : make_float2(0.f, 0.f);
-      put_split(aHi, aLo, koff(r, kc), v.x);
-      put_split(aHi, aLo, koff(r, kc + TK), v.y);
+      ra[i] = (gm < g.M && gk < g.K) ? A[gm + (size_t)g.lda * gk] : make_float2(0.f, 0.f);
     }
-    // B tiles for output columns n0..n0+63: row n holds op(B)(k, n) over k
-    // (8 rows n x 4 k per warp, as for A: conflict-free stores; loads are runs
-    // of 4 k (B(k, n) at k + ldb n) or of 8 n (B(n, k) at n + ldb k))
-    for (int e = tid; e < TN * TK; e += kThreads) {
-      const int rest = e >> 5;
-      const int n = ((rest % (TN / 8)) << 3) | ((e >> 2) & 7);
-      const int kc = ((rest / (TN / 8)) << 2) | (e & 3);
+#pragma unroll
+    for (int i = 0; i < kPb; ++i) {
+      int n, kc;
+      b_pos(i, n, kc);
       const int gn = n0 + n, gk = k0 + kc;
       float2 v = make_float2(0.f, 0.f);
       if (gn < g.N && gk < g.K) {
         v = OPB == 0 ? B[gk + (size_t)g.ldb * gn] : B[gn + (size_t)g.ldb * gk];
         if (OPB == 1) v.y = -v.y;
       }
-      put_split(bReHi, bReLo, koff(n, kc), v.x);        // [Re B | -Im B]
-      put_split(bReHi, bReLo, koff(n, kc + TK), -v.y);
-      put_split(bImHi, bImLo, koff(n, kc), v.y);        // [Im B | Re B]
-      put_split(bImHi, bImLo, koff(n, kc + TK), v.x);
+      rb[i] = v;
+    }
+  };
+  if (nchunks > 0) load_chunk(0);
+  for (int ch = 0; ch < nchunks && ok; ++ch) {
+#pragma unroll
+    for (int i = 0; i < kPa; ++i) {
+      int r, kc;
+      a_pos(i, r, kc);
+      put_split<PREC>(aHi, aLo, koff<PREC>(r, kc), ra[i].x);
+      put_split<PREC>(aHi, aLo, koff<PREC>(r, kc + TK), ra[i].y);
+    }
+#pragma unroll
+    for (int i = 0; i < kPb; ++i) {
+      int n, kc;
+      b_pos(i, n, kc);
+      const float2 v = rb[i];
+      put_split<PREC>(bReHi, bReLo, koff<PREC>(n, kc), v.x);  // [Re B | -Im B]
+      put_split<PREC>(bReHi, bReLo, koff<PREC>(n, kc + TK), -v.y);
+      put_split<PREC>(bImHi, bImLo, koff<PREC>(n, kc), v.y);  // [Im B | Re B]
+      put_split<PREC>(bImHi, bImLo, koff<PREC>(n, kc + TK), v.x);
     }
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -180,20 +251,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(CGemm g, int *err) {
       const uint32_t br_hi = smem_u32(bReHi), br_lo = smem_u32(bReLo);
       const uint32_t bi_hi = smem_u32(bImHi), bi_lo = smem_u32(bImLo);
 #pragma unroll
-      for (int j = 0; j < KR / 8; ++j) {  // K = 8 per instruction = two core matrices
+      for (int j = 0; j < KR / P::kMmaK; ++j) {  // one instruction spans two core matrices
         const uint32_t ko = (uint32_t)j * 2 * kLBO;
         const uint32_t acc0 = j > 0 ? 1u : 0u;  // a fresh tile per chunk
-        // Re C (TMEM columns 0..63), Im C (64..127); 3xTF32 per product
-        mma_tf32(tmem, sdesc(a_hi + ko), sdesc(br_hi + ko), idesc, acc0);
-        mma_tf32(tmem, sdesc(a_hi + ko), sdesc(br_lo + ko), idesc, 1u);
-        mma_tf32(tmem, sdesc(a_lo + ko), sdesc(br_hi + ko), idesc, 1u);
-        mma_tf32(tmem + TN, sdesc(a_hi + ko), sdesc(bi_hi + ko), idesc, acc0);
-        mma_tf32(tmem + TN, sdesc(a_hi + ko), sdesc(bi_lo + ko), idesc, 1u);
-        mma_tf32(tmem + TN, sdesc(a_lo + ko), sdesc(bi_hi + ko), idesc, 1u);
+        // Re C (TMEM columns 0..63), Im C (64..127); three split products each
+        mma<PREC>(tmem, sdesc<PREC>(a_hi + ko), sdesc<PREC>(br_hi + ko), idesc, acc0);
+        mma<PREC>(tmem, sdesc<PREC>(a_hi + ko), sdesc<PREC>(br_lo + ko), idesc, 1u);
+        mma<PREC>(tmem, sdesc<PREC>(a_lo + ko), sdesc<PREC>(br_hi + ko), idesc, 1u);
+        mma<PREC>(tmem + TN, sdesc<PREC>(a_hi + ko), sdesc<PREC>(bi_hi + ko), idesc, acc0);
+        mma<PREC>(tmem + TN, sdesc<PREC>(a_hi + ko), sdesc<PREC>(bi_lo + ko), idesc, 1u);
+        mma<PREC>(tmem + TN, sdesc<PREC>(a_lo + ko), sdesc<PREC>(bi_hi + ko), idesc, 1u);
       }
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar));
     }
+    if (ch + 1 < nchunks) load_chunk((ch + 1) * TK);  // in flight during the MMAs
     // the MMAs must finish reading the tiles before they are restaged
     if (!mbar_wait(bar, phase)) {
       ok = false;
@@ -260,32 +332,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(CGemm g, int *err) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
 }
 
+template <int PREC>
+size_t smem_bytes() {
+  return 2 * Prec<PREC>::kTileA + 4 * Prec<PREC>::kTileB;
+}
+
+template <int OPB, int EPI, int PREC>
+cudaError_t launch_one(const CGemm &g, int *err, cudaStream_t st) {
+  const size_t smem = smem_bytes<PREC>();
+  cudaError_t e = cudaFuncSetAttribute(k_cgemm_tc<OPB, EPI, PREC>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((g.M + TM - 1) / TM, (g.N + TN - 1) / TN, g.batch);
+  k_cgemm_tc<OPB, EPI, PREC><<<grid, kThreads, smem, st>>>(g, err);
+  return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t launch_prec(const CGemm &g, int *err, cudaStream_t st) {
+  if (g.opB == 0 && g.epi == 0) return launch_one<0, 0, PREC>(g, err, st);
+  if (g.opB == 0 && g.epi == 1) return launch_one<0, 1, PREC>(g, err, st);
+  if (g.opB == 1 && g.epi == 0) return launch_one<1, 0, PREC>(g, err, st);
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace
 
-size_t cgemm_tc_smem() { return sizeof(float) * (2 * (size_t)kTileA + 4 * (size_t)kTileB); }
+size_t cgemm_tc_smem() { return smem_bytes<0>(); }
 
-cudaError_t launch_cgemm_tc(const CGemm &g, int *err, cudaStream_t st) {
+cudaError_t launch_cgemm_tc(const CGemm &g, int *err, cudaStream_t st, int prec) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
   if (g.opA != 0 || g.epi == 2) return cudaErrorInvalidValue;  // SIMT kernel only
-  const size_t smem = cgemm_tc_smem();
-  dim3 grid((g.M + TM - 1) / TM, (g.N + TN - 1) / TN, g.batch);
-  cudaError_t e;
-#define LRSTV_TC_LAUNCH(OPB, EPI)                                                              \
-  e = cudaFuncSetAttribute(k_cgemm_tc<OPB, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                           (int)smem);                                                        \
-  if (e != cudaSuccess) return e;                                                             \
-  k_cgemm_tc<OPB, EPI><<<grid, kThreads, smem, st>>>(g, err);
-  if (g.opB == 0 && g.epi == 0) {
-    LRSTV_TC_LAUNCH(0, 0)
-  } else if (g.opB == 0 && g.epi == 1) {
-    LRSTV_TC_LAUNCH(0, 1)
-  } else if (g.opB == 1 && g.epi == 0) {
-    LRSTV_TC_LAUNCH(1, 0)
-  } else {
-    return cudaErrorInvalidValue;
-  }
-#undef LRSTV_TC_LAUNCH
-  return cudaGetLastError();
+  if (prec == 0) return launch_prec<0>(g, err, st);
+  if (prec == 1) return launch_prec<1>(g, err, st);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace lrstv

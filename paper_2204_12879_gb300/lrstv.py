@@ -21,7 +21,8 @@ __all__ = [
     "lrstv_diff", "lrstv_diff_adjoint", "lrstv_soft_threshold", "lrstv_zsolve", "lrstv_tsvt",
     "lrstv_tsvt_noalloc",
     "lrstv_denoise", "BLOCK", "FLAG_F_THRESH_EXACT", "FLAG_NO_GAMMA4", "FLAG_GRAPH",
-    "FLAG_STRICT", "FLAG_SIMT_GEMM", "FLAG_WARM_START", "FLAG_ISO_TV", "EXPORTED",
+    "FLAG_STRICT", "FLAG_SIMT_GEMM", "FLAG_WARM_START", "FLAG_ISO_TV", "FLAG_BF16X3",
+    "EXPORTED",
 ]
 
 FLAG_F_THRESH_EXACT = 1
@@ -31,6 +32,7 @@ FLAG_STRICT = 8
 FLAG_SIMT_GEMM = 16
 FLAG_WARM_START = 32
 FLAG_ISO_TV = 64
+FLAG_BF16X3 = 128
 
 BLOCK = {"Y": 0, "L": 1, "Z": 2, "S": 3, "G1": 4, "G2": 5, "F": 6, "E": 7, "G3": 8, "G4": 9,
          "TZ": 10}
