@@ -95,6 +95,25 @@ def test_tsvt_low_rank_and_large(L, orc):
         assert maxabs(out, ref) <= 2e-5 * np.abs(B).max(), shape
 
 
+def test_tsvt_and_run_at_the_maximum_slice_height(L, orc):
+    """Slice heights of 512, the largest the Jacobi kernels take (either side
+    of the slice), for the standalone t-SVT and for whole iterations."""
+    assert L.load().lrstv_max_spatial() == 512
+    for shape in ((512, 12, 3), (12, 512, 2)):
+        B = rnd(shape, 8)
+        out = host(L.lrstv_tsvt(dev(B), B.shape, 2.0), B.shape)
+        ref, _ = orc.tsvt(B, 2.0)
+        assert maxabs(out, ref) <= 2e-5 * np.abs(B).max(), shape
+    shape = (512, 16, 4)
+    _, Y = _noisy(shape, 9)
+    with L.Plan(*shape, L.Params.make(512, 16, max_iter=6)) as pl:
+        X, S = pl.run(dev(Y))
+        X = host(X, shape)
+    ost = orc.State(Y, orc.Params(n1=512, n2=16))
+    ost.iterate(6)
+    assert maxabs(X, ost.X) <= 1e-4
+
+
 # ------------------------------------------------------------ ADMM steps ---
 def _noisy(shape, seed):
     from synthetic import Recipe, make_cube
