@@ -237,6 +237,19 @@ int lrstv_plan_run(lrstv_plan *plan, const float *Y, float *X, float *S, lrstv_s
  * asynchronous copies; pageable memory works too. */
 int lrstv_plan_run_host(lrstv_plan *plan, const float *Y_host, float *X_host, float *S_host,
                         lrstv_stats *stats, void *stream);
+/* Autotuner (no counterpart in the paper): times `iters` iterations
+ * (params.max_iter when 0) of the plan from the device cube Y for every
+ * combination of the flags in `allowed` (a subset of LRSTV_FLAG_SIMT_GEMM |
+ * LRSTV_FLAG_WARM_START; combinations params rejects are skipped), each after
+ * one untimed pass, with CUDA events on `stream`, and keeps the fastest in
+ * the plan's params.flags.  These choices change the work (GEMM engine,
+ * Jacobi starting basis), not the result beyond the FP32 bound.  *chosen and
+ * *ms_out (may be NULL) receive the flags kept and their time in ms.  Leaves
+ * the plan initialised from Y (lrstv_init) and synchronises `stream`.
+ * ERR_ARG for a NULL plan or Y, iters < 0 or other bits in `allowed`; on any
+ * CUDA error the plan's flags are restored. */
+int lrstv_plan_autotune(lrstv_plan *plan, const float *Y, int iters, unsigned allowed,
+                        unsigned *chosen, float *ms_out, void *stream);
 /* One-shot form: creates a plan, runs it, destroys it (synchronises). */
 int lrstv_denoise(const float *Y, int n1, int n2, int n3, const lrstv_params *params, float *X,
                   float *S, lrstv_stats *stats, void *stream);

@@ -874,6 +874,62 @@ int lrstv_plan_run(lrstv_plan *pl, const float *Y, float *X, float *S, lrstv_sta
   return LRSTV_OK;
 }
 
+int lrstv_plan_autotune(lrstv_plan *pl, const float *Y, int iters, unsigned allowed,
+                        unsigned *chosen, float *ms_out, void *stream) {
+  if (!pl || !Y || iters < 0) return LRSTV_ERR_ARG;
+  if (allowed & ~(unsigned)(LRSTV_FLAG_SIMT_GEMM | LRSTV_FLAG_WARM_START)) return LRSTV_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = iters > 0 ? iters : pl->prm.max_iter;
+  const unsigned base = pl->prm.flags & ~allowed;
+  // candidates: every subset of `allowed` that check_params accepts
+  unsigned cands[4];
+  int nc = 0;
+  for (unsigned sub = 0; sub <= allowed; ++sub) {
+    if ((sub & ~allowed) != 0) continue;
+    lrstv_params trial = pl->prm;
+    trial.flags = base | sub;
+    if (check_params(&trial) == LRSTV_OK && nc < 4) cands[nc++] = base | sub;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return LRSTV_ERR_CUDA;
+  }
+  const unsigned keep = pl->prm.flags;
+  unsigned best = keep;
+  float best_ms = -1.0f;
+  int rc = LRSTV_OK;
+  for (int c = 0; c < nc && rc == LRSTV_OK; ++c) {
+    pl->prm.flags = cands[c];
+    drop_graph(pl);
+    // one untimed pass (first-launch costs), then the timed one
+    for (int pass = 0; pass < 2 && rc == LRSTV_OK; ++pass) {
+      if (pass == 1 && cudaEventRecord(e0, st) != cudaSuccess) rc = LRSTV_ERR_CUDA;
+      if (rc == LRSTV_OK) rc = init_async(pl, Y, st);
+      if (rc == LRSTV_OK) rc = iterate_async(pl, n, st);
+      if (rc == LRSTV_OK && pass == 1 && cudaEventRecord(e1, st) != cudaSuccess) rc = LRSTV_ERR_CUDA;
+    }
+    float ms = 0.0f;
+    if (rc == LRSTV_OK && (cudaEventSynchronize(e1) != cudaSuccess ||
+                           cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      rc = LRSTV_ERR_CUDA;
+    if (rc == LRSTV_OK && (best_ms < 0.0f || ms < best_ms)) {
+      best_ms = ms;
+      best = cands[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  pl->prm.flags = rc == LRSTV_OK ? best : keep;
+  drop_graph(pl);
+  if (rc != LRSTV_OK) return rc;
+  if (chosen) *chosen = best;
+  if (ms_out) *ms_out = best_ms;
+  // leave the plan initialised from Y with the chosen flags
+  return init_async(pl, Y, st);
+}
+
 int lrstv_plan_run_host(lrstv_plan *pl, const float *Y_host, float *X_host, float *S_host,
                         lrstv_stats *stats, void *stream) {
   if (!pl || !Y_host) return LRSTV_ERR_ARG;

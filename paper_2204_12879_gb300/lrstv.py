@@ -119,6 +119,8 @@ _SIGS = {
     "lrstv_set_mu": [_P, ctypes.c_double, _I],
     "lrstv_plan_run": [_P, _P, _P, _P, ctypes.POINTER(Stats), _P],
     "lrstv_plan_run_host": [_P, _P, _P, _P, ctypes.POINTER(Stats), _P],
+    "lrstv_plan_autotune": [_P, _P, _I, ctypes.c_uint, ctypes.POINTER(ctypes.c_uint),
+                            ctypes.POINTER(_F), _P],
     "lrstv_denoise": [_P, _I, _I, _I, ctypes.POINTER(Params), _P, _P, ctypes.POINTER(Stats), _P],
     "lrstv_diff": [_P, _I, _I, _I, ctypes.POINTER(_F), _P, _P],
     "lrstv_diff_adjoint": [_P, _I, _I, _I, ctypes.POINTER(_F), _P, _P],
@@ -332,6 +334,19 @@ class Plan:
         _call("lrstv_plan_run", self._h, _dev(Y, self.N), _dev(X, self.N), _dev(S, self.N),
               ctypes.byref(st) if stats else None, _stream(stream))
         return (X, S, st) if stats else (X, S)
+
+    def autotune(self, Y, iters=0, allowed=None, stream=None):
+        """lrstv_plan_autotune: keeps the fastest combination of the allowed
+        flags (default: SIMT_GEMM and WARM_START) for this plan and cube.
+        Returns (flags kept, their time in ms); leaves the plan initialised
+        from Y."""
+        if allowed is None:
+            allowed = FLAG_SIMT_GEMM | FLAG_WARM_START
+        chosen = ctypes.c_uint()
+        ms = _F()
+        _call("lrstv_plan_autotune", self._h, _dev(Y, self.N), int(iters), int(allowed),
+              ctypes.byref(chosen), ctypes.byref(ms), _stream(stream))
+        return int(chosen.value), float(ms.value)
 
     def run_host(self, Y, X, S, stats=False, stream=None):
         """lrstv_plan_run_host on host float32 buffers (numpy arrays or pinned

@@ -77,6 +77,7 @@ def test_argument_errors_before_any_cuda_call(lib):
     bad = lrstv.Params.make(8, 8, flags=lrstv.FLAG_BF16X3 | lrstv.FLAG_SIMT_GEMM)
     assert lib.lrstv_plan_create(8, 8, 8, ctypes.byref(bad), ctypes.byref(h)) == 1
     assert lib.lrstv_plan_destroy(None) == 1
+    assert lib.lrstv_plan_autotune(None, None, 0, 0, None, None, None) == 1
     assert lib.lrstv_step_z(None, None) == 1
     assert lib.lrstv_soft_threshold(None, 5, 0.1, None, None) == 1
     sz = ctypes.c_size_t()
