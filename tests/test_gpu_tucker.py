@@ -132,3 +132,37 @@ def test_tucker_argument_checks(L):
     with L.Plan(8, 8, 600, L.Params.make(8, 8)) as pl:
         with pytest.raises(L.LrstvError, match="status 2"):
             pl.set_tucker((6, 6, 2))
+
+
+def test_tucker_with_the_isotropic_variant(L, orc):
+    """Both NEXT-4 parts together: the Tucker L-update and the isotropic
+    F-update, against the FP64 reference run with the oracle's isotropic flag."""
+    from oracle import tucker as tk
+    shape, ranks, iters = (24, 20, 9), (3, 3, 3), 8
+    _, Y = _low_rank(shape, 3, 31)
+    X, S = _run(L, shape, ranks, iters, Y, flags=L.FLAG_ISO_TV)
+    ref = tk.TuckerState(orc, Y, orc.Params(n1=24, n2=20), ranks, flags=orc.FLAG_ISO_TV)
+    ref.iterate(iters)
+    assert maxabs(X, ref.X) <= 1e-4
+    assert maxabs(S, ref.st.get("S")) <= 1e-4
+
+
+def test_tucker_inside_a_batch_equals_the_plan(L):
+    """A batch whose second cube has the Tucker L-update (set through
+    lrstv_batch_plan) gives, for every cube, the standalone plan's bits."""
+    import torch
+    shapes = [(24, 20, 9), (20, 24, 8), (32, 32, 6)]
+    Ys = [dev(_low_rank(s, 3, 40 + i)[1]) for i, s in enumerate(shapes)]
+    p = L.Params.make(24, 20, max_iter=6)
+    with L.Batch(shapes, p) as b:
+        b.plan(1).set_tucker((3, 3, 3))
+        Xs, _ = b.run(Ys)
+        torch.cuda.synchronize()
+        got = [x.cpu() for x in Xs]
+    for i, sh in enumerate(shapes):
+        with L.Plan(*sh, p) as pl:
+            if i == 1:
+                pl.set_tucker((3, 3, 3))
+            X, _ = pl.run(Ys[i])
+            torch.cuda.synchronize()
+            assert torch.equal(X.cpu(), got[i]), i
