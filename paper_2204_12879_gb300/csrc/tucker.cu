@@ -13,6 +13,7 @@
 // by the one-sided Jacobi kernel of the t-SVT (svt.cu): the right singular
 // vectors of a symmetric positive semi-definite matrix are its eigenvectors
 // and its column norms after the sweeps are the eigenvalues.
+#include <float.h>
 #include <stdint.h>
 
 #include "lrstv_internal.cuh"
@@ -261,6 +262,194 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// ------------------------------------------------ symmetric eigen-solver
+// Two-sided cyclic Jacobi for a real symmetric n x n matrix B (n <= kSyevjMax)
+// held in shared memory: B := J^T B J and V := V J over rounds of n/2 disjoint
+// column pairs (the round-robin order of the t-SVT's kernel), each rotation
+// the symmetric Schur 2x2 (Golub & Van Loan, Matrix Computations, Section
+// 8.4) with its angle in FP64.  A pair is rotated while
+// |b_pq| > tol sqrt(|b_pp b_qq|) and |b_pq| > eps max_i |b_ii|: the second
+// test leaves entries at the rounding level of B alone, so that the null
+// block of a rank-deficient matrix does not chase its own rounding, while a
+// leading eigenvector's component of size c along a null direction (an entry
+// of about lambda c) is still rotated away down to c ~ eps.  Checking a pair
+// reads three entries of B, and the disjoint pairs of a round are applied in
+// parallel as 2 x 2 blocks of B (rows of pair P, columns of pair Q), so a
+// sweep over a nearly diagonal B (a warm start) costs little more than its
+// pair checks.  One CTA; V is n x n column-major in global memory (the
+// identity is written when warm = 0); lam receives diag(B); *sweeps_out the
+// sweeps used, -max_sweeps at the cap.
+constexpr int kSyevjMax = 224;
+constexpr int kSyevjThreads = 1024;
+
+size_t syevj_smem(int n) {
+  const int m = n + (n & 1);
+  return sizeof(float) * (size_t)m * m;
+}
+
+__global__ void __launch_bounds__(kSyevjThreads, 1)
+    k_syevj(int n, const float *__restrict__ B0, float *__restrict__ V, int warm,
+            float *__restrict__ lam, int max_sweeps, int *__restrict__ sweeps_out) {
+  extern __shared__ float sB[];  // m x m, row-major
+  __shared__ int s_p[kSyevjMax / 2], s_q[kSyevjMax / 2], s_go[kSyevjMax / 2];
+  __shared__ float s_c[kSyevjMax / 2], s_s[kSyevjMax / 2], s_t[kSyevjMax / 2];
+  __shared__ float s_red[32];
+  __shared__ int s_any, s_sweep_any;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m = n + (n & 1), h = m / 2;
+  const float eps = FLT_EPSILON * 0.5f;
+  const float tol = 8.0f * sqrtf((float)n) * eps;
+  // B0 is symmetric to rounding (V^T (G V) rounds its two triangles apart):
+  // the mean of the two is exact for an exactly symmetric B0
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e % m;
+    sB[e] = (i < n && j < n) ? 0.5f * (B0[i + (size_t)n * j] + B0[j + (size_t)n * i]) : 0.0f;
+  }
+  if (!warm)
+    for (int e = tid; e < n * n; e += blockDim.x) V[e] = (e % n) == (e / n) ? 1.0f : 0.0f;
+  float dmax = 0.0f;
+  for (int i = tid; i < n; i += blockDim.x) dmax = fmaxf(dmax, fabsf(B0[i + (size_t)n * i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  if (lane == 0) s_red[warp] = dmax;
+  __syncthreads();
+  if (warp == 0) {
+    float v = lane < (int)(blockDim.x >> 5) ? s_red[lane] : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) s_red[0] = v;
+  }
+  __syncthreads();
+  const float floor_abs = eps * s_red[0];
+
+  int sweeps = 0;
+  bool converged = n < 2;
+  if (converged) sweeps = 1;
+  for (int sweep = 1; sweep <= max_sweeps && !converged; ++sweep) {
+    if (tid == 0) s_sweep_any = 0;
+    for (int r = 0; r < m - 1; ++r) {
+      if (tid == 0) s_any = 0;
+      __syncthreads();
+      if (tid < h) {
+        int p, q;
+        if (tid == 0) {
+          p = r;
+          q = m - 1;
+        } else {
+          p = (r + tid) % (m - 1);
+          q = (r - tid + m - 1) % (m - 1);
+        }
+        if (p > q) {
+          const int x = p;
+          p = q;
+          q = x;
+        }
+        int go = 0;
+        float c = 1.0f, sn = 0.0f, t = 0.0f;
+        if (q < n) {
+          const float app = sB[p * m + p], aqq = sB[q * m + q], apq = sB[p * m + q];
+          const float aa = fabsf(apq);
+          if (aa > floor_abs && aa > tol * sqrtf(fabsf(app)) * sqrtf(fabsf(aqq))) {
+            const double tau = ((double)aqq - (double)app) / (2.0 * (double)apq);
+            const double td = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            const double cd = 1.0 / sqrt(1.0 + td * td);
+            c = (float)cd;
+            sn = (float)(td * cd);
+            t = (float)td;
+            go = 1;
+          }
+        }
+        s_p[tid] = p;
+        s_q[tid] = q;
+        s_c[tid] = c;
+        s_s[tid] = sn;
+        s_t[tid] = t;
+        s_go[tid] = go;
+        if (go) {
+          s_any = 1;
+          s_sweep_any = 1;
+        }
+      }
+      __syncthreads();
+      if (s_any) {
+        // B := J^T B J, one 2 x 2 block (rows of pair P, columns of pair Q) per item
+        for (int e = tid; e < h * h; e += blockDim.x) {
+          const int P = e / h, Q = e % h;
+          const int gp = s_go[P], gq = s_go[Q];
+          if (!gp && !gq) continue;
+          const int a0 = s_p[P], a1 = s_q[P], b0 = s_p[Q], b1 = s_q[Q];
+          float x00 = sB[a0 * m + b0], x01 = sB[a0 * m + b1];
+          float x10 = sB[a1 * m + b0], x11 = sB[a1 * m + b1];
+          if (P == Q) {  // the rotated pair's own block: exact diagonal form
+            const float tt = s_t[P];
+            sB[a0 * m + a0] = x00 - tt * x01;
+            sB[a1 * m + a1] = x11 + tt * x01;
+            sB[a0 * m + a1] = 0.0f;
+            sB[a1 * m + a0] = 0.0f;
+            continue;
+          }
+          if (gp) {
+            const float c = s_c[P], sn = s_s[P];
+            const float y00 = c * x00 - sn * x10, y10 = sn * x00 + c * x10;
+            const float y01 = c * x01 - sn * x11, y11 = sn * x01 + c * x11;
+            x00 = y00; x10 = y10; x01 = y01; x11 = y11;
+          }
+          if (gq) {
+            const float c = s_c[Q], sn = s_s[Q];
+            const float y00 = c * x00 - sn * x01, y01 = sn * x00 + c * x01;
+            const float y10 = c * x10 - sn * x11, y11 = sn * x10 + c * x11;
+            x00 = y00; x01 = y01; x10 = y10; x11 = y11;
+          }
+          sB[a0 * m + b0] = x00;
+          sB[a0 * m + b1] = x01;
+          sB[a1 * m + b0] = x10;
+          sB[a1 * m + b1] = x11;
+        }
+        // V := V J on the rotated pairs' columns
+        for (int e = tid; e < h * n; e += blockDim.x) {
+          const int P = e / n, row = e % n;
+          if (!s_go[P]) continue;
+          const int p = s_p[P], q = s_q[P];
+          const float c = s_c[P], sn = s_s[P];
+          const float vp = V[row + (size_t)n * p], vq = V[row + (size_t)n * q];
+          V[row + (size_t)n * p] = c * vp - sn * vq;
+          V[row + (size_t)n * q] = sn * vp + c * vq;
+        }
+      }
+      __syncthreads();
+    }
+    sweeps = sweep;
+    converged = (s_sweep_any == 0);
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += blockDim.x) lam[i] = sB[i * m + i];
+  if (tid == 0) *sweeps_out = converged ? sweeps : -max_sweeps;
+}
+
+// U (n x r) receives the r columns of V (n x n, real) with the largest lam,
+// in decreasing order (ties by index).  One block.
+__global__ void __launch_bounds__(256)
+    k_select_top_real(int n, int r, const float *__restrict__ lam, const float *__restrict__ V,
+                      float *__restrict__ U) {
+  __shared__ float sl[kMaxSpatial];
+  __shared__ int pos[kMaxSpatial];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < n; i += blockDim.x) sl[i] = lam[i];
+  __syncthreads();
+  for (int i = tid; i < n; i += blockDim.x) {
+    int k = 0;
+    const float li = sl[i];
+    for (int j = 0; j < n; ++j) k += (sl[j] > li) || (sl[j] == li && j < i);
+    pos[i] = k;
+  }
+  __syncthreads();
+  for (size_t e = tid; e < (size_t)n * n; e += blockDim.x) {
+    const int i = (int)(e / n), row = (int)(e % n);
+    const int k = pos[i];
+    if (k < r) U[(size_t)n * k + row] = V[(size_t)n * i + row];
+  }
+}
+
 // T_z = mu L + Gamma2 + D_w^*(mu F - Gamma3) for a given L (eq. Z_solution),
 // D_n^T q(v) = q(v - e_n) - q(v).
 __global__ void __launch_bounds__(256)
@@ -336,64 +525,92 @@ size_t tucker_ws_bytes(int n1, int n2, int n3, const int r[3]) {
 
 namespace {
 
+// One Newton-Schulz step U := 1.5 U - 0.5 U (U^T U) on an n x r factor, with
+// FP64-accumulated products (scratch: r x r in sA, n x r in sB).
+cudaError_t ns_step(float *U, int n, int r, float *sA, float *sB, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = sgemm(mk(U, 0, n, U, 0, n, sA, 0, r, r, r, n, 1), 1, 0, st))) return e;  // U^T U
+  if ((e = sgemm(mk(U, 0, n, sA, 0, r, sB, 0, n, n, r, r, 1), 0, 0, st))) return e;
+  const size_t nr = (size_t)n * r;
+  k_ns_real<<<grid_for(nr), 256, 0, st>>>(nr, U, sB);
+  return cudaGetLastError();
+}
+
 // The r_n leading eigenvectors of the n x n Gram matrix t.G of mode `mode`
-// into U.  With t.warm set, the Jacobi starts from the eigenvectors of that
-// mode's previous solve when there is one (made unitary again by one
-// Newton-Schulz step, as the E-step's warm start does), otherwise from the
-// identity.  Its sweep count goes to t.sweeps[slot].
+// into U.  With t.warm set, the solve starts from the eigenvectors of that
+// mode's previous solve when there is one, otherwise from the identity.  Its
+// sweep count goes to t.sweeps[slot].
 //
-// G and the eigenvectors are real (rotations of real columns have real phase
-// factors), so a warm start's W = G V is a real product, formed with FP64
-// accumulation: each column of W is then exact to its own rounding, and the
-// small eigenvalues' columns are not buried under the largest one's.
+// n <= kSyevjMax: the two-sided Jacobi (k_syevj) on B = V^T G V, V the warm
+// basis made orthonormal again by one Newton-Schulz step (B = G cold), both
+// products real and FP64-accumulated; V (real) is kept in Vm[mode].
+// Larger n: the t-SVT's one-sided Jacobi on W = G V (the right singular
+// vectors of a symmetric positive semi-definite matrix are its eigenvectors,
+// its column norms the eigenvalues), with every nonzero column rotated
+// (negl_rel = 0): a Gram matrix of a cube of lower multilinear rank than n
+// has null columns at the rounding level, and skipping them would leave the
+// leading eigenvectors with null-space components of about
+// (n eps) ||G|| / lambda_r, which nothing else corrects.
 //
-// Every nonzero column is rotated (negl_rel = 0): a Gram matrix of a cube of
-// lower multilinear rank than n has null columns at the rounding level, and
-// skipping them would leave the leading eigenvectors with null-space
-// components of about (n eps) ||G|| / lambda_r, which nothing else corrects
-// and which the projection then carries into L.
+// Either way the selected factor then gets one Newton-Schulz step with
+// FP64-accumulated products: each rotation is orthogonal only to about an
+// ulp, and a rank-deficient Gram matrix takes many sweeps, so the columns of
+// U drift from unit norm by up to 1e-4, which U U^T would turn into a scaling
+// of the projection.
 cudaError_t eig_top(TuckerWs &t, int mode, int n, int r, float *U, int slot, cudaStream_t st) {
   const size_t nn = (size_t)n * n;
-  float2 *V = t.Vm[mode];
   const int warm = t.warm && t.vvalid[mode];
   cudaError_t e;
-  if (warm) {
-    CGemm g{};
-    g.batch = 1;
-    g.M = n; g.N = n; g.K = n;
-    g.lda = n; g.ldb = n; g.ldc = n;
-    g.A = V; g.B = V; g.opB = 1; g.C = t.W;  // V V^H
-    if ((e = launch_cgemm(g, st)) != cudaSuccess) return e;
-    g.A = t.W; g.B = V; g.opB = 0; g.C = t.D;  // (V V^H) V
-    if ((e = launch_cgemm(g, st)) != cudaSuccess) return e;
-    if ((e = launch_ns_update(n, 1, nn, V, t.D, st)) != cudaSuccess) return e;
-    k_c2_to_real<<<grid_for(nn), 256, 0, st>>>(nn, V, t.Vr);
+  if (n <= kSyevjMax) {
+    float *V = reinterpret_cast<float *>(t.Vm[mode]);
+    float *scr = reinterpret_cast<float *>(t.W);  // 2 n^2 floats
+    float *lam = reinterpret_cast<float *>(t.D);
+    const float *B0 = t.G;
+    if (warm) {
+      if ((e = ns_step(V, n, n, scr, scr + nn, st)) != cudaSuccess) return e;
+      if ((e = sgemm(mk(t.G, 0, n, V, 0, n, t.Wr, 0, n, n, n, n, 1), 0, 0, st))) return e;  // G V
+      if ((e = sgemm(mk(V, 0, n, t.Wr, 0, n, t.Vr, 0, n, n, n, n, 1), 1, 0, st))) return e;
+      B0 = t.Vr;  // V^T G V
+    }
+    const size_t smem = syevj_smem(n);
+    if ((e = cudaFuncSetAttribute(k_syevj, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+      return e;
+    k_syevj<<<1, kSyevjThreads, smem, st>>>(n, B0, V, warm, lam, kMaxSweeps, t.sweeps + slot);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = sgemm(mk(t.G, 0, n, t.Vr, 0, n, t.Wr, 0, n, n, n, n, 1), 0, 0, st))) return e;  // G V
+    k_select_top_real<<<1, 256, 0, st>>>(n, r, lam, V, U);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else {
+    float2 *V = t.Vm[mode];
+    if (warm) {
+      CGemm g{};
+      g.batch = 1;
+      g.M = n; g.N = n; g.K = n;
+      g.lda = n; g.ldb = n; g.ldc = n;
+      g.A = V; g.B = V; g.opB = 1; g.C = t.W;  // V V^H
+      if ((e = launch_cgemm(g, st)) != cudaSuccess) return e;
+      g.A = t.W; g.B = V; g.opB = 0; g.C = t.D;  // (V V^H) V
+      if ((e = launch_cgemm(g, st)) != cudaSuccess) return e;
+      if ((e = launch_ns_update(n, 1, nn, V, t.D, st)) != cudaSuccess) return e;
+      k_c2_to_real<<<grid_for(nn), 256, 0, st>>>(nn, V, t.Vr);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = sgemm(mk(t.G, 0, n, t.Vr, 0, n, t.Wr, 0, n, n, n, n, 1), 0, 0, st))) return e;
+    }
+    k_real_to_c2<<<grid_for(nn), 256, 0, st>>>(nn, warm ? t.Wr : t.G, t.W);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const Dims dj = make_dims(n, n, 1);
+    JacOpt o;
+    o.warm = warm;
+    o.negl_rel = 0.0f;
+    if ((e = launch_jacobi(dj, 1, t.W, V, -1.0f, kMaxSweeps, t.sweeps + slot, nullptr, st, o)) !=
+        cudaSuccess)
+      return e;
+    k_select_top<<<1, 256, 0, st>>>(n, r, t.W, V, U);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  k_real_to_c2<<<grid_for(nn), 256, 0, st>>>(nn, warm ? t.Wr : t.G, t.W);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const Dims dj = make_dims(n, n, 1);
-  JacOpt o;
-  o.warm = warm;
-  o.negl_rel = 0.0f;
-  if ((e = launch_jacobi(dj, 1, t.W, V, -1.0f, kMaxSweeps, t.sweeps + slot, nullptr, st, o)) !=
-      cudaSuccess)
-    return e;
-  k_select_top<<<1, 256, 0, st>>>(n, r, t.W, V, U);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  // Each rotation is unitary only to about an ulp (its phase factor and
-  // cosine come from a rounded reciprocal square root), and a rank-deficient
-  // Gram matrix takes many sweeps: the columns of U drift from unit norm by
-  // up to 1e-4, which U U^T would turn into a scaling of the projection.  One
-  // Newton-Schulz step with FP64-accumulated products takes the drift to its
-  // square.
-  const size_t nr = (size_t)n * r;
-  if ((e = sgemm(mk(U, 0, n, U, 0, n, t.Wr, 0, r, r, r, n, 1), 1, 0, st))) return e;  // U^T U
-  if ((e = sgemm(mk(U, 0, n, t.Wr, 0, r, t.Vr, 0, n, n, r, r, 1), 0, 0, st))) return e;
-  k_ns_real<<<grid_for(nr), 256, 0, st>>>(nr, U, t.Vr);
+  if ((e = ns_step(U, n, r, t.Wr, t.Vr, st)) != cudaSuccess) return e;
   t.vvalid[mode] = 1;
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 // Gram matrix of mode `mode` of X x_m Uo[m]^T (m != mode), into t.G, then
