@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(256)
 // held in shared memory: B := J^T B J and V := V J over rounds of n/2 disjoint
 // column pairs (the round-robin order of the t-SVT's kernel), each rotation
 // the symmetric Schur 2x2 (Golub & Van Loan, Matrix Computations, Section
-// 8.4) with its angle in FP64.  A pair is rotated while
+// 8.4) in FP32 (IEEE square roots and divisions).  A pair is rotated while
 // |b_pq| > tol sqrt(|b_pp b_qq|) and |b_pq| > eps max_i |b_ii|: the second
 // test leaves entries at the rounding level of B alone, so that the null
 // block of a rank-deficient matrix does not chase its own rounding, while a
@@ -281,6 +281,7 @@ __global__ void __launch_bounds__(256)
 // sweeps used, -max_sweeps at the cap.
 constexpr int kSyevjMax = 224;
 constexpr int kSyevjThreads = 1024;
+constexpr int kVBatch = 8;  // V items a thread has in flight
 
 size_t syevj_smem(int n) {
   const int m = n + (n & 1);
@@ -293,8 +294,9 @@ __global__ void __launch_bounds__(kSyevjThreads, 1)
   extern __shared__ float sB[];  // m x m, row-major
   __shared__ int s_p[kSyevjMax / 2], s_q[kSyevjMax / 2], s_go[kSyevjMax / 2];
   __shared__ float s_c[kSyevjMax / 2], s_s[kSyevjMax / 2], s_t[kSyevjMax / 2];
+  __shared__ int s_rot[kSyevjMax / 2], s_still[kSyevjMax / 2];  // rotated / other pairs
   __shared__ float s_red[32];
-  __shared__ int s_any, s_sweep_any;
+  __shared__ int s_any, s_nrot, s_nstill, s_sweep_any;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int m = n + (n & 1), h = m / 2;
   const float eps = FLT_EPSILON * 0.5f;
@@ -328,7 +330,11 @@ __global__ void __launch_bounds__(kSyevjThreads, 1)
   for (int sweep = 1; sweep <= max_sweeps && !converged; ++sweep) {
     if (tid == 0) s_sweep_any = 0;
     for (int r = 0; r < m - 1; ++r) {
-      if (tid == 0) s_any = 0;
+      if (tid == 0) {
+        s_any = 0;
+        s_nrot = 0;
+        s_nstill = 0;
+      }
       __syncthreads();
       if (tid < h) {
         int p, q;
@@ -350,12 +356,14 @@ __global__ void __launch_bounds__(kSyevjThreads, 1)
           const float app = sB[p * m + p], aqq = sB[q * m + q], apq = sB[p * m + q];
           const float aa = fabsf(apq);
           if (aa > floor_abs && aa > tol * sqrtf(fabsf(app)) * sqrtf(fabsf(aqq))) {
-            const double tau = ((double)aqq - (double)app) / (2.0 * (double)apq);
-            const double td = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            const double cd = 1.0 / sqrt(1.0 + td * td);
-            c = (float)cd;
-            sn = (float)(td * cd);
-            t = (float)td;
+            // tan of the angle, |t| <= 1; for |tau| beyond 1e18 (tau^2 would
+            // overflow) t = 1 / (2 tau) to within rounding
+            const float tau = (aqq - app) / (2.0f * apq);
+            const float at = fabsf(tau);
+            const float tn = at > 1e18f ? 0.5f / at : 1.0f / (at + sqrtf(fmaf(at, at, 1.0f)));
+            t = tau >= 0.0f ? tn : -tn;
+            c = 1.0f / sqrtf(fmaf(t, t, 1.0f));
+            sn = t * c;
             go = 1;
           }
         }
@@ -365,55 +373,97 @@ __global__ void __launch_bounds__(kSyevjThreads, 1)
         s_s[tid] = sn;
         s_t[tid] = t;
         s_go[tid] = go;
+        // the rotated pairs and the others, each in some order: every block
+        // update depends only on its own entries and its two pairs, so the
+        // order of the lists does not change any result
         if (go) {
+          s_rot[atomicAdd(&s_nrot, 1)] = tid;
           s_any = 1;
           s_sweep_any = 1;
+        } else {
+          s_still[atomicAdd(&s_nstill, 1)] = tid;
         }
       }
       __syncthreads();
       if (s_any) {
-        // B := J^T B J, one 2 x 2 block (rows of pair P, columns of pair Q) per item
-        for (int e = tid; e < h * h; e += blockDim.x) {
-          const int P = e / h, Q = e % h;
-          const int gp = s_go[P], gq = s_go[Q];
-          if (!gp && !gq) continue;
-          const int a0 = s_p[P], a1 = s_q[P], b0 = s_p[Q], b1 = s_q[Q];
-          float x00 = sB[a0 * m + b0], x01 = sB[a0 * m + b1];
-          float x10 = sB[a1 * m + b0], x11 = sB[a1 * m + b1];
-          if (P == Q) {  // the rotated pair's own block: exact diagonal form
-            const float tt = s_t[P];
-            sB[a0 * m + a0] = x00 - tt * x01;
-            sB[a1 * m + a1] = x11 + tt * x01;
-            sB[a0 * m + a1] = 0.0f;
-            sB[a1 * m + a0] = 0.0f;
-            continue;
+        // B := J^T B J over the 2 x 2 blocks (rows of pair P, columns of pair
+        // Q) that a rotation touches: with Q = thread mod h fixed (its
+        // columns and rotation in registers) a thread walks the rows of every
+        // rotated pair, then, if Q itself is rotated, the rows of the others.
+        // A warp shares P, so the pair data it reads are broadcasts.
+        const int k = s_nrot;
+        const int groups = kSyevjThreads / h;
+        const int Q = tid % h, g = tid / h;
+        if (g < groups) {
+          const int b0 = s_p[Q], b1 = s_q[Q], gq = s_go[Q];
+          const float cq = s_c[Q], sq = s_s[Q];
+          for (int i = g; i < k; i += groups) {
+            const int P = s_rot[i];
+            const int a0 = s_p[P], a1 = s_q[P];
+            float x00 = sB[a0 * m + b0], x01 = sB[a0 * m + b1];
+            float x10 = sB[a1 * m + b0], x11 = sB[a1 * m + b1];
+            if (P == Q) {  // the rotated pair's own block: exact diagonal form
+              const float tt = s_t[P];
+              sB[a0 * m + a0] = x00 - tt * x01;
+              sB[a1 * m + a1] = x11 + tt * x01;
+              sB[a0 * m + a1] = 0.0f;
+              sB[a1 * m + a0] = 0.0f;
+              continue;
+            }
+            const float cp = s_c[P], sp = s_s[P];
+            float y00 = cp * x00 - sp * x10, y10 = sp * x00 + cp * x10;
+            float y01 = cp * x01 - sp * x11, y11 = sp * x01 + cp * x11;
+            if (gq) {
+              x00 = cq * y00 - sq * y01;
+              x01 = sq * y00 + cq * y01;
+              x10 = cq * y10 - sq * y11;
+              x11 = sq * y10 + cq * y11;
+            } else {
+              x00 = y00; x01 = y01; x10 = y10; x11 = y11;
+            }
+            sB[a0 * m + b0] = x00;
+            sB[a0 * m + b1] = x01;
+            sB[a1 * m + b0] = x10;
+            sB[a1 * m + b1] = x11;
           }
-          if (gp) {
-            const float c = s_c[P], sn = s_s[P];
-            const float y00 = c * x00 - sn * x10, y10 = sn * x00 + c * x10;
-            const float y01 = c * x01 - sn * x11, y11 = sn * x01 + c * x11;
-            x00 = y00; x10 = y10; x01 = y01; x11 = y11;
-          }
-          if (gq) {
-            const float c = s_c[Q], sn = s_s[Q];
-            const float y00 = c * x00 - sn * x01, y01 = sn * x00 + c * x01;
-            const float y10 = c * x10 - sn * x11, y11 = sn * x10 + c * x11;
-            x00 = y00; x01 = y01; x10 = y10; x11 = y11;
-          }
-          sB[a0 * m + b0] = x00;
-          sB[a0 * m + b1] = x01;
-          sB[a1 * m + b0] = x10;
-          sB[a1 * m + b1] = x11;
+          if (gq)
+            for (int i = g; i < h - k; i += groups) {
+              const int P = s_still[i];
+              const int a0 = s_p[P], a1 = s_q[P];
+              const float x00 = sB[a0 * m + b0], x01 = sB[a0 * m + b1];
+              const float x10 = sB[a1 * m + b0], x11 = sB[a1 * m + b1];
+              sB[a0 * m + b0] = cq * x00 - sq * x01;
+              sB[a0 * m + b1] = sq * x00 + cq * x01;
+              sB[a1 * m + b0] = cq * x10 - sq * x11;
+              sB[a1 * m + b1] = sq * x10 + cq * x11;
+            }
         }
-        // V := V J on the rotated pairs' columns
-        for (int e = tid; e < h * n; e += blockDim.x) {
-          const int P = e / n, row = e % n;
-          if (!s_go[P]) continue;
-          const int p = s_p[P], q = s_q[P];
-          const float c = s_c[P], sn = s_s[P];
-          const float vp = V[row + (size_t)n * p], vq = V[row + (size_t)n * q];
-          V[row + (size_t)n * p] = c * vp - sn * vq;
-          V[row + (size_t)n * q] = sn * vp + c * vq;
+        // V := V J on the rotated pairs' columns (global memory, L2-resident):
+        // each thread loads a batch of its items before it stores any, so the
+        // loads' latencies overlap
+        for (int base = tid; base < k * n; base += kSyevjThreads * kVBatch) {
+          float vp[kVBatch], vq[kVBatch];
+          int ip[kVBatch], iq[kVBatch], pr[kVBatch];
+#pragma unroll
+          for (int u = 0; u < kVBatch; ++u) {
+            const int e = base + kSyevjThreads * u;
+            pr[u] = -1;
+            if (e < k * n) {
+              const int P = s_rot[e / n], row = e % n;
+              pr[u] = P;
+              ip[u] = row + n * s_p[P];
+              iq[u] = row + n * s_q[P];
+              vp[u] = V[ip[u]];
+              vq[u] = V[iq[u]];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kVBatch; ++u) {
+            if (pr[u] < 0) continue;
+            const float c = s_c[pr[u]], sn = s_s[pr[u]];
+            V[ip[u]] = c * vp[u] - sn * vq[u];
+            V[iq[u]] = sn * vp[u] + c * vq[u];
+          }
         }
       }
       __syncthreads();
