@@ -1,6 +1,7 @@
 """The pins catch plausible mistakes: each test compiles a copy of the oracle
-with one planted error (a sign, a dropped term, a transposed index), runs a pin
-against it on the CPU and checks that the pin fails."""
+with one planted error (a sign, a dropped term, a transposed index, the wrong
+threshold rule), runs a pin against it on the CPU and checks that the pin
+fails."""
 import os
 import shutil
 import subprocess
@@ -31,6 +32,14 @@ MUTATIONS = {
     # DFT with the conjugate twiddle
     "dft_sign": ("cos(ang) + (double)sign * sin(ang) * I", "cos(ang) - (double)sign * sin(ang) * I",
                  "test_dft_matches_fft"),
+    # isotropic threshold: a component left out of the group norm
+    "iso_norm_component": ("for (int i = 0; i < m; ++i) s += x[i] * x[i];",
+                           "for (int i = 1; i < m; ++i) s += x[i] * x[i];",
+                           "test_group_soft_is_the_prox_of_the_two_norm"),
+    # isotropic F-update thresholding each component on its own (the anisotropic rule)
+    "iso_per_component": ("orc_group_soft(x, 3, thr);",
+                          "for (int c = 0; c < 3; ++c) x[c] = orc_soft(x[c], thr);",
+                          "test_iso_admm_iterations_brute_force"),
 }
 
 
@@ -56,6 +65,7 @@ def test_planted_mistake_is_caught(tmp_path, monkeypatch, name):
     params = {
         "test_diff_adjoint_identity": {"shape": (5, 4, 3)},
         "test_svt_matrix_vs_numpy": {"m": 9, "n": 6},
+        "test_iso_admm_iterations_brute_force": {"exact": False},
     }.get(pin, {})
     with pytest.raises(AssertionError):
         fn(oracle, **params)

@@ -89,3 +89,40 @@ def test_full_rank_tdlrstv_equals_the_plain_iteration(orc):
     for name in ("L", "Z", "S", "G1", "G2"):
         assert np.max(np.abs(plain.get(name) - tuck.st.get(name))) < 1e-10, name
     assert abs(plain.mu - tuck.st.mu) < 1e-15
+
+
+# -------------------------------------------------- planted mistakes ---
+def test_pins_catch_planted_mistakes(monkeypatch):
+    """Plausible mistakes in the HOOI reference each fail a pin above: the
+    smallest eigenvectors instead of the largest, a mode left out of the
+    projection, and a sweep that ignores the other modes' factors."""
+    def smallest(G, r):
+        w, V = np.linalg.eigh(G)
+        return V[:, :r]
+
+    with monkeypatch.context() as m:
+        m.setattr(tk, "leading_eigvecs", smallest)
+        with pytest.raises(AssertionError):
+            test_exact_multilinear_rank_is_recovered()
+
+    def project_two_modes(X, U):
+        C = X
+        for n in range(2):
+            C = tk.mode_product(C, U[n].T, n)
+        for n in range(2):
+            C = tk.mode_product(C, U[n], n)
+        return C
+
+    with monkeypatch.context() as m:
+        m.setattr(tk, "project", project_two_modes)
+        with pytest.raises(AssertionError):
+            test_projection_is_the_kronecker_projector()
+
+    def sweep_ignoring_other_factors(X, U, ranks):
+        # each factor from the Gram of X itself: the HOSVD again, no HOOI
+        return tk.hosvd(X, ranks)
+
+    with monkeypatch.context() as m:
+        m.setattr(tk, "hooi_sweep", sweep_ignoring_other_factors)
+        with pytest.raises(AssertionError):
+            test_hooi_fit_never_decreases_and_beats_hosvd()
