@@ -46,43 +46,57 @@ __global__ void k_lam(int n, double w, float *__restrict__ lam) {
 }
 
 // --------------------------------------------------------- mode-3 DFTs
+// One thread per pixel and kKF frequencies (r2c) or bands (c2r).  The block
+// stages the twiddles of its kKF frequencies for a chunk of kCB bands (or
+// the reverse) in shared memory, so the inner loop is a broadcast 16-byte
+// read of two twiddles and four FMAs; every sum runs over bands (or
+// frequencies) in increasing order.
 constexpr int kPix = 128;  // pixels per block
-constexpr int kKF = 16;    // frequencies (or bands) per thread
+constexpr int kKF = 48;    // frequencies (or bands) per thread
+constexpr int kCB = 64;    // bands (or frequencies) per staged chunk
 
 // X_k(p) = sum_c (x(p, c) - ycoef y(p, c)) exp(-2 pi i k c / n3), k < h.
 __global__ void __launch_bounds__(kPix)
     k_r2c3(int n1, int n2, int n3, int h, size_t N, size_t P, const float *__restrict__ x,
            const float *__restrict__ y, float ycoef, float2 *__restrict__ out, int trans,
            const float2 *__restrict__ tw3) {
-  extern __shared__ float2 s_tw[];
-  for (int m = threadIdx.x; m < n3; m += blockDim.x) s_tw[m] = tw3[m];
-  __syncthreads();
+  __shared__ float4 s_t[kCB][kKF / 2];  // s_t[c][f/2] = twiddles of frequencies f, f + 1
   const size_t p = blockIdx.x * (size_t)kPix + threadIdx.x;
-  if (p >= P) return;
+  const bool live = p < P;
   const int kbase = blockIdx.y * kKF;
   const int b = blockIdx.z;
   const float *xb = x + (size_t)b * N;
   const float *yb = y ? y + (size_t)b * N : nullptr;
   float2 acc[kKF];
-  int idx[kKF], step[kKF];
 #pragma unroll
-  for (int f = 0; f < kKF; ++f) {
-    acc[f] = make_float2(0.f, 0.f);
-    idx[f] = 0;
-    step[f] = (kbase + f) % n3;
-  }
-  for (int c = 0; c < n3; ++c) {
-    float v = xb[p + P * c];
-    if (yb) v -= ycoef * yb[p + P * c];
+  for (int f = 0; f < kKF; ++f) acc[f] = make_float2(0.f, 0.f);
+  for (int c0 = 0; c0 < n3; c0 += kCB) {
+    const int cn = min(kCB, n3 - c0);
+    __syncthreads();
+    float2 *st = reinterpret_cast<float2 *>(&s_t[0][0]);
+    for (int e = threadIdx.x; e < cn * kKF; e += blockDim.x) {
+      const int cc = e / kKF, f = e % kKF;
+      const unsigned m = ((unsigned)(kbase + f) * (unsigned)(c0 + cc)) % (unsigned)n3;  // k c < 2^24
+      st[cc * kKF + f] = tw3[m];
+    }
+    __syncthreads();
+    if (live) {
+      for (int cc = 0; cc < cn; ++cc) {
+        const int c = c0 + cc;
+        float v = xb[p + P * c];
+        if (yb) v -= ycoef * yb[p + P * c];
 #pragma unroll
-    for (int f = 0; f < kKF; ++f) {
-      const float2 t = s_tw[idx[f]];
-      acc[f].x = fmaf(v, t.x, acc[f].x);
-      acc[f].y = fmaf(v, t.y, acc[f].y);
-      idx[f] += step[f];  // (k c) mod n3, advanced by k each band
-      if (idx[f] >= n3) idx[f] -= n3;
+        for (int f2 = 0; f2 < kKF / 2; ++f2) {
+          const float4 t = s_t[cc][f2];
+          acc[2 * f2].x = fmaf(v, t.x, acc[2 * f2].x);
+          acc[2 * f2].y = fmaf(v, t.y, acc[2 * f2].y);
+          acc[2 * f2 + 1].x = fmaf(v, t.z, acc[2 * f2 + 1].x);
+          acc[2 * f2 + 1].y = fmaf(v, t.w, acc[2 * f2 + 1].y);
+        }
+      }
     }
   }
+  if (!live) return;
   size_t pos = p;
   if (trans) {
     const size_t i = p % n1, j = p / n1;
@@ -102,11 +116,9 @@ __global__ void __launch_bounds__(kPix)
     k_c2r3(int n1, int n2, int n3, int h, size_t N, size_t P, const float2 *__restrict__ spec,
            int trans, const float2 *__restrict__ tw3, float *__restrict__ out, int mode,
            float *__restrict__ G4, const float *__restrict__ F, float mu, int gamma4) {
-  extern __shared__ float2 s_tw[];
-  for (int m = threadIdx.x; m < n3; m += blockDim.x) s_tw[m] = tw3[m];
-  __syncthreads();
+  __shared__ float4 s_t[kCB][kKF / 2];  // s_t[k][c/2] = twiddles of bands c, c + 1
   const size_t p = blockIdx.x * (size_t)kPix + threadIdx.x;
-  if (p >= P) return;
+  const bool live = p < P;
   const int cbase = blockIdx.y * kKF;
   const int b = blockIdx.z;
   size_t pos = p;
@@ -116,28 +128,38 @@ __global__ void __launch_bounds__(kPix)
   }
   const float2 *sb = spec + (size_t)b * h * P + pos;
   float acc[kKF];
-  int idx[kKF], step[kKF];
 #pragma unroll
-  for (int f = 0; f < kKF; ++f) {
-    acc[f] = 0.f;
-    idx[f] = 0;
-    step[f] = (cbase + f) % n3;
-  }
-  for (int k = 0; k < h; ++k) {
-    float2 X = sb[(size_t)k * P];
-    if (trans) X.y = -X.y;
-    const float wk = (k == 0 || 2 * k == n3) ? 1.0f : 2.0f;
-    X.x *= wk;
-    X.y *= wk;
+  for (int f = 0; f < kKF; ++f) acc[f] = 0.f;
+  for (int k0 = 0; k0 < h; k0 += kCB) {
+    const int kn = min(kCB, h - k0);
+    __syncthreads();
+    float2 *st = reinterpret_cast<float2 *>(&s_t[0][0]);
+    for (int e = threadIdx.x; e < kn * kKF; e += blockDim.x) {
+      const int kk = e / kKF, f = e % kKF;
+      const unsigned m = ((unsigned)(k0 + kk) * (unsigned)(cbase + f)) % (unsigned)n3;  // k c < 2^24
+      st[kk * kKF + f] = tw3[m];  // (cos, -sin) of 2 pi k c / n3
+    }
+    __syncthreads();
+    if (live) {
+      for (int kk = 0; kk < kn; ++kk) {
+        const int k = k0 + kk;
+        float2 X = sb[(size_t)k * P];
+        if (trans) X.y = -X.y;
+        const float wk = (k == 0 || 2 * k == n3) ? 1.0f : 2.0f;
+        X.x *= wk;
+        X.y *= wk;
 #pragma unroll
-    for (int f = 0; f < kKF; ++f) {
-      const float2 t = s_tw[idx[f]];  // (cos, -sin) of 2 pi k c / n3
-      acc[f] = fmaf(X.x, t.x, acc[f]);
-      acc[f] = fmaf(X.y, t.y, acc[f]);
-      idx[f] += step[f];
-      if (idx[f] >= n3) idx[f] -= n3;
+        for (int f2 = 0; f2 < kKF / 2; ++f2) {
+          const float4 t = s_t[kk][f2];
+          acc[2 * f2] = fmaf(X.x, t.x, acc[2 * f2]);
+          acc[2 * f2] = fmaf(X.y, t.y, acc[2 * f2]);
+          acc[2 * f2 + 1] = fmaf(X.x, t.z, acc[2 * f2 + 1]);
+          acc[2 * f2 + 1] = fmaf(X.y, t.w, acc[2 * f2 + 1]);
+        }
+      }
     }
   }
+  if (!live) return;
   const float inv = 1.0f / (float)n3;
   float *ob = out + (size_t)b * N;
 #pragma unroll
@@ -276,9 +298,8 @@ cudaError_t launch_tables(const Dims &d, const float w[3], float2 *tw3, float2 *
 cudaError_t launch_r2c3(const Dims &d, int nb, const float *x, const float *y, float ycoef,
                         float2 *out, int work_orient, const float2 *tw3, cudaStream_t st) {
   dim3 grid((unsigned)((d.P + kPix - 1) / kPix), (unsigned)((d.h + kKF - 1) / kKF), nb);
-  const size_t smem = sizeof(float2) * d.n3;
-  k_r2c3<<<grid, kPix, smem, st>>>(d.n1, d.n2, d.n3, d.h, d.N, d.P, x, y, ycoef, out,
-                                   work_orient && d.trans, tw3);
+  k_r2c3<<<grid, kPix, 0, st>>>(d.n1, d.n2, d.n3, d.h, d.N, d.P, x, y, ycoef, out,
+                                work_orient && d.trans, tw3);
   return cudaGetLastError();
 }
 
@@ -286,9 +307,8 @@ cudaError_t launch_c2r3(const Dims &d, int nb, const float2 *spec, int work_orie
                         const float2 *tw3, float *out, int mode, float *G4, const float *F,
                         float mu, int gamma4, cudaStream_t st) {
   dim3 grid((unsigned)((d.P + kPix - 1) / kPix), (unsigned)((d.n3 + kKF - 1) / kKF), nb);
-  const size_t smem = sizeof(float2) * d.n3;
-  k_c2r3<<<grid, kPix, smem, st>>>(d.n1, d.n2, d.n3, d.h, d.N, d.P, spec, work_orient && d.trans,
-                                   tw3, out, mode, G4, F, mu, gamma4);
+  k_c2r3<<<grid, kPix, 0, st>>>(d.n1, d.n2, d.n3, d.h, d.N, d.P, spec, work_orient && d.trans,
+                                tw3, out, mode, G4, F, mu, gamma4);
   return cudaGetLastError();
 }
 
