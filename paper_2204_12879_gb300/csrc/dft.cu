@@ -81,10 +81,16 @@ __global__ void __launch_bounds__(kPix)
     }
     __syncthreads();
     if (live) {
+      // band c + 1's inputs are loaded while band c's products run
+      float xn = xb[p + P * c0], yn = yb ? yb[p + P * c0] : 0.0f;
       for (int cc = 0; cc < cn; ++cc) {
-        const int c = c0 + cc;
-        float v = xb[p + P * c];
-        if (yb) v -= ycoef * yb[p + P * c];
+        float v = xn;
+        const float yv = yn;
+        if (cc + 1 < cn) {
+          xn = xb[p + P * (c0 + cc + 1)];
+          if (yb) yn = yb[p + P * (c0 + cc + 1)];
+        }
+        if (yb) v -= ycoef * yv;
 #pragma unroll
         for (int f2 = 0; f2 < kKF / 2; ++f2) {
           const float4 t = s_t[cc][f2];
@@ -141,9 +147,12 @@ __global__ void __launch_bounds__(kPix)
     }
     __syncthreads();
     if (live) {
+      // frequency k + 1's coefficient is loaded while frequency k's products run
+      float2 Xn = sb[(size_t)k0 * P];
       for (int kk = 0; kk < kn; ++kk) {
         const int k = k0 + kk;
-        float2 X = sb[(size_t)k * P];
+        float2 X = Xn;
+        if (kk + 1 < kn) Xn = sb[(size_t)(k + 1) * P];
         if (trans) X.y = -X.y;
         const float wk = (k == 0 || 2 * k == n3) ? 1.0f : 2.0f;
         X.x *= wk;

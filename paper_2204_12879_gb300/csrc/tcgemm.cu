@@ -105,6 +105,15 @@ __device__ __forceinline__ void put_split(char *hi, char *lo, int off, float x) 
   }
 }
 
+// Two consecutive-k values as BF16 hi and lo halves, one 4-byte word each
+// (off 4-byte aligned: k even).
+__device__ __forceinline__ void put_split2(char *hi, char *lo, int off, float x0, float x1) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+  const float2 hf = __bfloat1622float2(h);
+  *(__nv_bfloat162 *)(hi + off) = h;
+  *(__nv_bfloat162 *)(lo + off) = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+}
+
 template <int PREC>
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
                                     uint32_t accumulate) {
@@ -192,15 +201,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(CGemm g, int *err) {
   // B(k, n) at k + ldb n, or of 8 n, B(n, k) at n + ldb k).
   constexpr int kPa = TM * TK / kThreads, kPb = TN * TK / kThreads;
   float2 ra[kPa], rb[kPb];
+  // 3xBF16: a thread takes two consecutive k of one row (items i, i + 1 with
+  // i even), so that each hi or lo store is one 4-byte word of two halves and
+  // a warp's 32 words (8 rows x 4 k pairs) again fall in 32 distinct banks
   auto a_pos = [&](int i, int &r, int &kc) {
-    const int e = tid + kThreads * i, rest = e >> 5;
+    const int e = tid + kThreads * (PREC ? i >> 1 : i), rest = e >> 5;
     r = ((rest % (TM / 8)) << 3) | ((e >> 2) & 7);
     kc = ((rest / (TM / 8)) << 2) | (e & 3);
+    if (PREC) kc = (kc << 1) | (i & 1);
   };
   auto b_pos = [&](int i, int &n, int &kc) {
-    const int e = tid + kThreads * i, rest = e >> 5;
+    const int e = tid + kThreads * (PREC ? i >> 1 : i), rest = e >> 5;
     n = ((rest % (TN / 8)) << 3) | ((e >> 2) & 7);
     kc = ((rest / (TN / 8)) << 2) | (e & 3);
+    if (PREC) kc = (kc << 1) | (i & 1);
   };
   auto load_chunk = [&](int k0) {
 #pragma unroll
@@ -225,22 +239,42 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(CGemm g, int *err) {
   };
   if (nchunks > 0) load_chunk(0);
   for (int ch = 0; ch < nchunks && ok; ++ch) {
+    if (PREC == 0) {
 #pragma unroll
-    for (int i = 0; i < kPa; ++i) {
-      int r, kc;
-      a_pos(i, r, kc);
-      put_split<PREC>(aHi, aLo, koff<PREC>(r, kc), ra[i].x);
-      put_split<PREC>(aHi, aLo, koff<PREC>(r, kc + TK), ra[i].y);
-    }
+      for (int i = 0; i < kPa; ++i) {
+        int r, kc;
+        a_pos(i, r, kc);
+        put_split<PREC>(aHi, aLo, koff<PREC>(r, kc), ra[i].x);
+        put_split<PREC>(aHi, aLo, koff<PREC>(r, kc + TK), ra[i].y);
+      }
 #pragma unroll
-    for (int i = 0; i < kPb; ++i) {
-      int n, kc;
-      b_pos(i, n, kc);
-      const float2 v = rb[i];
-      put_split<PREC>(bReHi, bReLo, koff<PREC>(n, kc), v.x);  // [Re B | -Im B]
-      put_split<PREC>(bReHi, bReLo, koff<PREC>(n, kc + TK), -v.y);
-      put_split<PREC>(bImHi, bImLo, koff<PREC>(n, kc), v.y);  // [Im B | Re B]
-      put_split<PREC>(bImHi, bImLo, koff<PREC>(n, kc + TK), v.x);
+      for (int i = 0; i < kPb; ++i) {
+        int n, kc;
+        b_pos(i, n, kc);
+        const float2 v = rb[i];
+        put_split<PREC>(bReHi, bReLo, koff<PREC>(n, kc), v.x);  // [Re B | -Im B]
+        put_split<PREC>(bReHi, bReLo, koff<PREC>(n, kc + TK), -v.y);
+        put_split<PREC>(bImHi, bImLo, koff<PREC>(n, kc), v.y);  // [Im B | Re B]
+        put_split<PREC>(bImHi, bImLo, koff<PREC>(n, kc + TK), v.x);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < kPa; i += 2) {  // k pairs (kc even, kc + 1)
+        int r, kc;
+        a_pos(i, r, kc);
+        put_split2(aHi, aLo, koff<PREC>(r, kc), ra[i].x, ra[i + 1].x);
+        put_split2(aHi, aLo, koff<PREC>(r, kc + TK), ra[i].y, ra[i + 1].y);
+      }
+#pragma unroll
+      for (int i = 0; i < kPb; i += 2) {
+        int n, kc;
+        b_pos(i, n, kc);
+        const float2 v0 = rb[i], v1 = rb[i + 1];
+        put_split2(bReHi, bReLo, koff<PREC>(n, kc), v0.x, v1.x);  // [Re B | -Im B]
+        put_split2(bReHi, bReLo, koff<PREC>(n, kc + TK), -v0.y, -v1.y);
+        put_split2(bImHi, bImLo, koff<PREC>(n, kc), v0.y, v1.y);  // [Im B | Re B]
+        put_split2(bImHi, bImLo, koff<PREC>(n, kc + TK), v0.x, v1.x);
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
