@@ -81,23 +81,30 @@ __global__ void __launch_bounds__(kPix)
     }
     __syncthreads();
     if (live) {
-      // band c + 1's inputs are loaded while band c's products run
-      float xn = xb[p + P * c0], yn = yb ? yb[p + P * c0] : 0.0f;
-      for (int cc = 0; cc < cn; ++cc) {
-        float v = xn;
-        const float yv = yn;
-        if (cc + 1 < cn) {
-          xn = xb[p + P * (c0 + cc + 1)];
-          if (yb) yn = yb[p + P * (c0 + cc + 1)];
-        }
-        if (yb) v -= ycoef * yv;
+      // four bands' inputs are loaded before their products run, so that
+      // several loads per thread are in flight
+      for (int cc = 0; cc < cn; cc += 4) {
+        float v[4];
 #pragma unroll
-        for (int f2 = 0; f2 < kKF / 2; ++f2) {
-          const float4 t = s_t[cc][f2];
-          acc[2 * f2].x = fmaf(v, t.x, acc[2 * f2].x);
-          acc[2 * f2].y = fmaf(v, t.y, acc[2 * f2].y);
-          acc[2 * f2 + 1].x = fmaf(v, t.z, acc[2 * f2 + 1].x);
-          acc[2 * f2 + 1].y = fmaf(v, t.w, acc[2 * f2 + 1].y);
+        for (int u = 0; u < 4; ++u) {
+          const int c = c0 + cc + u;
+          v[u] = 0.0f;
+          if (cc + u < cn) {
+            v[u] = xb[p + P * c];
+            if (yb) v[u] -= ycoef * yb[p + P * c];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (cc + u >= cn) break;
+#pragma unroll
+          for (int f2 = 0; f2 < kKF / 2; ++f2) {
+            const float4 t = s_t[cc + u][f2];
+            acc[2 * f2].x = fmaf(v[u], t.x, acc[2 * f2].x);
+            acc[2 * f2].y = fmaf(v[u], t.y, acc[2 * f2].y);
+            acc[2 * f2 + 1].x = fmaf(v[u], t.z, acc[2 * f2 + 1].x);
+            acc[2 * f2 + 1].y = fmaf(v[u], t.w, acc[2 * f2 + 1].y);
+          }
         }
       }
     }
@@ -147,23 +154,29 @@ __global__ void __launch_bounds__(kPix)
     }
     __syncthreads();
     if (live) {
-      // frequency k + 1's coefficient is loaded while frequency k's products run
-      float2 Xn = sb[(size_t)k0 * P];
-      for (int kk = 0; kk < kn; ++kk) {
-        const int k = k0 + kk;
-        float2 X = Xn;
-        if (kk + 1 < kn) Xn = sb[(size_t)(k + 1) * P];
-        if (trans) X.y = -X.y;
-        const float wk = (k == 0 || 2 * k == n3) ? 1.0f : 2.0f;
-        X.x *= wk;
-        X.y *= wk;
+      // four frequencies' coefficients are loaded before their products run
+      for (int kk = 0; kk < kn; kk += 4) {
+        float2 Xs[4];
 #pragma unroll
-        for (int f2 = 0; f2 < kKF / 2; ++f2) {
-          const float4 t = s_t[kk][f2];
-          acc[2 * f2] = fmaf(X.x, t.x, acc[2 * f2]);
-          acc[2 * f2] = fmaf(X.y, t.y, acc[2 * f2]);
-          acc[2 * f2 + 1] = fmaf(X.x, t.z, acc[2 * f2 + 1]);
-          acc[2 * f2 + 1] = fmaf(X.y, t.w, acc[2 * f2 + 1]);
+        for (int u = 0; u < 4; ++u)
+          Xs[u] = kk + u < kn ? sb[(size_t)(k0 + kk + u) * P] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (kk + u >= kn) break;
+          const int k = k0 + kk + u;
+          float2 X = Xs[u];
+          if (trans) X.y = -X.y;
+          const float wk = (k == 0 || 2 * k == n3) ? 1.0f : 2.0f;
+          X.x *= wk;
+          X.y *= wk;
+#pragma unroll
+          for (int f2 = 0; f2 < kKF / 2; ++f2) {
+            const float4 t = s_t[kk + u][f2];
+            acc[2 * f2] = fmaf(X.x, t.x, acc[2 * f2]);
+            acc[2 * f2] = fmaf(X.y, t.y, acc[2 * f2]);
+            acc[2 * f2 + 1] = fmaf(X.x, t.z, acc[2 * f2 + 1]);
+            acc[2 * f2 + 1] = fmaf(X.y, t.w, acc[2 * f2 + 1]);
+          }
         }
       }
     }
