@@ -633,6 +633,36 @@ def run_micro(args):
                       "sweeps": sweeps, "slices": shape[2] // 2 + 1}))
 
 
+def run_sweep_profile(args):
+    """One warm-started denoise of the workload, printing after every ADMM
+    iteration the distribution of the Jacobi's per-slice sweep counts (all
+    slices of an E-step run concurrently, one CTA each, so the slowest slice
+    sets the E-step's time)."""
+    import numpy as np
+    import torch
+
+    from paper_2204_12879_gb300 import builder, lrstv
+    from synthetic import flat
+
+    builder.build()
+    lrstv.load()
+    wl = WORKLOADS[args.workload]
+    shape, _, Y = make_input(wl, 0)
+    n1, n2, n3 = shape
+    y = torch.from_numpy(flat(Y)).cuda()
+    flags = lrstv.FLAG_WARM_START if args.jacobi_start == "warm" else 0
+    with lrstv.Plan(n1, n2, n3, lrstv.Params.make(n1, n2, max_iter=wl["iters"], flags=flags)) as pl:
+        pl.init(y)
+        for it in range(wl["iters"]):
+            pl.iterate(1)
+            sw = np.abs(pl.slice_sweeps())
+            torch.cuda.synchronize()
+            print(json.dumps({"iteration": it, "max": int(sw.max()), "median": float(np.median(sw)),
+                              "mean": round(float(sw.mean()), 3),
+                              "slowest_slice": [int(v) for v in np.unravel_index(sw.argmax(), sw.shape)],
+                              "histogram": np.bincount(sw.ravel()).tolist()}), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -656,9 +686,15 @@ def main(argv=None):
     ap.add_argument("--micro", choices=["tsvt"], default=None,
                     help="time one standalone operator instead of the iteration")
     ap.add_argument("--shape", default="200,200,16", help="n1,n2,n3 for --micro")
+    ap.add_argument("--sweep-profile", action="store_true",
+                    help="print the per-slice Jacobi sweep distribution of every iteration of one "
+                         "denoise (c1-c3) instead of timing")
     args = ap.parse_args(argv)
     if args.micro:
         run_micro(args)
+        return
+    if args.sweep_profile:
+        run_sweep_profile(args)
         return
     if args.workload == "c4" and args.impl == "ours":
         print(json.dumps(run_batch(args)), flush=True)

@@ -239,6 +239,22 @@ def test_end_to_end_reading_flags(L, orc, flags):
     assert maxabs(X, ost.X) <= 1e-4
 
 
+@pytest.mark.parametrize("shape", [(1, 7, 5), (6, 1, 3), (5, 4, 1), (2, 2, 2), (9, 3, 2)])
+def test_end_to_end_degenerate_shapes(L, orc, shape):
+    """Whole runs on a single row or column, a single band (one Fourier
+    slice, no mode-3 differences to speak of) and the smallest cubes."""
+    rng = np.random.default_rng(sum(shape))
+    Y = f32(rng.uniform(0.0, 1.0, shape))
+    n1, n2, n3 = shape
+    with L.Plan(n1, n2, n3, L.Params.make(n1, n2, max_iter=8)) as pl:
+        X, S = pl.run(dev(Y))
+        X, S = host(X, shape), host(S, shape)
+    ost = orc.State(Y, orc.Params(n1=n1, n2=n2))
+    ost.iterate(8)
+    assert maxabs(X, ost.X) <= 1e-4, shape
+    assert maxabs(S, ost.get("S")) <= 1e-4, shape
+
+
 def test_end_to_end_ragged(L, orc):
     clean, X, S, stats, ost = _run_both(L, orc, (37, 29, 11), 15, 3)
     assert maxabs(X, ost.X) <= 1e-4

@@ -166,3 +166,17 @@ def test_tucker_inside_a_batch_equals_the_plan(L):
             X, _ = pl.run(Ys[i])
             torch.cuda.synchronize()
             assert torch.equal(X.cpu(), got[i]), i
+
+
+def test_rank_one_tucker(L, orc):
+    """The smallest Tucker model, multilinear rank (1, 1, 1), and ranks equal
+    to the size in one mode only."""
+    from oracle import tucker as tk
+    shape, iters = (20, 24, 8), 6
+    _, Y = _low_rank(shape, 3, 50)
+    for ranks in ((1, 1, 1), (20, 2, 1)):
+        X, S = _run(L, shape, ranks, iters, Y)
+        ref = tk.TuckerState(orc, Y, orc.Params(n1=20, n2=24), ranks)
+        ref.iterate(iters)
+        assert maxabs(X, ref.X) <= 1e-4, ranks
+        assert maxabs(S, ref.st.get("S")) <= 1e-4, ranks
