@@ -11,9 +11,9 @@
 // hi*hi + hi*lo + lo*hi with FP32 accumulation (the lo*lo term is below FP32
 // resolution), so the result carries about 2^-21 relative error per term
 // instead of TF32's 2^-11.  The tensor core accumulates with truncation, so
-// each K chunk (32 real terms) goes into a fresh TMEM tile that the threads
+// each K chunk (16 real terms) goes into a fresh TMEM tile that the threads
 // drain into FP32 register accumulators: accumulation error then grows over
-// 32 terms, not over the whole K.
+// 16 terms, not over the whole K.
 //
 // Complex arithmetic as real GEMMs with K doubled: for a K chunk,
 //   Re C += [Re A | Im A] . [Re B | -Im B]^T,   Im C += [Re A | Im A] . [Im B | Re B]^T.
@@ -25,14 +25,17 @@
 // MMA instructions of 3xTF32 (K = 16 per instruction instead of 8).
 //
 // Tile: 128 rows of C (M = 128 MMA), 64 complex columns (two N = 64 MMAs
-// into 128 TMEM columns), 16 complex K per chunk (four K = 8 TF32 or two
-// K = 16 BF16 MMA steps per product).  Operands are staged by the CTA's
-// threads into shared memory in the canonical K-major layout without swizzle:
-// 8-row x 16-byte core matrices, K-adjacent core matrices 128 B apart (LBO),
-// 8-row groups one chunk row (KR elements) apart (SBO).
-// One thread issues the MMAs and commits them to an mbarrier; every wait on
-// that barrier is bounded and, if it runs out, the CTA records an error flag,
-// skips its epilogue and still frees its tensor memory.
+// into 128 TMEM columns), 8 (3xTF32) or 16 (3xBF16) complex K per chunk: two
+// K = 8 TF32 or two K = 16 BF16 MMA steps per product, a 32 KB stage either
+// way.  Operands are staged by the CTA's threads into shared memory in the
+// canonical K-major layout without swizzle: 8-row x 16-byte core matrices,
+// K-adjacent core matrices 128 B apart (LBO), 8-row groups one chunk row
+// (KR elements) apart (SBO).  Two stages and two TMEM tiles pipeline the
+// chunks: chunk k is loaded and staged while chunk k - 1's MMAs run, and
+// chunk k - 1's tile is drained while chunk k's MMAs run.
+// One thread issues the MMAs and commits them to the stage's mbarrier; every
+// wait on a barrier is bounded and, if it runs out, the CTA records an error
+// flag, skips its epilogue and still frees its tensor memory.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -44,8 +47,6 @@ namespace {
 
 constexpr int TM = 128;       // rows of C per CTA
 constexpr int TN = 64;        // complex columns of C per CTA
-constexpr int TK = 16;        // complex K per chunk (32 real K)
-constexpr int KR = 2 * TK;    // real K per chunk
 constexpr int kThreads = 128; // four warps: TMEM lanes 0..127
 constexpr uint32_t kLBO = 128;  // bytes
 constexpr long long kWaitLimit = 20000000;
@@ -56,12 +57,16 @@ constexpr long long kWaitLimit = 20000000;
 template <int PREC>
 struct Prec {
   static constexpr int kBytes = PREC ? 2 : 4;
+  // complex K per chunk: 8 for 3xTF32 (16 real terms per TMEM tile), 16 for
+  // 3xBF16; either way a stage is 32 KB and two stages fit two CTAs per SM
+  static constexpr int kTK = PREC ? 16 : 8;
+  static constexpr int kKR = 2 * kTK;                             // real K per chunk
   static constexpr int kPerCore = 16 / kBytes;                    // along K
-  static constexpr uint32_t kSBO = (KR / kPerCore) * 128;         // bytes
+  static constexpr uint32_t kSBO = (kKR / kPerCore) * 128;        // bytes
   static constexpr int kMmaK = PREC ? 16 : 8;                     // K per instruction
   static constexpr uint32_t kFmt = PREC ? 1u : 2u;
-  static constexpr size_t kTileA = (size_t)TM * KR * kBytes;      // bytes, one split
-  static constexpr size_t kTileB = (size_t)TN * KR * kBytes;      // bytes, one split, re or im
+  static constexpr size_t kTileA = (size_t)TM * kKR * kBytes;     // bytes, one split
+  static constexpr size_t kTileB = (size_t)TN * kKR * kBytes;     // bytes, one split, re or im
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -146,10 +151,11 @@ template <int OPB, int EPI, int PREC>
 __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(CGemm g, int *err) {
   extern __shared__ __align__(1024) char smem[];
   using P = Prec<PREC>;
-  char *aHi = smem, *aLo = aHi + P::kTileA;
-  char *bReHi = aLo + P::kTileA, *bReLo = bReHi + P::kTileB;
-  char *bImHi = bReLo + P::kTileB, *bImLo = bImHi + P::kTileB;
-  __shared__ __align__(8) uint64_t mbar;
+  // two shared-memory stages, so that a chunk is staged while the previous
+  // chunk's MMAs run, and two TMEM tiles (one per stage)
+  constexpr uint32_t kCols = 256;
+  constexpr size_t kStageBytes = 2 * P::kTileA + 4 * P::kTileB;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tslot;
   __shared__ int s_ok;
 
@@ -161,13 +167,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(CGemm g, int *err) {
   const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
 
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
     asm volatile("fence.mbarrier_init.release.cluster;");
     s_ok = 1;
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
-        smem_u32(&tslot)));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tslot)),
+                 "n"(kCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -177,9 +185,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(CGemm g, int *err) {
   // D format F32, A and B in the precision's format, both K-major, N, M
   const uint32_t idesc = (1u << 4) | (P::kFmt << 7) | (P::kFmt << 10) |
                          ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
-  const uint32_t bar = smem_u32(&mbar);
-
-  uint32_t phase = 0;
+  const uint32_t bar0 = smem_u32(&mbar[0]), bar1 = smem_u32(&mbar[1]);
+  // per stage: the parity of its next MMA commit, and whether a commit is
+  // outstanding (issued, not yet seen complete)
+  uint32_t ph0 = 0u, ph1 = 0u;
+  bool out0 = false, out1 = false;
   bool ok = true;
   const int row = 32 * warp + lane;  // TMEM lane = row of the tile this thread drains
   const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);
@@ -189,6 +199,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(CGemm g, int *err) {
     accRe[c] = 0.f;
     accIm[c] = 0.f;
   }
+  constexpr int TK = P::kTK, KR = P::kKR;
   const int nchunks = (g.K + TK - 1) / TK;
   // Staging is software-pipelined: chunk ch + 1's operands are loaded from
   // global memory into registers while chunk ch's MMAs run, then split and
@@ -237,8 +248,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(CGemm g, int *err) {
       rb[i] = v;
     }
   };
-  if (nchunks > 0) load_chunk(0);
-  for (int ch = 0; ch < nchunks && ok; ++ch) {
+  // split the registers' chunk into the hi / lo tiles of stage `st`
+  auto store_chunk = [&](int st) {
+    char *aHi = smem + st * kStageBytes, *aLo = aHi + P::kTileA;
+    char *bReHi = aLo + P::kTileA, *bReLo = bReHi + P::kTileB;
+    char *bImHi = bReLo + P::kTileB, *bImLo = bImHi + P::kTileB;
     if (PREC == 0) {
 #pragma unroll
       for (int i = 0; i < kPa; ++i) {
@@ -276,70 +290,118 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(CGemm g, int *err) {
         put_split2(bImHi, bImLo, koff<PREC>(n, kc + TK), v0.x, v1.x);
       }
     }
+  };
+  // one thread: the chunk's MMAs on stage `st` into a fresh TMEM tile `st`,
+  // committed to barrier `st`
+  auto issue = [&](int st) {
+    const char *base = smem + st * kStageBytes;
+    const uint32_t a_hi = smem_u32(base), a_lo = a_hi + (uint32_t)P::kTileA;
+    const uint32_t br_hi = a_lo + (uint32_t)P::kTileA, br_lo = br_hi + (uint32_t)P::kTileB;
+    const uint32_t bi_hi = br_lo + (uint32_t)P::kTileB, bi_lo = bi_hi + (uint32_t)P::kTileB;
+    const uint32_t dt = tmem + (uint32_t)st * (2 * TN);
+#pragma unroll
+    for (int j = 0; j < KR / P::kMmaK; ++j) {  // one instruction spans two core matrices
+      const uint32_t ko = (uint32_t)j * 2 * kLBO;
+      const uint32_t acc0 = j > 0 ? 1u : 0u;  // a fresh tile per chunk
+      // Re C (tile columns 0..63), Im C (64..127); three split products each
+      mma<PREC>(dt, sdesc<PREC>(a_hi + ko), sdesc<PREC>(br_hi + ko), idesc, acc0);
+      mma<PREC>(dt, sdesc<PREC>(a_hi + ko), sdesc<PREC>(br_lo + ko), idesc, 1u);
+      mma<PREC>(dt, sdesc<PREC>(a_lo + ko), sdesc<PREC>(br_hi + ko), idesc, 1u);
+      mma<PREC>(dt + TN, sdesc<PREC>(a_hi + ko), sdesc<PREC>(bi_hi + ko), idesc, acc0);
+      mma<PREC>(dt + TN, sdesc<PREC>(a_hi + ko), sdesc<PREC>(bi_lo + ko), idesc, 1u);
+      mma<PREC>(dt + TN, sdesc<PREC>(a_lo + ko), sdesc<PREC>(bi_hi + ko), idesc, 1u);
+    }
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            st ? bar1 : bar0));
+  };
+  auto mark_issued = [&](int st) {
+    if (st) out1 = true;
+    else out0 = true;
+  };
+  // add TMEM tile `st` into the FP32 register accumulators
+  auto drain = [&](int st) {
+    const uint32_t tile = (uint32_t)st * (2 * TN);
+#pragma unroll
+    for (int c0 = 0; c0 < TN; c0 += 16) {
+      uint32_t re[16], im[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]),
+            "=r"(re[6]), "=r"(re[7]), "=r"(re[8]), "=r"(re[9]), "=r"(re[10]), "=r"(re[11]),
+            "=r"(re[12]), "=r"(re[13]), "=r"(re[14]), "=r"(re[15])
+          : "r"(tl + tile + c0));
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]),
+            "=r"(im[6]), "=r"(im[7]), "=r"(im[8]), "=r"(im[9]), "=r"(im[10]), "=r"(im[11]),
+            "=r"(im[12]), "=r"(im[13]), "=r"(im[14]), "=r"(im[15])
+          : "r"(tl + tile + TN + c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        accRe[c0 + c] += __uint_as_float(re[c]);
+        accIm[c0 + c] += __uint_as_float(im[c]);
+      }
+    }
+    // the tile is rewritten only after every thread's reads
+    asm volatile("tcgen05.fence::before_thread_sync;");
+  };
+  // every thread waits for the MMAs committed to barrier `st`; on a timeout
+  // the commit stays outstanding for the last bounded wait before the free
+  auto wait_mmas = [&](int st) {
+    const bool done = mbar_wait(st ? bar1 : bar0, st ? ph1 : ph0);
+    if (done) {
+      if (st) {
+        ph1 ^= 1u;
+        out1 = false;
+      } else {
+        ph0 ^= 1u;
+        out0 = false;
+      }
+    } else {
+      ok = false;
+      if (tid == 0) s_ok = 0;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+  };
+  auto stage_barrier = [&]() {
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (tid == 0) {
-      const uint32_t a_hi = smem_u32(aHi), a_lo = smem_u32(aLo);
-      const uint32_t br_hi = smem_u32(bReHi), br_lo = smem_u32(bReLo);
-      const uint32_t bi_hi = smem_u32(bImHi), bi_lo = smem_u32(bImLo);
-#pragma unroll
-      for (int j = 0; j < KR / P::kMmaK; ++j) {  // one instruction spans two core matrices
-        const uint32_t ko = (uint32_t)j * 2 * kLBO;
-        const uint32_t acc0 = j > 0 ? 1u : 0u;  // a fresh tile per chunk
-        // Re C (TMEM columns 0..63), Im C (64..127); three split products each
-        mma<PREC>(tmem, sdesc<PREC>(a_hi + ko), sdesc<PREC>(br_hi + ko), idesc, acc0);
-        mma<PREC>(tmem, sdesc<PREC>(a_hi + ko), sdesc<PREC>(br_lo + ko), idesc, 1u);
-        mma<PREC>(tmem, sdesc<PREC>(a_lo + ko), sdesc<PREC>(br_hi + ko), idesc, 1u);
-        mma<PREC>(tmem + TN, sdesc<PREC>(a_hi + ko), sdesc<PREC>(bi_hi + ko), idesc, acc0);
-        mma<PREC>(tmem + TN, sdesc<PREC>(a_hi + ko), sdesc<PREC>(bi_lo + ko), idesc, 1u);
-        mma<PREC>(tmem + TN, sdesc<PREC>(a_lo + ko), sdesc<PREC>(bi_hi + ko), idesc, 1u);
-      }
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar));
+  };
+  if (nchunks > 0) load_chunk(0);
+  // chunk ch: stage s = ch & 1 is written while chunk ch - 1's MMAs (stage
+  // s ^ 1) run; once those are done, chunk ch's MMAs are issued and chunk
+  // ch - 1's tile is drained while they run
+  for (int ch = 0; ch < nchunks && ok; ++ch) {
+    const int st = ch & 1;
+    store_chunk(st);  // stage st was last read by chunk ch - 2, already waited for
+    if (ch + 1 < nchunks) load_chunk((ch + 1) * TK);
+    stage_barrier();
+    if (ch > 0) {
+      wait_mmas(st ^ 1);
+      __syncthreads();
+      ok = ok && s_ok;
+      if (!ok) break;
     }
-    if (ch + 1 < nchunks) load_chunk((ch + 1) * TK);  // in flight during the MMAs
-    // the MMAs must finish reading the tiles before they are restaged
-    if (!mbar_wait(bar, phase)) {
-      ok = false;
-      if (tid == 0) s_ok = 0;
-    }
-    phase ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) issue(st);
+    mark_issued(st);
+    if (ch > 0) drain(st ^ 1);
+  }
+  if (ok && nchunks > 0) {
+    const int last = (nchunks - 1) & 1;
+    wait_mmas(last);
     __syncthreads();
     ok = ok && s_ok;
-    if (ok) {  // drain this chunk's tile into the register accumulators
-#pragma unroll
-      for (int c0 = 0; c0 < TN; c0 += 16) {
-        uint32_t re[16], im[16];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]),
-              "=r"(re[6]), "=r"(re[7]), "=r"(re[8]), "=r"(re[9]), "=r"(re[10]), "=r"(re[11]),
-              "=r"(re[12]), "=r"(re[13]), "=r"(re[14]), "=r"(re[15])
-            : "r"(tl + c0));
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]),
-              "=r"(im[6]), "=r"(im[7]), "=r"(im[8]), "=r"(im[9]), "=r"(im[10]), "=r"(im[11]),
-              "=r"(im[12]), "=r"(im[13]), "=r"(im[14]), "=r"(im[15])
-            : "r"(tl + TN + c0));
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          accRe[c0 + c] += __uint_as_float(re[c]);
-          accIm[c0 + c] += __uint_as_float(im[c]);
-        }
-      }
-      // the next chunk's MMAs overwrite the tile only after every thread's reads
-      asm volatile("tcgen05.fence::before_thread_sync;");
-    }
+    if (ok) drain(last);
   }
   if (!ok) {
     if (tid == 0 && err) atomicExch(err, 1);
     // give MMAs still in flight a last bounded chance to land before the free
-    mbar_wait(bar, phase ^ 1u);
+    if (out0) mbar_wait(bar0, ph0);
+    if (out1) mbar_wait(bar1, ph1);
   } else if (nchunks > 0) {
     // epilogue: thread (warp w, lane l) owns row m0 + 32 w + l of the tile
     const int gm = m0 + row;
@@ -363,12 +425,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(CGemm g, int *err) {
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kCols));
 }
 
 template <int PREC>
 size_t smem_bytes() {
-  return 2 * Prec<PREC>::kTileA + 4 * Prec<PREC>::kTileB;
+  return 2 * (2 * Prec<PREC>::kTileA + 4 * Prec<PREC>::kTileB);
 }
 
 template <int OPB, int EPI, int PREC>
