@@ -252,6 +252,12 @@ struct lrstv_plan {
   cudaStream_t side;
   cudaEvent_t ev_fs, ev_side;
   float2 *zA, *zB;
+  // ... and, with the warm start, the next E-step's Newton-Schulz step on V,
+  // as soon as the current E-step has read V (ns_req: schedule it; ns_ready:
+  // V has had it, after ev_ns; Vn1, Vn2: its products)
+  cudaEvent_t ev_sig, ev_ns;
+  float2 *Vn1, *Vn2;
+  int ns_req, ns_ready;
   // Tucker (HOOI) L-update of the full TDLRSTV model (lrstv_plan_set_tucker)
   int tucker;
   void *tk_mem;
@@ -275,12 +281,14 @@ GemmSel plan_gemm(const lrstv_plan *pl) {
 // E-step's right singular vectors): C = V V^H (into Vs), D = C V (into Dscr),
 // V := 1.5 V - 0.5 D; then W = A V into Wout (A, Wout, Dscr: the plan's
 // specA / specB in either role; Dscr may be Wout).
-cudaError_t warm_basis(lrstv_plan *pl, const float2 *A, float2 *Wout, float2 *Dscr,
-                       cudaStream_t st) {
+// One Newton-Schulz step on every slice's V on stream st: C = V V^H (into
+// Cscr), D = C V (into Dscr, slice stride dstride), V := 1.5 V - 0.5 D.
+cudaError_t ns_basis(lrstv_plan *pl, float2 *Cscr, float2 *Dscr, long long dstride,
+                     cudaStream_t st) {
   const Dims &d = pl->d;
   const int ns = 3 * d.h;
   const GemmSel gs = plan_gemm(pl);
-  const long long nc2 = (long long)d.nc * d.nc, P = (long long)d.P;
+  const long long nc2 = (long long)d.nc * d.nc;
   auto run = [&](const CGemm &g) {
     Span sp(&pl->prof, LRSTV_K_WARM_E, st);
     return gemm(g, gs, st);
@@ -290,21 +298,39 @@ cudaError_t warm_basis(lrstv_plan *pl, const float2 *A, float2 *Wout, float2 *Ds
   g.batch = ns;
   g.A = pl->V; g.sA = nc2; g.lda = d.nc;
   g.B = pl->V; g.sB = nc2; g.ldb = d.nc; g.opB = 1;
-  g.C = pl->Vs; g.sC = nc2; g.ldc = d.nc;
+  g.C = Cscr; g.sC = nc2; g.ldc = d.nc;
   g.M = d.nc; g.N = d.nc; g.K = d.nc;
   if ((e = run(g)) != cudaSuccess) return e;
-  g.A = pl->Vs; g.B = pl->V; g.opB = 0;
-  g.C = Dscr; g.sC = P; g.ldc = d.nc;
+  g.A = Cscr; g.B = pl->V; g.opB = 0;
+  g.C = Dscr; g.sC = dstride; g.ldc = d.nc;
   if ((e = run(g)) != cudaSuccess) return e;
-  {
-    Span sp(&pl->prof, LRSTV_K_WARM_E, st);
-    if ((e = launch_ns_update(d.nc, ns, (size_t)P, pl->V, Dscr, st)) != cudaSuccess) return e;
+  Span sp(&pl->prof, LRSTV_K_WARM_E, st);
+  return launch_ns_update(d.nc, ns, (size_t)dstride, pl->V, Dscr, st);
+}
+
+// Warm start of a plan's E-step: the Newton-Schulz step on V (unless it
+// already ran, ns_ready), then W = A V into Wout (A, Wout, Dscr: the plan's
+// specA / specB in either role; Dscr may be Wout).
+cudaError_t warm_basis(lrstv_plan *pl, const float2 *A, float2 *Wout, float2 *Dscr,
+                       cudaStream_t st) {
+  const Dims &d = pl->d;
+  const int ns = 3 * d.h;
+  const long long nc2 = (long long)d.nc * d.nc, P = (long long)d.P;
+  cudaError_t e;
+  if (pl->ns_ready) {
+    if ((e = cudaStreamWaitEvent(st, pl->ev_ns, 0)) != cudaSuccess) return e;
+  } else if ((e = ns_basis(pl, pl->Vs, Dscr, P, st)) != cudaSuccess) {
+    return e;
   }
+  pl->ns_ready = 0;
+  CGemm g{};
+  g.batch = ns;
   g.A = A; g.sA = P; g.lda = d.nr;
   g.B = pl->V; g.sB = nc2; g.ldb = d.nc; g.opB = 0;
   g.C = Wout; g.sC = P; g.ldc = d.nr;
   g.M = d.nr; g.N = d.nc; g.K = d.nc;
-  return run(g);
+  Span sp(&pl->prof, LRSTV_K_WARM_E, st);
+  return gemm(g, plan_gemm(pl), st);
 }
 
 // The E-step with a warm-started Jacobi (LRSTV_FLAG_WARM_START).  V keeps the
@@ -344,6 +370,15 @@ cudaError_t tsvt_warm(lrstv_plan *pl, float ycoef, float t, float mu, int gamma4
     if ((e = launch_sigma_scale(d, ns, Wm, pl->V, t, nullptr, pl->Vs, st)) != cudaSuccess)
       return e;
   }
+  if (pl->ns_req) {
+    // V is read: the next E-step's Newton-Schulz step runs on the side
+    // stream, with scratch of its own, while this E-step finishes
+    if ((e = cudaEventRecord(pl->ev_sig, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(pl->side, pl->ev_sig, 0)) != cudaSuccess) return e;
+    if ((e = ns_basis(pl, pl->Vn1, pl->Vn2, nc2, pl->side)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(pl->ev_ns, pl->side)) != cudaSuccess) return e;
+    pl->ns_ready = 1;
+  }
   CGemm g{};
   g.A = Wm; g.sA = P; g.lda = d.nr;
   g.B = pl->Vs; g.sB = nc2; g.ldb = d.nc; g.opB = 1;
@@ -376,6 +411,8 @@ size_t plan_layout(lrstv_plan *pl, void *base) {
   pl->specB = c.take<float2>(3 * (size_t)d.h * d.P);
   pl->V = c.take<float2>(3 * (size_t)d.h * d.nc * d.nc);
   pl->Vs = c.take<float2>(3 * (size_t)d.h * d.nc * d.nc);
+  pl->Vn1 = c.take<float2>(3 * (size_t)d.h * d.nc * d.nc);
+  pl->Vn2 = c.take<float2>(3 * (size_t)d.h * d.nc * d.nc);
   pl->ms2 = c.take<float>(3);
   pl->zA = c.take<float2>((size_t)d.h * d.P);
   pl->zB = c.take<float2>((size_t)d.h * d.P);
@@ -431,6 +468,7 @@ int init_async(lrstv_plan *pl, const float *Y, cudaStream_t st) {
   pl->mu = pl->prm.mu0;
   pl->iter = 0;
   pl->vwarm = 0;
+  pl->ns_ready = 0;
   pl->tk.valid = 0;
   pl->tk.vvalid[0] = pl->tk.vvalid[1] = pl->tk.vvalid[2] = 0;
   if (pl->tucker) CK(cudaMemsetAsync(pl->tk.sweeps, 0, sizeof(int) * kTuckerSweepSlots, st));
@@ -484,7 +522,12 @@ int iterate_async(lrstv_plan *pl, int iters, cudaStream_t st) {
       if ((rc = step_z_mu(pl, mu_next, pl->zA, pl->zB, pl->side)) != LRSTV_OK) return rc;
       CK(cudaEventRecord(pl->ev_side, pl->side));
     }
-    if ((rc = lrstv_step_e(pl, st)) != LRSTV_OK) return rc;
+    // with another iteration to follow (whose E-step joins the side stream
+    // back), the next Newton-Schulz step may start early
+    pl->ns_req = it + 1 < iters ? 1 : 0;
+    rc = lrstv_step_e(pl, st);
+    pl->ns_req = 0;
+    if (rc != LRSTV_OK) return rc;
     if ((rc = lrstv_step_mu(pl)) != LRSTV_OK) return rc;
   }
   return LRSTV_OK;
@@ -590,6 +633,8 @@ int lrstv_plan_create(int n1, int n2, int n3, const lrstv_params *params, lrstv_
       cudaStreamCreateWithPriority(&pl->side, cudaStreamNonBlocking, lo_prio) != cudaSuccess ||
       cudaEventCreateWithFlags(&pl->ev_fs, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&pl->ev_side, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&pl->ev_sig, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&pl->ev_ns, cudaEventDisableTiming) != cudaSuccess ||
       cudaMemsetAsync(pl->arena, 0, pl->arena_bytes, pl->cap_stream) != cudaSuccess ||
       launch_tables(pl->d, pl->prm.w, pl->tb.tw3, pl->tb.F1, pl->tb.G1, pl->tb.F2, pl->tb.G2,
                     pl->tb.lam1, pl->tb.lam2, pl->tb.lam3, pl->cap_stream) != cudaSuccess ||
@@ -599,6 +644,8 @@ int lrstv_plan_create(int n1, int n2, int n3, const lrstv_params *params, lrstv_
     if (pl->side) cudaStreamDestroy(pl->side);
     if (pl->ev_fs) cudaEventDestroy(pl->ev_fs);
     if (pl->ev_side) cudaEventDestroy(pl->ev_side);
+    if (pl->ev_sig) cudaEventDestroy(pl->ev_sig);
+    if (pl->ev_ns) cudaEventDestroy(pl->ev_ns);
     cudaFree(pl->arena);
     delete pl;
     return LRSTV_ERR_CUDA;
@@ -620,6 +667,8 @@ int lrstv_plan_destroy(lrstv_plan *pl) {
   if (cudaStreamDestroy(pl->side) != cudaSuccess) rc = LRSTV_ERR_CUDA;
   if (cudaEventDestroy(pl->ev_fs) != cudaSuccess) rc = LRSTV_ERR_CUDA;
   if (cudaEventDestroy(pl->ev_side) != cudaSuccess) rc = LRSTV_ERR_CUDA;
+  if (cudaEventDestroy(pl->ev_sig) != cudaSuccess) rc = LRSTV_ERR_CUDA;
+  if (cudaEventDestroy(pl->ev_ns) != cudaSuccess) rc = LRSTV_ERR_CUDA;
   if (cudaFree(pl->arena) != cudaSuccess) rc = LRSTV_ERR_CUDA;
   if (pl->tk_mem && cudaFree(pl->tk_mem) != cudaSuccess) rc = LRSTV_ERR_CUDA;
   delete pl;
@@ -809,6 +858,7 @@ int lrstv_state_set(lrstv_plan *pl, int block, const float *src, void *stream) {
   if (!dst) return LRSTV_ERR_ARG;
   CK(cudaMemcpyAsync(dst, src, sizeof(float) * n, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
   pl->vwarm = 0;  // the imported state has no Jacobi history
+  pl->ns_ready = 0;
   pl->tk.valid = 0;  // nor Tucker factors
   pl->tk.vvalid[0] = pl->tk.vvalid[1] = pl->tk.vvalid[2] = 0;
   return LRSTV_OK;
