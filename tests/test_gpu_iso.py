@@ -90,3 +90,40 @@ def test_iso_differs_from_anisotropic(L):
             torch.cuda.synchronize()
             outs.append(host3(pl.get("F"), shape))
     assert np.max(np.abs(outs[0] - outs[1])) > 1e-4
+
+
+def test_all_extensions_together(L, orc):
+    """The isotropic F-update, the Tucker L-update, the warm start and the
+    mixed-precision GEMMs in one plan, against the FP64 reference with the
+    isotropic flag (the mixed-precision bound, 1e-3)."""
+    from oracle import tucker as tk
+    from tests.test_gpu_tucker import _low_rank
+    shape, ranks, iters = (24, 20, 9), (3, 3, 3), 8
+    _, Y = _low_rank(shape, 3, 61)
+    flags = L.FLAG_ISO_TV | L.FLAG_WARM_START | L.FLAG_BF16X3
+    with L.Plan(*shape, L.Params.make(24, 20, max_iter=iters, flags=flags)) as pl:
+        pl.set_tucker(ranks)
+        X, S, st = pl.run(dev(Y), stats=True)
+        X = host(X, shape)
+    assert st.jacobi_unconverged == 0 and st.gemm_errors == 0
+    ref = tk.TuckerState(orc, Y, orc.Params(n1=24, n2=20), ranks, flags=orc.FLAG_ISO_TV)
+    ref.iterate(iters)
+    print("all extensions: max-abs", maxabs(X, ref.X))
+    assert maxabs(X, ref.X) <= 1e-3
+
+
+def test_iso_batch_equals_plans(L):
+    """A batch of isotropic cubes gives each plan's bits."""
+    import torch
+    shapes = [(32, 32, 16), (20, 28, 9)]
+    Ys = [dev(_noisy(s, 70 + i)[1]) for i, s in enumerate(shapes)]
+    p = L.Params.make(32, 32, max_iter=6, flags=L.FLAG_ISO_TV | L.FLAG_WARM_START)
+    with L.Batch(shapes, p) as b:
+        Xs, _ = b.run(Ys)
+        torch.cuda.synchronize()
+        got = [x.cpu() for x in Xs]
+    for i, sh in enumerate(shapes):
+        with L.Plan(*sh, p) as pl:
+            X, _ = pl.run(Ys[i])
+            torch.cuda.synchronize()
+            assert torch.equal(X.cpu(), got[i]), i
