@@ -652,6 +652,8 @@ def run_sweep_profile(args):
     y = torch.from_numpy(flat(Y)).cuda()
     flags = lrstv.FLAG_WARM_START if args.jacobi_start == "warm" else 0
     with lrstv.Plan(n1, n2, n3, lrstv.Params.make(n1, n2, max_iter=wl["iters"], flags=flags)) as pl:
+        if args.tucker:
+            pl.set_tucker((max(1, round(0.8 * n1)), max(1, round(0.8 * n2)), min(args.tucker, n3)))
         pl.init(y)
         for it in range(wl["iters"]):
             pl.iterate(1)
