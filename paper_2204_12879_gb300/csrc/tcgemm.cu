@@ -47,7 +47,9 @@ namespace {
 
 constexpr int TM = 128;       // rows of C per CTA
 constexpr int TN = 64;        // complex columns of C per CTA
-constexpr int kThreads = 128; // four warps: TMEM lanes 0..127
+// eight warps: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (rows of the tile)
+// and, by warpgroup, columns 0..31 or 32..63 of each Re / Im tile
+constexpr int kThreads = 256;
 constexpr uint32_t kLBO = 128;  // bytes
 constexpr long long kWaitLimit = 20000000;
 
@@ -148,7 +150,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 }
 
 template <int OPB, int EPI, int PREC>
-__global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(CGemm g, int *err) {
+__global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, int *err) {
   extern __shared__ __align__(1024) char smem[];
   using P = Prec<PREC>;
   // two shared-memory stages, so that a chunk is staged while the previous
@@ -191,11 +193,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(CGemm g, int *err) {
   uint32_t ph0 = 0u, ph1 = 0u;
   bool out0 = false, out1 = false;
   bool ok = true;
-  const int row = 32 * warp + lane;  // TMEM lane = row of the tile this thread drains
-  const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);
-  float accRe[TN], accIm[TN];
+  const int row = 32 * (warp & 3) + lane;  // TMEM lane = row of the tile this thread drains
+  const int colh = (warp >> 2) * (TN / 2);  // first of the 32 columns it drains
+  const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)colh;
+  float accRe[TN / 2], accIm[TN / 2];
 #pragma unroll
-  for (int c = 0; c < TN; ++c) {
+  for (int c = 0; c < TN / 2; ++c) {
     accRe[c] = 0.f;
     accIm[c] = 0.f;
   }
@@ -323,7 +326,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(CGemm g, int *err) {
   auto drain = [&](int st) {
     const uint32_t tile = (uint32_t)st * (2 * TN);
 #pragma unroll
-    for (int c0 = 0; c0 < TN; c0 += 16) {
+    for (int c0 = 0; c0 < TN / 2; c0 += 16) {
       uint32_t re[16], im[16];
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -403,13 +406,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(CGemm g, int *err) {
     if (out0) mbar_wait(bar0, ph0);
     if (out1) mbar_wait(bar1, ph1);
   } else if (nchunks > 0) {
-    // epilogue: thread (warp w, lane l) owns row m0 + 32 w + l of the tile
+    // epilogue: thread (warp w, lane l) owns row m0 + 32 (w mod 4) + l of the
+    // tile, columns colh .. colh + 31
     const int gm = m0 + row;
     const int lb = g.lam3_period > 0 ? b % g.lam3_period : b;
     if (gm < g.M) {
 #pragma unroll
-      for (int c = 0; c < TN; ++c) {
-        const int n = n0 + c;
+      for (int c = 0; c < TN / 2; ++c) {
+        const int n = n0 + colh + c;
         if (n >= g.N) break;
         float2 v = make_float2(accRe[c], accIm[c]);
         if (EPI == 1) {
