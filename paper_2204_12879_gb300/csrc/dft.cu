@@ -50,26 +50,46 @@ __global__ void k_lam(int n, double w, float *__restrict__ lam) {
 // stages the twiddles of its kKF frequencies for a chunk of kCB bands (or
 // the reverse) in shared memory, so the inner loop is a broadcast 16-byte
 // read of two twiddles and four FMAs; every sum runs over bands (or
-// frequencies) in increasing order.
+// frequencies) in increasing order.  The inputs of the next four bands (or
+// frequencies) are loaded while the current four's products run.  The
+// blocks of one pixel tile's frequency (or band) groups are adjacent in
+// launch order (blockIdx.x = tile * groups + group), so the tile's inputs,
+// which every group reads, come from DRAM once and from L2 after that.
 constexpr int kPix = 128;  // pixels per block
 constexpr int kKF = 48;    // frequencies (or bands) per thread
 constexpr int kCB = 64;    // bands (or frequencies) per staged chunk
+static_assert(kCB % 4 == 0, "the four-deep loads step across chunks");
 
-// X_k(p) = sum_c (x(p, c) - ycoef y(p, c)) exp(-2 pi i k c / n3), k < h.
-__global__ void __launch_bounds__(kPix)
+// X_k(p) = sum_c (x(p, c) - ycoef y(p, c)) exp(-2 pi i k c / n3), k < h; the
+// y term is present when kY.
+template <bool kY>
+__global__ void __launch_bounds__(kPix, 4)
     k_r2c3(int n1, int n2, int n3, int h, size_t N, size_t P, const float *__restrict__ x,
            const float *__restrict__ y, float ycoef, float2 *__restrict__ out, int trans,
            const float2 *__restrict__ tw3) {
   __shared__ float4 s_t[kCB][kKF / 2];  // s_t[c][f/2] = twiddles of frequencies f, f + 1
-  const size_t p = blockIdx.x * (size_t)kPix + threadIdx.x;
+  const int groups = (h + kKF - 1) / kKF;
+  const size_t p = (blockIdx.x / groups) * (size_t)kPix + threadIdx.x;
   const bool live = p < P;
-  const int kbase = blockIdx.y * kKF;
+  const int kbase = (blockIdx.x % groups) * kKF;
   const int b = blockIdx.z;
   const float *xb = x + (size_t)b * N;
-  const float *yb = y ? y + (size_t)b * N : nullptr;
+  const float *yb = kY ? y + (size_t)b * N : nullptr;
   float2 acc[kKF];
 #pragma unroll
   for (int f = 0; f < kKF; ++f) acc[f] = make_float2(0.f, 0.f);
+  // the inputs of bands c .. c + 3 (zero past n3), combined only when they
+  // are used, so that no thread waits for its loads where it issues them
+  float nx[4], ny[4];
+  auto load4 = [&](int c) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const bool in = c + u < n3;
+      nx[u] = in ? xb[p + P * (c + u)] : 0.0f;
+      if (kY) ny[u] = in ? yb[p + P * (c + u)] : 0.0f;
+    }
+  };
+  if (live) load4(0);
   for (int c0 = 0; c0 < n3; c0 += kCB) {
     const int cn = min(kCB, n3 - c0);
     __syncthreads();
@@ -81,19 +101,13 @@ __global__ void __launch_bounds__(kPix)
     }
     __syncthreads();
     if (live) {
-      // four bands' inputs are loaded before their products run, so that
-      // several loads per thread are in flight
+      // kCB is a multiple of 4, so the next four bands start the next
+      // chunk when this one ends
       for (int cc = 0; cc < cn; cc += 4) {
         float v[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int c = c0 + cc + u;
-          v[u] = 0.0f;
-          if (cc + u < cn) {
-            v[u] = xb[p + P * c];
-            if (yb) v[u] -= ycoef * yb[p + P * c];
-          }
-        }
+        for (int u = 0; u < 4; ++u) v[u] = kY ? nx[u] - ycoef * ny[u] : nx[u];
+        load4(c0 + cc + 4);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           if (cc + u >= cn) break;
@@ -125,14 +139,15 @@ __global__ void __launch_bounds__(kPix)
 
 // x(p, c) = (1/n3) [X_0 + 2 sum_{0<k<n3/2} Re(X_k e^{2 pi i k c/n3}) + X_{n3/2} (-1)^c],
 // the Nyquist term present for even n3 only.
-__global__ void __launch_bounds__(kPix)
+__global__ void __launch_bounds__(kPix, 5)
     k_c2r3(int n1, int n2, int n3, int h, size_t N, size_t P, const float2 *__restrict__ spec,
            int trans, const float2 *__restrict__ tw3, float *__restrict__ out, int mode,
            float *__restrict__ G4, const float *__restrict__ F, float mu, int gamma4) {
   __shared__ float4 s_t[kCB][kKF / 2];  // s_t[k][c/2] = twiddles of bands c, c + 1
-  const size_t p = blockIdx.x * (size_t)kPix + threadIdx.x;
+  const int groups = (n3 + kKF - 1) / kKF;
+  const size_t p = (blockIdx.x / groups) * (size_t)kPix + threadIdx.x;
   const bool live = p < P;
-  const int cbase = blockIdx.y * kKF;
+  const int cbase = (blockIdx.x % groups) * kKF;
   const int b = blockIdx.z;
   size_t pos = p;
   if (trans) {
@@ -143,6 +158,13 @@ __global__ void __launch_bounds__(kPix)
   float acc[kKF];
 #pragma unroll
   for (int f = 0; f < kKF; ++f) acc[f] = 0.f;
+  // the coefficients of frequencies k .. k + 3 (zero past h)
+  float2 nX[4];
+  auto load4 = [&](int k) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) nX[u] = k + u < h ? sb[(size_t)(k + u) * P] : make_float2(0.f, 0.f);
+  };
+  if (live) load4(0);
   for (int k0 = 0; k0 < h; k0 += kCB) {
     const int kn = min(kCB, h - k0);
     __syncthreads();
@@ -154,12 +176,13 @@ __global__ void __launch_bounds__(kPix)
     }
     __syncthreads();
     if (live) {
-      // four frequencies' coefficients are loaded before their products run
+      // kCB is a multiple of 4, so the next four frequencies start the next
+      // chunk when this one ends
       for (int kk = 0; kk < kn; kk += 4) {
         float2 Xs[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          Xs[u] = kk + u < kn ? sb[(size_t)(k0 + kk + u) * P] : make_float2(0.f, 0.f);
+        for (int u = 0; u < 4; ++u) Xs[u] = nX[u];
+        load4(k0 + kk + 4);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           if (kk + u >= kn) break;
@@ -319,16 +342,22 @@ cudaError_t launch_tables(const Dims &d, const float w[3], float2 *tw3, float2 *
 
 cudaError_t launch_r2c3(const Dims &d, int nb, const float *x, const float *y, float ycoef,
                         float2 *out, int work_orient, const float2 *tw3, cudaStream_t st) {
-  dim3 grid((unsigned)((d.P + kPix - 1) / kPix), (unsigned)((d.h + kKF - 1) / kKF), nb);
-  k_r2c3<<<grid, kPix, 0, st>>>(d.n1, d.n2, d.n3, d.h, d.N, d.P, x, y, ycoef, out,
-                                work_orient && d.trans, tw3);
+  const size_t tiles = (d.P + kPix - 1) / kPix, groups = (d.h + kKF - 1) / kKF;
+  dim3 grid((unsigned)(tiles * groups), 1, nb);
+  if (y)
+    k_r2c3<true><<<grid, kPix, 0, st>>>(d.n1, d.n2, d.n3, d.h, d.N, d.P, x, y, ycoef, out,
+                                        work_orient && d.trans, tw3);
+  else
+    k_r2c3<false><<<grid, kPix, 0, st>>>(d.n1, d.n2, d.n3, d.h, d.N, d.P, x, y, ycoef, out,
+                                         work_orient && d.trans, tw3);
   return cudaGetLastError();
 }
 
 cudaError_t launch_c2r3(const Dims &d, int nb, const float2 *spec, int work_orient,
                         const float2 *tw3, float *out, int mode, float *G4, const float *F,
                         float mu, int gamma4, cudaStream_t st) {
-  dim3 grid((unsigned)((d.P + kPix - 1) / kPix), (unsigned)((d.n3 + kKF - 1) / kKF), nb);
+  const size_t tiles = (d.P + kPix - 1) / kPix, groups = (d.n3 + kKF - 1) / kKF;
+  dim3 grid((unsigned)(tiles * groups), 1, nb);
   k_c2r3<<<grid, kPix, 0, st>>>(d.n1, d.n2, d.n3, d.h, d.N, d.P, spec, work_orient && d.trans,
                                 tw3, out, mode, G4, F, mu, gamma4);
   return cudaGetLastError();
