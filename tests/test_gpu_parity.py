@@ -114,6 +114,66 @@ def test_tsvt_and_run_at_the_maximum_slice_height(L, orc):
     assert maxabs(X, ost.X) <= 1e-4
 
 
+# Long spectra: the mode-3 DFT kernels stage twiddles in chunks of 64 bands
+# (or frequencies), give each thread 48 frequencies (or bands) and each block
+# 128 pixels; these shapes cross every one of those boundaries with ragged
+# tails (h = 66, 96, 129, 2049; P = 300 and 180 span several pixel tiles), in
+# both slice orientations (n1 < n2 transposes the slices), up to the largest
+# n3 a plan takes.
+LONG_SPECTRA = [(20, 15, 191), (9, 20, 130), (4, 3, 257), (2, 3, 4096)]
+
+
+def _slice_sigma_percentiles(A, qs):
+    """Percentiles of the Fourier-slice singular values (picks thresholds
+    that cut some but not all of them; no expected value comes from here)."""
+    Ah = np.fft.fft(A.astype(np.float64), axis=2)
+    sig = np.concatenate([np.linalg.svd(Ah[:, :, k], compute_uv=False)
+                          for k in range(A.shape[2] // 2 + 1)])
+    return [float(np.percentile(sig, q)) for q in qs]
+
+
+@pytest.mark.parametrize("shape", LONG_SPECTRA)
+def test_zsolve_long_spectra(L, orc, shape):
+    T = rnd(shape, 14)
+    w = (1.0, 0.6, 1.4)
+    for mu in (0.01, 3.7):
+        Z = host(L.lrstv_zsolve(dev(T), shape, mu, w), shape)
+        ref = orc.zsolve(T, mu, w)
+        err = maxabs(Z, ref)
+        print(shape, mu, "zsolve max-abs / max|ref|", err / np.abs(ref).max())
+        assert err <= 1e-5 * np.abs(ref).max(), mu
+
+
+@pytest.mark.parametrize("shape", LONG_SPECTRA)
+def test_tsvt_long_spectra(L, orc, shape):
+    A = rnd(shape, 15)
+    for t in [0.0] + _slice_sigma_percentiles(A, (30, 90)):
+        out, sw = L.lrstv_tsvt(dev(A), shape, t, sweeps=True)
+        ref, _ = orc.tsvt(A, t)
+        err = maxabs(host(out, shape), ref)
+        print(shape, t, "tsvt max-abs / max|A|", err / np.abs(A).max())
+        assert sw >= 0, "Jacobi hit its sweep cap"
+        assert err <= 2e-5 * np.abs(A).max(), t
+
+
+def test_run_long_spectrum_and_band_limit(L, orc):
+    """Whole iterations on a 12x10x191 cube (two frequency groups, two
+    frequency chunks, four band groups), against the oracle at the run
+    bound; one band more than the largest n3 is a shape error."""
+    shape = (12, 10, 191)
+    clean, Y = _noisy(shape, 16)
+    with L.Plan(*shape, L.Params.make(12, 10, max_iter=5)) as pl:
+        X, S = pl.run(dev(Y))
+        X, S = host(X, shape), host(S, shape)
+    ost = orc.State(Y, orc.Params(n1=12, n2=10))
+    ost.iterate(5)
+    print("12x10x191 run max-abs", maxabs(X, ost.X), "S", maxabs(S, ost.get("S")))
+    assert maxabs(X, ost.X) <= 1e-4
+    assert maxabs(S, ost.get("S")) <= 1e-4
+    with pytest.raises(L.LrstvError, match="status 2"):
+        L.Plan(2, 2, 4097, L.Params.make(2, 2))
+
+
 # ------------------------------------------------------------ ADMM steps ---
 def _noisy(shape, seed):
     from synthetic import Recipe, make_cube
