@@ -111,6 +111,19 @@ const char *lrstv_status_string(int status);
 /* Largest n1, n2 supported by the SVT kernels (min(n1, n2) and max(n1, n2)
  * bound the Jacobi working matrix). */
 int lrstv_max_spatial(void);
+/* Checks the bounded wait that the tensor-core GEMM puts on its MMA
+ * barriers, and its timeout path, without a fault: one warp allocates tensor
+ * memory as the GEMM does and waits on an mbarrier with the wait cut to
+ * `tries` tries (1 .. the GEMM's own limit, 250000 tries, about a second:
+ * one try that finds the phase incomplete suspends for a few microseconds).
+ * With arrive != 0 the
+ * barrier's phase is completed first and the wait ends; with arrive == 0
+ * nothing arrives and the wait runs out.  *timed_out = 1 when it ran out,
+ * else 0; *lanes_freed = the lanes that freed the tensor memory and
+ * returned (32).  Synchronous on the legacy default stream; makes and frees
+ * one 8-byte device allocation.  ERR_ARG (null output, tries out of range),
+ * ERR_ALLOC, ERR_CUDA. */
+int lrstv_check_bounded_wait(long long tries, int arrive, int *timed_out, int *lanes_freed);
 
 /* ------------------------------------------------- full TDLRSTV (Tucker) */
 /* Turns the L-update of a plan into the Tucker projection of the full TDLRSTV
@@ -172,7 +185,8 @@ int lrstv_profile_read(lrstv_plan *plan, lrstv_profile *out);
  * the 18 state cubes of Algorithm 1, the half spectrum (n3/2 + 1 complex
  * frontal slices) for the Z-solve and the t-SVT, the per-slice Jacobi
  * matrices, and DFT tables.  Errors: ERR_ARG (null, n < 1), ERR_SHAPE (n1 or
- * n2 above lrstv_max_spatial()), ERR_ALLOC, ERR_CUDA.  Uses the current
+ * n2 above lrstv_max_spatial(), n3 above 4096, or 3 n1 n2 n3 above 2e9),
+ * ERR_ALLOC, ERR_CUDA.  Uses the current
  * device; the plan must be used with that device current. */
 int lrstv_plan_create(int n1, int n2, int n3, const lrstv_params *params, lrstv_plan **plan);
 int lrstv_plan_destroy(lrstv_plan *plan);

@@ -40,7 +40,7 @@ void carve_tables(Carver &c, const Dims &d, Tables &t) {
 int check_shape(int n1, int n2, int n3) {
   if (n1 < 1 || n2 < 1 || n3 < 1) return LRSTV_ERR_ARG;
   if (n1 > kMaxSpatial || n2 > kMaxSpatial) return LRSTV_ERR_SHAPE;
-  if (n3 > kMaxBands) return LRSTV_ERR_SHAPE;  // mode-3 twiddles are staged in shared memory
+  if (n3 > kMaxBands) return LRSTV_ERR_SHAPE;  // the mode-3 DFTs' twiddle indices k c < 2^24
   if ((double)n1 * n2 * n3 * 3.0 > 2.0e9) return LRSTV_ERR_SHAPE;  // 3N fits a 32-bit grid walk
   return LRSTV_OK;
 }
@@ -559,6 +559,22 @@ const char *lrstv_status_string(int s) {
 }
 
 int lrstv_max_spatial(void) { return kMaxSpatial; }
+
+int lrstv_check_bounded_wait(long long tries, int arrive, int *timed_out, int *lanes_freed) {
+  if (!timed_out || !lanes_freed || tries < 1 || tries > cgemm_tc_wait_limit())
+    return LRSTV_ERR_ARG;
+  int *d = nullptr;
+  if (cudaMalloc(&d, 2 * sizeof(int)) != cudaSuccess) return LRSTV_ERR_ALLOC;
+  int h[2] = {0, 0};
+  cudaError_t e = cudaMemset(d, 0, sizeof h);
+  if (e == cudaSuccess) e = launch_wait_probe(tries, arrive ? 1 : 0, d, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof h, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return LRSTV_ERR_CUDA;
+  *timed_out = h[0];
+  *lanes_freed = h[1];
+  return LRSTV_OK;
+}
 
 const char *lrstv_kernel_name(int k) {
   static const char *names[LRSTV_NKERNEL] = {"l_tz", "r2c_z", "cgemm_z", "c2r_z", "fs_dual",

@@ -81,6 +81,10 @@ cudaError_t launch_cgemm(const CGemm &g, cudaStream_t st);
 // *err (may be null) is set to 1 if a CTA's wait for its MMAs runs out.
 cudaError_t launch_cgemm_tc(const CGemm &g, int *err, cudaStream_t st, int prec = 0);
 size_t cgemm_tc_smem();
+// the tries of the GEMM's bounded barrier wait, and a one-warp check of that
+// wait and its timeout path (out: two device ints, zeroed by the caller)
+long long cgemm_tc_wait_limit();
+cudaError_t launch_wait_probe(long long tries, int arrive, int *out, cudaStream_t st);
 
 // -------------------------------------------------------------------- svt.cu
 // One-sided Jacobi on `nslices` working matrices W_s (nr x nc, column-major,

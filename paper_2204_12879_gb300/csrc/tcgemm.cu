@@ -51,7 +51,11 @@ constexpr int TN = 64;        // complex columns of C per CTA
 // and, by warpgroup, columns 0..31 or 32..63 of each Re / Im tile
 constexpr int kThreads = 256;
 constexpr uint32_t kLBO = 128;  // bytes
-constexpr long long kWaitLimit = 20000000;
+// tries of a bounded barrier wait: one mbarrier.try_wait that finds the
+// phase incomplete suspends the thread for about 3.8 us on GB300 (measured
+// by the wait probe below), so the bound is about a second, against the
+// microseconds one chunk's MMAs take
+constexpr long long kWaitLimit = 250000;
 
 // Per precision: element bytes, elements per 16-byte core-matrix row, the
 // 8-row group stride, tile sizes and the instruction descriptor's operand
@@ -136,9 +140,10 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          long long tries = kWaitLimit) {
   uint32_t done = 0;
-  for (long long it = 0; it < kWaitLimit && !done; ++it) {
+  for (long long it = 0; it < tries && !done; ++it) {
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
@@ -432,6 +437,38 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, int *err) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kCols));
 }
 
+// Checks the GEMM's bounded barrier wait and its timeout path: one warp
+// allocates tensor memory as the GEMM does, then waits on an mbarrier with
+// the wait cut to `tries` tries.  With `arrive`, lane 0 arrives first and the
+// phase completes; without, nothing arrives and the wait runs out.  A timeout
+// is recorded in out[0]; the tensor memory is freed on both paths, and
+// out[1] counts the lanes that got past the free.
+__global__ void __launch_bounds__(32) k_wait_probe(long long tries, int arrive, int *out) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t slot;
+  const uint32_t b = smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(
+                   smem_u32(&slot)));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = slot;
+  if (arrive && threadIdx.x == 0)
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(b)
+                 : "memory");
+  __syncwarp();
+  if (!mbar_wait(b, 0u, tries)) atomicOr(out, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
+  atomicAdd(out + 1, 1);
+}
+
 template <int PREC>
 size_t smem_bytes() {
   return 2 * (2 * Prec<PREC>::kTileA + 4 * Prec<PREC>::kTileB);
@@ -459,6 +496,13 @@ cudaError_t launch_prec(const CGemm &g, int *err, cudaStream_t st) {
 }  // namespace
 
 size_t cgemm_tc_smem() { return smem_bytes<0>(); }
+
+long long cgemm_tc_wait_limit() { return kWaitLimit; }
+
+cudaError_t launch_wait_probe(long long tries, int arrive, int *out, cudaStream_t st) {
+  k_wait_probe<<<1, 32, 0, st>>>(tries, arrive, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_cgemm_tc(const CGemm &g, int *err, cudaStream_t st, int prec) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;

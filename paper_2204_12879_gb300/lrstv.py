@@ -99,6 +99,7 @@ _SZ = ctypes.c_size_t
 _SIGS = {
     "lrstv_status_string": [_I],
     "lrstv_max_spatial": [],
+    "lrstv_check_bounded_wait": [ctypes.c_longlong, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "lrstv_plan_create": [_I, _I, _I, ctypes.POINTER(Params), ctypes.POINTER(_P)],
     "lrstv_plan_destroy": [_P],
     "lrstv_plan_bytes": [_P, ctypes.POINTER(_SZ)],
@@ -588,6 +589,15 @@ def lrstv_tsvt_noalloc(A, shape, t, out, sweeps=False, stream=None):
     _call("lrstv_tsvt_noalloc", _dev(A, N), n1, n2, n3, float(t), _dev(out, N),
           ctypes.byref(sw) if sweeps else None, _stream(stream))
     return (out, sw.value) if sweeps else out
+
+
+def lrstv_check_bounded_wait(tries, arrive=False):
+    """lrstv_check_bounded_wait: returns (timed_out, lanes_freed)."""
+    _torch()
+    t, n = _I(), _I()
+    _call("lrstv_check_bounded_wait", int(tries), 1 if arrive else 0, ctypes.byref(t),
+          ctypes.byref(n))
+    return t.value, n.value
 
 
 def lrstv_denoise(Y, shape, params: Params, stream=None):
