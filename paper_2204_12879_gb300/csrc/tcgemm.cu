@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, int *err) {
   // Staging is software-pipelined: chunk ch + 1's operands are loaded from
   // global memory into registers while chunk ch's MMAs run, then split and
   // stored to shared memory once those MMAs are done with the tiles.
-  // A tile: rows m0..m0+127, complex k0..k0+15 -> real kk = k (re), k + 16
+  // A tile: rows m0..m0+127, complex k0..k0+TK-1 -> real kk = k (re), k + TK
   // (im).  Element e of a tile: a warp covers 8 rows x 4 k, so its 32 stores
   // hit 32 distinct banks of a core-matrix row group and its loads are four
   // 64-byte runs of a column.  B tiles (output columns n0..n0+63): row n holds
