@@ -40,6 +40,27 @@ MUTATIONS = {
     "iso_per_component": ("orc_group_soft(x, 3, thr);",
                           "for (int c = 0; c < 3; ++c) x[c] = orc_soft(x[c], thr);",
                           "test_iso_admm_iterations_brute_force"),
+    # inverse DFT without the 1/n factor
+    "idft_normalisation": ("double scale = sign > 0 ? 1.0 / (double)n : 1.0;", "double scale = 1.0;",
+                           "test_dft_roundtrip_parseval_symmetry"),
+    # the soft threshold's second case as printed (x < d instead of x < -d)
+    "soft_negative_branch": ("if (x < -d) return x + d;", "if (x < d) return x + d;",
+                             "test_soft_threshold_prox"),
+    # Z-solve denominator without mu on the identity term
+    "zsolve_mu": ("double d = mu + mu * pz[v];", "double d = 1.0 + mu * pz[v];",
+                  "test_zsolve_dense_brute_force"),
+    # E-step threshold alpha instead of alpha / mu
+    "e_threshold_mu": ("orc_tsvt(B, n1, n2, n3, p[ORC_P_ALPHA] / mu,", "orc_tsvt(B, n1, n2, n3, p[ORC_P_ALPHA],",
+                       "test_admm_iterations_brute_force"),
+    # S-update threshold lambda instead of lambda / mu
+    "s_threshold_mu": ("double thr = p[ORC_P_LAMBDA] / mu;", "double thr = p[ORC_P_LAMBDA];",
+                       "test_admm_iterations_brute_force"),
+    # S-update with the multiplier subtracted
+    "s_multiplier_sign": ("orc_soft(Y[v] - L[v] + G1[v] / mu, thr)", "orc_soft(Y[v] - L[v] - G1[v] / mu, thr)",
+                          "test_admm_iterations_brute_force"),
+    # Gamma3 update with the wrong sign
+    "gamma3_sign": ("G3[v] += mu * (g[v] - F[v]);", "G3[v] += mu * (F[v] - g[v]);",
+                    "test_admm_iterations_brute_force"),
 }
 
 
