@@ -209,3 +209,46 @@ def test_unrolled_gradient_matches_c_oracle_fd(orc):
     h = 1e-6
     want = (c_loss(noisy + h * dY, thetas) - c_loss(noisy - h * dY, thetas)) / (2 * h)
     assert abs(float(np.sum(g_Y * dY)) - want) <= 1e-6 * max(abs(want), 1e-9)
+
+
+# -------------------------------------------------- planted mistakes ---
+def _mutated_adjoint(old, new):
+    """A copy of oracle/adjoint.py with one planted mistake."""
+    import types
+    src = open(adj.__file__).read()
+    assert old in src, old
+    mod = types.ModuleType("adjoint_mutated")
+    mod.__file__ = adj.__file__
+    exec(compile(src.replace(old, new, 1), adj.__file__, "exec"), mod.__dict__)
+    return mod
+
+
+_ADJ_MUTATIONS = {
+    # the SVD differential's off-diagonal coefficients exchanged
+    "svt_ab_swapped": ("M = a * H + b * H.conj().T", "M = b * H + a * H.conj().T",
+                       lambda orc: test_svt_backward_matches_torch_autograd(7, 5)),
+    # the directions outside the column space left out (a tall matrix has them)
+    "svt_range_term": ("Abar = Abar + Pu @ G", "Abar = Abar + 0.0 * Pu @ G",
+                       lambda orc: test_svt_backward_matches_finite_differences(*_svt_cases()[0])),
+    # the threshold's gradient with the wrong sign
+    "svt_threshold_sign": ("tbar = -float(np.sum(fp * d.real))", "tbar = float(np.sum(fp * d.real))",
+                           lambda orc: test_svt_backward_matches_finite_differences(*_svt_cases()[0])),
+    # the adjoint of Re ifft without its 1/n3
+    "tsvt_scale": ("Gh = np.fft.fft(Ebar, axis=2) / n3", "Gh = np.fft.fft(Ebar, axis=2)",
+                   lambda orc: test_tsvt_backward_matches_c_oracle_fd(orc, (6, 5, 4))),
+    # the F-update's one half dropped on the path to E
+    "f_half": ('out["E"] += 0.5 * ba', 'out["E"] += ba',
+               lambda orc: test_iteration_backward_matches_c_oracle_fd(orc)),
+    # the S threshold's derivative in mu dropped
+    "s_threshold_mu": ("dmu += np.sum(bS * sgn) * lam / mu ** 2", "dmu += 0.0",
+                       lambda orc: test_iteration_backward_matches_c_oracle_fd(orc)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(_ADJ_MUTATIONS))
+def test_pins_catch_planted_mistakes(orc, monkeypatch, name):
+    import sys
+    old, new, pin = _ADJ_MUTATIONS[name]
+    monkeypatch.setattr(sys.modules[__name__], "adj", _mutated_adjoint(old, new))
+    with pytest.raises(AssertionError):
+        pin(orc)
