@@ -48,6 +48,12 @@ BATCH = {"count": 64, "seed": 4, "iters": 50,
          "desc": "batch of 64 uneven synthetic cubes drawn by seed from 64x64x31, 128x128x64, 145x145x220 (Indian Pines shape) and 200x200x80, each with Gaussian U[0.05,0.2] and impulse U[0,0.3] noise, 50 ADMM iterations, one persistent Jacobi launch per step"}
 METRIC = "ADMM iterations/s (plain LRSTV, FP32, 1e-4 max-abs vs FP64 oracle)"
 UNIT = "iter/s"
+METRIC_TUCKER = "ADMM iterations/s (full TDLRSTV, Tucker L-update, FP32)"
+METRIC_BF16X3 = "ADMM iterations/s (plain LRSTV, mixed precision: 3xBF16 tensor-core GEMMs)"
+METRIC_BATCH = "cube-ADMM-iterations/s (batched plain LRSTV, FP32)"
+UNIT_BATCH = "cube-iter/s"
+METRIC_UNROLL = "unrolled-LRSTV training steps/s (forward + backward + update, FP32)"
+UNIT_UNROLL = "step/s"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -155,6 +161,24 @@ def gemm_precision(args, wl_name):
     return "bf16x3" if wl_name == "c3" else "tf32x3"
 
 
+def tucker_ranks(args, shape):
+    """Multilinear ranks of the full TDLRSTV L-update (--tucker R3): r1 =
+    0.8 n1, r2 = 0.8 n2 (Section IV-D), r3 given; None for plain LRSTV."""
+    if not args.tucker:
+        return None
+    n1, n2, n3 = shape
+    return (max(1, round(0.8 * n1)), max(1, round(0.8 * n2)), min(args.tucker, n3))
+
+
+def metric_for(args, wl_name):
+    """The metric of a single-cube workload's line, the same for both arms."""
+    if args.tucker:
+        return METRIC_TUCKER
+    if gemm_precision(args, wl_name) == "bf16x3":
+        return METRIC_BF16X3
+    return METRIC
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -259,10 +283,8 @@ def run_ours(args, wl_name):
         flags |= lrstv.FLAG_BF16X3
     params = lrstv.Params.make(n1, n2, max_iter=iters, flags=flags)
     plan = lrstv.Plan(n1, n2, n3, params)
-    ranks = None
-    if args.tucker:
-        # full TDLRSTV: Tucker L-update, r1 = 0.8 n1, r2 = 0.8 n2 (Section IV-D), r3 given
-        ranks = (max(1, round(0.8 * n1)), max(1, round(0.8 * n2)), min(args.tucker, n3))
+    ranks = tucker_ranks(args, (n1, n2, n3))
+    if ranks:
         plan.set_tucker(ranks)
     y_dev = torch.from_numpy(flat(Y)).cuda()
     stream = torch.cuda.current_stream()
@@ -368,12 +390,7 @@ def run_ours(args, wl_name):
                             "FP32 FMA: 152 SMs x 128 lanes x 2 x sm_max_mhz") + f" ({pk_kind})")
     roof["traffic"] = traffic_for(dom, wl_name)
     value = world * args.steps / (ms_max / 1e3)
-    if ranks:
-        metric = "ADMM iterations/s (full TDLRSTV, Tucker L-update, FP32)"
-    elif precision == "bf16x3":
-        metric = "ADMM iterations/s (plain LRSTV, mixed precision: 3xBF16 tensor-core GEMMs)"
-    else:
-        metric = METRIC
+    metric = metric_for(args, wl_name)
     line = {
         "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -399,7 +416,7 @@ def run_ours(args, wl_name):
         "clocks": clk,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_baseline(wl, Y, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = oracle_baseline(wl, Y, budget_s=args.cpu_budget, ranks=ranks)
     return line
 
 
@@ -468,8 +485,8 @@ def run_batch(args):
     value = n * args.steps / (ms / 1e3)
     slices = sum(3 * (sh[2] // 2 + 1) for sh in shapes)
     return {
-        "metric": "cube-ADMM-iterations/s (batched plain LRSTV, FP32)", "value": value,
-        "unit": "cube-iter/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "metric": METRIC_BATCH, "value": value,
+        "unit": UNIT_BATCH, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": BATCH["desc"], "cubes": n,
@@ -553,8 +570,8 @@ def run_unroll(args):
     unconv, gerr = model.handle.stats()
     value = args.steps / (ms / 1e3)
     return {
-        "metric": "unrolled-LRSTV training steps/s (forward + backward + update, FP32)",
-        "value": value, "unit": "step/s", "n_gpus": 1, "steps": args.steps,
+        "metric": METRIC_UNROLL,
+        "value": value, "unit": UNIT_UNROLL, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": UNROLL["desc"], "shape": [n1, n2, n3], "batch": B,
@@ -569,44 +586,127 @@ def run_unroll(args):
     }
 
 
-def oracle_baseline(wl, Y, budget_s=25.0, max_iters=None):
+def oracle_baseline(wl, Y, budget_s=25.0, max_iters=None, ranks=None):
     """Times the FP64 oracle (as it stands) on the same cube: whole ADMM
-    iterations from the initial state until the time budget is spent."""
+    iterations from the initial state until the time budget is spent; with
+    ranks, the full TDLRSTV iteration (Tucker L-update of oracle/tucker.py)."""
     import numpy as np
 
     import oracle
     r = Y.shape
-    st = oracle.State(Y.astype(np.float64), oracle.Params(n1=r[0], n2=r[1]))
+    params = oracle.Params(n1=r[0], n2=r[1])
+    if ranks:
+        from oracle import tucker
+        st = tucker.TuckerState(oracle, Y.astype(np.float64), params, ranks)
+    else:
+        st = oracle.State(Y.astype(np.float64), params)
     done, t = 0, 0.0
     while (t < budget_s or done == 0) and (max_iters is None or done < max_iters):
         a = time.perf_counter()
         st.iterate(1)
         t += time.perf_counter() - a
         done += 1
+    what = "TDLRSTV iteration(s), Tucker ranks %s," % (ranks,) if ranks else "ADMM iteration(s)"
     return {"value": done / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{done} ADMM iteration(s) of the {r[0]}x{r[1]}x{r[2]} cube from its initial state ({t:.1f} s)"}
+            "sample": f"{done} {what} of the {r[0]}x{r[1]}x{r[2]} cube from its initial state ({t:.1f} s)"}
+
+
+def _reference_line(args, world, metric, unit, cb, config):
+    return {
+        "impl": "reference", "metric": metric, "value": cb["value"], "unit": unit,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 / cb["value"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+        "cpu_baseline": cb,
+        "e2e": {"value": cb["value"], "unit": unit, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def _reference_batch(args, world):
+    """The FP64 oracle on the batch's cubes (the GPU arm's recipes and seeds):
+    one ADMM iteration of each cube from its initial state, in batch order,
+    until the time budget is spent; cube-iterations per second."""
+    import numpy as np
+
+    import oracle
+    from synthetic import batch_recipes, make_cube
+    recs = batch_recipes(BATCH["count"], BATCH["seed"])
+    budget = args.cpu_budget * 4
+    done, t = 0, 0.0
+    for i, r in enumerate(recs):
+        if done and t >= budget:
+            break
+        Y = make_cube(r, 5000 + i)[1].astype(np.float32).astype(np.float64)
+        st = oracle.State(Y, oracle.Params(n1=r.shape[0], n2=r.shape[1]))
+        a = time.perf_counter()
+        st.iterate(1)
+        t += time.perf_counter() - a
+        done += 1
+    cb = {"value": done / t, "unit": UNIT_BATCH, "cores": oracle.num_threads(), "kind": "oracle",
+          "sample": f"one ADMM iteration of each of the first {done} of the batch's "
+                    f"{len(recs)} cubes, from their initial states ({t:.1f} s)"}
+    return _reference_line(args, world, METRIC_BATCH, UNIT_BATCH, cb,
+                           {"workload": BATCH["desc"], "cubes_timed": done,
+                            "note": "FP64 CPU oracle on the host cores, one cube after another"})
+
+
+def _reference_unroll(args, world):
+    """The FP64 reference of the unrolled iteration and its hand-derived
+    adjoint (oracle/adjoint.py) on the GPU arm's pairs: forward with the
+    iterates kept and backward to the 40 scalars, one pair after another
+    until the time budget is spent.  A training step is a batch of pairs (the
+    update of 40 scalars is negligible): steps/s = pairs/s / batch."""
+    import numpy as np
+
+    from oracle import adjoint
+    from synthetic import RECIPES, make_cube
+    rec = RECIPES["c5"]
+    n1, n2, n3 = rec.shape
+    B, K = UNROLL["batch"], UNROLL["iters"]
+    # the solver's default scalars: tau, alpha, lambda = 1 / sqrt(n1 n2), mu_k = 1e-2 1.5^k
+    thetas = np.array([[1e-3, 0.2, 1.0 / np.sqrt(n1 * n2), min(1e-2 * 1.5 ** k, 1e6)]
+                       for k in range(K)])
+    budget = args.cpu_budget * 4
+    done, t = 0, 0.0
+    while done == 0 or (t < budget and done < UNROLL["pool"]):
+        clean, noisy = make_cube(rec, 70000 + done)
+        c = clean.astype(np.float32).astype(np.float64)
+        y = noisy.astype(np.float32).astype(np.float64)
+        a = time.perf_counter()
+        adjoint.unrolled_loss_grad(y, c, thetas)
+        t += time.perf_counter() - a
+        done += 1
+    value = done / t / B
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    cb = {"value": value, "unit": UNIT_UNROLL, "cores": cores, "kind": "oracle",
+          "sample": f"forward and backward of {done} pair(s) of {n1}x{n2}x{n3}, {K} iterations "
+                    f"each ({t:.1f} s; numpy FP64, LAPACK threads up to the {cores} cores)"}
+    return _reference_line(args, world, METRIC_UNROLL, UNIT_UNROLL, cb,
+                           {"workload": UNROLL["desc"], "pairs_timed": done,
+                            "note": "FP64 CPU reference of the unrolled iteration and its adjoint"})
 
 
 def run_reference(args, wl_name):
     rank, world, _ = dist_env()
     if rank != 0:
         return None
+    if wl_name == "c4":
+        return _reference_batch(args, world)
+    if wl_name == "c5":
+        return _reference_unroll(args, world)
     wl = WORKLOADS[wl_name]
     shape, clean, Y = make_input(wl, 0)
-    cb = oracle_baseline(wl, Y, budget_s=args.cpu_budget * 4, max_iters=max(args.steps, 1))
+    ranks = tucker_ranks(args, shape)
+    cb = oracle_baseline(wl, Y, budget_s=args.cpu_budget * 4, max_iters=max(args.steps, 1),
+                         ranks=ranks)
     steps_run = int(cb["sample"].split()[0])
-    return {
-        "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 / cb["value"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl["desc"], "shape": list(shape), "iters_per_cube": wl["iters"],
-                   "steps_timed": steps_run,
-                   "note": "FP64 CPU oracle on the host cores; a bounded number of the requested steps"},
-        "cpu_baseline": cb,
-        "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 0},
-    }
+    config = {"workload": wl["desc"], "shape": list(shape), "iters_per_cube": wl["iters"],
+              "steps_timed": steps_run,
+              "note": "FP64 CPU oracle on the host cores; a bounded number of the requested steps"}
+    if ranks:
+        config["tucker_ranks"] = list(ranks)
+    return _reference_line(args, world, metric_for(args, wl_name), UNIT, cb, config)
 
 
 def run_micro(args):
