@@ -27,7 +27,8 @@ def _worker(rank, world, port, q):
         bench.barrier(w)
         m = bench.max_over_ranks(float(10 * (r + 1)), w)
         # the reference arm reports on rank 0 only
-        args = type("A", (), {"steps": 1, "warmup": 0, "cpu_budget": 0.0})()
+        args = type("A", (), {"steps": 1, "warmup": 0, "cpu_budget": 0.0, "tucker": 0,
+                              "precision": "auto"})()
         ref = bench.run_reference(args, "c1")
         q.put((r, w, local, seed, m, ref is None))
     finally:
