@@ -171,6 +171,8 @@ typedef struct lrstv_profile {
   unsigned long long jacobi_rotations;  /* pairs that were rotated                 */
 } lrstv_profile;
 
+/* Short name of a lrstv_kernel index ("l_tz", "jacobi", ...; the keys of the
+ * benchmark's per-kernel table); "unknown" out of range.  Static storage. */
 const char *lrstv_kernel_name(int kernel);
 /* on != 0: clears the counters and brackets every later kernel launch of the
  * plan with CUDA events (none while a stream is being captured; at most 4096
