@@ -435,7 +435,7 @@ size_t unroll_layout(lrstv_unroll *u, void *base) {
 
 GemmSel unroll_gemm(const lrstv_unroll *u) {
   if (u->flags & LRSTV_FLAG_SIMT_GEMM) return kSimt;
-  return GemmSel{true, u->gemm_err};
+  return GemmSel{true, u->gemm_err, 0};  // 3xTF32: the unrolled form has no mixed-precision mode
 }
 
 #define UCK(x)                                  \
