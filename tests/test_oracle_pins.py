@@ -443,13 +443,17 @@ def test_noise_free_constant_cube_is_fixed_point(orc):
 
 # ------------------------------------------------------------ generator ---
 def test_generator_noisy_psnr_matches_paper():
-    """Gaussian noise of 'variance' G gives the paper's noisy MPSNR (Table I,
-    cases 1 and 2), which fixes G as a standard deviation on [0, 1] data."""
+    """Gaussian noise of 'variance' G gives the paper's noisy MPSNR (Tables I
+    and II, cases 1 and 2), which fixes G as a standard deviation on [0, 1]
+    data; the Pavia entries are checked at the Pavia shape, 200 x 200 x 80."""
     from synthetic import Recipe, make_cube, mpsnr
     gold = json.load(open(os.path.join(GOLDEN, "paper_noisy_psnr.json")))
-    for key, sigma in (("case1_gaussian_0.1", 0.1), ("case2_gaussian_0.2", 0.2)):
-        clean, noisy = make_cube(Recipe(64, 64, 32, 4, 12, (sigma, sigma), 0.0), 7)
-        assert abs(mpsnr(noisy, clean) - gold[key]["noisy_mpsnr_db"]) < 0.05
+    for key, sigma, shape in (("case1_gaussian_0.1", 0.1, (64, 64, 32)),
+                              ("case2_gaussian_0.2", 0.2, (64, 64, 32)),
+                              ("pavia_case1_gaussian_0.1", 0.1, (200, 200, 80)),
+                              ("pavia_case2_gaussian_0.2", 0.2, (200, 200, 80))):
+        clean, noisy = make_cube(Recipe(*shape, 4, 12, (sigma, sigma), 0.0), 7)
+        assert abs(mpsnr(noisy, clean) - gold[key]["noisy_mpsnr_db"]) < 0.05, key
 
 
 def test_generator_is_deterministic_and_in_range():
