@@ -84,3 +84,11 @@ def test_argument_errors_before_any_cuda_call(lib):
     assert lib.lrstv_tsvt_workspace_size(200, 200, 80, ctypes.byref(sz)) == 0
     assert sz.value >= 41 * 200 * 200 * 8 * 3
     assert lib.lrstv_zsolve_workspace_size(7, 0, 3, ctypes.byref(sz)) == 1
+    # the bounded-wait probe: tries within 1 .. the GEMM's limit, both outputs
+    t, n = ctypes.c_int(), ctypes.c_int()
+    assert lib.lrstv_check_bounded_wait(0, 0, ctypes.byref(t), ctypes.byref(n)) == 1
+    assert lib.lrstv_check_bounded_wait(250001, 0, ctypes.byref(t), ctypes.byref(n)) == 1
+    assert lib.lrstv_check_bounded_wait(10, 0, None, ctypes.byref(n)) == 1
+    assert lib.lrstv_check_bounded_wait(10, 0, ctypes.byref(t), None) == 1
+    # one band above the largest n3 a plan takes
+    assert lib.lrstv_plan_create(2, 2, 4097, ctypes.byref(p), ctypes.byref(h)) == 2
