@@ -228,6 +228,40 @@ def jacobi_flops(prof, shape):
     return 16.0 * nr * prof.jacobi_pairs + 18.0 * (nr + nc) * prof.jacobi_rotations
 
 
+def stage_bounds(kernels, shape, steps, precision, jacobi_flops_total, pk):
+    """Each stage's algorithmic work per iteration at its own roof, in ms:
+    HBM bytes at the measured bandwidth for the stencil and threshold
+    kernels; max(FP32 ALU, HBM) for the mode-3 DFTs (4 flops per
+    real-by-complex product); three products per complex multiply-add at the
+    split's tensor rate (BF16, or TF32 at half of it) for the tensor-core
+    GEMMs; the Jacobi's device-counted flops at the FP32 peak.  kernels is the
+    per-kernel table of the timed region ({name: {"launches", ...}}), steps
+    the iterations it covers.  Stages without a stated bound are listed."""
+    n1, n2, n3 = shape
+    P, h = n1 * n2, n3 // 2 + 1
+    hbm = pk["hbm_gbs"] * 1e9
+    fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6
+    tensor = pk["bf16_tflops"] * 1e12 * (1.0 if precision == "bf16x3" else 0.5)
+    per, unbounded = {}, []
+    for name, v in kernels.items():
+        per_it = v["launches"] / steps
+        if name == "jacobi":
+            sec = jacobi_flops_total / steps / fp32
+        elif name in ("cgemm_z", "cgemm_e", "warm_e"):
+            sec = 3 * kernel_work(name, shape)[1] * per_it / tensor
+        elif name in ("r2c_z", "c2r_z", "r2c_e", "c2r_e"):
+            flops = 4 * n3 * h * P * (3 if name.endswith("_e") else 1)
+            sec = max(flops / fp32, kernel_work(name, shape)[1] / hbm) * per_it
+        else:
+            kind, work = kernel_work(name, shape)
+            if kind != "hbm":
+                unbounded.append(name)
+                continue
+            sec = work * per_it / hbm
+        per[name] = sec * 1e3
+    return {"ms_per_iteration": per, "sum_ms": sum(per.values()), "without_bound": unbounded}
+
+
 def traffic_for(kernel: str, workload: str):
     """DRAM bytes per launch from a committed ncu summary, if taken on the
     current kernel source (else None)."""
@@ -389,6 +423,9 @@ def run_ours(args, wl_name):
     roof["peak_source"] = (("measured hbm_gbs" if roof["bound"] == "hbm" else
                             "FP32 FMA: 152 SMs x 128 lanes x 2 x sm_max_mhz") + f" ({pk_kind})")
     roof["traffic"] = traffic_for(dom, wl_name)
+    bounds = stage_bounds(kernels, shape, args.steps, precision, jacobi_flops(prof, shape), pk)
+    bounds["iteration_ms"] = ms_max / args.steps
+    bounds["frac"] = bounds["sum_ms"] / bounds["iteration_ms"]
     value = world * args.steps / (ms_max / 1e3)
     metric = metric_for(args, wl_name)
     line = {
@@ -404,6 +441,7 @@ def run_ours(args, wl_name):
                                 if ranks else "plain (full Tucker ranks)"),
                    "l2": "working set (18 state cubes + spectra, ~330 MB) exceeds the 129 MB L2"},
         "roofline": roof,
+        "stage_bounds": bounds,
         "kernels": kernels,
         "gpu_launches": int(sum(prof.launches)),
         "jacobi": {"max_sweeps_last": stats.jacobi_max_sweeps,

@@ -75,3 +75,34 @@ def test_reference_batch_and_unrolled_lines(monkeypatch):
     line = bench.run_reference(_args(), "c5")
     _check_line(line, bench.METRIC_UNROLL, bench.UNIT_UNROLL)
     assert line["config"]["pairs_timed"] == 1
+
+
+def test_stage_bounds_closed_forms():
+    """The per-stage bounds of a 200x200x80 iteration against their closed
+    forms: stencil kernels at HBM bytes / bandwidth, the DFTs at the larger
+    of FP32 ALU and HBM time, the GEMMs at three products per complex
+    multiply-add at the TF32 (half of BF16) rate, the Jacobi's counted flops at
+    the FP32 peak; a kernel without a stated bound is listed, not summed."""
+    shape, steps = (200, 200, 80), 10
+    n1, n2, n3 = shape
+    N, P, h = n1 * n2 * n3, n1 * n2, n3 // 2 + 1
+    per_it = {"l_tz": 1, "r2c_z": 1, "cgemm_z": 4, "c2r_z": 1, "fs_dual": 1, "r2c_e": 1,
+              "jacobi": 1, "cgemm_e": 1, "c2r_e": 1, "warm_e": 5, "tucker": 1}
+    kernels = {k: {"launches": v * steps, "ms_per_launch": 1.0} for k, v in per_it.items()}
+    pk = {"hbm_gbs": 6000.0, "bf16_tflops": 2000.0, "sm_max_mhz": 2000.0}
+    jac = 7.0e10 * steps
+    b = bench.stage_bounds(kernels, shape, steps, "tf32x3", jac, pk)
+    ms = b["ms_per_iteration"]
+    fp32 = 152 * 128 * 2 * 2.0e9
+    assert ms["l_tz"] == pytest.approx(13 * 4 * N / 6.0e12 * 1e3)
+    assert ms["fs_dual"] == pytest.approx(23 * 4 * N / 6.0e12 * 1e3)
+    assert ms["jacobi"] == pytest.approx(7.0e10 / fp32 * 1e3)
+    # Z-step DFT: 4 flops per product, n3 x h products per pixel, on the ALUs
+    assert ms["r2c_z"] == pytest.approx(max(4 * n3 * h * P / fp32, (4 * N + 8 * h * P) / 6.0e12) * 1e3)
+    # four spatial passes of 8 P h (n1 + n2) / 2 flops, three split products, TF32 = 1e15
+    assert ms["cgemm_z"] == pytest.approx(4 * 3 * 8 * P * h * (n1 + n2) // 2 / 1.0e15 * 1e3)
+    assert b["without_bound"] == ["tucker"] and "tucker" not in ms
+    assert b["sum_ms"] == pytest.approx(sum(ms.values()))
+    # the BF16 split runs at the full BF16 rate
+    b16 = bench.stage_bounds(kernels, shape, steps, "bf16x3", jac, pk)["ms_per_iteration"]
+    assert b16["cgemm_e"] == pytest.approx(ms["cgemm_e"] / 2)
