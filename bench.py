@@ -803,7 +803,7 @@ def run_sweep_profile(args):
                               "histogram": np.bincount(sw.ravel()).tolist()}), flush=True)
 
 
-def main(argv=None):
+def build_parser():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=60)
@@ -829,6 +829,11 @@ def main(argv=None):
     ap.add_argument("--sweep-profile", action="store_true",
                     help="print the per-slice Jacobi sweep distribution of every iteration of one "
                          "denoise (c1-c3) instead of timing")
+    return ap
+
+
+def main(argv=None):
+    ap = build_parser()
     args = ap.parse_args(argv)
     if args.micro:
         run_micro(args)

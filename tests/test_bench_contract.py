@@ -106,3 +106,23 @@ def test_stage_bounds_closed_forms():
     # the BF16 split runs at the full BF16 rate
     b16 = bench.stage_bounds(kernels, shape, steps, "bf16x3", jac, pk)["ms_per_iteration"]
     assert b16["cgemm_e"] == pytest.approx(ms["cgemm_e"] / 2)
+
+
+def test_profile_commands_parse():
+    """Every `python bench.py ...` command a profile summary cites is one the
+    committed benchmark accepts (the summaries' commands run committed files)."""
+    import os
+    import re
+    import shlex
+    root = os.path.dirname(bench.__file__)
+    cmds = []
+    for f in sorted(os.listdir(os.path.join(root, "profiles"))):
+        if f.endswith(".md"):
+            for line in open(os.path.join(root, "profiles", f)):
+                m = re.search(r"python bench\.py([^#`\\]*)", line)
+                if m:
+                    cmds.append((f, shlex.split(m.group(1))))
+    assert cmds
+    parser = bench.build_parser()
+    for f, argv in cmds:
+        parser.parse_args(argv)  # exits (SystemExit) on an unknown flag or value
