@@ -2,7 +2,7 @@
 
 Each translation unit under csrc/ is compiled by nvcc in parallel, then linked
 into ``_build/liblrstv.so`` (CUDA runtime linked statically, so the library
-only needs the driver).  Rebuilds when a source or header is newer than the
+only needs the NVIDIA kernel-mode driver).  Rebuilds when a source or header is newer than the
 library.
 """
 from __future__ import annotations
