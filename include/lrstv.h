@@ -346,9 +346,20 @@ int lrstv_tsvt(const float *A, int n1, int n2, int n3, float t, float *out, void
  *    n3/2 + 1, each term rounded up to 256) must not exceed the array;
  *    larger cubes return LRSTV_ERR_SHAPE without touching the GPU.  Examples
  *    that fit: 64x64x31, 128x128x31, 100x100x80.
- *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *  - The call works in the calling thread's current device and context and
+ *    looks up the array's device address there (cudaGetSymbolAddress) on
+ *    every call, so it stays valid if the host application destroys its
+ *    context and makes a new one.  Make the first call on a device before
+ *    any stream capture.
+ *  - Under CUDA's lazy module loading (the default; CUDA_MODULE_LOADING=LAZY)
+ *    the library's device code, and with it the 16 MiB array, is loaded into
+ *    a context only when first used: the FIRST call in each context loads
+ *    the modules it needs, and that load does reach the driver's allocator
+ *    (and can fail with LRSTV_ERR_CUDA when the device is full).  A caller
+ *    that must not see that at run time makes one call during its set-up
+ *    (any cube that fits, e.g. 8x8x4), or sets CUDA_MODULE_LOADING=EAGER so
+ *    that everything is loaded with the context; every later call allocates
+ *    nothing.
  *  - Every call on a device shares the one array and leaves the last call's
  *    contents in it; each call writes every scratch byte before reading it,
  *    so nothing has to start at zero.  Calls that overlap on the GPU (on two

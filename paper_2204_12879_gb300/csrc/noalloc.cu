@@ -10,7 +10,7 @@
 // library, so every GPU that loads liblrstv.so holds it until the process
 // exits; the entry point itself calls no cudaMalloc, cudaFree or other
 // allocating routine.
-#include <mutex>
+#include <math.h>
 
 #include "lrstv.h"
 #include "lrstv_internal.cuh"
@@ -19,29 +19,19 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_scratch[LRSTV_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-void *g_scratch_addr[kMaxDevices];  // device address of g_scratch, per device ordinal
-std::mutex g_scratch_mu;
-
 // The name g_scratch in host code is only a host-side handle for the symbol;
-// the device address comes from cudaGetSymbolAddress, asked once per device
-// with that device current.
+// the array's device address belongs to the context that loaded this file's
+// device code.  It is asked for on every call, in the calling thread's current
+// context: a cached address would go stale if the host application tore its
+// context down and made a new one (cudaDeviceReset, or a driver-API context of
+// its own).  Once the module is loaded the lookup allocates nothing.
 int scratch_address(void **out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
     cudaGetLastError();
     return LRSTV_ERR_CUDA;
   }
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
-      return LRSTV_ERR_CUDA;
-    }
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return LRSTV_OK;
 }
 
@@ -51,11 +41,11 @@ size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
 extern "C" int lrstv_tsvt_noalloc(const float *A, int n1, int n2, int n3, float t, float *out,
                                   int *sweeps_host, void *stream) {
+  // the argument and shape checks of lrstv_tsvt
   if (!A || !out) return LRSTV_ERR_ARG;
-  if (n1 < 1 || n2 < 1 || n3 < 1) return LRSTV_ERR_ARG;
-  if (n1 > lrstv::kMaxSpatial || n2 > lrstv::kMaxSpatial || n3 > lrstv::kMaxBands)
-    return LRSTV_ERR_SHAPE;
-  if (!(t >= 0.0f) || t > 3.0e38f) return LRSTV_ERR_ARG;
+  const int rc_shape = lrstv::check_shape(n1, n2, n3);
+  if (rc_shape != LRSTV_OK) return rc_shape;
+  if (!isfinite(t) || t < 0.0f) return LRSTV_ERR_ARG;
   const lrstv::Dims d = lrstv::make_dims(n1, n2, n3);
   // scratch layout: specA, specB (h P complex), V (h nc^2 complex), twiddles, sweeps
   const size_t spec = up256(sizeof(float2) * (size_t)d.h * d.P);

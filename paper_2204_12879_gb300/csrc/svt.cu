@@ -11,13 +11,11 @@
 // W (V diag g)^H is a batched complex GEMM (dft.cu).  One CTA per slice; the
 // sweep loop is capped and a slice that reaches the cap reports it.
 //
-// Three kernels share the rotation formula and differ in how columns move:
+// Two kernels share the rotation formula and differ in how columns move:
 //  - k_jacobi_pk (nr <= 256, the common case): 32-column panels staged in
 //    shared memory, a panel's W and V columns held in registers while later
 //    panels stream past, one column pair per half-warp, paired FP32
 //    instructions (__ffma2_rn) on a split row-pair layout;
-//  - k_jacobi_panel: the same panel order with full warps (kept for reference
-//    shapes; no longer dispatched);
 //  - k_jacobi (any nr up to 512): round-robin over all columns in global
 //    memory (L2-resident), one pair per warp.
 #include <float.h>
@@ -196,17 +194,8 @@ __global__ void __launch_bounds__(R <= 8 ? 1024 : 512)
 }
 
 // ---------------------------------------------------------------------------
-// Panel kernel (nr <= 256).  Same one-sided Jacobi and rotation formula, with
-// the columns visited panel by panel: the 32 columns of panel a are first
-// rotated among themselves in shared memory (round-robin, 16 disjoint pairs per
-// round), then held in registers, two per warp, while every later panel b is
-// staged in shared memory and swept past them: in round r warp w rotates
-// panel-b column (w + r) mod 32 against both of its own columns, so one staged
-// column serves two rotations.  Every pair is visited once per sweep (a block
-// row-cyclic ordering), and between rounds each column is touched by a single
-// warp.
-constexpr int kPW = 32;      // panel width (columns)
-constexpr int kPWarps = 16;  // warps per CTA; warp w holds panel columns 2w, 2w+1
+// Shared pieces of the packed kernel: panel width, rotation formula.
+constexpr int kPW = 32;  // panel width (columns)
 
 struct Rot {
   float c, s, er, ei;
@@ -243,219 +232,6 @@ __device__ __forceinline__ bool make_rot(float al, float be, float gr, float gi,
   return true;
 }
 
-template <int R>
-__device__ __forceinline__ void pair_dots(const float2 (&a)[R], const float2 (&b)[R], float &al,
-                                          float &be, float &gr, float &gi) {
-  al = be = gr = gi = 0.f;
-#pragma unroll
-  for (int k = 0; k < R; ++k) {
-    al = fmaf(a[k].x, a[k].x, fmaf(a[k].y, a[k].y, al));
-    be = fmaf(b[k].x, b[k].x, fmaf(b[k].y, b[k].y, be));
-    gr = fmaf(a[k].x, b[k].x, fmaf(a[k].y, b[k].y, gr));
-    gi = fmaf(a[k].x, b[k].y, fmaf(-a[k].y, b[k].x, gi));
-  }
-  al = warp_sum(al);
-  be = warp_sum(be);
-  gr = warp_sum(gr);
-  gi = warp_sum(gi);
-}
-
-// (a, b) <- (c a - s e b, s a + c e b), e = er + i ei; padded rows stay 0.
-template <int R>
-__device__ __forceinline__ void pair_apply(float2 (&a)[R], float2 (&b)[R], const Rot &r) {
-#pragma unroll
-  for (int k = 0; k < R; ++k) {
-    const float2 bb = make_float2(r.er * b[k].x - r.ei * b[k].y, r.er * b[k].y + r.ei * b[k].x);
-    const float2 x = a[k];
-    a[k] = make_float2(r.c * x.x - r.s * bb.x, r.c * x.y - r.s * bb.y);
-    b[k] = make_float2(r.s * x.x + r.c * bb.x, r.s * x.y + r.c * bb.y);
-  }
-}
-
-template <int R>
-__device__ __forceinline__ void col_load(float2 (&x)[R], const float2 *src, int n, int lane) {
-#pragma unroll
-  for (int k = 0; k < R; ++k) {
-    const int row = lane + 32 * k;
-    x[k] = row < n ? src[row] : make_float2(0.f, 0.f);
-  }
-}
-
-template <int R>
-__device__ __forceinline__ void col_store(const float2 (&x)[R], float2 *dst, int n, int lane) {
-#pragma unroll
-  for (int k = 0; k < R; ++k) {
-    const int row = lane + 32 * k;
-    if (row < n) dst[row] = x[k];
-  }
-}
-
-__device__ __forceinline__ void block_copy(float2 *dst, const float2 *src, size_t n) {
-  for (size_t e = threadIdx.x; e < n; e += blockDim.x) dst[e] = src[e];
-}
-
-template <int R>
-__global__ void __launch_bounds__(kPWarps * 32, 1)
-    k_jacobi_panel(int nr, int nc, size_t wstride, size_t vstride, float2 *W_all, float2 *V_all,
-                   float t, int max_sweeps, float tol, float negl_rel,
-                   int *__restrict__ sweeps_out, unsigned long long *__restrict__ work) {
-  extern __shared__ float4 smem_f4[];
-  float2 *sW = reinterpret_cast<float2 *>(smem_f4);  // kPW columns of nr rows
-  float2 *sV = sW + (size_t)kPW * nr;                // kPW columns of nc rows
-  float2 *W = W_all + (size_t)blockIdx.x * wstride;
-  float2 *V = V_all + (size_t)blockIdx.x * vstride;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  __shared__ float s_red[32];
-  __shared__ int s_rot;
-
-  for (int e = tid; e < nc * nc; e += blockDim.x)
-    V[e] = make_float2((e % nc) == (e / nc) ? 1.0f : 0.0f, 0.0f);
-  float part = 0.0f;
-  for (size_t e = tid; e < (size_t)nr * nc; e += blockDim.x) {
-    const float2 x = W[e];
-    part = fmaf(x.x, x.x, fmaf(x.y, x.y, part));
-  }
-  part = warp_sum(part);
-  if (lane == 0) s_red[warp] = part;
-  __syncthreads();
-  if (warp == 0) {
-    float v = lane < kPWarps ? s_red[lane] : 0.0f;
-    v = warp_sum(v);
-    if (lane == 0) s_red[0] = v;
-  }
-  __syncthreads();
-  const float negl = negl_rel * s_red[0];
-
-  const int npan = (nc + kPW - 1) / kPW;
-  unsigned long long n_pairs = 0, n_rot = 0;
-  int sweeps = (nc < 2) ? 1 : 0;
-  bool converged = (nc < 2);
-  float2 aW0[R], aV0[R], aW1[R], aV1[R], bW[R], bV[R];
-  for (int sweep = 1; sweep <= max_sweeps && !converged; ++sweep) {
-    if (tid == 0) s_rot = 0;
-    int rotated = 0;
-    for (int a = 0; a < npan; ++a) {
-      const int ca = a * kPW, wa = min(kPW, nc - ca);
-      __syncthreads();
-      block_copy(sW, W + (size_t)nr * ca, (size_t)nr * wa);
-      block_copy(sV, V + (size_t)nc * ca, (size_t)nc * wa);
-      __syncthreads();
-      // pairs inside panel a
-      for (int r = 0; r < kPW - 1; ++r) {
-        int p, q;
-        pair_of(r, warp, kPW, p, q);
-        if (p < wa && q < wa) {
-          col_load<R>(aW0, sW + (size_t)nr * p, nr, lane);
-          col_load<R>(bW, sW + (size_t)nr * q, nr, lane);
-          float al, be, gr, gi;
-          pair_dots<R>(aW0, bW, al, be, gr, gi);
-          n_pairs += 1;
-          Rot rt;
-          if (make_rot(al, be, gr, gi, tol, negl, rt)) {
-            pair_apply<R>(aW0, bW, rt);
-            col_store<R>(aW0, sW + (size_t)nr * p, nr, lane);
-            col_store<R>(bW, sW + (size_t)nr * q, nr, lane);
-            col_load<R>(aV0, sV + (size_t)nc * p, nc, lane);
-            col_load<R>(bV, sV + (size_t)nc * q, nc, lane);
-            pair_apply<R>(aV0, bV, rt);
-            col_store<R>(aV0, sV + (size_t)nc * p, nc, lane);
-            col_store<R>(bV, sV + (size_t)nc * q, nc, lane);
-            n_rot += 1;
-            rotated = 1;
-          }
-        }
-        __syncthreads();
-      }
-      // panel a's columns 2w, 2w+1 move to registers
-      const int i0 = 2 * warp, i1 = 2 * warp + 1;
-      const bool h0 = i0 < wa, h1 = i1 < wa;
-      if (h0) {
-        col_load<R>(aW0, sW + (size_t)nr * i0, nr, lane);
-        col_load<R>(aV0, sV + (size_t)nc * i0, nc, lane);
-      }
-      if (h1) {
-        col_load<R>(aW1, sW + (size_t)nr * i1, nr, lane);
-        col_load<R>(aV1, sV + (size_t)nc * i1, nc, lane);
-      }
-      for (int b = a + 1; b < npan; ++b) {
-        const int cb = b * kPW, wb = min(kPW, nc - cb);
-        __syncthreads();
-        block_copy(sW, W + (size_t)nr * cb, (size_t)nr * wb);
-        block_copy(sV, V + (size_t)nc * cb, (size_t)nc * wb);
-        __syncthreads();
-        for (int r = 0; r < kPW; ++r) {
-          const int j = (warp + r) & (kPW - 1);
-          if (j < wb && (h0 || h1)) {
-            col_load<R>(bW, sW + (size_t)nr * j, nr, lane);
-            col_load<R>(bV, sV + (size_t)nc * j, nc, lane);
-            bool dirty = false;
-            if (h0) {
-              float al, be, gr, gi;
-              pair_dots<R>(aW0, bW, al, be, gr, gi);
-              n_pairs += 1;
-              Rot rt;
-              if (make_rot(al, be, gr, gi, tol, negl, rt)) {
-                pair_apply<R>(aW0, bW, rt);
-                pair_apply<R>(aV0, bV, rt);
-                n_rot += 1;
-                dirty = true;
-              }
-            }
-            if (h1) {
-              float al, be, gr, gi;
-              pair_dots<R>(aW1, bW, al, be, gr, gi);
-              n_pairs += 1;
-              Rot rt;
-              if (make_rot(al, be, gr, gi, tol, negl, rt)) {
-                pair_apply<R>(aW1, bW, rt);
-                pair_apply<R>(aV1, bV, rt);
-                n_rot += 1;
-                dirty = true;
-              }
-            }
-            if (dirty) {
-              col_store<R>(bW, sW + (size_t)nr * j, nr, lane);
-              col_store<R>(bV, sV + (size_t)nc * j, nc, lane);
-              rotated = 1;
-            }
-          }
-          __syncthreads();
-        }
-        block_copy(W + (size_t)nr * cb, sW, (size_t)nr * wb);
-        block_copy(V + (size_t)nc * cb, sV, (size_t)nc * wb);
-      }
-      if (h0) {
-        col_store<R>(aW0, W + (size_t)nr * (ca + i0), nr, lane);
-        col_store<R>(aV0, V + (size_t)nc * (ca + i0), nc, lane);
-      }
-      if (h1) {
-        col_store<R>(aW1, W + (size_t)nr * (ca + i1), nr, lane);
-        col_store<R>(aV1, V + (size_t)nc * (ca + i1), nc, lane);
-      }
-    }
-    if (rotated && lane == 0) s_rot = 1;
-    __syncthreads();
-    sweeps = sweep;
-    converged = (s_rot == 0);
-    __syncthreads();
-  }
-
-  for (int i = warp; i < nc; i += kPWarps) {
-    const float2 *wi = W + (size_t)nr * i;
-    float n2 = 0.f;
-    for (int row = lane; row < nr; row += 32) n2 = fmaf(wi[row].x, wi[row].x, fmaf(wi[row].y, wi[row].y, n2));
-    n2 = warp_sum(n2);
-    const double sigma = sqrt((double)n2);
-    const float g = t < 0.0f ? 1.0f : (sigma > (double)t ? (float)(1.0 - (double)t / sigma) : 0.0f);
-    float2 *vi = V + (size_t)nc * i;
-    for (int row = lane; row < nc; row += 32) vi[row] = make_float2(vi[row].x * g, vi[row].y * g);
-  }
-  if (tid == 0) sweeps_out[blockIdx.x] = converged ? sweeps : -max_sweeps;
-  if (work && lane == 0) {
-    atomicAdd(work + 0, n_pairs);
-    atomicAdd(work + 1, n_rot);
-  }
-}
 
 constexpr int kHW = 16;  // warps per CTA of the packed kernel (32 half-warps)
 
@@ -874,19 +650,6 @@ cudaError_t launch_pk(int nslices, int nr, int nc, size_t ws, size_t vs, float2 
   return cudaGetLastError();
 }
 
-template <int R>
-cudaError_t launch_panel(int nslices, int nr, int nc, size_t ws, size_t vs, float2 *W, float2 *V,
-                         float t, int max_sweeps, float tol, float negl, int *sweeps,
-                         unsigned long long *work, cudaStream_t st) {
-  const size_t smem = sizeof(float2) * (size_t)kPW * (nr + nc);
-  cudaError_t e = cudaFuncSetAttribute(k_jacobi_panel<R>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_jacobi_panel<R><<<nslices, kPWarps * 32, smem, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol,
-                                                         negl, sweeps, work);
-  return cudaGetLastError();
-}
-
 // sigma_i = |w_i| and V_s = V diag(g), g = max(1 - t / sigma, 0), with the same
 // arithmetic and summation order as the Jacobi kernels' epilogue (so a Jacobi
 // run with t < 0 followed by this kernel equals a run with threshold t).
@@ -1003,7 +766,6 @@ cudaError_t launch_jacobi_batch(const SliceTask *tasks, int ntasks, int *counter
 cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, float t,
                           int max_sweeps, int *sweeps, unsigned long long *work,
                           cudaStream_t st, const JacOpt &o) {
-  const int warm = o.warm;
   const int nr = d.nr, nc = d.nc;
   if (nslices <= 0) return cudaSuccess;
   const int np = nc + (nc & 1);
@@ -1024,12 +786,6 @@ cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, floa
     if (KP <= 4) return launch_pk<4>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
     if (KP <= 7) return launch_pk<7>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
     return launch_pk<8>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
-  }
-  if (R <= 8 && nc >= 2 && !warm) {
-    if (R <= 1) return launch_panel<1>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
-    if (R <= 2) return launch_panel<2>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
-    if (R <= 4) return launch_panel<4>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
-    return launch_panel<8>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, st);
   }
   dim3 grid(nslices), block(32 * nw);
   if (R <= 1) k_jacobi<1><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o);
