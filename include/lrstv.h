@@ -125,6 +125,24 @@ int lrstv_max_spatial(void);
  * ERR_ALLOC, ERR_CUDA. */
 int lrstv_check_bounded_wait(long long tries, int arrive, int *timed_out, int *lanes_freed);
 
+/* Throughput probe (no counterpart in the paper; it gives the benchmark
+ * measured peaks for its roofline fractions): runs one kernel of this library
+ * over every SM of the current device and reports its rate.
+ *  unit 0: FP32 FMA, scalar fmaf (8 independent chains a thread, 32 warps per SM);
+ *  unit 1: FP32 FMA, the paired instruction __ffma2_rn (16 chains);
+ *  unit 2: tensor pipe, tcgen05.mma kind::tf32, M = 128, N = 256, K = 8 per
+ *          instruction, operands in shared memory, one CTA and one issuing
+ *          thread per SM, two alternating TMEM accumulators;
+ *  unit 3: the same with kind::f16 on BF16 operands (K = 16 per instruction).
+ * work: loop trips per thread (units 0, 1) or MMAs per SM (units 2, 3), in
+ * 1 .. 2^40; about 2e7 FMA trips or 4e6 MMAs take a few hundred ms.  One
+ * untimed launch of work/16 + 1 comes first.  *tflops = floating-point
+ * operations (2 per FMA, 2 M N K per MMA) / the timed launch's CUDA-event
+ * time, *ms that time.  Synchronous on the legacy default stream; makes and
+ * frees one 4 KB device allocation.  ERR_ARG, ERR_ALLOC, ERR_CUDA (also when
+ * an MMA probe's bounded wait ran out). */
+int lrstv_peak_probe(int unit, long long work, double *tflops, double *ms);
+
 /* ------------------------------------------------- full TDLRSTV (Tucker) */
 /* Turns the L-update of a plan into the Tucker projection of the full TDLRSTV
  * model (eq. TDLRSTV, Section III-C step 1, eq. X_solution with the Tucker-3

@@ -576,6 +576,47 @@ int lrstv_check_bounded_wait(long long tries, int arrive, int *timed_out, int *l
   return LRSTV_OK;
 }
 
+int lrstv_peak_probe(int unit, long long work, double *tflops, double *ms) {
+  if (!tflops || !ms || unit < 0 || unit > 3 || work < 1 || work > (1ll << 40))
+    return LRSTV_ERR_ARG;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) {
+    cudaGetLastError();
+    return LRSTV_ERR_CUDA;
+  }
+  void *d = nullptr;
+  if (cudaMalloc(&d, 1024 * sizeof(float)) != cudaSuccess) return LRSTV_ERR_ALLOC;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double flops = 0.0;
+  float t = 0.0f;
+  int err = 0;
+  auto launch = [&](long long w) {
+    return unit < 2 ? launch_fma_peak(unit, nsm, w, (float *)d, 0, &flops)
+                    : launch_mma_peak(unit - 2, nsm, w, (int *)d, 0, &flops);
+  };
+  cudaError_t e = cudaMemset(d, 0, 1024 * sizeof(float));
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = launch(work / 16 + 1);  // untimed: loads the module, wakes the clocks
+  if (e == cudaSuccess) e = cudaEventRecord(e0, 0);
+  if (e == cudaSuccess) e = launch(work);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  if (e == cudaSuccess && unit >= 2) e = cudaMemcpy(&err, d, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(d);
+  if (e != cudaSuccess || err || !(t > 0.0f)) {
+    cudaGetLastError();
+    return LRSTV_ERR_CUDA;
+  }
+  *ms = t;
+  *tflops = flops / (t * 1e-3) / 1e12;
+  return LRSTV_OK;
+}
+
 const char *lrstv_kernel_name(int k) {
   static const char *names[LRSTV_NKERNEL] = {"l_tz", "r2c_z", "cgemm_z", "c2r_z", "fs_dual",
                                              "r2c_e", "jacobi", "cgemm_e", "c2r_e", "warm_e",

@@ -85,6 +85,12 @@ size_t cgemm_tc_smem();
 // wait and its timeout path (out: two device ints, zeroed by the caller)
 long long cgemm_tc_wait_limit();
 cudaError_t launch_wait_probe(long long tries, int arrive, int *out, cudaStream_t st);
+// throughput probes (peaks.cu, tcgemm.cu): *flops receives the launch's
+// floating-point operations; one launch covers nsm SMs
+cudaError_t launch_fma_peak(int paired, int nsm, long long iters, float *sink, cudaStream_t st,
+                            double *flops);
+cudaError_t launch_mma_peak(int prec, int nsm, long long n_mma, int *err, cudaStream_t st,
+                            double *flops);
 
 // -------------------------------------------------------------------- svt.cu
 // One-sided Jacobi on `nslices` working matrices W_s (nr x nc, column-major,

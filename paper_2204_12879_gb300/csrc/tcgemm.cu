@@ -469,6 +469,66 @@ __global__ void __launch_bounds__(32) k_wait_probe(long long tries, int arrive, 
   atomicAdd(out + 1, 1);
 }
 
+// Tensor-pipe throughput probe: one CTA per SM, one thread issuing n_mma
+// MMAs of M = 128, N = 256 (K = 8 TF32 or 16 BF16 per instruction) from
+// shared-memory tiles into two alternating TMEM accumulators, then one
+// commit and a bounded wait.  The tiles hold a fixed non-zero pattern (the
+// tensor core's power, and so its clock under the power cap, depends on the
+// data).  A wait that runs out sets *err; tensor memory is freed either way.
+constexpr int kProbeN = 256;
+constexpr size_t kProbeSmem = 120 * 1024;  // more than half the SM's shared memory: one CTA per SM
+
+template <int PREC>
+__global__ void __launch_bounds__(128, 1) k_mma_peak(long long n_mma, int *err) {
+  extern __shared__ __align__(1024) char smem[];
+  using P = Prec<PREC>;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const size_t tile_bytes = (size_t)(TM + kProbeN) * P::kKR * P::kBytes;
+  for (size_t e = tid; e < tile_bytes / 4; e += blockDim.x) {
+    const uint32_t h = (uint32_t)e * 2654435761u;
+    const float x = 0.25f + (float)(h >> 9) * (1.0f / 16777216.0f);  // in [0.25, 1.25)
+    if (PREC == 0) {
+      ((float *)smem)[e] = tf32_hi(x);
+    } else {
+      __nv_bfloat162 v = __floats2bfloat162_rn(x, 1.5f - x);
+      ((__nv_bfloat162 *)smem)[e] = v;
+    }
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+        smem_u32(&tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tslot;
+  const uint32_t idesc = (1u << 4) | (P::kFmt << 7) | (P::kFmt << 10) |
+                         ((uint32_t)(kProbeN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+  const uint32_t bar = smem_u32(&mbar);
+  if (tid == 0) {
+    const uint64_t a = sdesc<PREC>(smem_u32(smem));
+    const uint64_t b = sdesc<PREC>(smem_u32(smem + (size_t)TM * P::kKR * P::kBytes));
+    for (long long i = 0; i < n_mma; ++i)
+      mma<PREC>(tmem + (uint32_t)(i & 1) * kProbeN, a, b, idesc, i > 1 ? 1u : 0u);
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar));
+  }
+  __syncwarp();
+  if (!mbar_wait(bar, 0u) && tid == 0) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+}
+
 template <int PREC>
 size_t smem_bytes() {
   return 2 * (2 * Prec<PREC>::kTileA + 4 * Prec<PREC>::kTileB);
@@ -501,6 +561,24 @@ long long cgemm_tc_wait_limit() { return kWaitLimit; }
 
 cudaError_t launch_wait_probe(long long tries, int arrive, int *out, cudaStream_t st) {
   k_wait_probe<<<1, 32, 0, st>>>(tries, arrive, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mma_peak(int prec, int nsm, long long n_mma, int *err, cudaStream_t st,
+                            double *flops) {
+  const double per = 2.0 * TM * kProbeN * (prec ? 16 : 8);
+  *flops = per * (double)n_mma * nsm;
+  if (prec == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k_mma_peak<0>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kProbeSmem);
+    if (e != cudaSuccess) return e;
+    k_mma_peak<0><<<nsm, 128, kProbeSmem, st>>>(n_mma, err);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_mma_peak<1>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kProbeSmem);
+    if (e != cudaSuccess) return e;
+    k_mma_peak<1><<<nsm, 128, kProbeSmem, st>>>(n_mma, err);
+  }
   return cudaGetLastError();
 }
 

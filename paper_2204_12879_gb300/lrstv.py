@@ -19,7 +19,7 @@ from . import builder as _build
 __all__ = [
     "Params", "Stats", "Profile", "Plan", "Batch", "Unroll", "load", "status_string", "kernel_name", "LrstvError",
     "lrstv_diff", "lrstv_diff_adjoint", "lrstv_soft_threshold", "lrstv_zsolve", "lrstv_tsvt",
-    "lrstv_tsvt_noalloc",
+    "lrstv_tsvt_noalloc", "lrstv_peak_probe", "PEAK_UNITS",
     "lrstv_denoise", "BLOCK", "FLAG_F_THRESH_EXACT", "FLAG_NO_GAMMA4", "FLAG_GRAPH",
     "FLAG_STRICT", "FLAG_SIMT_GEMM", "FLAG_WARM_START", "FLAG_ISO_TV", "FLAG_BF16X3",
     "EXPORTED",
@@ -100,6 +100,8 @@ _SIGS = {
     "lrstv_status_string": [_I],
     "lrstv_max_spatial": [],
     "lrstv_check_bounded_wait": [ctypes.c_longlong, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "lrstv_peak_probe": [_I, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double),
+                         ctypes.POINTER(ctypes.c_double)],
     "lrstv_plan_create": [_I, _I, _I, ctypes.POINTER(Params), ctypes.POINTER(_P)],
     "lrstv_plan_destroy": [_P],
     "lrstv_plan_bytes": [_P, ctypes.POINTER(_SZ)],
@@ -598,6 +600,18 @@ def lrstv_check_bounded_wait(tries, arrive=False):
     _call("lrstv_check_bounded_wait", int(tries), 1 if arrive else 0, ctypes.byref(t),
           ctypes.byref(n))
     return t.value, n.value
+
+
+PEAK_UNITS = {"fp32_fma": 0, "fp32_fma2": 1, "tf32_mma": 2, "bf16_mma": 3}
+
+
+def lrstv_peak_probe(unit, work):
+    """lrstv_peak_probe: one throughput probe on the current device; unit is a
+    key of PEAK_UNITS.  Returns (TFLOP/s, ms of the timed launch)."""
+    _torch()
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _call("lrstv_peak_probe", PEAK_UNITS[unit], int(work), ctypes.byref(tf), ctypes.byref(ms))
+    return tf.value, ms.value
 
 
 def lrstv_denoise(Y, shape, params: Params, stream=None):

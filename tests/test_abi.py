@@ -90,5 +90,10 @@ def test_argument_errors_before_any_cuda_call(lib):
     assert lib.lrstv_check_bounded_wait(250001, 0, ctypes.byref(t), ctypes.byref(n)) == 1
     assert lib.lrstv_check_bounded_wait(10, 0, None, ctypes.byref(n)) == 1
     assert lib.lrstv_check_bounded_wait(10, 0, ctypes.byref(t), None) == 1
+    # the throughput probe: a known unit, work in 1 .. 2^40, both outputs
+    d = ctypes.c_double()
+    assert lib.lrstv_peak_probe(4, 10, ctypes.byref(d), ctypes.byref(d)) == 1
+    assert lib.lrstv_peak_probe(0, 0, ctypes.byref(d), ctypes.byref(d)) == 1
+    assert lib.lrstv_peak_probe(0, 10, None, ctypes.byref(d)) == 1
     # one band above the largest n3 a plan takes
     assert lib.lrstv_plan_create(2, 2, 4097, ctypes.byref(p), ctypes.byref(h)) == 2

@@ -18,6 +18,7 @@ def _check_line(line, metric, unit):
     assert line["impl"] == "reference" and line["metric"] == metric and line["unit"] == unit
     assert line["higher_is_better"] is True and line["vs_baseline"] is None
     assert line["value"] > 0 and line["ms_per_step"] == pytest.approx(1e3 / line["value"])
+    assert line["steps"] >= 1 and line["warmup"] == 0  # the units actually timed, no warm-up
     assert "workload" in line["config"]
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["unit"] == unit
@@ -91,7 +92,8 @@ def test_stage_bounds_closed_forms():
     kernels = {k: {"launches": v * steps, "ms_per_launch": 1.0} for k, v in per_it.items()}
     pk = {"hbm_gbs": 6000.0, "bf16_tflops": 2000.0, "sm_max_mhz": 2000.0}
     jac = 7.0e10 * steps
-    b = bench.stage_bounds(kernels, shape, steps, "tf32x3", jac, pk)
+    peak = bench.derived_peaks(pk, "measured", None, 152)
+    b = bench.stage_bounds(kernels, shape, steps, "tf32x3", jac, pk, peak)
     ms = b["ms_per_iteration"]
     fp32 = 152 * 128 * 2 * 2.0e9
     assert ms["l_tz"] == pytest.approx(13 * 4 * N / 6.0e12 * 1e3)
@@ -104,8 +106,29 @@ def test_stage_bounds_closed_forms():
     assert b["without_bound"] == ["tucker"] and "tucker" not in ms
     assert b["sum_ms"] == pytest.approx(sum(ms.values()))
     # the BF16 split runs at the full BF16 rate
-    b16 = bench.stage_bounds(kernels, shape, steps, "bf16x3", jac, pk)["ms_per_iteration"]
+    b16 = bench.stage_bounds(kernels, shape, steps, "bf16x3", jac, pk, peak)["ms_per_iteration"]
     assert b16["cgemm_e"] == pytest.approx(ms["cgemm_e"] / 2)
+
+
+def test_peaks_measured_or_derived():
+    """Measured probes set the FP32 (larger of scalar and paired FMA) and TF32
+    roofs; without them FP32 is derived from the SM count and TF32 is half of
+    BF16.  The tensor fraction counts three split products per complex MAC."""
+    pk = {"hbm_gbs": 6000.0, "bf16_tflops": 2000.0, "sm_max_mhz": 2000.0}
+    d = bench.derived_peaks(pk, "measured", None, 148)
+    assert d["fp32"] == pytest.approx(148 * 128 * 2 * 2.0e9 / 1e12)
+    assert d["tf32"] == 1000.0 and "derived" in d["fp32_source"]
+    probes = {u: {"tflops": v, "ms": 400.0, "clocks": {"sm_mhz": 1900.0, "reasons": []}}
+              for u, v in (("fp32_fma", 70.0), ("fp32_fma2", 72.0), ("tf32_mma", 900.0),
+                           ("bf16_mma", 1800.0))}
+    m = bench.derived_peaks(pk, "measured", probes, 152)
+    assert m["fp32"] == 72.0 and m["tf32"] == 900.0 and "fp32_fma2" in m["fp32_source"]
+    shape = (200, 200, 80)
+    kernels = {"cgemm_e": {"launches": 1, "ms_per_launch": 1.0}}
+    f = bench.tensor_fracs(kernels, shape, "tf32x3", m)["cgemm_e"]
+    useful = 8 * 200 * 200 * 200 * 3 * 41
+    assert f["useful_tflops"] == pytest.approx(useful / 1e-3 / 1e12)
+    assert f["frac"] == pytest.approx(3 * useful / 1e-3 / 1e12 / 900.0)
 
 
 def test_profile_commands_parse():
