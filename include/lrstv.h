@@ -163,6 +163,15 @@ int lrstv_peak_probe(int unit, long long work, double *tflops, double *ms);
  * allocation fails. */
 int lrstv_plan_set_tucker(lrstv_plan *plan, const int ranks[3]);
 
+/* The Tucker factor U_n of the last L-update (mode = n - 1 in 0..2): the
+ * n_n x r_n matrix (column-major FP32) whose orthonormal columns are the r_n
+ * leading eigenvectors of the mode-n Gram matrix of that iteration's HOOI
+ * sweep (eq. LRTAmodel's factor matrices), copied to caller device memory U
+ * (n_n r_n floats), stream-ordered.  ERR_ARG (null, mode out of range),
+ * ERR_STATE (the Tucker L-update is off, or no L-update has run since
+ * lrstv_init, lrstv_state_set or lrstv_plan_set_tucker). */
+int lrstv_plan_tucker_factor(const lrstv_plan *plan, int mode, float *U, void *stream);
+
 /* ------------------------------------------------------------- profiling */
 /* Kernels a plan launches (lrstv_profile indices). */
 typedef enum lrstv_kernel {

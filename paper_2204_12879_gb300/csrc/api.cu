@@ -759,6 +759,15 @@ int lrstv_plan_set_tucker(lrstv_plan *pl, const int ranks[3]) {
   return LRSTV_OK;
 }
 
+int lrstv_plan_tucker_factor(const lrstv_plan *pl, int mode, float *U, void *stream) {
+  if (!pl || !U || mode < 0 || mode > 2) return LRSTV_ERR_ARG;
+  if (!pl->tucker || !pl->tk.valid) return LRSTV_ERR_STATE;
+  const size_t n = (size_t)pl->tk.n[mode] * pl->tk.r[mode];
+  CK(cudaMemcpyAsync(U, pl->tk.U[mode], sizeof(float) * n, cudaMemcpyDeviceToDevice,
+                     (cudaStream_t)stream));
+  return LRSTV_OK;
+}
+
 int lrstv_plan_bytes(const lrstv_plan *pl, size_t *bytes) {
   if (!pl || !bytes) return LRSTV_ERR_ARG;
   *bytes = pl->arena_bytes;

@@ -116,6 +116,7 @@ _SIGS = {
     "lrstv_get_stats": [_P, ctypes.POINTER(Stats), _P],
     "lrstv_get_slice_sweeps": [_P, ctypes.POINTER(_I), _I, _P],
     "lrstv_plan_set_tucker": [_P, ctypes.POINTER(_I)],
+    "lrstv_plan_tucker_factor": [_P, _I, _P, _P],
     "lrstv_state_get": [_P, _I, _P, _P],
     "lrstv_state_set": [_P, _I, _P, _P],
     "lrstv_get_mu": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)],
@@ -292,6 +293,16 @@ class Plan:
         (r1, r2, r3); None or (0, 0, 0) restores the plain L-update."""
         arr = None if ranks is None else (_I * 3)(*[int(r) for r in ranks])
         _call("lrstv_plan_set_tucker", self._h, arr)
+
+    def tucker_factor(self, mode, rank, stream=None):
+        """U_{mode+1} of the last Tucker L-update as an (n, rank) float32 CUDA
+        tensor (orthonormal columns)."""
+        torch = _torch()
+        n = self.shape[mode]
+        out = torch.empty(rank * n, dtype=torch.float32, device="cuda")
+        _call("lrstv_plan_tucker_factor", self._h, int(mode), ctypes.c_void_p(out.data_ptr()),
+              _stream(stream))
+        return out.view(rank, n).t()
 
     def slice_sweeps(self, stream=None):
         """Per-slice Jacobi sweep counts of the last E-step, shape (3, n3//2 + 1)."""

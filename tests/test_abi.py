@@ -90,6 +90,7 @@ def test_argument_errors_before_any_cuda_call(lib):
     assert lib.lrstv_check_bounded_wait(250001, 0, ctypes.byref(t), ctypes.byref(n)) == 1
     assert lib.lrstv_check_bounded_wait(10, 0, None, ctypes.byref(n)) == 1
     assert lib.lrstv_check_bounded_wait(10, 0, ctypes.byref(t), None) == 1
+    assert lib.lrstv_plan_tucker_factor(None, 0, None, None) == 1
     # the throughput probe: a known unit, work in 1 .. 2^40, both outputs
     d = ctypes.c_double()
     assert lib.lrstv_peak_probe(4, 10, ctypes.byref(d), ctypes.byref(d)) == 1

@@ -92,15 +92,21 @@ def test_iso_differs_from_anisotropic(L):
     assert np.max(np.abs(outs[0] - outs[1])) > 1e-4
 
 
-def test_all_extensions_together(L, orc):
-    """The isotropic F-update, the Tucker L-update, the warm start and the
-    mixed-precision GEMMs in one plan, against the FP64 reference with the
-    isotropic flag (the mixed-precision bound, 1e-3)."""
+@pytest.mark.parametrize("bf16", [False, True])
+def test_all_extensions_together(L, orc, bf16):
+    """The isotropic F-update, the Tucker L-update and the warm start in one
+    plan, with 3xTF32 or 3xBF16 tensor-core GEMMs, against the FP64 reference
+    with the isotropic flag, to the 1e-4 bound of whole runs.  For 3xBF16:
+    each product term errs by at most 3 * 2^-18 relative (the dropped lo*lo
+    term and the halves' rounding), so one Z-solve or t-SVT step errs by about
+    1e-5 of its data (measured 4.7e-6 and 1.3e-6); the steps of an ADMM
+    iteration are proximal maps and averages (non-expansive), so eight
+    iterations add at most 8e-5."""
     from oracle import tucker as tk
     from tests.test_gpu_tucker import _low_rank
     shape, ranks, iters = (24, 20, 9), (3, 3, 3), 8
     _, Y = _low_rank(shape, 3, 61)
-    flags = L.FLAG_ISO_TV | L.FLAG_WARM_START | L.FLAG_BF16X3
+    flags = L.FLAG_ISO_TV | L.FLAG_WARM_START | (L.FLAG_BF16X3 if bf16 else 0)
     with L.Plan(*shape, L.Params.make(24, 20, max_iter=iters, flags=flags)) as pl:
         pl.set_tucker(ranks)
         X, S, st = pl.run(dev(Y), stats=True)
@@ -108,8 +114,8 @@ def test_all_extensions_together(L, orc):
     assert st.jacobi_unconverged == 0 and st.gemm_errors == 0
     ref = tk.TuckerState(orc, Y, orc.Params(n1=24, n2=20), ranks, flags=orc.FLAG_ISO_TV)
     ref.iterate(iters)
-    print("all extensions: max-abs", maxabs(X, ref.X))
-    assert maxabs(X, ref.X) <= 1e-3
+    print("all extensions (bf16x3=%s): max-abs" % bf16, maxabs(X, ref.X))
+    assert maxabs(X, ref.X) <= 1e-4
 
 
 def test_iso_batch_equals_plans(L):

@@ -70,3 +70,10 @@ def test_no_cpu_fallback():
         lrstv.Plan(8, 8, 4, lrstv.Params.make(8, 8))
     with pytest.raises(RuntimeError, match="CUDA"):
         lrstv.lrstv_check_bounded_wait(10)
+
+
+def test_stored_expected_values_come_from_the_oracle_only():
+    # the scripts under tests/golden that write expected values call oracle/
+    # (and the seeded generators), never the CUDA path
+    names = _py_imports(os.path.join("tests", "golden"))
+    assert PKG not in names and "torch" not in names, names
