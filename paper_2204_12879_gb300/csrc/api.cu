@@ -121,7 +121,7 @@ cudaError_t zsolve_core(const Dims &d, int nb, const Tables &tb, const float *T,
   cudaError_t e;
   {
     Span sp(prof, LRSTV_K_R2C_Z, st);
-    e = launch_r2c3(d, nb, T, nullptr, 0.0f, specA, 0, tb.tw3, st);
+    e = launch_r2c3(d, nb, T, nullptr, 0.0f, specA, 0, tb.tw3, st, gs);
   }
   if (e != cudaSuccess) return e;
   CGemm g{};
@@ -148,7 +148,7 @@ cudaError_t zsolve_core(const Dims &d, int nb, const Tables &tb, const float *T,
   g.A = specB; g.sA = (long long)d.P; g.B = tb.G2; g.sB = 0; g.ldb = d.n2; g.K = d.n2; g.C = specA;
   if ((e = gemm_z(g, st, prof, gs)) != cudaSuccess) return e;
   Span sp(prof, LRSTV_K_C2R_Z, st);
-  return launch_c2r3(d, nb, specA, 0, tb.tw3, Z, 0, nullptr, nullptr, 0.0f, 0, st);
+  return launch_c2r3(d, nb, specA, 0, tb.tw3, Z, 0, nullptr, nullptr, 0.0f, 0, st, gs);
 }
 
 namespace {
@@ -157,9 +157,10 @@ namespace {
 // DFT along mode 3 into the working orientation (tsvt_pre), Jacobi + g-scaling
 // (tsvt_jac), W V^H and the inverse DFT (tsvt_post).
 cudaError_t tsvt_pre(const Dims &d, int nb, const float *x, const float *y, float ycoef,
-                     const float2 *tw3, float2 *specA, cudaStream_t st, Prof *prof) {
+                     const float2 *tw3, float2 *specA, cudaStream_t st, Prof *prof,
+                     GemmSel gs = kSimt) {
   Span sp(prof, LRSTV_K_R2C_E, st);
-  return launch_r2c3(d, nb, x, y, ycoef, specA, 1, tw3, st);
+  return launch_r2c3(d, nb, x, y, ycoef, specA, 1, tw3, st, gs);
 }
 
 // ms2 (may be null): nb floats for the tensors' largest mean-square column
@@ -195,7 +196,7 @@ cudaError_t tsvt_post(const Dims &d, int nb, float *out, int mode, float *G4, co
   }
   if (e != cudaSuccess) return e;
   Span sp(prof, LRSTV_K_C2R_E, st);
-  return launch_c2r3(d, nb, specB, 1, tw3, out, mode, G4, F, mu, gamma4, st);
+  return launch_c2r3(d, nb, specB, 1, tw3, out, mode, G4, F, mu, gamma4, st, gs);
 }
 
 cudaError_t tsvt_core(const Dims &d, int nb, const float *x, const float *y, float ycoef, float t,
@@ -203,7 +204,7 @@ cudaError_t tsvt_core(const Dims &d, int nb, const float *x, const float *y, flo
                       const float2 *tw3, float2 *specA, float2 *specB, float2 *V, int *sweeps,
                       cudaStream_t st, Prof *prof = nullptr, GemmSel gs = kSimt,
                       float *ms2 = nullptr) {
-  cudaError_t e = tsvt_pre(d, nb, x, y, ycoef, tw3, specA, st, prof);
+  cudaError_t e = tsvt_pre(d, nb, x, y, ycoef, tw3, specA, st, prof, gs);
   if (e != cudaSuccess) return e;
   if ((e = tsvt_jac(d, nb, t, specA, V, sweeps, st, prof, ms2)) != cudaSuccess) return e;
   return tsvt_post(d, nb, out, mode, G4, F, mu, gamma4, tw3, specA, specB, V, st, prof, gs);
@@ -345,7 +346,7 @@ cudaError_t tsvt_warm(lrstv_plan *pl, float ycoef, float t, float mu, int gamma4
   const int ns = 3 * d.h;
   const GemmSel gs = plan_gemm(pl);
   const long long nc2 = (long long)d.nc * d.nc, P = (long long)d.P;
-  cudaError_t e = tsvt_pre(d, 3, pl->F, pl->G4, ycoef, pl->tb.tw3, pl->specA, st, &pl->prof);
+  cudaError_t e = tsvt_pre(d, 3, pl->F, pl->G4, ycoef, pl->tb.tw3, pl->specA, st, &pl->prof, gs);
   if (e != cudaSuccess) return e;
   float2 *Wm = pl->specA, *R = pl->specB;
   if (pl->vwarm) {
@@ -390,7 +391,7 @@ cudaError_t tsvt_warm(lrstv_plan *pl, float ycoef, float t, float mu, int gamma4
   }
   pl->vwarm = 1;
   Span sp(&pl->prof, LRSTV_K_C2R_E, st);
-  return launch_c2r3(d, 3, R, 1, pl->tb.tw3, pl->E, 1, pl->G4, pl->F, mu, gamma4, st);
+  return launch_c2r3(d, 3, R, 1, pl->tb.tw3, pl->E, 1, pl->G4, pl->F, mu, gamma4, st, gs);
 }
 
 size_t plan_layout(lrstv_plan *pl, void *base) {
@@ -1131,7 +1132,7 @@ int batch_e_step(lrstv_batch *b, cudaStream_t st) {
   for (int i = 0; i < b->n; ++i) {
     lrstv_plan *pl = b->plans[i];
     CK(tsvt_pre(pl->d, 3, pl->F, pl->G4, (float)(1.0 / pl->mu), pl->tb.tw3,
-                warm ? pl->specB : pl->specA, st, &pl->prof));
+                warm ? pl->specB : pl->specA, st, &pl->prof, plan_gemm(pl)));
     if (warm) CK(warm_basis(pl, pl->specB, pl->specA, pl->specA, st));
     CK(launch_group_ms2(pl->d, 3 * pl->d.h, pl->specA, pl->d.h, pl->ms2, st));
   }

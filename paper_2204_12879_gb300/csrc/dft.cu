@@ -341,7 +341,24 @@ cudaError_t launch_tables(const Dims &d, const float w[3], float2 *tw3, float2 *
 }
 
 cudaError_t launch_r2c3(const Dims &d, int nb, const float *x, const float *y, float ycoef,
-                        float2 *out, int work_orient, const float2 *tw3, cudaStream_t st) {
+                        float2 *out, int work_orient, const float2 *tw3, cudaStream_t st,
+                        GemmSel gs) {
+  if (gs.tc) {
+    Dft3 f{};
+    f.x = x;
+    f.y = y;
+    f.ycoef = ycoef;
+    f.spec_out = out;
+    f.tw3 = tw3;
+    f.n1 = d.n1;
+    f.n2 = d.n2;
+    f.n3 = d.n3;
+    f.h = d.h;
+    f.trans = work_orient && d.trans;
+    f.P = d.P;
+    f.N = d.N;
+    return launch_dft3_tc(1, f, nb, gs.err, st, gs.prec);
+  }
   const size_t tiles = (d.P + kPix - 1) / kPix, groups = (d.h + kKF - 1) / kKF;
   dim3 grid((unsigned)(tiles * groups), 1, nb);
   if (y)
@@ -355,7 +372,26 @@ cudaError_t launch_r2c3(const Dims &d, int nb, const float *x, const float *y, f
 
 cudaError_t launch_c2r3(const Dims &d, int nb, const float2 *spec, int work_orient,
                         const float2 *tw3, float *out, int mode, float *G4, const float *F,
-                        float mu, int gamma4, cudaStream_t st) {
+                        float mu, int gamma4, cudaStream_t st, GemmSel gs) {
+  if (gs.tc) {
+    Dft3 f{};
+    f.spec = spec;
+    f.out = out;
+    f.G4 = G4;
+    f.F = F;
+    f.mu = mu;
+    f.mode = mode;
+    f.gamma4 = gamma4;
+    f.tw3 = tw3;
+    f.n1 = d.n1;
+    f.n2 = d.n2;
+    f.n3 = d.n3;
+    f.h = d.h;
+    f.trans = work_orient && d.trans;
+    f.P = d.P;
+    f.N = d.N;
+    return launch_dft3_tc(2, f, nb, gs.err, st, gs.prec);
+  }
   const size_t tiles = (d.P + kPix - 1) / kPix, groups = (d.n3 + kKF - 1) / kKF;
   dim3 grid((unsigned)(tiles * groups), 1, nb);
   k_c2r3<<<grid, kPix, 0, st>>>(d.n1, d.n2, d.n3, d.h, d.N, d.P, spec, work_orient && d.trans,

@@ -48,17 +48,26 @@ cudaError_t launch_tables(const Dims &d, const float w[3], float2 *tw3, float2 *
                           float2 *F2, float2 *G2, float *lam1, float *lam2, float *lam3,
                           cudaStream_t st);
 cudaError_t launch_tw3(int n3, float2 *tw3, cudaStream_t st);
+// Which engine runs the GEMM-shaped work (the spatial and spectral DFTs, the
+// SVT reconstruction): the tensor cores (tcgen05; err receives bounded-wait
+// timeouts, prec the split: 0 = 3xTF32, 1 = 3xBF16) or the FP32 SIMT kernels.
+struct GemmSel {
+  bool tc;
+  int *err;
+  int prec;  // tensor-core split precision (launch_cgemm_tc)
+};
 // Mode-3 real-to-half-complex DFT of `nb` cubes x_b - ycoef * y_b (y may be
 // null), written as slices b*h + k of `out` (P complex each), in the working
 // orientation (A^H when d.trans and `work_orient`).
 cudaError_t launch_r2c3(const Dims &d, int nb, const float *x, const float *y, float ycoef,
-                        float2 *out, int work_orient, const float2 *tw3, cudaStream_t st);
+                        float2 *out, int work_orient, const float2 *tw3, cudaStream_t st,
+                        GemmSel gs = {false, nullptr, 0});
 // Inverse mode-3 DFT (half-complex to real, 1/n3 included) of `nb` spectra.
 // mode 0: out_b = result.  mode 1 (E-step epilogue): E_b = result and
 // G4_b += mu (E_b - F_b) when `gamma4` (F, G4 given).
 cudaError_t launch_c2r3(const Dims &d, int nb, const float2 *spec, int work_orient,
                         const float2 *tw3, float *out, int mode, float *G4, const float *F,
-                        float mu, int gamma4, cudaStream_t st);
+                        float mu, int gamma4, cudaStream_t st, GemmSel gs = {false, nullptr, 0});
 // Batched complex GEMM, column-major: C_b = A_b * op(B_b), op(B) = B or B^H.
 // epi 1: C(a, b) *= scale / (mu (1 + lam1[a] + lam2[b] + lam3[batch])).
 // opA 1 (SIMT kernel only): op(A) = A^H, A stored K x M.  epi 2 (SIMT kernel
@@ -80,6 +89,26 @@ cudaError_t launch_cgemm(const CGemm &g, cudaStream_t st);
 // (3xBF16, about 2^-17 relative error per term, the mixed-precision mode).
 // *err (may be null) is set to 1 if a CTA's wait for its MMAs runs out.
 cudaError_t launch_cgemm_tc(const CGemm &g, int *err, cudaStream_t st, int prec = 0);
+// The mode-3 DFTs of nb cubes on the same tensor-core pipeline (kind 1: real
+// cube x - ycoef y -> half spectrum at the working orientation, as
+// launch_r2c3; kind 2: half spectrum -> real cube, with the Gamma4 epilogue
+// of mode 1, as launch_c2r3).
+struct Dft3 {
+  const float *x, *y;  // kind 1: cubes (nb N floats each), y may be null
+  float ycoef;
+  float2 *spec_out;    // kind 1: nb h P complex
+  const float2 *spec;  // kind 2: nb h P complex
+  float *out;          // kind 2: nb N floats
+  float *G4;           // kind 2, mode 1: Gamma4 += mu (out - F)
+  const float *F;
+  float mu;
+  int mode, gamma4;
+  const float2 *tw3;   // exp(-2 pi i m / n3), m < n3
+  int n1, n2, n3, h, trans;
+  size_t P, N;
+};
+cudaError_t launch_dft3_tc(int kind, const Dft3 &f, int nb, int *err, cudaStream_t st,
+                           int prec = 0);
 size_t cgemm_tc_smem();
 // the tries of the GEMM's bounded barrier wait, and a one-warp check of that
 // wait and its timeout path (out: two device ints, zeroed by the caller)
@@ -192,11 +221,6 @@ struct Prof;  // per-kernel event profiler of a plan; null: not profiled
 
 // Which GEMM implementation a call uses: the tensor cores (with an error
 // slot for bounded-wait timeouts) or the FP32 SIMT kernel.
-struct GemmSel {
-  bool tc;
-  int *err;
-  int prec;  // tensor-core split precision (launch_cgemm_tc)
-};
 constexpr GemmSel kSimt = {false, nullptr, 0};
 cudaError_t gemm(const CGemm &g, GemmSel gs, cudaStream_t st);
 

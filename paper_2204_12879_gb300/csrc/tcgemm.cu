@@ -154,8 +154,23 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
   return done != 0;
 }
 
-template <int OPB, int EPI, int PREC>
-__global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, int *err) {
+// KIND 0: the complex GEMM C = A op(B) of CGemm.  KIND 1 and 2: the mode-3
+// DFTs of the cubes of Dft3 as GEMMs over the pixels (M = n1 n2):
+//  KIND 1 (real -> half spectrum): C(p, k) = sum_c x(p, c) exp(-2 pi i k c / n3),
+//    k < h, a real A (x, or x - ycoef y) against the twiddles; a K chunk holds
+//    KR real bands in the A tile, and the B tiles hold the real and the
+//    imaginary twiddle parts of those bands, so that the MMAs form Re C and
+//    Im C directly.  Written at the working orientation's pixel (conjugated
+//    when transposed).
+//  KIND 2 (half spectrum -> real): x(p, c) = (1/n3) sum_{k<h} w_k Re(X_k(p)
+//    exp(2 pi i k c / n3)) with w_k = 1 at k = 0 and k = n3/2, else 2: the
+//    complex GEMM's Re C alone, B(k, c) = w_k exp(2 pi i k c / n3); the
+//    epilogue scales by 1/n3 and, in mode 1, updates Gamma4 += mu (x - F).
+// The DFT kinds take their tile indices from blockIdx.x with the N tiles of
+// one M tile adjacent in launch order, so the M tile's inputs come from DRAM
+// once and from L2 for the other N tiles.
+template <int OPB, int EPI, int PREC, int KIND = 0>
+__global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, Dft3 f, int *err) {
   extern __shared__ __align__(1024) char smem[];
   using P = Prec<PREC>;
   // two shared-memory stages, so that a chunk is staged while the previous
@@ -171,7 +186,31 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, int *err) {
   const float2 *A = g.A + (size_t)b * g.sA;
   const float2 *B = g.B + (size_t)b * g.sB;
   float2 *C = g.C + (size_t)b * g.sC;
-  const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
+  int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
+  // the DFT kinds: problem size, this batch entry's cubes
+  int gM = g.M, gN = g.N, gK = g.K;
+  const float *xb = nullptr, *yb = nullptr;
+  const float2 *specb = nullptr;
+  if (KIND != 0) {
+    const int nt = ((KIND == 1 ? f.h : f.n3) + TN - 1) / TN;
+    m0 = (blockIdx.x / nt) * TM;
+    n0 = (blockIdx.x % nt) * TN;
+    gM = (int)f.P;
+    gN = KIND == 1 ? f.h : f.n3;
+    gK = KIND == 1 ? f.n3 : f.h;
+    if (KIND == 1) {
+      xb = f.x + (size_t)b * f.N;
+      if (f.y) yb = f.y + (size_t)b * f.N;
+    } else {
+      specb = f.spec + (size_t)b * f.h * f.P;
+    }
+  }
+  // pixel p of the cube -> its index in the working orientation's slice
+  auto wpos = [&](int p) -> size_t {
+    if (!f.trans) return (size_t)p;
+    const int i = p % f.n1, j = p / f.n1;
+    return (size_t)j + (size_t)f.n2 * i;
+  };
 
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
@@ -208,7 +247,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, int *err) {
     accIm[c] = 0.f;
   }
   constexpr int TK = P::kTK, KR = P::kKR;
-  const int nchunks = (g.K + TK - 1) / TK;
+  // a chunk is TK complex K (KIND 0, 2) or KR real bands (KIND 1)
+  const int nchunks = KIND == 1 ? (gK + KR - 1) / KR : (gK + TK - 1) / TK;
   // Staging is software-pipelined: chunk ch + 1's operands are loaded from
   // global memory into registers while chunk ch's MMAs run, then split and
   // stored to shared memory once those MMAs are done with the tiles.
@@ -220,6 +260,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, int *err) {
   // B(k, n) at k + ldb n, or of 8 n, B(n, k) at n + ldb k).
   constexpr int kPa = TM * TK / kThreads, kPb = TN * TK / kThreads;
   float2 ra[kPa], rb[kPb];
+  float2 rb1[KIND == 1 ? kPb : 1];  // KIND 1: twiddles of the chunk's second half of bands
   // 3xBF16: a thread takes two consecutive k of one row (items i, i + 1 with
   // i even), so that each hi or lo store is one 4-byte word of two halves and
   // a warp's 32 words (8 rows x 4 k pairs) again fall in 32 distinct banks
@@ -235,25 +276,67 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, int *err) {
     kc = ((rest / (TN / 8)) << 2) | (e & 3);
     if (PREC) kc = (kc << 1) | (i & 1);
   };
+  // x - ycoef y at pixel gm, band c (0 outside the cube)
+  auto xval = [&](int gm, int c) -> float {
+    if (gm >= gM || c >= gK) return 0.0f;
+    const size_t v = (size_t)gm + f.P * c;
+    return yb ? xb[v] - f.ycoef * yb[v] : xb[v];
+  };
+  // exp(-2 pi i k c / n3) (0 outside the half spectrum or the bands)
+  auto twid = [&](int k, int c) -> float2 {
+    if (k >= f.h || c >= f.n3) return make_float2(0.f, 0.f);
+    return f.tw3[(unsigned)(k * c) % (unsigned)f.n3];
+  };
   auto load_chunk = [&](int k0) {
+    if constexpr (KIND == 1) {
 #pragma unroll
-    for (int i = 0; i < kPa; ++i) {
-      int r, kc;
-      a_pos(i, r, kc);
-      const int gm = m0 + r, gk = k0 + kc;
-      ra[i] = (gm < g.M && gk < g.K) ? A[gm + (size_t)g.lda * gk] : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int i = 0; i < kPb; ++i) {
-      int n, kc;
-      b_pos(i, n, kc);
-      const int gn = n0 + n, gk = k0 + kc;
-      float2 v = make_float2(0.f, 0.f);
-      if (gn < g.N && gk < g.K) {
-        v = OPB == 0 ? B[gk + (size_t)g.ldb * gn] : B[gn + (size_t)g.ldb * gk];
-        if (OPB == 1) v.y = -v.y;
+      for (int i = 0; i < kPa; ++i) {
+        int r, kc;
+        a_pos(i, r, kc);
+        ra[i] = make_float2(xval(m0 + r, k0 + kc), xval(m0 + r, k0 + TK + kc));
       }
-      rb[i] = v;
+#pragma unroll
+      for (int i = 0; i < kPb; ++i) {
+        int n, kc;
+        b_pos(i, n, kc);
+        rb[i] = twid(n0 + n, k0 + kc);
+        rb1[KIND == 1 ? i : 0] = twid(n0 + n, k0 + TK + kc);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < kPa; ++i) {
+        int r, kc;
+        a_pos(i, r, kc);
+        const int gm = m0 + r, gk = k0 + kc;
+        if (KIND == 2) {
+          float2 v = make_float2(0.f, 0.f);
+          if (gm < gM && gk < gK) {
+            v = specb[wpos(gm) + f.P * gk];
+            if (f.trans) v.y = -v.y;
+          }
+          ra[i] = v;
+        } else {
+          ra[i] = (gm < g.M && gk < g.K) ? A[gm + (size_t)g.lda * gk] : make_float2(0.f, 0.f);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < kPb; ++i) {
+        int n, kc;
+        b_pos(i, n, kc);
+        const int gn = n0 + n, gk = k0 + kc;
+        float2 v = make_float2(0.f, 0.f);
+        if (KIND == 2) {
+          if (gn < gN && gk < gK) {
+            const float2 t = f.tw3[(unsigned)(gk * gn) % (unsigned)f.n3];
+            const float wk = (gk == 0 || 2 * gk == f.n3) ? 1.0f : 2.0f;
+            v = make_float2(wk * t.x, -wk * t.y);  // w_k exp(+2 pi i k c / n3)
+          }
+        } else if (gn < g.N && gk < g.K) {
+          v = OPB == 0 ? B[gk + (size_t)g.ldb * gn] : B[gn + (size_t)g.ldb * gk];
+          if (OPB == 1) v.y = -v.y;
+        }
+        rb[i] = v;
+      }
     }
   };
   // split the registers' chunk into the hi / lo tiles of stage `st`
@@ -274,8 +357,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, int *err) {
         int n, kc;
         b_pos(i, n, kc);
         const float2 v = rb[i];
+        if (KIND == 1) {  // real and imaginary twiddle parts of the chunk's bands
+          const float2 w = rb1[KIND == 1 ? i : 0];
+          put_split<PREC>(bReHi, bReLo, koff<PREC>(n, kc), v.x);
+          put_split<PREC>(bReHi, bReLo, koff<PREC>(n, kc + TK), w.x);
+          put_split<PREC>(bImHi, bImLo, koff<PREC>(n, kc), v.y);
+          put_split<PREC>(bImHi, bImLo, koff<PREC>(n, kc + TK), w.y);
+          continue;
+        }
         put_split<PREC>(bReHi, bReLo, koff<PREC>(n, kc), v.x);  // [Re B | -Im B]
         put_split<PREC>(bReHi, bReLo, koff<PREC>(n, kc + TK), -v.y);
+        if (KIND == 2) continue;  // Re C only
         put_split<PREC>(bImHi, bImLo, koff<PREC>(n, kc), v.y);  // [Im B | Re B]
         put_split<PREC>(bImHi, bImLo, koff<PREC>(n, kc + TK), v.x);
       }
@@ -292,8 +384,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, int *err) {
         int n, kc;
         b_pos(i, n, kc);
         const float2 v0 = rb[i], v1 = rb[i + 1];
+        if (KIND == 1) {
+          const float2 w0 = rb1[KIND == 1 ? i : 0], w1 = rb1[KIND == 1 ? i + 1 : 0];
+          put_split2(bReHi, bReLo, koff<PREC>(n, kc), v0.x, v1.x);
+          put_split2(bReHi, bReLo, koff<PREC>(n, kc + TK), w0.x, w1.x);
+          put_split2(bImHi, bImLo, koff<PREC>(n, kc), v0.y, v1.y);
+          put_split2(bImHi, bImLo, koff<PREC>(n, kc + TK), w0.y, w1.y);
+          continue;
+        }
         put_split2(bReHi, bReLo, koff<PREC>(n, kc), v0.x, v1.x);  // [Re B | -Im B]
         put_split2(bReHi, bReLo, koff<PREC>(n, kc + TK), -v0.y, -v1.y);
+        if (KIND == 2) continue;  // Re C only
         put_split2(bImHi, bImLo, koff<PREC>(n, kc), v0.y, v1.y);  // [Im B | Re B]
         put_split2(bImHi, bImLo, koff<PREC>(n, kc + TK), v0.x, v1.x);
       }
@@ -315,6 +416,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, int *err) {
       mma<PREC>(dt, sdesc<PREC>(a_hi + ko), sdesc<PREC>(br_hi + ko), idesc, acc0);
       mma<PREC>(dt, sdesc<PREC>(a_hi + ko), sdesc<PREC>(br_lo + ko), idesc, 1u);
       mma<PREC>(dt, sdesc<PREC>(a_lo + ko), sdesc<PREC>(br_hi + ko), idesc, 1u);
+      if (KIND == 2) continue;  // the real part is the whole result
       mma<PREC>(dt + TN, sdesc<PREC>(a_hi + ko), sdesc<PREC>(bi_hi + ko), idesc, acc0);
       mma<PREC>(dt + TN, sdesc<PREC>(a_hi + ko), sdesc<PREC>(bi_lo + ko), idesc, 1u);
       mma<PREC>(dt + TN, sdesc<PREC>(a_lo + ko), sdesc<PREC>(bi_hi + ko), idesc, 1u);
@@ -339,17 +441,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, int *err) {
             "=r"(re[6]), "=r"(re[7]), "=r"(re[8]), "=r"(re[9]), "=r"(re[10]), "=r"(re[11]),
             "=r"(re[12]), "=r"(re[13]), "=r"(re[14]), "=r"(re[15])
           : "r"(tl + tile + c0));
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]),
-            "=r"(im[6]), "=r"(im[7]), "=r"(im[8]), "=r"(im[9]), "=r"(im[10]), "=r"(im[11]),
-            "=r"(im[12]), "=r"(im[13]), "=r"(im[14]), "=r"(im[15])
-          : "r"(tl + tile + TN + c0));
+      if (KIND != 2)
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]),
+              "=r"(im[6]), "=r"(im[7]), "=r"(im[8]), "=r"(im[9]), "=r"(im[10]), "=r"(im[11]),
+              "=r"(im[12]), "=r"(im[13]), "=r"(im[14]), "=r"(im[15])
+            : "r"(tl + tile + TN + c0));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
         accRe[c0 + c] += __uint_as_float(re[c]);
-        accIm[c0 + c] += __uint_as_float(im[c]);
+        if (KIND != 2) accIm[c0 + c] += __uint_as_float(im[c]);
       }
     }
     // the tile is rewritten only after every thread's reads
@@ -386,7 +489,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, int *err) {
   for (int ch = 0; ch < nchunks && ok; ++ch) {
     const int st = ch & 1;
     store_chunk(st);  // stage st was last read by chunk ch - 2, already waited for
-    if (ch + 1 < nchunks) load_chunk((ch + 1) * TK);
+    if (ch + 1 < nchunks) load_chunk((ch + 1) * (KIND == 1 ? KR : TK));
     stage_barrier();
     if (ch > 0) {
       wait_mmas(st ^ 1);
@@ -415,7 +518,27 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, int *err) {
     // tile, columns colh .. colh + 31
     const int gm = m0 + row;
     const int lb = g.lam3_period > 0 ? b % g.lam3_period : b;
-    if (gm < g.M) {
+    if (KIND == 1 && gm < gM) {
+      float2 *ob = f.spec_out + (size_t)b * f.h * f.P + wpos(gm);
+#pragma unroll
+      for (int c = 0; c < TN / 2; ++c) {
+        const int n = n0 + colh + c;
+        if (n >= gN) break;
+        ob[f.P * n] = make_float2(accRe[c], f.trans ? -accIm[c] : accIm[c]);
+      }
+    } else if (KIND == 2 && gm < gM) {
+      const float inv = 1.0f / (float)f.n3;
+      const size_t base = (size_t)b * f.N + gm;
+#pragma unroll
+      for (int c = 0; c < TN / 2; ++c) {
+        const int n = n0 + colh + c;
+        if (n >= gN) break;
+        const size_t v = base + f.P * n;
+        const float r = accRe[c] * inv;
+        f.out[v] = r;
+        if (f.mode == 1 && f.gamma4) f.G4[v] = f.G4[v] + f.mu * (r - f.F[v]);
+      }
+    } else if (KIND == 0 && gm < g.M) {
 #pragma unroll
       for (int c = 0; c < TN / 2; ++c) {
         const int n = n0 + colh + c;
@@ -541,7 +664,20 @@ cudaError_t launch_one(const CGemm &g, int *err, cudaStream_t st) {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((g.M + TM - 1) / TM, (g.N + TN - 1) / TN, g.batch);
-  k_cgemm_tc<OPB, EPI, PREC><<<grid, kThreads, smem, st>>>(g, err);
+  k_cgemm_tc<OPB, EPI, PREC><<<grid, kThreads, smem, st>>>(g, Dft3{}, err);
+  return cudaGetLastError();
+}
+
+template <int KIND, int PREC>
+cudaError_t launch_dft(const Dft3 &f, int nb, int *err, cudaStream_t st) {
+  const size_t smem = smem_bytes<PREC>();
+  cudaError_t e = cudaFuncSetAttribute(k_cgemm_tc<0, 0, PREC, KIND>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const size_t mt = (f.P + TM - 1) / TM;
+  const size_t nt = ((KIND == 1 ? f.h : f.n3) + TN - 1) / TN;
+  dim3 grid((unsigned)(mt * nt), 1, nb);
+  k_cgemm_tc<0, 0, PREC, KIND><<<grid, kThreads, smem, st>>>(CGemm{}, f, err);
   return cudaGetLastError();
 }
 
@@ -580,6 +716,14 @@ cudaError_t launch_mma_peak(int prec, int nsm, long long n_mma, int *err, cudaSt
     k_mma_peak<1><<<nsm, 128, kProbeSmem, st>>>(n_mma, err);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_dft3_tc(int kind, const Dft3 &f, int nb, int *err, cudaStream_t st, int prec) {
+  if (f.P == 0 || nb <= 0) return cudaSuccess;
+  if (f.P > (size_t)TM * 0x7fffffff / 4) return cudaErrorInvalidValue;
+  if (kind == 1) return prec ? launch_dft<1, 1>(f, nb, err, st) : launch_dft<1, 0>(f, nb, err, st);
+  if (kind == 2) return prec ? launch_dft<2, 1>(f, nb, err, st) : launch_dft<2, 0>(f, nb, err, st);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_cgemm_tc(const CGemm &g, int *err, cudaStream_t st, int prec) {

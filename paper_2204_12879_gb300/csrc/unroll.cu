@@ -479,7 +479,7 @@ int unroll_forward(lrstv_unroll *u, cudaStream_t st) {
       // start from the previous iteration's right singular vectors, made
       // unitary again by one Newton-Schulz step, exactly as a plan does
       const long long nc2 = (long long)d.nc * d.nc, P = (long long)d.P;
-      UCK(launch_r2c3(d, 3 * B, s.F, s.G4, (float)(1.0 / mu), u->specA, 1, u->tb.tw3, st));
+      UCK(launch_r2c3(d, 3 * B, s.F, s.G4, (float)(1.0 / mu), u->specA, 1, u->tb.tw3, st, gs));
       UCK(cudaMemcpyAsync(Vk, Vk - ns * d.nc * d.nc, sizeof(float2) * ns * d.nc * d.nc,
                           cudaMemcpyDeviceToDevice, st));
       CGemm g{};
@@ -499,7 +499,7 @@ int unroll_forward(lrstv_unroll *u, cudaStream_t st) {
       g.M = d.nr; g.N = d.nc; g.K = d.nc;
       UCK(gemm(g, gs, st));
     } else {
-      UCK(launch_r2c3(d, 3 * B, s.F, s.G4, (float)(1.0 / mu), Wk, 1, u->tb.tw3, st));
+      UCK(launch_r2c3(d, 3 * B, s.F, s.G4, (float)(1.0 / mu), Wk, 1, u->tb.tw3, st, gs));
     }
     const float t = (float)(alpha / mu);
     UCK(launch_group_ms2(d, (int)ns, Wk, d.h, u->ms2, st));
@@ -517,7 +517,7 @@ int unroll_forward(lrstv_unroll *u, cudaStream_t st) {
     g.C = u->specB; g.sC = (long long)d.P; g.ldc = d.nr;
     g.M = d.nr; g.N = d.nc; g.K = d.nc; g.batch = (int)ns;
     UCK(gemm(g, gs, st));
-    UCK(launch_c2r3(d, 3 * B, u->specB, 1, u->tb.tw3, s.E, 1, s.G4, s.F, muf, 1, st));
+    UCK(launch_c2r3(d, 3 * B, u->specB, 1, u->tb.tw3, s.E, 1, s.G4, s.F, muf, 1, st, gs));
   }
   return LRSTV_OK;
 }
@@ -554,7 +554,7 @@ int unroll_backward(lrstv_unroll *u, double *dtheta, cudaStream_t st) {
     float2 *Wk = u->W + (size_t)k * ns * d.P;
     float2 *Vk = u->V + (size_t)k * ns * d.nc * d.nc;
     const double *sk = u->sig + (size_t)k * ns * d.nc;
-    UCK(launch_r2c3(d, 3 * B, a.E, nullptr, 0.0f, u->specA, 1, u->tb.tw3, st));
+    UCK(launch_r2c3(d, 3 * B, a.E, nullptr, 0.0f, u->specA, 1, u->tb.tw3, st, gs));
     CGemm g{};
     g.batch = (int)ns;
     // P = G V
@@ -587,7 +587,7 @@ int unroll_backward(lrstv_unroll *u, double *dtheta, cudaStream_t st) {
     g.B = Vk; g.sB = (long long)d.nc * d.nc; g.ldb = d.nc; g.opB = 1;
     g.C = u->specA; g.sC = (long long)d.P; g.ldc = d.nr; g.epi = 0;
     UCK(gemm(g, kSimt, st));
-    UCK(launch_c2r3(d, 3 * B, u->specA, 1, u->tb.tw3, u->X3, 0, nullptr, nullptr, 0.0f, 0, st));
+    UCK(launch_c2r3(d, 3 * B, u->specA, 1, u->tb.tw3, u->X3, 0, nullptr, nullptr, 0.0f, 0, st, gs));
     Lin lf{};  // the F threshold tau / mu and B = F - Gamma4 / mu
     lf.m[kMu][0] = 1.0 / m2; lf.m[kMu][1] = tau / m2; lf.m[kMu][2] = -0.5 / m2;
     lf.m[kTau][1] = -1.0 / mu;

@@ -442,3 +442,48 @@ def test_tensor_core_zsolve_shapes(L, orc, shape):
         ref = orc.zsolve(T, mu)
         assert maxabs(host(pl.get("Z"), shape), ref) <= 1e-5 * np.abs(ref).max()
         assert pl.stats().gemm_errors == 0
+
+
+@pytest.mark.parametrize("shape", LONG_SPECTRA + [(37, 29, 11), (29, 37, 10)])
+@pytest.mark.parametrize("bf16", [False, True])
+def test_tensor_core_mode3_dfts(L, orc, shape, bf16):
+    """The mode-3 (spectral) DFTs on the tensor cores, through a plan's Z-step
+    and E-step, against the oracle's Z-solve and t-SVT: long spectra (K and N
+    chunks with ragged tails: h = 66, 96, 129, 2049) and both slice
+    orientations (n1 < n2 writes and reads the transposed, conjugated
+    slices).  Bounds: 3xTF32 as the SIMT kernels' (1e-5 of the Z-solve's
+    largest value, 2e-5 of max|F| for the t-SVT); 3xBF16 2e-4, the
+    mixed-precision step bound (about 1e-5 relative per product term)."""
+    n1, n2, n3 = shape
+    rng = np.random.default_rng(31)
+    flags = L.FLAG_BF16X3 if bf16 else 0
+    tz, te = (2e-4, 2e-4) if bf16 else (1e-5, 2e-5)
+    with _plan(L, shape, flags=flags) as pl:
+        pl.init(dev(np.zeros(shape)))
+        T = f32(rng.standard_normal(shape))
+        pl.set("TZ", dev(T))
+        pl.step_z()
+        mu, _ = pl.mu
+        ref = orc.zsolve(T, mu)
+        err = maxabs(host(pl.get("Z"), shape), ref)
+        print(shape, bf16, "Z-step max-abs / max|ref|", err / np.abs(ref).max())
+        assert err <= tz * np.abs(ref).max()
+        # E-step with Gamma4 = 0: E_n = t-SVT(F_n, alpha / mu), Gamma4_n = mu (E_n - F_n)
+        F = [f32(rng.standard_normal(shape)) for _ in range(3)]
+        t = _slice_sigma_percentiles(F[0], (60,))[0]
+        mu_e = 0.2 / t  # the plan's alpha is 0.2
+        pl.set_mu(mu_e, 5)
+        pl.set("F", dev3(F))
+        pl.set("G4", dev3([np.zeros(shape)] * 3))
+        pl.step_e()
+        s = pl.stats()
+        assert s.gemm_errors == 0 and s.jacobi_unconverged == 0
+        E = host3(pl.get("E"), shape)
+        G4 = host3(pl.get("G4"), shape)
+        tf = float(np.float32(float(np.float32(0.2)) / mu_e))  # the plan's alpha / mu, rounded
+        for n in range(3):
+            want, _ = orc.tsvt(F[n], tf)
+            err = maxabs(E[n], want)
+            print(shape, bf16, n, "E-step max-abs / max|F|", err / np.abs(F[n]).max())
+            assert err <= te * np.abs(F[n]).max(), n
+            assert maxabs(G4[n], mu_e * (E[n] - F[n])) <= 1e-5 * mu_e * np.abs(F[n]).max(), n
