@@ -656,7 +656,7 @@ def run_batch(args):
     }
 
 
-UNROLL = {"batch": 8, "iters": 10, "pool": 64, "seed": 5,
+UNROLL = {"batch": 8, "iters": 10, "pool": 2000, "seed": 5,
           "desc": "unrolled plain LRSTV, 10 iterations with 40 learnable scalars (tau, alpha, lambda, mu per iteration), batch 8 of 64x64x31 synthetic pairs (4 endmembers, 12 Voronoi cells, Gaussian 0.1 + 10% impulse), MSE to the clean cube, Adam on the log-scalars, warm-started Jacobi"}
 
 

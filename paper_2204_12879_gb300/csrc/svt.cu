@@ -199,6 +199,7 @@ constexpr int kPW = 32;  // panel width (columns)
 
 struct Rot {
   float c, s, er, ei;
+  float d;  // |a'|^2 = |a|^2 - d and |b'|^2 = |b|^2 + d (d = t |g|, the 2x2 Schur rotation's shift)
 };
 
 // Rotation of the 2x2 Hermitian [[al, g], [conj g, be]], or false when the
@@ -229,6 +230,7 @@ __device__ __forceinline__ bool make_rot(float al, float be, float gr, float gi,
   r.s = r.c * tt;
   r.er = gr * inv_ag;
   r.ei = -gi * inv_ag;
+  r.d = tt * (g2 * inv_ag);
   return true;
 }
 
@@ -309,6 +311,45 @@ __device__ __forceinline__ void pk_dots(const float4 (&a)[K], const float4 (&b)[
   gi = ((i1[0].x + i1[1].x) + (i1[0].y + i1[1].y)) - ((i2[0].x + i2[1].x) + (i2[0].y + i2[1].y));
 }
 
+// lane partial sums of re(a^H b), im(a^H b) only (pk_dots without the norms,
+// in the same order, so the inner product is bit-identical to pk_dots')
+template <int K>
+__device__ __forceinline__ void pk_cross(const float4 (&a)[K], const float4 (&b)[K], float &gr,
+                                         float &gi) {
+  const float2 z = make_float2(0.f, 0.f);
+  float2 rr[2] = {z, z}, i1[2] = {z, z}, i2[2] = {z, z};
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int c = k & 1;
+    const float2 Ra = lo2(a[k]), Ia = hi2(a[k]), Rb = lo2(b[k]), Ib = hi2(b[k]);
+    rr[c] = fma2(Ia, Ib, fma2(Ra, Rb, rr[c]));
+    i1[c] = fma2(Ra, Ib, i1[c]);
+    i2[c] = fma2(Ia, Rb, i2[c]);
+  }
+  gr = (rr[0].x + rr[1].x) + (rr[0].y + rr[1].y);
+  gi = ((i1[0].x + i1[1].x) + (i1[0].y + i1[1].y)) - ((i2[0].x + i2[1].x) + (i2[0].y + i2[1].y));
+}
+
+// lane partial sum of |a|^2 over K row pairs
+template <int K>
+__device__ __forceinline__ float pk_norm(const float4 (&a)[K]) {
+  const float2 z = make_float2(0.f, 0.f);
+  float2 aa[2] = {z, z};
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int c = k & 1;
+    const float2 Ra = lo2(a[k]), Ia = hi2(a[k]);
+    aa[c] = fma2(Ia, Ia, fma2(Ra, Ra, aa[c]));
+  }
+  return (aa[0].x + aa[1].x) + (aa[0].y + aa[1].y);
+}
+
+// A tracked squared norm that fell below this fraction of its value before
+// the rotation is marked for recomputation from the column itself (when the
+// column is next read): the update |a|^2 - d cancels there, and its absolute
+// rounding (about eps |a|^2) would become a large relative error.
+constexpr float kNormDrop = 0.0625f;
+
 // rotates two shared-memory columns (row-pair layout), lane stride `step`
 template <int K, int STEP>
 __device__ __forceinline__ void pk_rot_smem(float4 *ca, float4 *cb, const PRot &q, int l) {
@@ -349,18 +390,26 @@ __device__ __forceinline__ void pk_rot_stream(float4 (&a)[K], float4 *col, const
 
 // shared panel (ld2 row pairs per column, split layout, zero padded) <-
 // wcols interleaved columns of n rows; warp w copies columns w, w + 16, ...
+// With nrm (kPW floats), also each staged column's squared norm (0 for the
+// padding columns).
 __device__ __forceinline__ void pk_stage_in(float4 *dst, int ld2, const float2 *src, int n,
-                                            int wcols) {
+                                            int wcols, float *nrm = nullptr) {
   const int lane = threadIdx.x & 31;
   for (int c = threadIdx.x >> 5; c < kPW; c += kHW) {
     const float2 *s = src + (size_t)n * c;
     float4 *d = dst + ld2 * c;
     const bool real = c < wcols;
+    float part = 0.0f;
     for (int m = lane; m < ld2; m += 32) {
       const int r0 = 2 * m, r1 = 2 * m + 1;
       const float2 x0 = (real && r0 < n) ? s[r0] : make_float2(0.f, 0.f);
       const float2 x1 = (real && r1 < n) ? s[r1] : make_float2(0.f, 0.f);
       d[m] = make_float4(x0.x, x1.x, x0.y, x1.y);
+      if (nrm) part = fmaf(x0.x, x0.x, fmaf(x0.y, x0.y, fmaf(x1.x, x1.x, fmaf(x1.y, x1.y, part))));
+    }
+    if (nrm) {
+      part = warp_sum(part);
+      if (lane == 0) nrm[c] = part;
     }
   }
 }
@@ -405,6 +454,10 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
   const int unit = tid >> 4, ul = tid & 15;
   __shared__ float s_red[32];
   __shared__ int s_rot;
+  // squared column norms of panel a and of the streamed panel b: exact when
+  // a panel is staged, then carried through each rotation by the 2x2 update
+  // (|a|^2 - d, |b|^2 + d), so that a pair's test needs only its inner product
+  __shared__ float s_na[kPW], s_nb[kPW];
 
   if (!warm)  // warm: V holds the basis W was multiplied by
     for (int e = tid; e < nc * nc; e += blockDim.x)
@@ -454,7 +507,7 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
     for (int a = 0; a < npan; ++a) {
       const int ca = a * kPW, wa = min(kPW, nc - ca);
       __syncthreads();
-      pk_stage_in(sW, LD2, W + (size_t)nr * ca, nr, wa);
+      pk_stage_in(sW, LD2, W + (size_t)nr * ca, nr, wa, s_na);
       pk_stage_in(sVa, LD2, V + (size_t)nc * ca, nc, wa);
       __syncthreads();
       // pairs inside panel a: 16 disjoint pairs per round, one per warp
@@ -468,12 +521,15 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
             xa[k] = sW[LD2 * p + lane + 32 * k];
             xb[k] = sW[LD2 * q + lane + 32 * k];
           }
-          float al, be, gr, gi;
-          pk_dots<KPF>(xa, xb, al, be, gr, gi);
-          al = warp_sum(al);
-          be = warp_sum(be);
+          float gr, gi;
+          pk_cross<KPF>(xa, xb, gr, gi);
           gr = warp_sum(gr);
           gi = warp_sum(gi);
+          // a norm marked negative after a rotation that cancelled it is
+          // recomputed from the column (warp-uniform: p, q are the warp's)
+          float al = s_na[p], be = s_na[q];
+          if (al < 0.0f) al = warp_sum(pk_norm<KPF>(xa));
+          if (be < 0.0f) be = warp_sum(pk_norm<KPF>(xb));
           if (lane == 0) n_pairs += 1;
           Rot rt;
           if (make_rot(al, be, gr, gi, tol, negl, rt)) {
@@ -485,7 +541,12 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
               sW[LD2 * q + lane + 32 * k] = xb[k];
             }
             pk_rot_smem<KPF, 32>(sVa + LD2 * p, sVa + LD2 * q, pq, lane);
-            if (lane == 0) n_rot += 1;
+            const float na = al - rt.d, nb = be + rt.d;
+            if (lane == 0) {
+              s_na[p] = na < kNormDrop * al ? -1.0f : na;
+              s_na[q] = nb < kNormDrop * be ? -1.0f : nb;
+              n_rot += 1;
+            }
             rotated = 1;
           }
         }
@@ -501,8 +562,11 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
       for (int b = a + 1; b < npan; ++b) {
         const int cb = b * kPW, wb = min(kPW, nc - cb);
         __syncthreads();
-        pk_stage_in(sW, LD2, W + (size_t)nr * cb, nr, wb);
+        pk_stage_in(sW, LD2, W + (size_t)nr * cb, nr, wb, s_nb);
         pk_stage_in(sVb, LD2, V + (size_t)nc * cb, nc, wb);
+        // the register column's squared norm, exact at the start of each
+        // streamed panel (the whole warp shuffles: both halves compute theirs)
+        float al_reg = half_sum(pk_norm<KP>(aW));
         __syncthreads();
         // 16 double rounds: warp w owns streamed columns 2c, 2c+1 (c = (w + R) mod 16); its
         // half-warps rotate them in swapped order, so only the warp synchronises between the
@@ -514,14 +578,23 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
           const bool real = mine && j < wb;
 #pragma unroll
           for (int k = 0; k < KP; ++k) bW[k] = sW[LD2 * j + ul + 16 * k];
-          float al, be, gr, gi;
-          pk_dots<KP>(aW, bW, al, be, gr, gi);
-          al = half_sum(al);
-          be = half_sum(be);
+          float gr, gi;
+          pk_cross<KP>(aW, bW, gr, gi);
           gr = half_sum(gr);
           gi = half_sum(gi);
+          // norms marked negative after a rotation that cancelled them are
+          // recomputed here, where both columns are in registers; the
+          // decision is made per warp so that both halves take part in the
+          // shuffles
+          float be = s_nb[j];
+          if (__any_sync(0xffffffffu, be < 0.0f || al_reg < 0.0f)) {
+            const float xa = half_sum(pk_norm<KP>(aW));
+            const float xb = half_sum(pk_norm<KP>(bW));
+            if (al_reg < 0.0f) al_reg = xa;
+            if (be < 0.0f) be = xb;
+          }
           Rot rt;
-          const bool go = real && make_rot(al, be, gr, gi, tol, negl, rt);
+          const bool go = real && make_rot(al_reg, be, gr, gi, tol, negl, rt);
           if (ul == 0 && real) n_pairs += 1;
           if (__any_sync(0xffffffffu, go)) {
             // the other half-warp may rotate: this half applies the identity,
@@ -531,6 +604,7 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
               rt.s = 0.0f;
               rt.er = 1.0f;
               rt.ei = 0.0f;
+              rt.d = 0.0f;
             }
             const PRot pq = packed(rt);
 #pragma unroll
@@ -540,7 +614,12 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
             }
             pk_rot_stream<KP>(aV, sVb + LD2 * j, pq, ul);
             if (go) {
-              if (ul == 0) n_rot += 1;
+              const float na = al_reg - rt.d, nb = be + rt.d;
+              al_reg = na < kNormDrop * al_reg ? -1.0f : na;
+              if (ul == 0) {
+                s_nb[j] = nb < kNormDrop * be ? -1.0f : nb;
+                n_rot += 1;
+              }
               rotated = 1;
             }
           }
