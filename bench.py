@@ -390,6 +390,8 @@ def run_ours(args, wl_name):
     precision = gemm_precision(args, wl_name)
     if precision == "bf16x3":
         flags |= lrstv.FLAG_BF16X3
+    if args.dft == "simt":
+        flags |= lrstv.FLAG_SIMT_DFT
     params = lrstv.Params.make(n1, n2, max_iter=iters, flags=flags)
     plan = lrstv.Plan(n1, n2, n3, params)
     ranks = tucker_ranks(args, (n1, n2, n3))
@@ -526,6 +528,7 @@ def run_ours(args, wl_name):
                    "parallelism": "replicas" if world > 1 else "single",
                    "jacobi_start": args.jacobi_start,
                    "gemm_precision": precision,
+                   "mode3_dft": "tensor cores" if args.dft == "tc" else "SIMT direct sums",
                    "l_update": ("Tucker projection, one HOOI sweep per iteration, ranks %s" % (ranks,)
                                 if ranks else "plain (full Tucker ranks)"),
                    "l2": "working set (18 state cubes + spectra, ~330 MB) exceeds the 129 MB L2",
@@ -952,6 +955,9 @@ def build_parser():
     ap.add_argument("--precision", choices=["auto", "tf32x3", "bf16x3"], default="auto",
                     help="tensor-core GEMM split: 3xTF32 (FP32-accurate) or 3xBF16 "
                          "(LRSTV_FLAG_BF16X3); auto = 3xBF16 for c3 only")
+    ap.add_argument("--dft", choices=["tc", "simt"], default="tc",
+                    help="mode-3 DFT engine: the tensor-core pipeline or the SIMT direct sums "
+                         "(LRSTV_FLAG_SIMT_DFT)")
     ap.add_argument("--micro", choices=["tsvt"], default=None,
                     help="time one standalone operator instead of the iteration")
     ap.add_argument("--shape", default="200,200,16", help="n1,n2,n3 for --micro")

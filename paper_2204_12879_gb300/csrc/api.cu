@@ -58,6 +58,7 @@ int check_params(const lrstv_params *p) {
   if (!(p->mu0 > 0.0f) || !(p->mu_max >= p->mu0) || p->max_iter < 0) return LRSTV_ERR_ARG;
   if (p->flags & ~(unsigned)(LRSTV_FLAG_F_THRESH_EXACT | LRSTV_FLAG_NO_GAMMA4 | LRSTV_FLAG_GRAPH |
                              LRSTV_FLAG_STRICT | LRSTV_FLAG_SIMT_GEMM | LRSTV_FLAG_WARM_START |
+                             LRSTV_FLAG_SIMT_DFT |
                              LRSTV_FLAG_ISO_TV | LRSTV_FLAG_BF16X3))
     return LRSTV_ERR_ARG;
   // the split-BF16 products exist on the tensor-core path only
@@ -275,7 +276,8 @@ namespace {
 
 GemmSel plan_gemm(const lrstv_plan *pl) {
   if (pl->prm.flags & LRSTV_FLAG_SIMT_GEMM) return kSimt;
-  return GemmSel{true, pl->gemm_err, (pl->prm.flags & LRSTV_FLAG_BF16X3) ? 1 : 0};
+  return GemmSel{true, pl->gemm_err, (pl->prm.flags & LRSTV_FLAG_BF16X3) ? 1 : 0,
+                 (pl->prm.flags & LRSTV_FLAG_SIMT_DFT) == 0};
 }
 
 // Warm start of a plan's E-step: one Newton-Schulz step on V (the previous
@@ -994,18 +996,21 @@ int lrstv_plan_run(lrstv_plan *pl, const float *Y, float *X, float *S, lrstv_sta
 int lrstv_plan_autotune(lrstv_plan *pl, const float *Y, int iters, unsigned allowed,
                         unsigned *chosen, float *ms_out, void *stream) {
   if (!pl || !Y || iters < 0) return LRSTV_ERR_ARG;
-  if (allowed & ~(unsigned)(LRSTV_FLAG_SIMT_GEMM | LRSTV_FLAG_WARM_START)) return LRSTV_ERR_ARG;
+  if (allowed & ~(unsigned)(LRSTV_FLAG_SIMT_GEMM | LRSTV_FLAG_WARM_START | LRSTV_FLAG_SIMT_DFT))
+    return LRSTV_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   const int n = iters > 0 ? iters : pl->prm.max_iter;
   const unsigned base = pl->prm.flags & ~allowed;
   // candidates: every subset of `allowed` that check_params accepts
-  unsigned cands[4];
+  unsigned cands[8];
   int nc = 0;
   for (unsigned sub = 0; sub <= allowed; ++sub) {
     if ((sub & ~allowed) != 0) continue;
+    // SIMT_GEMM already puts the DFTs on the SIMT kernels
+    if ((sub & LRSTV_FLAG_SIMT_GEMM) && (sub & LRSTV_FLAG_SIMT_DFT)) continue;
     lrstv_params trial = pl->prm;
     trial.flags = base | sub;
-    if (check_params(&trial) == LRSTV_OK && nc < 4) cands[nc++] = base | sub;
+    if (check_params(&trial) == LRSTV_OK && nc < 8) cands[nc++] = base | sub;
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {

@@ -343,7 +343,7 @@ cudaError_t launch_tables(const Dims &d, const float w[3], float2 *tw3, float2 *
 cudaError_t launch_r2c3(const Dims &d, int nb, const float *x, const float *y, float ycoef,
                         float2 *out, int work_orient, const float2 *tw3, cudaStream_t st,
                         GemmSel gs) {
-  if (gs.tc) {
+  if (gs.tc && gs.dft) {
     Dft3 f{};
     f.x = x;
     f.y = y;
@@ -373,7 +373,7 @@ cudaError_t launch_r2c3(const Dims &d, int nb, const float *x, const float *y, f
 cudaError_t launch_c2r3(const Dims &d, int nb, const float2 *spec, int work_orient,
                         const float2 *tw3, float *out, int mode, float *G4, const float *F,
                         float mu, int gamma4, cudaStream_t st, GemmSel gs) {
-  if (gs.tc) {
+  if (gs.tc && gs.dft) {
     Dft3 f{};
     f.spec = spec;
     f.out = out;

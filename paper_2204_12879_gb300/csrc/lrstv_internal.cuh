@@ -55,19 +55,21 @@ struct GemmSel {
   bool tc;
   int *err;
   int prec;  // tensor-core split precision (launch_cgemm_tc)
+  bool dft;  // with tc: the mode-3 DFTs on the tensor cores too (else the SIMT kernels)
 };
 // Mode-3 real-to-half-complex DFT of `nb` cubes x_b - ycoef * y_b (y may be
 // null), written as slices b*h + k of `out` (P complex each), in the working
 // orientation (A^H when d.trans and `work_orient`).
 cudaError_t launch_r2c3(const Dims &d, int nb, const float *x, const float *y, float ycoef,
                         float2 *out, int work_orient, const float2 *tw3, cudaStream_t st,
-                        GemmSel gs = {false, nullptr, 0});
+                        GemmSel gs = {false, nullptr, 0, false});
 // Inverse mode-3 DFT (half-complex to real, 1/n3 included) of `nb` spectra.
 // mode 0: out_b = result.  mode 1 (E-step epilogue): E_b = result and
 // G4_b += mu (E_b - F_b) when `gamma4` (F, G4 given).
 cudaError_t launch_c2r3(const Dims &d, int nb, const float2 *spec, int work_orient,
                         const float2 *tw3, float *out, int mode, float *G4, const float *F,
-                        float mu, int gamma4, cudaStream_t st, GemmSel gs = {false, nullptr, 0});
+                        float mu, int gamma4, cudaStream_t st,
+                        GemmSel gs = {false, nullptr, 0, false});
 // Batched complex GEMM, column-major: C_b = A_b * op(B_b), op(B) = B or B^H.
 // epi 1: C(a, b) *= scale / (mu (1 + lam1[a] + lam2[b] + lam3[batch])).
 // opA 1 (SIMT kernel only): op(A) = A^H, A stored K x M.  epi 2 (SIMT kernel
@@ -225,7 +227,7 @@ struct Prof;  // per-kernel event profiler of a plan; null: not profiled
 
 // Which GEMM implementation a call uses: the tensor cores (with an error
 // slot for bounded-wait timeouts) or the FP32 SIMT kernel.
-constexpr GemmSel kSimt = {false, nullptr, 0};
+constexpr GemmSel kSimt = {false, nullptr, 0, false};
 cudaError_t gemm(const CGemm &g, GemmSel gs, cudaStream_t st);
 
 // Z-solve (eq. Z_solution) of nb cubes of shape d stored back to back:

@@ -170,7 +170,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
 // one M tile adjacent in launch order, so the M tile's inputs come from DRAM
 // once and from L2 for the other N tiles.
 template <int OPB, int EPI, int PREC, int KIND = 0>
-__global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, Dft3 f, int *err) {
+// The forward DFT kind holds both cubes' next chunk in registers (152 of them
+// with 3xTF32) and runs one CTA per SM without spills; the others fit two.
+__global__ void __launch_bounds__(kThreads, KIND == 1 ? 1 : 2) k_cgemm_tc(CGemm g, Dft3 f, int *err) {
   extern __shared__ __align__(1024) char smem[];
   using P = Prec<PREC>;
   // two shared-memory stages, so that a chunk is staged while the previous
@@ -259,8 +261,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, Dft3 f, int *
   // op(B)(k, n) over k, 8 rows n x 4 k per warp (loads are runs of 4 k,
   // B(k, n) at k + ldb n, or of 8 n, B(n, k) at n + ldb k).
   constexpr int kPa = TM * TK / kThreads, kPb = TN * TK / kThreads;
-  float2 ra[kPa], rb[kPb];
-  float2 rb1[KIND == 1 ? kPb : 1];  // KIND 1: twiddles of the chunk's second half of bands
+  float2 ra[kPa], rb[kPb] = {};
+  // KIND 1 with a second cube: its raw values, combined (x - ycoef y) only when
+  // the chunk is stored, so that the loads stay in flight meanwhile.  The DFT
+  // kinds' B operand (twiddles from a table of n3 entries that stays in L1) is
+  // read when the chunk is stored, not held in registers across the pipeline.
+  float2 ry[KIND == 1 ? kPa : 1] = {};
   // 3xBF16: a thread takes two consecutive k of one row (items i, i + 1 with
   // i even), so that each hi or lo store is one 4-byte word of two halves and
   // a warp's 32 words (8 rows x 4 k pairs) again fall in 32 distinct banks
@@ -276,11 +282,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, Dft3 f, int *
     kc = ((rest / (TN / 8)) << 2) | (e & 3);
     if (PREC) kc = (kc << 1) | (i & 1);
   };
-  // x - ycoef y at pixel gm, band c (0 outside the cube)
-  auto xval = [&](int gm, int c) -> float {
-    if (gm >= gM || c >= gK) return 0.0f;
-    const size_t v = (size_t)gm + f.P * c;
-    return yb ? xb[v] - f.ycoef * yb[v] : xb[v];
+  // the raw value of cube q at pixel gm, band c (0 outside the cube)
+  auto cval = [&](const float *q, int gm, int c) -> float {
+    return (gm < gM && c < gK) ? q[(size_t)gm + f.P * c] : 0.0f;
   };
   // exp(-2 pi i k c / n3) (0 outside the half spectrum or the bands)
   auto twid = [&](int k, int c) -> float2 {
@@ -293,14 +297,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, Dft3 f, int *
       for (int i = 0; i < kPa; ++i) {
         int r, kc;
         a_pos(i, r, kc);
-        ra[i] = make_float2(xval(m0 + r, k0 + kc), xval(m0 + r, k0 + TK + kc));
-      }
-#pragma unroll
-      for (int i = 0; i < kPb; ++i) {
-        int n, kc;
-        b_pos(i, n, kc);
-        rb[i] = twid(n0 + n, k0 + kc);
-        rb1[KIND == 1 ? i : 0] = twid(n0 + n, k0 + TK + kc);
+        ra[i] = make_float2(cval(xb, m0 + r, k0 + kc), cval(xb, m0 + r, k0 + TK + kc));
+        if (yb)
+          ry[KIND == 1 ? i : 0] =
+              make_float2(cval(yb, m0 + r, k0 + kc), cval(yb, m0 + r, k0 + TK + kc));
       }
     } else {
 #pragma unroll
@@ -308,57 +308,81 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, Dft3 f, int *
         int r, kc;
         a_pos(i, r, kc);
         const int gm = m0 + r, gk = k0 + kc;
-        if (KIND == 2) {
-          float2 v = make_float2(0.f, 0.f);
-          if (gm < gM && gk < gK) {
-            v = specb[wpos(gm) + f.P * gk];
-            if (f.trans) v.y = -v.y;
-          }
-          ra[i] = v;
+        if (KIND == 2) {  // raw; conjugated (transposed slices) when stored
+          ra[i] = (gm < gM && gk < gK) ? specb[wpos(gm) + f.P * gk] : make_float2(0.f, 0.f);
         } else {
           ra[i] = (gm < g.M && gk < g.K) ? A[gm + (size_t)g.lda * gk] : make_float2(0.f, 0.f);
         }
       }
+      if (KIND == 0) {
 #pragma unroll
-      for (int i = 0; i < kPb; ++i) {
-        int n, kc;
-        b_pos(i, n, kc);
-        const int gn = n0 + n, gk = k0 + kc;
-        float2 v = make_float2(0.f, 0.f);
-        if (KIND == 2) {
-          if (gn < gN && gk < gK) {
-            const float2 t = f.tw3[(unsigned)(gk * gn) % (unsigned)f.n3];
-            const float wk = (gk == 0 || 2 * gk == f.n3) ? 1.0f : 2.0f;
-            v = make_float2(wk * t.x, -wk * t.y);  // w_k exp(+2 pi i k c / n3)
+        for (int i = 0; i < kPb; ++i) {
+          int n, kc;
+          b_pos(i, n, kc);
+          const int gn = n0 + n, gk = k0 + kc;
+          float2 v = make_float2(0.f, 0.f);
+          if (gn < g.N && gk < g.K) {
+            v = OPB == 0 ? B[gk + (size_t)g.ldb * gn] : B[gn + (size_t)g.ldb * gk];
+            if (OPB == 1) v.y = -v.y;
           }
-        } else if (gn < g.N && gk < g.K) {
-          v = OPB == 0 ? B[gk + (size_t)g.ldb * gn] : B[gn + (size_t)g.ldb * gk];
-          if (OPB == 1) v.y = -v.y;
+          rb[i] = v;
         }
-        rb[i] = v;
+      }
+    }
+  };
+  // B item i of the chunk at k0: (v, w) = KIND 0 the loaded op(B) value (w
+  // unused); KIND 1 the twiddles of bands k0 + kc and k0 + TK + kc; KIND 2
+  // w_k exp(+2 pi i k c / n3) of frequency k0 + kc (w unused)
+  auto bval = [&](int i, int k0, float2 &v, float2 &w) {
+    int n, kc;
+    b_pos(i, n, kc);
+    if (KIND == 0) {
+      v = rb[i];
+    } else if (KIND == 1) {
+      v = twid(n0 + n, k0 + kc);
+      w = twid(n0 + n, k0 + TK + kc);
+    } else {
+      const int gn = n0 + n, gk = k0 + kc;
+      v = make_float2(0.f, 0.f);
+      if (gn < gN && gk < gK) {
+        const float2 t = f.tw3[(unsigned)(gk * gn) % (unsigned)f.n3];
+        const float wk = (gk == 0 || 2 * gk == f.n3) ? 1.0f : 2.0f;
+        v = make_float2(wk * t.x, -wk * t.y);
       }
     }
   };
   // split the registers' chunk into the hi / lo tiles of stage `st`
-  auto store_chunk = [&](int st) {
+  auto store_chunk = [&](int st, int k0) {
     char *aHi = smem + st * kStageBytes, *aLo = aHi + P::kTileA;
     char *bReHi = aLo + P::kTileA, *bReLo = bReHi + P::kTileB;
     char *bImHi = bReLo + P::kTileB, *bImLo = bImHi + P::kTileB;
+    // the A values as the MMAs take them: KIND 1 x - ycoef y, KIND 2 the
+    // conjugate on transposed slices
+    auto aval = [&](int i) -> float2 {
+      float2 v = ra[i];
+      if (KIND == 1 && yb) {
+        const float2 w = ry[KIND == 1 ? i : 0];
+        v = make_float2(v.x - f.ycoef * w.x, v.y - f.ycoef * w.y);
+      }
+      if (KIND == 2 && f.trans) v.y = -v.y;
+      return v;
+    };
     if (PREC == 0) {
 #pragma unroll
       for (int i = 0; i < kPa; ++i) {
         int r, kc;
         a_pos(i, r, kc);
-        put_split<PREC>(aHi, aLo, koff<PREC>(r, kc), ra[i].x);
-        put_split<PREC>(aHi, aLo, koff<PREC>(r, kc + TK), ra[i].y);
+        const float2 v = aval(i);
+        put_split<PREC>(aHi, aLo, koff<PREC>(r, kc), v.x);
+        put_split<PREC>(aHi, aLo, koff<PREC>(r, kc + TK), v.y);
       }
 #pragma unroll
       for (int i = 0; i < kPb; ++i) {
         int n, kc;
         b_pos(i, n, kc);
-        const float2 v = rb[i];
+        float2 v, w;
+        bval(i, k0, v, w);
         if (KIND == 1) {  // real and imaginary twiddle parts of the chunk's bands
-          const float2 w = rb1[KIND == 1 ? i : 0];
           put_split<PREC>(bReHi, bReLo, koff<PREC>(n, kc), v.x);
           put_split<PREC>(bReHi, bReLo, koff<PREC>(n, kc + TK), w.x);
           put_split<PREC>(bImHi, bImLo, koff<PREC>(n, kc), v.y);
@@ -376,16 +400,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, Dft3 f, int *
       for (int i = 0; i < kPa; i += 2) {  // k pairs (kc even, kc + 1)
         int r, kc;
         a_pos(i, r, kc);
-        put_split2(aHi, aLo, koff<PREC>(r, kc), ra[i].x, ra[i + 1].x);
-        put_split2(aHi, aLo, koff<PREC>(r, kc + TK), ra[i].y, ra[i + 1].y);
+        const float2 v0 = aval(i), v1 = aval(i + 1);
+        put_split2(aHi, aLo, koff<PREC>(r, kc), v0.x, v1.x);
+        put_split2(aHi, aLo, koff<PREC>(r, kc + TK), v0.y, v1.y);
       }
 #pragma unroll
       for (int i = 0; i < kPb; i += 2) {
         int n, kc;
         b_pos(i, n, kc);
-        const float2 v0 = rb[i], v1 = rb[i + 1];
+        float2 v0, v1, w0, w1;
+        bval(i, k0, v0, w0);
+        bval(i + 1, k0, v1, w1);
         if (KIND == 1) {
-          const float2 w0 = rb1[KIND == 1 ? i : 0], w1 = rb1[KIND == 1 ? i + 1 : 0];
           put_split2(bReHi, bReLo, koff<PREC>(n, kc), v0.x, v1.x);
           put_split2(bReHi, bReLo, koff<PREC>(n, kc + TK), w0.x, w1.x);
           put_split2(bImHi, bImLo, koff<PREC>(n, kc), v0.y, v1.y);
@@ -441,6 +467,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, Dft3 f, int *
             "=r"(re[6]), "=r"(re[7]), "=r"(re[8]), "=r"(re[9]), "=r"(re[10]), "=r"(re[11]),
             "=r"(re[12]), "=r"(re[13]), "=r"(re[14]), "=r"(re[15])
           : "r"(tl + tile + c0));
+      if (KIND == 1) {
+        // the real parts first: half the destination registers live at once,
+        // which leaves room for the next chunk's loads of both cubes
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+        for (int c = 0; c < 16; ++c) accRe[c0 + c] += __uint_as_float(re[c]);
+      }
       if (KIND != 2)
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -451,7 +484,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, Dft3 f, int *
       asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
-        accRe[c0 + c] += __uint_as_float(re[c]);
+        if (KIND != 1) accRe[c0 + c] += __uint_as_float(re[c]);
         if (KIND != 2) accIm[c0 + c] += __uint_as_float(im[c]);
       }
     }
@@ -488,7 +521,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_tc(CGemm g, Dft3 f, int *
   // ch - 1's tile is drained while they run
   for (int ch = 0; ch < nchunks && ok; ++ch) {
     const int st = ch & 1;
-    store_chunk(st);  // stage st was last read by chunk ch - 2, already waited for
+    store_chunk(st, ch * (KIND == 1 ? KR : TK));  // stage st was last read by chunk ch - 2
     if (ch + 1 < nchunks) load_chunk((ch + 1) * (KIND == 1 ? KR : TK));
     stage_barrier();
     if (ch > 0) {

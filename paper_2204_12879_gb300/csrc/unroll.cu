@@ -435,7 +435,8 @@ size_t unroll_layout(lrstv_unroll *u, void *base) {
 
 GemmSel unroll_gemm(const lrstv_unroll *u) {
   if (u->flags & LRSTV_FLAG_SIMT_GEMM) return kSimt;
-  return GemmSel{true, u->gemm_err, 0};  // 3xTF32: the unrolled form has no mixed-precision mode
+  // 3xTF32: the unrolled form has no mixed-precision mode
+  return GemmSel{true, u->gemm_err, 0, (u->flags & LRSTV_FLAG_SIMT_DFT) == 0};
 }
 
 #define UCK(x)                                  \
@@ -624,7 +625,8 @@ int lrstv_unroll_create(int n1, int n2, int n3, int batch, int iters, const floa
   int rc = check_shape(n1, n2, n3);
   if (rc) return rc;
   if (batch < 1 || iters < 1 || iters > 4096) return LRSTV_ERR_ARG;
-  if (flags & ~(unsigned)(LRSTV_FLAG_SIMT_GEMM | LRSTV_FLAG_WARM_START)) return LRSTV_ERR_ARG;
+  if (flags & ~(unsigned)(LRSTV_FLAG_SIMT_GEMM | LRSTV_FLAG_WARM_START | LRSTV_FLAG_SIMT_DFT))
+    return LRSTV_ERR_ARG;
   float wl[3] = {1.0f, 1.0f, 1.0f};
   if (w)
     for (int n = 0; n < 3; ++n) {

@@ -487,3 +487,21 @@ def test_tensor_core_mode3_dfts(L, orc, shape, bf16):
             print(shape, bf16, n, "E-step max-abs / max|F|", err / np.abs(F[n]).max())
             assert err <= te * np.abs(F[n]).max(), n
             assert maxabs(G4[n], mu_e * (E[n] - F[n])) <= 1e-5 * mu_e * np.abs(F[n]).max(), n
+
+
+def test_dft_engines_agree(L, orc):
+    """A whole run with the mode-3 DFTs on the SIMT kernels (LRSTV_FLAG_SIMT_DFT)
+    and one with them on the tensor cores: both within the run bound of the
+    oracle, and within 2e-6 of each other (3xTF32 against FP32 direct sums)."""
+    shape = (32, 32, 16)
+    _, Y = _noisy(shape, 19)
+    outs = []
+    for flags in (0, L.FLAG_SIMT_DFT):
+        with _plan(L, shape, max_iter=12, flags=flags | L.FLAG_WARM_START) as pl:
+            X, _ = pl.run(dev(Y))
+            outs.append(host(X, shape))
+    ost = orc.State(Y, orc.Params(n1=32, n2=32))
+    ost.iterate(12)
+    for X in outs:
+        assert maxabs(X, ost.X) <= 1e-4
+    assert maxabs(outs[0], outs[1]) <= 2e-6 * max(1.0, np.abs(outs[1]).max())
