@@ -392,6 +392,8 @@ def run_ours(args, wl_name):
         flags |= lrstv.FLAG_BF16X3
     if args.dft == "simt":
         flags |= lrstv.FLAG_SIMT_DFT
+    if args.jacobi_schedule == "slice":
+        flags |= lrstv.FLAG_JACOBI_PER_SLICE
     params = lrstv.Params.make(n1, n2, max_iter=iters, flags=flags)
     plan = lrstv.Plan(n1, n2, n3, params)
     ranks = tucker_ranks(args, (n1, n2, n3))
@@ -529,6 +531,8 @@ def run_ours(args, wl_name):
                    "jacobi_start": args.jacobi_start,
                    "gemm_precision": precision,
                    "mode3_dft": "tensor cores" if args.dft == "tc" else "SIMT direct sums",
+                   "jacobi_schedule": ("task graph: panel-pair tasks of every slice on all SMs"
+                                       if args.jacobi_schedule == "tasks" else "one CTA per slice"),
                    "l_update": ("Tucker projection, one HOOI sweep per iteration, ranks %s" % (ranks,)
                                 if ranks else "plain (full Tucker ranks)"),
                    "l2": "working set (18 state cubes + spectra, ~330 MB) exceeds the 129 MB L2",
@@ -958,6 +962,9 @@ def build_parser():
     ap.add_argument("--dft", choices=["tc", "simt"], default="tc",
                     help="mode-3 DFT engine: the tensor-core pipeline or the SIMT direct sums "
                          "(LRSTV_FLAG_SIMT_DFT)")
+    ap.add_argument("--jacobi-schedule", choices=["tasks", "slice"], default="tasks",
+                    help="the Jacobi's task-graph schedule over all SMs, or one CTA per slice "
+                         "(LRSTV_FLAG_JACOBI_PER_SLICE)")
     ap.add_argument("--micro", choices=["tsvt"], default=None,
                     help="time one standalone operator instead of the iteration")
     ap.add_argument("--shape", default="200,200,16", help="n1,n2,n3 for --micro")

@@ -68,6 +68,13 @@ typedef enum lrstv_status {
                                         2^-21); storage, the Jacobi and the thresholds stay
                                         FP32, the sigma-vs-threshold decisions FP64.  Not with
                                         LRSTV_FLAG_SIMT_GEMM (ERR_ARG). */
+#define LRSTV_FLAG_JACOBI_PER_SLICE 512u /* run each Fourier slice's Jacobi sweeps in one CTA
+                                        (its column panels in sequence) instead of the
+                                        task-graph schedule, in which every SM takes panel-pair
+                                        tasks of any slice (slices up to 256 rows; the same
+                                        t-SVT to rounding, the pairs visited in another
+                                        order).  Batches always run their slices this way, so
+                                        a batch's cube equals a plan made with this flag. */
 #define LRSTV_FLAG_SIMT_DFT 256u     /* the mode-3 (spectral) DFTs on the FP32 SIMT kernels (direct
                                         sums with twiddle tables) instead of the tensor-core
                                         pipeline (3xTF32, or 3xBF16 with LRSTV_FLAG_BF16X3);
@@ -287,11 +294,13 @@ int lrstv_plan_run_host(lrstv_plan *plan, const float *Y_host, float *X_host, fl
 /* Autotuner (no counterpart in the paper): times `iters` iterations
  * (params.max_iter when 0) of the plan from the device cube Y for every
  * combination of the flags in `allowed` (a subset of LRSTV_FLAG_SIMT_GEMM |
- * LRSTV_FLAG_SIMT_DFT | LRSTV_FLAG_WARM_START; combinations params rejects,
- * and SIMT_DFT together with SIMT_GEMM, are skipped), each after
+ * LRSTV_FLAG_SIMT_DFT | LRSTV_FLAG_JACOBI_PER_SLICE | LRSTV_FLAG_WARM_START;
+ * combinations params rejects, and SIMT_DFT together with SIMT_GEMM, are
+ * skipped), each after
  * one untimed pass, with CUDA events on `stream`, and keeps the fastest in
  * the plan's params.flags.  These choices change the work (GEMM and DFT
- * engines, Jacobi starting basis), not the result beyond the FP32 bound.  *chosen and
+ * engines, the Jacobi's schedule and starting basis), not the result beyond
+ * the FP32 bound.  *chosen and
  * *ms_out (may be NULL) receive the flags kept and their time in ms.  Leaves
  * the plan initialised from Y (lrstv_init) and synchronises `stream`.
  * ERR_ARG for a NULL plan or Y, iters < 0 or other bits in `allowed`; on any
@@ -417,7 +426,7 @@ int lrstv_tsvt_noalloc(const float *A, int n1, int n2, int n3, float t, float *o
  *   of every E-update (K x 3 B (n3/2+1) slices) and the scratch of both
  *   passes; lrstv_unroll_bytes reports its size.  w: weights of D_w (NULL =
  *   1, 1, 1).  flags: any of LRSTV_FLAG_SIMT_GEMM, LRSTV_FLAG_SIMT_DFT,
- *   LRSTV_FLAG_WARM_START (iteration
+ *   LRSTV_FLAG_JACOBI_PER_SLICE, LRSTV_FLAG_WARM_START (iteration
  *   k > 0 starts its Jacobi SVDs from iteration k-1's singular vectors, as a
  *   plan does).  iters in 1..4096.
  * lrstv_unroll_forward  Y: device, B cubes back to back (B N floats).

@@ -48,6 +48,13 @@ int check_shape(int n1, int n2, int n3) {
 namespace {
 
 constexpr int kResRing = 4096;     // per-iteration residual history
+// SMs a plan's task-graph Jacobi leaves to the side stream, which runs the
+// next iteration's L-update and Z-solve while the E-step's Jacobi runs.  The
+// Jacobi's time follows the SMs it has (200 x 200 x 80: 5.05 ms on 152 SMs,
+// 5.52 on 136), while the side stream's work, once the Jacobi's CTAs have
+// left, takes a fraction of a millisecond on the whole GPU: 16 spare SMs gave
+// 155.4 iterations/s against 163.9 with none, so none are kept.
+constexpr int kJacobiSpareSMs = 0;
 
 int check_params(const lrstv_params *p) {
   if (!p) return LRSTV_ERR_ARG;
@@ -58,7 +65,7 @@ int check_params(const lrstv_params *p) {
   if (!(p->mu0 > 0.0f) || !(p->mu_max >= p->mu0) || p->max_iter < 0) return LRSTV_ERR_ARG;
   if (p->flags & ~(unsigned)(LRSTV_FLAG_F_THRESH_EXACT | LRSTV_FLAG_NO_GAMMA4 | LRSTV_FLAG_GRAPH |
                              LRSTV_FLAG_STRICT | LRSTV_FLAG_SIMT_GEMM | LRSTV_FLAG_WARM_START |
-                             LRSTV_FLAG_SIMT_DFT |
+                             LRSTV_FLAG_SIMT_DFT | LRSTV_FLAG_JACOBI_PER_SLICE |
                              LRSTV_FLAG_ISO_TV | LRSTV_FLAG_BF16X3))
     return LRSTV_ERR_ARG;
   // the split-BF16 products exist on the tensor-core path only
@@ -167,7 +174,7 @@ cudaError_t tsvt_pre(const Dims &d, int nb, const float *x, const float *y, floa
 // ms2 (may be null): nb floats for the tensors' largest mean-square column
 // norms, which then set the threshold-aware tolerance tensor by tensor.
 cudaError_t tsvt_jac(const Dims &d, int nb, float t, float2 *specA, float2 *V, int *sweeps,
-                     cudaStream_t st, Prof *prof, float *ms2 = nullptr) {
+                     cudaStream_t st, Prof *prof, float *ms2 = nullptr, int *sched = nullptr) {
   if (ms2) {
     cudaError_t e = launch_group_ms2(d, nb * d.h, specA, d.h, ms2, st);
     if (e != cudaSuccess) return e;
@@ -176,6 +183,8 @@ cudaError_t tsvt_jac(const Dims &d, int nb, float t, float2 *specA, float2 *V, i
   o.t_svt = t;
   o.ms2 = ms2;
   o.group = d.h;
+  o.sched = sched;
+  o.spare_sms = sched ? kJacobiSpareSMs : 0;
   Span sp(prof, LRSTV_K_JACOBI, st);
   return launch_jacobi(d, nb * d.h, specA, V, t, kMaxSweeps, sweeps, prof ? prof->d_work : nullptr,
                        st, o);
@@ -204,10 +213,10 @@ cudaError_t tsvt_core(const Dims &d, int nb, const float *x, const float *y, flo
                       float *out, int mode, float *G4, const float *F, float mu, int gamma4,
                       const float2 *tw3, float2 *specA, float2 *specB, float2 *V, int *sweeps,
                       cudaStream_t st, Prof *prof = nullptr, GemmSel gs = kSimt,
-                      float *ms2 = nullptr) {
+                      float *ms2 = nullptr, int *sched = nullptr) {
   cudaError_t e = tsvt_pre(d, nb, x, y, ycoef, tw3, specA, st, prof, gs);
   if (e != cudaSuccess) return e;
-  if ((e = tsvt_jac(d, nb, t, specA, V, sweeps, st, prof, ms2)) != cudaSuccess) return e;
+  if ((e = tsvt_jac(d, nb, t, specA, V, sweeps, st, prof, ms2, sched)) != cudaSuccess) return e;
   return tsvt_post(d, nb, out, mode, G4, F, mu, gamma4, tw3, specA, specB, V, st, prof, gs);
 }
 
@@ -242,6 +251,7 @@ struct lrstv_plan {
   Tables tb;
   unsigned *res;  // kResRing x 2 residual maxima (float bits)
   int *sweeps;    // 3h
+  int *jsched;    // task-graph Jacobi scratch (jacobi_task_ints(3h))
   int *gemm_err;  // tensor-core GEMM wait timeouts
   // graph cache for lrstv_plan_run
   cudaGraphExec_t gexec;
@@ -273,6 +283,11 @@ struct lrstv_plan {
   } while (0)
 
 namespace {
+
+// The task-graph Jacobi's scratch, or null for one CTA per slice.
+int *plan_sched(const lrstv_plan *pl) {
+  return (pl->prm.flags & LRSTV_FLAG_JACOBI_PER_SLICE) ? nullptr : pl->jsched;
+}
 
 GemmSel plan_gemm(const lrstv_plan *pl) {
   if (pl->prm.flags & LRSTV_FLAG_SIMT_GEMM) return kSimt;
@@ -363,6 +378,8 @@ cudaError_t tsvt_warm(lrstv_plan *pl, float ycoef, float t, float mu, int gamma4
     o.t_svt = t;
     o.ms2 = pl->ms2;
     o.group = d.h;
+    o.sched = plan_sched(pl);
+    o.spare_sms = kJacobiSpareSMs;
     Span sp(&pl->prof, LRSTV_K_JACOBI, st);
     e = launch_jacobi(d, ns, Wm, pl->V, -1.0f, kMaxSweeps, pl->sweeps,
                       pl->prof.on ? pl->prof.d_work : nullptr, st, o);
@@ -422,6 +439,7 @@ size_t plan_layout(lrstv_plan *pl, void *base) {
   carve_tables(c, d, pl->tb);
   pl->res = c.take<unsigned>(2 * (size_t)kResRing);
   pl->sweeps = c.take<int>(3 * (size_t)d.h);
+  pl->jsched = c.take<int>(jacobi_task_ints(3 * d.h));
   pl->gemm_err = c.take<int>(1);
   pl->prof.d_work = c.take<unsigned long long>(2);
   return c.off;
@@ -836,7 +854,8 @@ int lrstv_step_e(lrstv_plan *pl, void *stream) {
   }
   CK(tsvt_core(pl->d, 3, pl->F, pl->G4, (float)(1.0 / mu), (float)(pl->prm.alpha / mu), pl->E, 1,
                pl->G4, pl->F, (float)mu, gamma4, pl->tb.tw3, pl->specA, pl->specB, pl->V,
-               pl->sweeps, (cudaStream_t)stream, &pl->prof, plan_gemm(pl), pl->ms2));
+               pl->sweeps, (cudaStream_t)stream, &pl->prof, plan_gemm(pl), pl->ms2,
+               plan_sched(pl)));
   return LRSTV_OK;
 }
 
@@ -996,13 +1015,14 @@ int lrstv_plan_run(lrstv_plan *pl, const float *Y, float *X, float *S, lrstv_sta
 int lrstv_plan_autotune(lrstv_plan *pl, const float *Y, int iters, unsigned allowed,
                         unsigned *chosen, float *ms_out, void *stream) {
   if (!pl || !Y || iters < 0) return LRSTV_ERR_ARG;
-  if (allowed & ~(unsigned)(LRSTV_FLAG_SIMT_GEMM | LRSTV_FLAG_WARM_START | LRSTV_FLAG_SIMT_DFT))
+  if (allowed & ~(unsigned)(LRSTV_FLAG_SIMT_GEMM | LRSTV_FLAG_WARM_START | LRSTV_FLAG_SIMT_DFT |
+                            LRSTV_FLAG_JACOBI_PER_SLICE))
     return LRSTV_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   const int n = iters > 0 ? iters : pl->prm.max_iter;
   const unsigned base = pl->prm.flags & ~allowed;
   // candidates: every subset of `allowed` that check_params accepts
-  unsigned cands[8];
+  unsigned cands[16];
   int nc = 0;
   for (unsigned sub = 0; sub <= allowed; ++sub) {
     if ((sub & ~allowed) != 0) continue;
@@ -1010,7 +1030,7 @@ int lrstv_plan_autotune(lrstv_plan *pl, const float *Y, int iters, unsigned allo
     if ((sub & LRSTV_FLAG_SIMT_GEMM) && (sub & LRSTV_FLAG_SIMT_DFT)) continue;
     lrstv_params trial = pl->prm;
     trial.flags = base | sub;
-    if (check_params(&trial) == LRSTV_OK && nc < 8) cands[nc++] = base | sub;
+    if (check_params(&trial) == LRSTV_OK && nc < 16) cands[nc++] = base | sub;
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {

@@ -153,7 +153,16 @@ struct JacOpt {
   const float *ms2 = nullptr;
   int group = 1;
   float negl_rel = -1.0f;
+  // scratch of jacobi_task_ints(nslices) ints: with it, slices of up to 256
+  // rows run on the task-graph schedule (all SMs share every slice's panel
+  // pairs); without it, one CTA per slice
+  int *sched = nullptr;
+  // SMs the task-graph grid leaves free for concurrent work (another stream's
+  // kernels cannot share an SM with a worker CTA, which takes its shared memory)
+  int spare_sms = 0;
 };
+// ints of task-graph scratch for nslices working matrices
+size_t jacobi_task_ints(int nslices);
 cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, float t,
                           int max_sweeps, int *sweeps, unsigned long long *work,
                           cudaStream_t st, const JacOpt &opt = JacOpt());

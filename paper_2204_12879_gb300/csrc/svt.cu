@@ -388,10 +388,18 @@ __device__ __forceinline__ void pk_rot_stream(float4 (&a)[K], float4 *col, const
   }
 }
 
+// Loads of W and V that another SM may have written during the same launch
+// (the task-graph schedule below) bypass L1, which is not coherent across SMs.
+template <bool CG>
+__device__ __forceinline__ float2 ldw(const float2 *p) {
+  return CG ? __ldcg(p) : *p;
+}
+
 // shared panel (ld2 row pairs per column, split layout, zero padded) <-
 // wcols interleaved columns of n rows; warp w copies columns w, w + 16, ...
 // With nrm (kPW floats), also each staged column's squared norm (0 for the
 // padding columns).
+template <bool CG = false>
 __device__ __forceinline__ void pk_stage_in(float4 *dst, int ld2, const float2 *src, int n,
                                             int wcols, float *nrm = nullptr) {
   const int lane = threadIdx.x & 31;
@@ -402,8 +410,8 @@ __device__ __forceinline__ void pk_stage_in(float4 *dst, int ld2, const float2 *
     float part = 0.0f;
     for (int m = lane; m < ld2; m += 32) {
       const int r0 = 2 * m, r1 = 2 * m + 1;
-      const float2 x0 = (real && r0 < n) ? s[r0] : make_float2(0.f, 0.f);
-      const float2 x1 = (real && r1 < n) ? s[r1] : make_float2(0.f, 0.f);
+      const float2 x0 = (real && r0 < n) ? ldw<CG>(s + r0) : make_float2(0.f, 0.f);
+      const float2 x1 = (real && r1 < n) ? ldw<CG>(s + r1) : make_float2(0.f, 0.f);
       d[m] = make_float4(x0.x, x1.x, x0.y, x1.y);
       if (nrm) part = fmaf(x0.x, x0.x, fmaf(x0.y, x0.y, fmaf(x1.x, x1.x, fmaf(x1.y, x1.y, part))));
     }
@@ -434,37 +442,19 @@ struct PkShape {
   static constexpr int LD2 = (16 * KP > 32 * KPF) ? 16 * KP : 32 * KPF;  // row pairs per column
 };
 
-// The packed Jacobi SVT of one slice by the whole CTA (kHW warps): W (nr x nc)
-// and V (nc x nc) in global memory, `smem` the CTA's dynamic shared memory
-// (3 kPW LD2 float4).  Writes the sweep count (negative at the cap) to
-// *sweeps_slot.  Shared by the one-slice-per-CTA kernel and the persistent
-// batch kernel, so both compute bit-identical results.
-template <int KP>
-__device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float2 *V, float t,
-                                                int max_sweeps, float tol, float negl_rel,
-                                                int *sweeps_slot, unsigned long long *work,
-                                                float4 *smem, int warm, float skip_t,
-                                                float gms2) {
-  constexpr int KPF = PkShape<KP>::KPF;
-  constexpr int LD2 = PkShape<KP>::LD2;
-  float4 *sW = smem;               // panel a (own pairs), then panel b: W
-  float4 *sVa = sW + kPW * LD2;    // panel a: V
-  float4 *sVb = sVa + kPW * LD2;   // panel b: V
+// Per-slice set-up of a packed Jacobi run by the whole CTA: V := I unless warm
+// (warm: V holds the basis W was multiplied by), then ||W||_F^2, returned to
+// every thread (s_red: 32 floats of shared memory).
+template <bool CG>
+__device__ __forceinline__ float pk_setup(int nr, int nc, const float2 *W, float2 *V, int warm,
+                                          float *s_red) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int unit = tid >> 4, ul = tid & 15;
-  __shared__ float s_red[32];
-  __shared__ int s_rot;
-  // squared column norms of panel a and of the streamed panel b: exact when
-  // a panel is staged, then carried through each rotation by the 2x2 update
-  // (|a|^2 - d, |b|^2 + d), so that a pair's test needs only its inner product
-  __shared__ float s_na[kPW], s_nb[kPW];
-
-  if (!warm)  // warm: V holds the basis W was multiplied by
+  if (!warm)
     for (int e = tid; e < nc * nc; e += blockDim.x)
       V[e] = make_float2((e % nc) == (e / nc) ? 1.0f : 0.0f, 0.0f);
   float part = 0.0f;
   for (size_t e = tid; e < (size_t)nr * nc; e += blockDim.x) {
-    const float2 x = W[e];
+    const float2 x = ldw<CG>(W + e);
     part = fmaf(x.x, x.x, fmaf(x.y, x.y, part));
   }
   part = warp_sum(part);
@@ -476,31 +466,255 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
     if (lane == 0) s_red[0] = v;
   }
   __syncthreads();
-  const float negl = negl_rel * s_red[0];
+  const float fro2 = s_red[0];
+  __syncthreads();
+  return fro2;
+}
 
+// A pair left with relative inner product g moves the SVT result by at most
+// about t g (both values kept: t g s_p / (s_p + s_q); one kept: g s_cut <= t g;
+// both cut: nothing), so with the threshold t below the columns' RMS norm the
+// relative tolerance is raised to tol rms / t: the absolute error stays at
+// the level tol rms that a threshold near the RMS norm already allows.  The
+// RMS norm is the largest over the slices of one tensor when it is given
+// (ms2 >= 0): the inverse DFT mixes the slices, so all of them are resolved to
+// the same absolute precision.
+__device__ __forceinline__ float pk_tolerance(float tol, float fro2, int nc, float skip_t,
+                                              float gms2) {
+  if (skip_t > 0.0f && nc > 0) {
+    const float ms2 = gms2 >= 0.0f ? gms2 : fro2 / (float)nc;
+    tol = fmaxf(tol, tol * (sqrtf(ms2) / skip_t));
+  }
+  return tol;
+}
+
+// The pairs inside one staged panel (W in sW with squared norms s_na, V in
+// sVa; wa real columns): 31 rounds of 16 disjoint pairs, one per warp.
+template <int KP>
+__device__ __forceinline__ void pk_intra(float4 *sW, float4 *sVa, float *s_na, int wa, float tol,
+                                         float negl, unsigned &n_pairs, unsigned &n_rot,
+                                         int &rotated) {
+  constexpr int KPF = PkShape<KP>::KPF;
+  constexpr int LD2 = PkShape<KP>::LD2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = 0; r < kPW - 1; ++r) {
+    int p, q;
+    pair_of(r, warp, kPW, p, q);
+    if (p < wa && q < wa) {
+      float4 xa[KPF], xb[KPF];
+#pragma unroll
+      for (int k = 0; k < KPF; ++k) {
+        xa[k] = sW[LD2 * p + lane + 32 * k];
+        xb[k] = sW[LD2 * q + lane + 32 * k];
+      }
+      float gr, gi;
+      pk_cross<KPF>(xa, xb, gr, gi);
+      gr = warp_sum(gr);
+      gi = warp_sum(gi);
+      // a norm marked negative after a rotation that cancelled it is
+      // recomputed from the column (warp-uniform: p, q are the warp's)
+      float al = s_na[p], be = s_na[q];
+      if (al < 0.0f) al = warp_sum(pk_norm<KPF>(xa));
+      if (be < 0.0f) be = warp_sum(pk_norm<KPF>(xb));
+      if (lane == 0) n_pairs += 1;
+      Rot rt;
+      if (make_rot(al, be, gr, gi, tol, negl, rt)) {
+        const PRot pq = packed(rt);
+#pragma unroll
+        for (int k = 0; k < KPF; ++k) {
+          pk_rot(xa[k], xb[k], pq);
+          sW[LD2 * p + lane + 32 * k] = xa[k];
+          sW[LD2 * q + lane + 32 * k] = xb[k];
+        }
+        pk_rot_smem<KPF, 32>(sVa + LD2 * p, sVa + LD2 * q, pq, lane);
+        const float na = al - rt.d, nb = be + rt.d;
+        if (lane == 0) {
+          s_na[p] = na < kNormDrop * al ? -1.0f : na;
+          s_na[q] = nb < kNormDrop * be ? -1.0f : nb;
+          n_rot += 1;
+        }
+        rotated = 1;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Panel a's columns (one per half-warp, `unit`; W in aW, V in aV, both in
+// registers; mine = the column is real) against the streamed panel b (W in
+// sW with squared norms s_nb, V in sVb; wb real columns): 16 double rounds in
+// which warp w owns streamed columns 2c, 2c+1 (c = (w + R) mod 16) and its
+// half-warps rotate them in swapped order, so only the warp synchronises
+// between the two sub-steps and the block once per double round.
+template <int KP>
+__device__ __forceinline__ void pk_cross_pass(float4 (&aW)[KP], float4 (&aV)[KP], bool mine,
+                                              float4 *sW, float4 *sVb, float *s_nb, int wb,
+                                              float tol, float negl, unsigned &n_pairs,
+                                              unsigned &n_rot, int &rotated) {
+  constexpr int LD2 = PkShape<KP>::LD2;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int unit = tid >> 4, ul = tid & 15;
+  float4 bW[KP];
+  // the register column's squared norm, exact at the start of each streamed
+  // panel (the whole warp shuffles: both halves compute theirs)
+  float al_reg = half_sum(pk_norm<KP>(aW));
+  __syncthreads();
+  for (int r = 0; r < kPW; ++r) {
+    const int sub = r & 1;
+    const int cpi = (warp + (r >> 1)) & (kPW / 2 - 1);
+    const int j = 2 * cpi + ((unit & 1) ^ sub);
+    const bool real = mine && j < wb;
+#pragma unroll
+    for (int k = 0; k < KP; ++k) bW[k] = sW[LD2 * j + ul + 16 * k];
+    float gr, gi;
+    pk_cross<KP>(aW, bW, gr, gi);
+    gr = half_sum(gr);
+    gi = half_sum(gi);
+    // norms marked negative after a rotation that cancelled them are
+    // recomputed here, where both columns are in registers; the decision is
+    // made per warp so that both halves take part in the shuffles
+    float be = s_nb[j];
+    if (__any_sync(0xffffffffu, be < 0.0f || al_reg < 0.0f)) {
+      const float xa = half_sum(pk_norm<KP>(aW));
+      const float xb = half_sum(pk_norm<KP>(bW));
+      if (al_reg < 0.0f) al_reg = xa;
+      if (be < 0.0f) be = xb;
+    }
+    Rot rt;
+    const bool go = real && make_rot(al_reg, be, gr, gi, tol, negl, rt);
+    if (ul == 0 && real) n_pairs += 1;
+    if (__any_sync(0xffffffffu, go)) {
+      // the other half-warp may rotate: this half applies the identity, which
+      // rewrites its columns unchanged
+      if (!go) {
+        rt.c = 1.0f;
+        rt.s = 0.0f;
+        rt.er = 1.0f;
+        rt.ei = 0.0f;
+        rt.d = 0.0f;
+      }
+      const PRot pq = packed(rt);
+#pragma unroll
+      for (int k = 0; k < KP; ++k) {
+        pk_rot(aW[k], bW[k], pq);
+        sW[LD2 * j + ul + 16 * k] = bW[k];
+      }
+      pk_rot_stream<KP>(aV, sVb + LD2 * j, pq, ul);
+      if (go) {
+        const float na = al_reg - rt.d, nb = be + rt.d;
+        al_reg = na < kNormDrop * al_reg ? -1.0f : na;
+        if (ul == 0) {
+          s_nb[j] = nb < kNormDrop * be ? -1.0f : nb;
+          n_rot += 1;
+        }
+        rotated = 1;
+      }
+    }
+    if (sub == 0)
+      __syncwarp();
+    else
+      __syncthreads();
+  }
+}
+
+// Panel a's W column `unit` of the staged panel moves to registers, with its V.
+template <int KP>
+__device__ __forceinline__ void pk_to_registers(const float4 *sW, const float4 *sVa,
+                                                float4 (&aW)[KP], float4 (&aV)[KP]) {
+  constexpr int LD2 = PkShape<KP>::LD2;
+  const int unit = threadIdx.x >> 4, ul = threadIdx.x & 15;
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    aW[k] = sW[LD2 * unit + ul + 16 * k];
+    aV[k] = sVa[LD2 * unit + ul + 16 * k];
+  }
+}
+
+// Panel a back to global memory from the registers (W) and, through sVa, V.
+template <int KP>
+__device__ __forceinline__ void pk_from_registers(const float4 (&aW)[KP], const float4 (&aV)[KP],
+                                                  bool mine, float4 *sVa, float2 *Wa,
+                                                  float2 *Va, int nr, int nc, int wa) {
+  constexpr int LD2 = PkShape<KP>::LD2;
+  const int unit = threadIdx.x >> 4, ul = threadIdx.x & 15;
+#pragma unroll
+  for (int k = 0; k < KP; ++k) sVa[LD2 * unit + ul + 16 * k] = aV[k];
+  __syncthreads();
+  if (mine) {
+    float2 *wcol = Wa + (size_t)nr * unit;
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      const int m = ul + 16 * k;
+      if (2 * m < nr) wcol[2 * m] = make_float2(aW[k].x, aW[k].z);
+      if (2 * m + 1 < nr) wcol[2 * m + 1] = make_float2(aW[k].y, aW[k].w);
+    }
+  }
+  pk_stage_out(Va, sVa, LD2, nc, wa);
+}
+
+// g_i = max(1 - t / sigma_i, 0) applied to V's columns (t < 0: V unscaled),
+// sigma_i = |w_i|; the sigma-vs-t decision is taken in FP64.
+template <bool CG>
+__device__ __forceinline__ void pk_epilogue(int nr, int nc, const float2 *W, float2 *V, float t) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (t < 0.0f) return;
+  for (int i = warp; i < nc; i += kHW) {
+    const float2 *wi = W + (size_t)nr * i;
+    float n2 = 0.f;
+    for (int row = lane; row < nr; row += 32) {
+      const float2 x = ldw<CG>(wi + row);
+      n2 = fmaf(x.x, x.x, fmaf(x.y, x.y, n2));
+    }
+    n2 = warp_sum(n2);
+    const double sigma = sqrt((double)n2);
+    const float g = sigma > (double)t ? (float)(1.0 - (double)t / sigma) : 0.0f;
+    float2 *vi = V + (size_t)nc * i;
+    for (int row = lane; row < nc; row += 32) {
+      const float2 v = ldw<CG>(vi + row);
+      vi[row] = make_float2(v.x * g, v.y * g);
+    }
+  }
+}
+
+// The packed Jacobi SVT of one slice by the whole CTA (kHW warps): W (nr x nc)
+// and V (nc x nc) in global memory, `smem` the CTA's dynamic shared memory
+// (3 kPW LD2 float4).  Panel by panel: panel a's own pairs, then panel a (in
+// registers) against every later panel b streamed through shared memory.
+// Writes the sweep count (negative at the cap) to *sweeps_slot.  Shared by the
+// one-slice-per-CTA kernel and the persistent batch kernel, so both compute
+// bit-identical results.
+template <int KP>
+__device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float2 *V, float t,
+                                                int max_sweeps, float tol, float negl_rel,
+                                                int *sweeps_slot, unsigned long long *work,
+                                                float4 *smem, int warm, float skip_t,
+                                                float gms2) {
+  constexpr int LD2 = PkShape<KP>::LD2;
+  float4 *sW = smem;               // panel a (own pairs), then panel b: W
+  float4 *sVa = sW + kPW * LD2;    // panel a: V
+  float4 *sVb = sVa + kPW * LD2;   // panel b: V
+  const int tid = threadIdx.x, ul = tid & 15, unit = tid >> 4;
+  __shared__ float s_red[32];
+  __shared__ int s_rot;
+  // squared column norms of panel a and of the streamed panel b: exact when
+  // a panel is staged, then carried through each rotation by the 2x2 update
+  // (|a|^2 - d, |b|^2 + d), so that a pair's test needs only its inner product
+  __shared__ float s_na[kPW], s_nb[kPW];
+
+  const float fro2 = pk_setup<false>(nr, nc, W, V, warm, s_red);
+  const float negl = negl_rel * fro2;
   const int npan = (nc + kPW - 1) / kPW;
   unsigned n_pairs = 0, n_rot = 0;  // lane 0 (own pairs) and ul 0 (cross pairs) count
   int sweeps = (nc < 2) ? 1 : 0;
   bool converged = (nc < 2);
   // every singular value is at most ||W||_F: at or below the threshold the SVT
   // is zero whatever the sweeps would find, so none is run
-  if (skip_t >= 0.0f && s_red[0] <= skip_t * skip_t) {
+  if (skip_t >= 0.0f && fro2 <= skip_t * skip_t) {
     sweeps = 0;
     converged = true;
   }
-  // A pair left with relative inner product g moves the SVT result by at most
-  // about t g (both values kept: t g s_p / (s_p + s_q); one kept: g s_cut <= t g;
-  // both cut: nothing), so with the threshold t below the columns' RMS norm the
-  // relative tolerance is raised to tol rms / t: the absolute error stays at
-  // the level tol rms that a threshold near the RMS norm already allows.  The
-  // RMS norm is the largest over the slices of one tensor when it is given
-  // (ms2): the inverse DFT mixes the slices, so all of them are resolved to
-  // the same absolute precision.
-  if (skip_t > 0.0f && nc > 0) {
-    const float ms2 = gms2 >= 0.0f ? gms2 : s_red[0] / (float)nc;
-    tol = fmaxf(tol, tol * (sqrtf(ms2) / skip_t));
-  }
-  float4 aW[KP], aV[KP], bW[KP];
+  tol = pk_tolerance(tol, fro2, nc, skip_t, gms2);
+  float4 aW[KP], aV[KP];
   for (int sweep = 1; sweep <= max_sweeps && !converged; ++sweep) {
     if (tid == 0) s_rot = 0;
     int rotated = 0;
@@ -510,140 +724,20 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
       pk_stage_in(sW, LD2, W + (size_t)nr * ca, nr, wa, s_na);
       pk_stage_in(sVa, LD2, V + (size_t)nc * ca, nc, wa);
       __syncthreads();
-      // pairs inside panel a: 16 disjoint pairs per round, one per warp
-      for (int r = 0; r < kPW - 1; ++r) {
-        int p, q;
-        pair_of(r, warp, kPW, p, q);
-        if (p < wa && q < wa) {
-          float4 xa[KPF], xb[KPF];
-#pragma unroll
-          for (int k = 0; k < KPF; ++k) {
-            xa[k] = sW[LD2 * p + lane + 32 * k];
-            xb[k] = sW[LD2 * q + lane + 32 * k];
-          }
-          float gr, gi;
-          pk_cross<KPF>(xa, xb, gr, gi);
-          gr = warp_sum(gr);
-          gi = warp_sum(gi);
-          // a norm marked negative after a rotation that cancelled it is
-          // recomputed from the column (warp-uniform: p, q are the warp's)
-          float al = s_na[p], be = s_na[q];
-          if (al < 0.0f) al = warp_sum(pk_norm<KPF>(xa));
-          if (be < 0.0f) be = warp_sum(pk_norm<KPF>(xb));
-          if (lane == 0) n_pairs += 1;
-          Rot rt;
-          if (make_rot(al, be, gr, gi, tol, negl, rt)) {
-            const PRot pq = packed(rt);
-#pragma unroll
-            for (int k = 0; k < KPF; ++k) {
-              pk_rot(xa[k], xb[k], pq);
-              sW[LD2 * p + lane + 32 * k] = xa[k];
-              sW[LD2 * q + lane + 32 * k] = xb[k];
-            }
-            pk_rot_smem<KPF, 32>(sVa + LD2 * p, sVa + LD2 * q, pq, lane);
-            const float na = al - rt.d, nb = be + rt.d;
-            if (lane == 0) {
-              s_na[p] = na < kNormDrop * al ? -1.0f : na;
-              s_na[q] = nb < kNormDrop * be ? -1.0f : nb;
-              n_rot += 1;
-            }
-            rotated = 1;
-          }
-        }
-        __syncthreads();
-      }
-      // panel a's W column `unit` moves to registers
+      pk_intra<KP>(sW, sVa, s_na, wa, tol, negl, n_pairs, n_rot, rotated);
       const bool mine = unit < wa;
-#pragma unroll
-      for (int k = 0; k < KP; ++k) {
-        aW[k] = sW[LD2 * unit + ul + 16 * k];
-        aV[k] = sVa[LD2 * unit + ul + 16 * k];
-      }
+      pk_to_registers<KP>(sW, sVa, aW, aV);
       for (int b = a + 1; b < npan; ++b) {
         const int cb = b * kPW, wb = min(kPW, nc - cb);
         __syncthreads();
         pk_stage_in(sW, LD2, W + (size_t)nr * cb, nr, wb, s_nb);
         pk_stage_in(sVb, LD2, V + (size_t)nc * cb, nc, wb);
-        // the register column's squared norm, exact at the start of each
-        // streamed panel (the whole warp shuffles: both halves compute theirs)
-        float al_reg = half_sum(pk_norm<KP>(aW));
-        __syncthreads();
-        // 16 double rounds: warp w owns streamed columns 2c, 2c+1 (c = (w + R) mod 16); its
-        // half-warps rotate them in swapped order, so only the warp synchronises between the
-        // two sub-steps and the block once per double round
-        for (int r = 0; r < kPW; ++r) {
-          const int sub = r & 1;
-          const int cpi = (warp + (r >> 1)) & (kPW / 2 - 1);
-          const int j = 2 * cpi + ((unit & 1) ^ sub);
-          const bool real = mine && j < wb;
-#pragma unroll
-          for (int k = 0; k < KP; ++k) bW[k] = sW[LD2 * j + ul + 16 * k];
-          float gr, gi;
-          pk_cross<KP>(aW, bW, gr, gi);
-          gr = half_sum(gr);
-          gi = half_sum(gi);
-          // norms marked negative after a rotation that cancelled them are
-          // recomputed here, where both columns are in registers; the
-          // decision is made per warp so that both halves take part in the
-          // shuffles
-          float be = s_nb[j];
-          if (__any_sync(0xffffffffu, be < 0.0f || al_reg < 0.0f)) {
-            const float xa = half_sum(pk_norm<KP>(aW));
-            const float xb = half_sum(pk_norm<KP>(bW));
-            if (al_reg < 0.0f) al_reg = xa;
-            if (be < 0.0f) be = xb;
-          }
-          Rot rt;
-          const bool go = real && make_rot(al_reg, be, gr, gi, tol, negl, rt);
-          if (ul == 0 && real) n_pairs += 1;
-          if (__any_sync(0xffffffffu, go)) {
-            // the other half-warp may rotate: this half applies the identity,
-            // which rewrites its columns unchanged
-            if (!go) {
-              rt.c = 1.0f;
-              rt.s = 0.0f;
-              rt.er = 1.0f;
-              rt.ei = 0.0f;
-              rt.d = 0.0f;
-            }
-            const PRot pq = packed(rt);
-#pragma unroll
-            for (int k = 0; k < KP; ++k) {
-              pk_rot(aW[k], bW[k], pq);
-              sW[LD2 * j + ul + 16 * k] = bW[k];
-            }
-            pk_rot_stream<KP>(aV, sVb + LD2 * j, pq, ul);
-            if (go) {
-              const float na = al_reg - rt.d, nb = be + rt.d;
-              al_reg = na < kNormDrop * al_reg ? -1.0f : na;
-              if (ul == 0) {
-                s_nb[j] = nb < kNormDrop * be ? -1.0f : nb;
-                n_rot += 1;
-              }
-              rotated = 1;
-            }
-          }
-          if (sub == 0)
-            __syncwarp();
-          else
-            __syncthreads();
-        }
+        pk_cross_pass<KP>(aW, aV, mine, sW, sVb, s_nb, wb, tol, negl, n_pairs, n_rot, rotated);
         pk_stage_out(W + (size_t)nr * cb, sW, LD2, nr, wb);
         pk_stage_out(V + (size_t)nc * cb, sVb, LD2, nc, wb);
       }
-#pragma unroll
-      for (int k = 0; k < KP; ++k) sVa[LD2 * unit + ul + 16 * k] = aV[k];
-      __syncthreads();
-      if (mine) {
-        float2 *wcol = W + (size_t)nr * (ca + unit);
-#pragma unroll
-        for (int k = 0; k < KP; ++k) {
-          const int m = ul + 16 * k;
-          if (2 * m < nr) wcol[2 * m] = make_float2(aW[k].x, aW[k].z);
-          if (2 * m + 1 < nr) wcol[2 * m + 1] = make_float2(aW[k].y, aW[k].w);
-        }
-      }
-      pk_stage_out(V + (size_t)nc * ca, sVa, LD2, nc, wa);
+      pk_from_registers<KP>(aW, aV, mine, sVa, W + (size_t)nr * ca, V + (size_t)nc * ca, nr, nc,
+                            wa);
     }
     if (rotated) s_rot = 1;
     __syncthreads();
@@ -651,17 +745,7 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
     converged = (s_rot == 0);
     __syncthreads();
   }
-
-  for (int i = warp; i < nc; i += kHW) {
-    const float2 *wi = W + (size_t)nr * i;
-    float n2 = 0.f;
-    for (int row = lane; row < nr; row += 32) n2 = fmaf(wi[row].x, wi[row].x, fmaf(wi[row].y, wi[row].y, n2));
-    n2 = warp_sum(n2);
-    const double sigma = sqrt((double)n2);
-    const float g = t < 0.0f ? 1.0f : (sigma > (double)t ? (float)(1.0 - (double)t / sigma) : 0.0f);
-    float2 *vi = V + (size_t)nc * i;
-    for (int row = lane; row < nc; row += 32) vi[row] = make_float2(vi[row].x * g, vi[row].y * g);
-  }
+  pk_epilogue<false>(nr, nc, W, V, t);
   if (tid == 0) *sweeps_slot = converged ? sweeps : -max_sweeps;
   if (work && ul == 0) {
     atomicAdd(work + 0, (unsigned long long)n_pairs);
@@ -680,6 +764,262 @@ __global__ void __launch_bounds__(kHW * 32, KP <= 2 ? 2 : 1)
                       V_all + (size_t)blockIdx.x * vstride, t, max_sweeps, tol, negl_rel,
                       sweeps_out + blockIdx.x, work, smem_f4, o.warm, o.t_svt,
                       o.ms2 ? o.ms2[blockIdx.x / o.group] : -1.0f);
+}
+
+// ---------------------------------------------------------------------------
+// Task-graph schedule of the packed Jacobi (nr <= 256).  In a sweep the
+// column panels of a slice are paired by a round-robin tournament (pair_of
+// over P + 1 players for an odd number P of panels, P + 2 for an even one,
+// the extra players being empty): in each round a slice's pairs are disjoint,
+// a panel paired with an empty player runs its own pairs, and every pair of
+// panels meets once per sweep, so every column pair is still visited once per
+// sweep.  Each (slice, round, pair) is a task: one cross pass (pk_cross_pass)
+// or one panel's own pairs (pk_intra), with the panels read from and written
+// back to global memory.  A persistent grid takes tasks from a queue in global
+// memory; the task that completes a slice's round queues the slice's next
+// round (or, at the end of a sweep, ends the slice when no pair rotated, or at
+// the cap), so slices advance independently and every SM works on whichever
+// slice has work: at 200 x 200 x 80 the 123 slices' work spreads over all 152
+// SMs, and slices that converge early leave their share to the others.  The
+// rotation formula, tolerances and convergence test are the one-CTA-per-slice
+// kernel's; the order of the pairs within a sweep differs.
+//
+// Scratch (ints, zeroed by the host before each launch; jacobi_task_ints):
+// [0] queue head, [1] queue tail, [2] finished slices, [3] error flag;
+// per slice: sweep, round, tasks left in the round, rotated-in-this-sweep;
+// per slice (floats): tolerance, negligible squared norm;
+// the queue: cap task ids and cap ready marks (the mark of slot i is i + 1).
+constexpr unsigned long long kTaskWaitNs = 2000000000ull;  // a wait for work gives up after 2 s
+
+__device__ __forceinline__ int ld_relaxed(const int *p) { return *(const volatile int *)p; }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// The rounds of one sweep.  An odd number of panels plays a round-robin
+// tournament with one empty player (npan + 1 players, npan rounds): the panel
+// paired with it runs its own pairs.  An even number first runs every
+// panel's own pairs in one round (round 0), then the npan - 1 rounds of the
+// tournament among the panels themselves.
+__device__ __forceinline__ int tour_players(int npan) { return npan + (npan & 1); }
+__device__ __forceinline__ int tour_rounds(int npan) { return npan; }
+// pair i of round r: panels p, q (q >= npan: p's own pairs); false if empty
+__device__ __forceinline__ bool tour_pair(int npan, int r, int i, int &p, int &q) {
+  if (!(npan & 1)) {
+    if (r == 0) {
+      p = i;
+      q = npan;  // own pairs
+      return i < npan;
+    }
+    r -= 1;
+  }
+  const int np = tour_players(npan);
+  if (i >= np / 2) return false;
+  pair_of(r, i, np, p, q);
+  if (p >= npan) {
+    const int x = p;
+    p = q;
+    q = x;
+  }
+  return p < npan;
+}
+// tasks per round at most: npan (even npan, round 0) or (npan + 1) / 2
+__device__ __forceinline__ int tour_width(int npan) { return (npan & 1) ? (npan + 1) / 2 : npan; }
+
+struct TaskView {
+  int *head, *tail, *finished, *err;
+  int *sweep, *round, *left, *rot;
+  float *tol, *negl;
+  int *qtask, *qready;
+  int cap;
+  __device__ TaskView(int *sched, int ns, int cap_) : cap(cap_) {
+    head = sched;
+    tail = sched + 1;
+    finished = sched + 2;
+    err = sched + 3;
+    sweep = sched + 4;
+    round = sweep + ns;
+    left = round + ns;
+    rot = left + ns;
+    tol = (float *)(rot + ns);
+    negl = tol + ns;
+    qtask = (int *)(negl + ns);
+    qready = qtask + cap;
+  }
+  // queues the tasks of round r of slice s (one thread)
+  __device__ void push_round(int s, int r, int npan) {
+    int ids[16], c = 0;
+    for (int i = 0; i < tour_width(npan); ++i) {
+      int p, q;
+      if (tour_pair(npan, r, i, p, q)) ids[c++] = i;
+    }
+    round[s] = r;
+    left[s] = c;
+    __threadfence();
+    for (int k = 0; k < c; ++k) {
+      const int idx = atomicAdd(tail, 1);
+      qtask[idx & (cap - 1)] = s * 16 + ids[k];
+      __threadfence();
+      atomicExch(qready + (idx & (cap - 1)), idx + 1);
+    }
+  }
+};
+
+// Set-up of the task-graph run, one CTA per slice: V := I unless warm,
+// ||W||_F^2, the slice's tolerance and negligible squared norm; a slice whose
+// singular values are all cut (||W||_F <= t) ends here with 0 sweeps, the
+// others queue their first round.
+__global__ void __launch_bounds__(kHW * 32)
+    k_jacobi_task_setup(int nr, int nc, int nslices, size_t wstride, size_t vstride,
+                        float2 *W_all, float2 *V_all, float t, int max_sweeps, float tol0,
+                        float negl_rel, int *__restrict__ sweeps_out, JacOpt o, int *sched,
+                        int cap) {
+  __shared__ float s_red[32];
+  const int s = blockIdx.x;
+  TaskView tv(sched, nslices, cap);
+  float2 *W = W_all + (size_t)s * wstride, *V = V_all + (size_t)s * vstride;
+  const float fro2 = pk_setup<false>(nr, nc, W, V, o.warm, s_red);
+  const float skip_t = o.t_svt;
+  const bool cut = skip_t >= 0.0f && fro2 <= skip_t * skip_t;
+  if (cut) pk_epilogue<false>(nr, nc, W, V, t);  // every g_i is 0 (t >= 0), or V is kept
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tv.tol[s] = pk_tolerance(tol0, fro2, nc, skip_t, o.ms2 ? o.ms2[s / o.group] : -1.0f);
+    tv.negl[s] = negl_rel * fro2;
+    tv.sweep[s] = 0;
+    tv.rot[s] = 0;
+    if (cut) {
+      sweeps_out[s] = 0;
+      __threadfence();
+      atomicAdd(tv.finished, 1);
+    } else {
+      sweeps_out[s] = -max_sweeps;  // until the slice ends: a run that stops early reports it
+      tv.push_round(s, 0, (nc + kPW - 1) / kPW);
+    }
+  }
+}
+
+// The persistent worker grid: every CTA takes tasks until every slice has
+// ended (or a wait for work runs out, after kTaskWaitNs; the slices still
+// open then stay reported as capped).
+template <int KP>
+__global__ void __launch_bounds__(kHW * 32, KP <= 2 ? 2 : 1)
+    k_jacobi_tasks(int nr, int nc, int nslices, size_t wstride, size_t vstride, float2 *W_all,
+                   float2 *V_all, float t, int max_sweeps, int *__restrict__ sweeps_out,
+                   unsigned long long *__restrict__ work, int *sched, int cap) {
+  extern __shared__ float4 smem_f4[];
+  constexpr int LD2 = PkShape<KP>::LD2;
+  float4 *sW = smem_f4, *sVa = sW + kPW * LD2, *sVb = sVa + kPW * LD2;
+  __shared__ float s_na[kPW], s_nb[kPW];
+  __shared__ int s_task, s_last, s_end;
+  const int tid = threadIdx.x, ul = tid & 15, unit = tid >> 4;
+  TaskView tv(sched, nslices, cap);
+  const int npan = (nc + kPW - 1) / kPW, nrounds = tour_rounds(npan);
+  unsigned n_pairs = 0, n_rot = 0;
+  float4 aW[KP], aV[KP];
+  for (;;) {
+    // one thread claims the next queue slot and waits (bounded) until it is
+    // filled or every slice has ended
+    if (tid == 0) {
+      const int idx = atomicAdd(tv.head, 1);
+      const int slot = idx & (cap - 1);
+      const unsigned long long t0 = gtimer();
+      int task = -1;
+      for (;;) {
+        if (ld_relaxed(tv.qready + slot) == idx + 1) {
+          __threadfence();
+          task = ld_relaxed(tv.qtask + slot);
+          break;
+        }
+        if (ld_relaxed(tv.finished) >= nslices) break;
+        if (gtimer() - t0 > kTaskWaitNs) {
+          atomicExch(tv.err, 1);
+          break;
+        }
+        __nanosleep(128);
+      }
+      s_task = task;
+    }
+    __syncthreads();
+    const int task = s_task;
+    if (task < 0) break;
+    const int s = task >> 4, pi = task & 15;
+    float2 *W = W_all + (size_t)s * wstride, *V = V_all + (size_t)s * vstride;
+    const int r = ld_relaxed(tv.round + s);
+    const float tol = ((const volatile float *)tv.tol)[s];
+    const float negl = ((const volatile float *)tv.negl)[s];
+    int pa, pb;
+    tour_pair(npan, r, pi, pa, pb);  // pa is a real panel; pb >= npan: pa's own pairs
+    int rotated = 0;
+    const int ca = pa * kPW, wa = min(kPW, nc - ca);
+    pk_stage_in<true>(sW, LD2, W + (size_t)nr * ca, nr, wa, s_na);
+    pk_stage_in<true>(sVa, LD2, V + (size_t)nc * ca, nc, wa);
+    __syncthreads();
+    if (pb >= npan) {  // panel pa's own pairs
+      pk_intra<KP>(sW, sVa, s_na, wa, tol, negl, n_pairs, n_rot, rotated);
+      pk_stage_out(W + (size_t)nr * ca, sW, LD2, nr, wa);
+      pk_stage_out(V + (size_t)nc * ca, sVa, LD2, nc, wa);
+    } else {  // panel pa (registers) against panel pb (streamed)
+      const int cb = pb * kPW, wb = min(kPW, nc - cb);
+      const bool mine = unit < wa;
+      pk_to_registers<KP>(sW, sVa, aW, aV);
+      __syncthreads();
+      pk_stage_in<true>(sW, LD2, W + (size_t)nr * cb, nr, wb, s_nb);
+      pk_stage_in<true>(sVb, LD2, V + (size_t)nc * cb, nc, wb);
+      pk_cross_pass<KP>(aW, aV, mine, sW, sVb, s_nb, wb, tol, negl, n_pairs, n_rot, rotated);
+      pk_stage_out(W + (size_t)nr * cb, sW, LD2, nr, wb);
+      pk_stage_out(V + (size_t)nc * cb, sVb, LD2, nc, wb);
+      pk_from_registers<KP>(aW, aV, mine, sVa, W + (size_t)nr * ca, V + (size_t)nc * ca, nr, nc,
+                            wa);
+    }
+    // the panels are written (every thread fences its own stores); then the
+    // task counts off its slice's round
+    __threadfence();
+    rotated = __syncthreads_or(rotated);
+    if (tid == 0) {
+      if (rotated) atomicOr(tv.rot + s, 1);
+      __threadfence();
+      s_last = atomicSub(tv.left + s, 1) == 1;
+      s_end = 0;
+      if (s_last) {  // this task completed the round: queue the next, or end the slice
+        __threadfence();
+        int next = r + 1;
+        if (next == nrounds) {  // the sweep is complete
+          const int sw = ld_relaxed(tv.sweep + s) + 1;
+          const int any = atomicExch(tv.rot + s, 0);
+          if (!any)
+            s_end = sw;  // converged: a sweep without a rotation
+          else if (sw >= max_sweeps)
+            s_end = -max_sweeps;
+          else {
+            tv.sweep[s] = sw;
+            next = 0;
+          }
+        }
+        if (!s_end) tv.push_round(s, next, npan);
+      }
+    }
+    __syncthreads();
+    if (s_end) {  // the slice ended: this CTA applies its epilogue and counts it
+      pk_epilogue<true>(nr, nc, W, V, t);
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) {
+        sweeps_out[s] = s_end;
+        __threadfence();
+        atomicAdd(tv.finished, 1);
+      }
+    }
+    __syncthreads();
+  }
+  if (work && ul == 0) {
+    atomicAdd(work + 0, (unsigned long long)n_pairs);
+    atomicAdd(work + 1, (unsigned long long)n_rot);
+  }
 }
 
 // Persistent kernel for a batch of cubes: each CTA takes the next slice from
@@ -714,6 +1054,50 @@ __global__ void __launch_bounds__(kHW * 32, 1)
     else
       jacobi_pk_slice<7>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
   }
+}
+
+int task_cap(int nslices) {
+  // a slot is reused only after the ring has wrapped: queued-but-untaken
+  // tasks stay below 5 per live slice and claimed-but-unfilled slots below one
+  // per worker CTA, far under the capacity
+  int cap = 4096;
+  while (cap < 16 * nslices + 4096) cap <<= 1;
+  return cap;
+}
+
+template <int KP>
+cudaError_t launch_tasks(int nslices, int nr, int nc, size_t ws, size_t vs, float2 *W, float2 *V,
+                         float t, int max_sweeps, float tol, float negl, int *sweeps,
+                         unsigned long long *work, const JacOpt &o, cudaStream_t st) {
+  const size_t smem = sizeof(float4) * 3 * (size_t)kPW * PkShape<KP>::LD2;
+  cudaError_t e = cudaFuncSetAttribute(k_jacobi_tasks<KP>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int dev = 0, nsm = 0, occ = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jacobi_tasks<KP>, kHW * 32, smem);
+  if (e != cudaSuccess) return e;
+  const int cap = task_cap(nslices);
+  const int npan = (nc + kPW - 1) / kPW;
+  const int width = (npan & 1) ? (npan + 1) / 2 : npan;
+  // workers: the resident CTAs of every SM but the spare ones, and no more
+  // than the tasks a round offers
+  const int per_sm = occ > 0 ? occ : 1;
+  long long grid = (long long)per_sm * (nsm - (o.spare_sms < nsm ? o.spare_sms : 0));
+  const long long most = (long long)nslices * width;
+  if (grid > most) grid = most;
+  if (grid < 1) grid = 1;
+  e = cudaMemsetAsync(o.sched, 0, sizeof(int) * jacobi_task_ints(nslices), st);
+  if (e != cudaSuccess) return e;
+  k_jacobi_task_setup<<<nslices, kHW * 32, 0, st>>>(nr, nc, nslices, ws, vs, W, V, t, max_sweeps,
+                                                     tol, negl, sweeps, o, o.sched, cap);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_jacobi_tasks<KP><<<(unsigned)grid, kHW * 32, smem, st>>>(nr, nc, nslices, ws, vs, W, V, t,
+                                                               max_sweeps, sweeps, work, o.sched,
+                                                               cap);
+  return cudaGetLastError();
 }
 
 template <int KP>
@@ -820,6 +1204,25 @@ cudaError_t launch_ns_update(int nc, int nslices, size_t dstride, float2 *V, con
   return cudaGetLastError();
 }
 
+// The task graph pays when one CTA per slice would leave SMs idle for a
+// whole wave (fewer slices than resident CTAs): it spreads the slices' work
+// over every SM.  With more slices than that the per-slice kernel keeps its
+// panel in registers across the streamed panels and reads each slice's data
+// fewer times, and the task graph's extra panel traffic costs more than its
+// balance gains (measured at 256 x 256 x 191: 288 slices, 17.1 against 13.3 ms).
+bool tasks_pay(int nslices, int nr) {
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const int per_sm = nr <= 64 ? 2 : 1;  // the packed kernel's CTAs per SM
+  return nslices < nsm * per_sm;
+}
+
+size_t jacobi_task_ints(int nslices) { return 4 + 6 * (size_t)nslices + 2 * (size_t)task_cap(nslices); }
+
 size_t jacobi_batch_smem(int max_nr) {
   const int KP = (max_nr + 31) / 32;
   const int LD2 = KP <= 1 ? PkShape<1>::LD2
@@ -858,6 +1261,14 @@ cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, floa
   const float tol = 8.0f * sqrtf((float)nr) * eps;
   const float negl = o.negl_rel >= 0.0f ? o.negl_rel : ((float)nr * eps) * ((float)nr * eps);
   const size_t ws = d.P, vs = (size_t)nc * nc;
+  if (nr <= 256 && nc >= 2 && o.sched && tasks_pay(nslices, nr)) {
+    const int KP = (nr + 31) / 32;
+    if (KP <= 1) return launch_tasks<1>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
+    if (KP <= 2) return launch_tasks<2>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
+    if (KP <= 4) return launch_tasks<4>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
+    if (KP <= 7) return launch_tasks<7>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
+    return launch_tasks<8>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
+  }
   if (nr <= 256 && nc >= 2) {
     const int KP = (nr + 31) / 32;  // row pairs per lane of a half-warp
     if (KP <= 1) return launch_pk<1>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);

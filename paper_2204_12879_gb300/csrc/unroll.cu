@@ -382,6 +382,7 @@ struct lrstv_unroll {
   double *sig;         // K x (3 B h) x nc
   float2 *Hs;          // 3 B h nc^2 complex: thresholded V, then H / K'
   int *sweeps;         // K x 3 B h
+  int *jsched;         // task-graph Jacobi scratch (jacobi_task_ints(3 B h))
   float *ms2;          // 3 B: per gradient tensor, largest mean-square column norm
   int *gemm_err;
   Tables tb;
@@ -427,6 +428,7 @@ size_t unroll_layout(lrstv_unroll *u, void *base) {
   u->sig = c.take<double>((size_t)u->K * ns * d.nc);
   u->Hs = c.take<float2>(ns * d.nc * d.nc);
   u->sweeps = c.take<int>((size_t)u->K * ns);
+  u->jsched = c.take<int>(jacobi_task_ints((int)ns));
   u->ms2 = c.take<float>((size_t)3 * u->B);
   u->gemm_err = c.take<int>(1);
   carve_tables(c, d, u->tb);
@@ -509,6 +511,7 @@ int unroll_forward(lrstv_unroll *u, cudaStream_t st) {
     o.t_svt = t;
     o.ms2 = u->ms2;
     o.group = d.h;
+    o.sched = (u->flags & LRSTV_FLAG_JACOBI_PER_SLICE) ? nullptr : u->jsched;
     UCK(launch_jacobi(d, (int)ns, Wk, Vk, -1.0f, kMaxSweeps, u->sweeps + (size_t)k * ns, nullptr,
                       st, o));
     UCK(launch_sigma_scale(d, (int)ns, Wk, Vk, t, sk, u->Hs, st));
@@ -625,7 +628,8 @@ int lrstv_unroll_create(int n1, int n2, int n3, int batch, int iters, const floa
   int rc = check_shape(n1, n2, n3);
   if (rc) return rc;
   if (batch < 1 || iters < 1 || iters > 4096) return LRSTV_ERR_ARG;
-  if (flags & ~(unsigned)(LRSTV_FLAG_SIMT_GEMM | LRSTV_FLAG_WARM_START | LRSTV_FLAG_SIMT_DFT))
+  if (flags & ~(unsigned)(LRSTV_FLAG_SIMT_GEMM | LRSTV_FLAG_WARM_START | LRSTV_FLAG_SIMT_DFT |
+                          LRSTV_FLAG_JACOBI_PER_SLICE))
     return LRSTV_ERR_ARG;
   float wl[3] = {1.0f, 1.0f, 1.0f};
   if (w)

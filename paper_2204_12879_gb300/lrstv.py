@@ -22,7 +22,7 @@ __all__ = [
     "lrstv_tsvt_noalloc", "lrstv_peak_probe", "PEAK_UNITS",
     "lrstv_denoise", "BLOCK", "FLAG_F_THRESH_EXACT", "FLAG_NO_GAMMA4", "FLAG_GRAPH",
     "FLAG_STRICT", "FLAG_SIMT_GEMM", "FLAG_WARM_START", "FLAG_ISO_TV", "FLAG_BF16X3",
-    "FLAG_SIMT_DFT",
+    "FLAG_SIMT_DFT", "FLAG_JACOBI_PER_SLICE",
     "EXPORTED",
 ]
 
@@ -35,6 +35,7 @@ FLAG_WARM_START = 32
 FLAG_ISO_TV = 64
 FLAG_BF16X3 = 128
 FLAG_SIMT_DFT = 256
+FLAG_JACOBI_PER_SLICE = 512
 
 BLOCK = {"Y": 0, "L": 1, "Z": 2, "S": 3, "G1": 4, "G2": 5, "F": 6, "E": 7, "G3": 8, "G4": 9,
          "TZ": 10}
@@ -353,12 +354,12 @@ class Plan:
 
     def autotune(self, Y, iters=0, allowed=None, stream=None):
         """lrstv_plan_autotune: keeps the fastest combination of the allowed
-        flags (default: SIMT_GEMM, SIMT_DFT and WARM_START) for this plan and
-        cube.
+        flags (default: SIMT_GEMM, SIMT_DFT, JACOBI_PER_SLICE and WARM_START)
+        for this plan and cube.
         Returns (flags kept, their time in ms); leaves the plan initialised
         from Y."""
         if allowed is None:
-            allowed = FLAG_SIMT_GEMM | FLAG_SIMT_DFT | FLAG_WARM_START
+            allowed = FLAG_SIMT_GEMM | FLAG_SIMT_DFT | FLAG_JACOBI_PER_SLICE | FLAG_WARM_START
         chosen = ctypes.c_uint()
         ms = _F()
         _call("lrstv_plan_autotune", self._h, _dev(Y, self.N), int(iters), int(allowed),

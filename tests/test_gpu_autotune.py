@@ -1,6 +1,7 @@
 """The plan autotuner (lrstv_plan_autotune): it times whole short denoises
-for each combination of the allowed flags, keeps the fastest, and leaves a
-plan that still meets the FP32 parity bound against the FP64 oracle."""
+for each combination of the allowed flags (GEMM and mode-3 DFT engines,
+Jacobi schedule, warm start), keeps the fastest, and leaves a plan that still
+meets the FP32 parity bound against the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -29,7 +30,8 @@ def _noisy(shape, seed):
 def test_autotune_keeps_a_candidate_and_parity(L, orc, shape):
     clean, Y = _noisy(shape, 3)
     n1, n2, _ = shape
-    allowed = L.FLAG_SIMT_GEMM | L.FLAG_WARM_START
+    # the default search: GEMM engine, mode-3 DFT engine, Jacobi schedule, warm start
+    allowed = L.FLAG_SIMT_GEMM | L.FLAG_SIMT_DFT | L.FLAG_JACOBI_PER_SLICE | L.FLAG_WARM_START
     with L.Plan(*shape, L.Params.make(n1, n2, max_iter=20, flags=L.FLAG_GRAPH)) as pl:
         flags, ms = pl.autotune(dev(Y), iters=10)
         assert (flags & ~allowed) == L.FLAG_GRAPH  # only the allowed bits move

@@ -1,6 +1,7 @@
 """Batched uneven cubes (lrstv_batch_*): every cube of a batch follows
 Algorithm 1 exactly as a single plan does, so its outputs must equal a
-standalone plan's run on the same input bit for bit; one cube is also checked
+standalone plan's run on the same input bit for bit (the plan made with
+LRSTV_FLAG_JACOBI_PER_SLICE, the Jacobi order a batch runs); one cube is also checked
 against the FP64 oracle.  The shapes mix slice heights of the persistent
 kernel's variants, a transposed slice (n1 < n2) and a cube taller than the
 persistent kernel takes (separate Jacobi launch)."""
@@ -54,7 +55,8 @@ def test_batch_equals_single_plans(L, warm):
             st = b.plan(i).stats()
             assert st.iters == iters and st.jacobi_unconverged == 0
     for i, sh in enumerate(SHAPES):
-        with L.Plan(*sh, params[i]) as pl:
+        # a batch runs each slice's Jacobi sweeps in one CTA: the plan's same order
+        with L.Plan(*sh, _params(L, sh, i, iters, flags | L.FLAG_JACOBI_PER_SLICE)) as pl:
             X, S = pl.run(Ys[i])
             torch.cuda.synchronize()
         assert torch.equal(X, Xs[i]), sh

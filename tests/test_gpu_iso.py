@@ -128,8 +128,10 @@ def test_iso_batch_equals_plans(L):
         Xs, _ = b.run(Ys)
         torch.cuda.synchronize()
         got = [x.cpu() for x in Xs]
+    p1 = L.Params.make(32, 32, max_iter=6,
+                       flags=L.FLAG_ISO_TV | L.FLAG_WARM_START | L.FLAG_JACOBI_PER_SLICE)
     for i, sh in enumerate(shapes):
-        with L.Plan(*sh, p) as pl:
+        with L.Plan(*sh, p1) as pl:
             X, _ = pl.run(Ys[i])
             torch.cuda.synchronize()
             assert torch.equal(X.cpu(), got[i]), i

@@ -232,8 +232,9 @@ def test_tucker_inside_a_batch_equals_the_plan(L):
         Xs, _ = b.run(Ys)
         torch.cuda.synchronize()
         got = [x.cpu() for x in Xs]
+    p1 = L.Params.make(24, 20, max_iter=6, flags=L.FLAG_JACOBI_PER_SLICE)  # a batch's order
     for i, sh in enumerate(shapes):
-        with L.Plan(*sh, p) as pl:
+        with L.Plan(*sh, p1) as pl:
             if i == 1:
                 pl.set_tucker((3, 3, 3))
             X, _ = pl.run(Ys[i])
