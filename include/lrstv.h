@@ -325,7 +325,7 @@ int lrstv_denoise(const float *Y, int n1, int n2, int n3, const lrstv_params *pa
  *          may differ.  Parameters are fixed when the batch is created.
  * The batch owns one plan per cube (lrstv_batch_plan lends it for stats and
  * state export; do not destroy it or change its parameters) and one small
- * allocation for the work list.  Slices taller than 224 rows (max(n1, n2))
+ * allocation for the work list.  Slices taller than 256 rows (max(n1, n2))
  * take a separate per-cube Jacobi launch.  The persistent launch is recorded
  * in cube 0's profile (lrstv_profile_*). */
 typedef struct lrstv_batch lrstv_batch;

@@ -1111,6 +1111,7 @@ struct lrstv_batch {
   size_t smem;
   int *big;              // cubes whose slices take their own Jacobi launch
   int nbig;
+  int max_nr;  // the tallest slice in the persistent work list
   cudaStream_t cap_stream;
   cudaGraphExec_t gexec;
   const float **gY;
@@ -1167,7 +1168,7 @@ int batch_e_step(lrstv_batch *b, cudaStream_t st) {
     Span sp(prof, LRSTV_K_JACOBI, st);
     CK(launch_jacobi_batch(b->d_tasks, b->ntasks, b->d_counter, mu, kMaxSweeps,
                            prof->on ? prof->d_work : nullptr, b->grid, b->smem, st, warm,
-                           wflag ? 1 : 0));
+                           wflag ? 1 : 0, b->max_nr));
   }
   for (int k = 0; k < b->nbig; ++k) {
     lrstv_plan *pl = b->plans[b->big[k]];
@@ -1318,6 +1319,7 @@ int lrstv_batch_create(int ncubes, const int *dims, const lrstv_params *params,
     }
     b->grid = ntasks < sms ? ntasks : sms;  // one 512-thread CTA fills an SM's registers
     b->smem = jacobi_batch_smem(maxnr);
+    b->max_nr = maxnr;
   }
   if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();

@@ -191,13 +191,14 @@ struct SliceTask {
   const float *ms2;  // the slice's group value of launch_group_ms2 (may be null)
 };
 // Largest slice height the persistent batch kernel takes.
-constexpr int kBatchMaxNr = 224;  // keeps the persistent kernel to a few bytes of spills
+constexpr int kBatchMaxNr = 256;  // the packed kernel's tallest slice
 size_t jacobi_batch_smem(int max_nr);
 // Persistent work-list Jacobi over `ntasks` slices; *counter must be 0.  warm:
 // as launch_jacobi; keep: V left unscaled (threshold taken as negative).
+// max_nr: the tallest slice (up to 256 rows).
 cudaError_t launch_jacobi_batch(const SliceTask *tasks, int ntasks, int *counter, double mu,
                                 int max_sweeps, unsigned long long *work, int grid, size_t smem,
-                                cudaStream_t st, int warm = 0, int keep = 0);
+                                cudaStream_t st, int warm, int keep, int max_nr);
 
 // ------------------------------------------------------------------- api.cu
 constexpr size_t kAlign = 256;

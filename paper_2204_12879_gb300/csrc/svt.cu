@@ -1027,6 +1027,10 @@ __global__ void __launch_bounds__(kHW * 32, KP <= 2 ? 2 : 1)
 // runs the same jacobi_pk_slice as the one-slice kernel on it.  Threshold and
 // tolerances are formed exactly as the per-cube launch forms them, so the two
 // paths agree bit for bit.
+// KPMAX: the tallest slice's row pairs per lane.  Slices of 225-256 rows (KP 8)
+// make the kernel spill some 380 bytes a thread, so only batches that hold
+// such slices take that instance.
+template <int KPMAX>
 __global__ void __launch_bounds__(kHW * 32, 1)
     k_jacobi_batch(const SliceTask *__restrict__ tasks, int ntasks, int *counter, double mu,
                    int max_sweeps, unsigned long long *work, int warm, int keep) {
@@ -1051,8 +1055,10 @@ __global__ void __launch_bounds__(kHW * 32, 1)
       jacobi_pk_slice<2>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
     else if (KP <= 4)
       jacobi_pk_slice<4>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
-    else
+    else if (KPMAX <= 7 || KP <= 7)
       jacobi_pk_slice<7>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
+    else
+      jacobi_pk_slice<KPMAX>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
   }
 }
 
@@ -1235,13 +1241,18 @@ size_t jacobi_batch_smem(int max_nr) {
 
 cudaError_t launch_jacobi_batch(const SliceTask *tasks, int ntasks, int *counter, double mu,
                                 int max_sweeps, unsigned long long *work, int grid, size_t smem,
-                                cudaStream_t st, int warm, int keep) {
+                                cudaStream_t st, int warm, int keep, int max_nr) {
   if (ntasks <= 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_jacobi_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  const bool tall = max_nr > 224;
+  cudaError_t e = cudaFuncSetAttribute(tall ? k_jacobi_batch<8> : k_jacobi_batch<7>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_jacobi_batch<<<grid, kHW * 32, smem, st>>>(tasks, ntasks, counter, mu, max_sweeps, work, warm,
-                                                keep);
+  if (tall)
+    k_jacobi_batch<8><<<grid, kHW * 32, smem, st>>>(tasks, ntasks, counter, mu, max_sweeps, work,
+                                                     warm, keep);
+  else
+    k_jacobi_batch<7><<<grid, kHW * 32, smem, st>>>(tasks, ntasks, counter, mu, max_sweeps, work,
+                                                     warm, keep);
   return cudaGetLastError();
 }
 

@@ -562,14 +562,31 @@ __global__ void __launch_bounds__(kThreads, KIND == 1 ? 1 : 2) k_cgemm_tc(CGemm 
     } else if (KIND == 2 && gm < gM) {
       const float inv = 1.0f / (float)f.n3;
       const size_t base = (size_t)b * f.N + gm;
+      const bool g4 = f.mode == 1 && f.gamma4;
+      // eight columns at a time: their Gamma4 and F loads are issued together
+      // before any is used
 #pragma unroll
-      for (int c = 0; c < TN / 2; ++c) {
-        const int n = n0 + colh + c;
-        if (n >= gN) break;
-        const size_t v = base + f.P * n;
-        const float r = accRe[c] * inv;
-        f.out[v] = r;
-        if (f.mode == 1 && f.gamma4) f.G4[v] = f.G4[v] + f.mu * (r - f.F[v]);
+      for (int c0 = 0; c0 < TN / 2; c0 += 8) {
+        float g[8], fv[8];
+        if (g4) {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const int n = n0 + colh + c0 + c;
+            const bool in = n < gN;
+            const size_t v = base + f.P * (in ? n : 0);
+            g[c] = in ? f.G4[v] : 0.0f;
+            fv[c] = in ? f.F[v] : 0.0f;
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int n = n0 + colh + c0 + c;
+          if (n >= gN) break;
+          const size_t v = base + f.P * n;
+          const float r = accRe[c0 + c] * inv;
+          f.out[v] = r;
+          if (g4) f.G4[v] = g[c] + f.mu * (r - fv[c]);
+        }
       }
     } else if (KIND == 0 && gm < g.M) {
 #pragma unroll
