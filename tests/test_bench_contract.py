@@ -124,8 +124,11 @@ def test_peaks_measured_or_derived():
     m = bench.derived_peaks(pk, "measured", probes, 152)
     assert m["fp32"] == 72.0 and m["tf32"] == 900.0 and "fp32_fma2" in m["fp32_source"]
     shape = (200, 200, 80)
-    kernels = {"cgemm_e": {"launches": 1, "ms_per_launch": 1.0}}
-    f = bench.tensor_fracs(kernels, shape, "tf32x3", m)["cgemm_e"]
+    kernels = {"cgemm_e": {"launches": 1, "ms_per_launch": 1.0},
+               "cgemm_z": {"launches": 4, "ms_per_launch": 1.0}}
+    fr = bench.tensor_fracs(kernels, shape, "tf32x3", m)
+    assert "cgemm_z" not in fr  # side stream: its in-region time includes waits
+    f = fr["cgemm_e"]
     useful = 8 * 200 * 200 * 200 * 3 * 41
     assert f["useful_tflops"] == pytest.approx(useful / 1e-3 / 1e12)
     assert f["frac"] == pytest.approx(3 * useful / 1e-3 / 1e12 / 900.0)
