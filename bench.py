@@ -638,12 +638,16 @@ def run_batch(args):
         clk = clocks.stop()
         unconv = sum(b.plan(i).stats().jacobi_unconverged for i in range(len(shapes)))
         # profiled pass over the same iterations of the denoise, for the
-        # persistent Jacobi's share
+        # persistent Jacobi's share (cube 0's profile) and the launches of a
+        # step (every group's launches are in the profile of its first cube)
+        ngroups, _ = b.groups()
         b.init(Ys)
         for _ in range(first):
             b.iterate(1)
-        p0 = b.plan(0)
-        p0.profile_enable(True)
+        plans = [b.plan(i) for i in range(len(shapes))]
+        for p in plans:
+            p.profile_enable(True)
+        p0 = plans[0]
         q0, q1 = ev(), ev()
         q0.record(stream)
         done = first
@@ -657,7 +661,9 @@ def run_batch(args):
         torch.cuda.synchronize()
         ms_prof = q0.elapsed_time(q1)
         prof = p0.profile_read()
-        p0.profile_enable(False)
+        spans = sum(sum(p.profile_read().launches) for p in plans)
+        for p in plans:
+            p.profile_enable(False)
     # unbatched comparison: the same cubes, one plan after another, over the
     # iterations right after the batch's warm-up (the first iterations, whose
     # thresholds cut every singular value, run no Jacobi sweep)
@@ -684,7 +690,13 @@ def run_batch(args):
         "config": {"workload": BATCH["desc"], "cubes": n,
                    "shapes": {f"{a}x{b_}x{c}": shapes.count((a, b_, c)) for (a, b_, c) in sorted(set(shapes))},
                    "fourier_slices_per_step": slices, "cubes_per_s": value / BATCH["iters"],
-                   "jacobi_start": args.jacobi_start},
+                   "jacobi_start": args.jacobi_start,
+                   "groups": ngroups},
+        "gpu_launches": int(spans),
+        "launches_per_step": {"profiled": spans / args.steps, "groups": ngroups,
+                              "note": "one launch per kernel and group of equal shape and "
+                                      "parameters, one persistent Jacobi launch; the profiler "
+                                      "brackets the DFT, GEMM, stencil and Jacobi launches"},
         "jacobi_persistent": {"launches": prof.launches[6],
                               "ms_per_launch": prof.ms[6] / max(prof.launches[6], 1),
                               "share_of_step": prof.ms[6] / max(ms_prof, 1e-9),

@@ -313,26 +313,37 @@ int lrstv_denoise(const float *Y, int n1, int n2, int n3, const lrstv_params *pa
 
 /* ------------------------------------------------------------ batches */
 /* A batch of independent cubes of possibly different shapes, run in
- * lockstep.  Each ADMM step launches the cheap per-cube kernels for every cube
- * and ONE persistent Jacobi launch that works through the Fourier slices of
- * all cubes (largest first) from a shared work list, so an uneven batch keeps
- * every SM busy.  Each cube follows Algorithm 1 exactly as a single plan does
- * (bit-identical results); the paper treats one cube at a time, and batching
- * is this library's serving form.
+ * lockstep.  The cubes are kept in groups of one shape and one parameter set,
+ * whose state the batch lays out as packed batches (block by block, the
+ * group's cubes back to back).  Each ADMM step launches every kernel but the
+ * Jacobi once per group, for all of its cubes, and ONE persistent Jacobi
+ * launch that works through the Fourier slices of all cubes (largest first)
+ * from a shared work list, so an uneven batch keeps every SM busy and a
+ * step's launches grow with the number of groups, not of cubes.  Each cube
+ * follows Algorithm 1 exactly as a single plan does (bit-identical results);
+ * the paper treats one cube at a time, and batching is this library's
+ * serving form.
  *  dims    3*ncubes ints: n1, n2, n3 of each cube.
  *  params  ncubes structs; mu0, rho, mu_max, max_iter and flags must agree
  *          (the cubes share one penalty schedule), tau, alpha, lambda and w
  *          may differ.  Parameters are fixed when the batch is created.
  * The batch owns one plan per cube (lrstv_batch_plan lends it for stats and
- * state export; do not destroy it or change its parameters) and one small
- * allocation for the work list.  Slices taller than 256 rows (max(n1, n2))
- * take a separate per-cube Jacobi launch.  The persistent launch is recorded
- * in cube 0's profile (lrstv_profile_*). */
+ * state export; do not destroy it or change its parameters), one allocation
+ * per group and one small allocation for the work list.  Slices taller than
+ * 256 rows (max(n1, n2)) take a separate Jacobi launch per group.  The
+ * persistent launch is recorded in cube 0's profile (lrstv_profile_*), a
+ * group's other launches in the profile of its first cube.  A cube whose plan
+ * has the Tucker L-update (lrstv_plan_set_tucker) takes its own launches for
+ * steps 1 and 2. */
 typedef struct lrstv_batch lrstv_batch;
 int lrstv_batch_create(int ncubes, const int *dims, const lrstv_params *params,
                        lrstv_batch **batch);
 int lrstv_batch_destroy(lrstv_batch *batch);
 int lrstv_batch_size(const lrstv_batch *batch, int *ncubes);
+/* Number of groups (distinct shape and parameter sets) and, in group_of
+ * (ncubes ints, may be NULL), each cube's group, numbered in order of first
+ * appearance.  ERR_ARG for a NULL batch or ngroups. */
+int lrstv_batch_groups(const lrstv_batch *batch, int *ngroups, int *group_of);
 int lrstv_batch_plan(const lrstv_batch *batch, int i, lrstv_plan **plan);
 /* Y: host array of ncubes device pointers (N_i floats each). */
 int lrstv_batch_init(lrstv_batch *batch, const float *const *Y, void *stream);

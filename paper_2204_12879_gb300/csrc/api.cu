@@ -243,6 +243,7 @@ struct lrstv_plan {
   int iter;
   void *arena;
   size_t arena_bytes;
+  int own_arena;  // 0: the plan is one of a batch group's, whose memory the batch owns
   float *Y, *L, *Z, *S, *G1, *G2, *F, *E, *G3, *G4, *T;
   float2 *specA, *specB, *V;
   float2 *Vs;     // V diag g for the reconstruction (warm start keeps V itself)
@@ -302,9 +303,9 @@ GemmSel plan_gemm(const lrstv_plan *pl) {
 // One Newton-Schulz step on every slice's V on stream st: C = V V^H (into
 // Cscr), D = C V (into Dscr, slice stride dstride), V := 1.5 V - 0.5 D.
 cudaError_t ns_basis(lrstv_plan *pl, float2 *Cscr, float2 *Dscr, long long dstride,
-                     cudaStream_t st) {
+                     cudaStream_t st, int nb = 1) {
   const Dims &d = pl->d;
-  const int ns = 3 * d.h;
+  const int ns = 3 * d.h * nb;
   const GemmSel gs = plan_gemm(pl);
   const long long nc2 = (long long)d.nc * d.nc;
   auto run = [&](const CGemm &g) {
@@ -328,16 +329,17 @@ cudaError_t ns_basis(lrstv_plan *pl, float2 *Cscr, float2 *Dscr, long long dstri
 
 // Warm start of a plan's E-step: the Newton-Schulz step on V (unless it
 // already ran, ns_ready), then W = A V into Wout (A, Wout, Dscr: the plan's
-// specA / specB in either role; Dscr may be Wout).
+// specA / specB in either role; Dscr may be Wout).  nb > 1: the first plan of
+// a batch group, for all nb cubes of the group.
 cudaError_t warm_basis(lrstv_plan *pl, const float2 *A, float2 *Wout, float2 *Dscr,
-                       cudaStream_t st) {
+                       cudaStream_t st, int nb = 1) {
   const Dims &d = pl->d;
-  const int ns = 3 * d.h;
+  const int ns = 3 * d.h * nb;
   const long long nc2 = (long long)d.nc * d.nc, P = (long long)d.P;
   cudaError_t e;
   if (pl->ns_ready) {
     if ((e = cudaStreamWaitEvent(st, pl->ev_ns, 0)) != cudaSuccess) return e;
-  } else if ((e = ns_basis(pl, pl->Vs, Dscr, P, st)) != cudaSuccess) {
+  } else if ((e = ns_basis(pl, pl->Vs, Dscr, P, st, nb)) != cudaSuccess) {
     return e;
   }
   pl->ns_ready = 0;
@@ -413,35 +415,51 @@ cudaError_t tsvt_warm(lrstv_plan *pl, float ycoef, float t, float mu, int gamma4
   return launch_c2r3(d, 3, R, 1, pl->tb.tw3, pl->E, 1, pl->G4, pl->F, mu, gamma4, st, gs);
 }
 
-size_t plan_layout(lrstv_plan *pl, void *base) {
-  const Dims &d = pl->d;
+// Block `field` of m plans: one piece of m * count elements, plan i's part i.
+template <class T>
+void take_each(Carver &c, lrstv_plan *const *pls, int m, size_t count, T *lrstv_plan::*field) {
+  T *p = c.take<T>((size_t)m * count);
+  for (int i = 0; i < m; ++i) pls[i]->*field = p ? p + (size_t)i * count : nullptr;
+}
+
+// The memory of m plans of one shape (m = 1: a plan on its own) carved out of
+// base (null: only the size), block by block: each block holds the m plans'
+// parts back to back, so that the m cubes form a packed batch (cube i's state
+// cube at i N floats, its Fourier slices at 3 i h P complex, ...) that one
+// launch per kernel serves.  The DFT tables are carved once and shared.
+size_t group_layout(lrstv_plan *const *pls, int m, void *base) {
+  const Dims &d = pls[0]->d;
+  const size_t h = (size_t)d.h, nc2 = (size_t)d.nc * d.nc;
   Carver c(base);
-  pl->Y = c.take<float>(d.N);
-  pl->L = c.take<float>(d.N);
-  pl->Z = c.take<float>(d.N);
-  pl->S = c.take<float>(d.N);
-  pl->G1 = c.take<float>(d.N);
-  pl->G2 = c.take<float>(d.N);
-  pl->F = c.take<float>(3 * d.N);
-  pl->E = c.take<float>(3 * d.N);
-  pl->G3 = c.take<float>(3 * d.N);
-  pl->G4 = c.take<float>(3 * d.N);
-  pl->T = c.take<float>(d.N);
-  pl->specA = c.take<float2>(3 * (size_t)d.h * d.P);
-  pl->specB = c.take<float2>(3 * (size_t)d.h * d.P);
-  pl->V = c.take<float2>(3 * (size_t)d.h * d.nc * d.nc);
-  pl->Vs = c.take<float2>(3 * (size_t)d.h * d.nc * d.nc);
-  pl->Vn1 = c.take<float2>(3 * (size_t)d.h * d.nc * d.nc);
-  pl->Vn2 = c.take<float2>(3 * (size_t)d.h * d.nc * d.nc);
-  pl->ms2 = c.take<float>(3);
-  pl->zA = c.take<float2>((size_t)d.h * d.P);
-  pl->zB = c.take<float2>((size_t)d.h * d.P);
-  carve_tables(c, d, pl->tb);
-  pl->res = c.take<unsigned>(2 * (size_t)kResRing);
-  pl->sweeps = c.take<int>(3 * (size_t)d.h);
-  pl->jsched = c.take<int>(jacobi_task_ints(3 * d.h));
-  pl->gemm_err = c.take<int>(1);
-  pl->prof.d_work = c.take<unsigned long long>(2);
+  take_each(c, pls, m, d.N, &lrstv_plan::Y);
+  take_each(c, pls, m, d.N, &lrstv_plan::L);
+  take_each(c, pls, m, d.N, &lrstv_plan::Z);
+  take_each(c, pls, m, d.N, &lrstv_plan::S);
+  take_each(c, pls, m, d.N, &lrstv_plan::G1);
+  take_each(c, pls, m, d.N, &lrstv_plan::G2);
+  take_each(c, pls, m, 3 * d.N, &lrstv_plan::F);
+  take_each(c, pls, m, 3 * d.N, &lrstv_plan::E);
+  take_each(c, pls, m, 3 * d.N, &lrstv_plan::G3);
+  take_each(c, pls, m, 3 * d.N, &lrstv_plan::G4);
+  take_each(c, pls, m, d.N, &lrstv_plan::T);
+  take_each(c, pls, m, 3 * h * d.P, &lrstv_plan::specA);
+  take_each(c, pls, m, 3 * h * d.P, &lrstv_plan::specB);
+  take_each(c, pls, m, 3 * h * nc2, &lrstv_plan::V);
+  take_each(c, pls, m, 3 * h * nc2, &lrstv_plan::Vs);
+  take_each(c, pls, m, 3 * h * nc2, &lrstv_plan::Vn1);
+  take_each(c, pls, m, 3 * h * nc2, &lrstv_plan::Vn2);
+  take_each(c, pls, m, 3, &lrstv_plan::ms2);
+  take_each(c, pls, m, h * d.P, &lrstv_plan::zA);
+  take_each(c, pls, m, h * d.P, &lrstv_plan::zB);
+  Tables tb;
+  carve_tables(c, d, tb);
+  for (int i = 0; i < m; ++i) pls[i]->tb = tb;
+  take_each(c, pls, m, 2 * (size_t)kResRing, &lrstv_plan::res);
+  take_each(c, pls, m, 3 * h, &lrstv_plan::sweeps);
+  take_each(c, pls, m, (size_t)jacobi_task_ints(3 * d.h), &lrstv_plan::jsched);
+  take_each(c, pls, m, 1, &lrstv_plan::gemm_err);
+  unsigned long long *work = c.take<unsigned long long>(2 * (size_t)m);
+  for (int i = 0; i < m; ++i) pls[i]->prof.d_work = work ? work + 2 * (size_t)i : nullptr;
   return c.off;
 }
 
@@ -550,6 +568,60 @@ int iterate_async(lrstv_plan *pl, int iters, cudaStream_t st) {
     pl->ns_req = 0;
     if (rc != LRSTV_OK) return rc;
     if ((rc = lrstv_step_mu(pl)) != LRSTV_OK) return rc;
+  }
+  return LRSTV_OK;
+}
+
+void plan_object_free(lrstv_plan *pl);
+
+// A plan object of one shape and parameter set with its streams and events,
+// but no device memory (group_layout and arena_start give it that).
+int plan_object(int n1, int n2, int n3, const lrstv_params *params, lrstv_plan **plan) {
+  int rc = check_shape(n1, n2, n3);
+  if (rc) return rc;
+  if ((rc = check_params(params))) return rc;
+  lrstv_plan *pl = new (std::nothrow) lrstv_plan();
+  if (!pl) return LRSTV_ERR_ALLOC;
+  pl->d = make_dims(n1, n2, n3);
+  pl->prm = *params;
+  pl->giters = -1;
+  pl->mu = pl->prm.mu0;
+  int lo_prio = 0, hi_prio = 0;
+  if (cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&pl->side, cudaStreamNonBlocking, lo_prio) != cudaSuccess ||
+      cudaEventCreateWithFlags(&pl->ev_fs, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&pl->ev_side, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&pl->ev_sig, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&pl->ev_ns, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    plan_object_free(pl);
+    return LRSTV_ERR_CUDA;
+  }
+  *plan = pl;
+  return LRSTV_OK;
+}
+
+void plan_object_free(lrstv_plan *pl) {
+  if (!pl) return;
+  if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+  if (pl->side) cudaStreamDestroy(pl->side);
+  if (pl->ev_fs) cudaEventDestroy(pl->ev_fs);
+  if (pl->ev_side) cudaEventDestroy(pl->ev_side);
+  if (pl->ev_sig) cudaEventDestroy(pl->ev_sig);
+  if (pl->ev_ns) cudaEventDestroy(pl->ev_ns);
+  delete pl;
+}
+
+// Zeroes a fresh arena of `bytes` and fills the DFT tables that pl holds
+// (shared by every plan carved from the arena); returns when done.
+int arena_start(lrstv_plan *pl, void *arena, size_t bytes) {
+  if (cudaMemsetAsync(arena, 0, bytes, pl->cap_stream) != cudaSuccess ||
+      launch_tables(pl->d, pl->prm.w, pl->tb.tw3, pl->tb.F1, pl->tb.G1, pl->tb.F2, pl->tb.G2,
+                    pl->tb.lam1, pl->tb.lam2, pl->tb.lam3, pl->cap_stream) != cudaSuccess ||
+      cudaStreamSynchronize(pl->cap_stream) != cudaSuccess) {
+    cudaGetLastError();
+    return LRSTV_ERR_CUDA;
   }
   return LRSTV_OK;
 }
@@ -690,45 +762,25 @@ int lrstv_profile_read(lrstv_plan *pl, lrstv_profile *out) {
 int lrstv_plan_create(int n1, int n2, int n3, const lrstv_params *params, lrstv_plan **plan) {
   if (!plan) return LRSTV_ERR_ARG;
   *plan = nullptr;
-  int rc = check_shape(n1, n2, n3);
-  if (rc) return rc;
-  if ((rc = check_params(params))) return rc;
-  lrstv_plan *pl = new (std::nothrow) lrstv_plan();
-  if (!pl) return LRSTV_ERR_ALLOC;
-  pl->d = make_dims(n1, n2, n3);
-  pl->prm = *params;
-  pl->giters = -1;
-  pl->arena_bytes = plan_layout(pl, nullptr);
-  if (cudaMalloc(&pl->arena, pl->arena_bytes) != cudaSuccess) {
+  lrstv_plan *pl = nullptr;
+  int rc = plan_object(n1, n2, n3, params, &pl);
+  if (rc != LRSTV_OK) return rc;
+  const size_t bytes = group_layout(&pl, 1, nullptr);
+  void *arena = nullptr;
+  if (cudaMalloc(&arena, bytes) != cudaSuccess) {
     cudaGetLastError();
-    delete pl;
+    plan_object_free(pl);
     return LRSTV_ERR_ALLOC;
   }
-  plan_layout(pl, pl->arena);
-  int lo_prio = 0, hi_prio = 0;
-  if (cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) != cudaSuccess ||
-      cudaStreamCreateWithPriority(&pl->side, cudaStreamNonBlocking, lo_prio) != cudaSuccess ||
-      cudaEventCreateWithFlags(&pl->ev_fs, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&pl->ev_side, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&pl->ev_sig, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&pl->ev_ns, cudaEventDisableTiming) != cudaSuccess ||
-      cudaMemsetAsync(pl->arena, 0, pl->arena_bytes, pl->cap_stream) != cudaSuccess ||
-      launch_tables(pl->d, pl->prm.w, pl->tb.tw3, pl->tb.F1, pl->tb.G1, pl->tb.F2, pl->tb.G2,
-                    pl->tb.lam1, pl->tb.lam2, pl->tb.lam3, pl->cap_stream) != cudaSuccess ||
-      cudaStreamSynchronize(pl->cap_stream) != cudaSuccess) {
-    cudaGetLastError();
-    if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
-    if (pl->side) cudaStreamDestroy(pl->side);
-    if (pl->ev_fs) cudaEventDestroy(pl->ev_fs);
-    if (pl->ev_side) cudaEventDestroy(pl->ev_side);
-    if (pl->ev_sig) cudaEventDestroy(pl->ev_sig);
-    if (pl->ev_ns) cudaEventDestroy(pl->ev_ns);
-    cudaFree(pl->arena);
-    delete pl;
-    return LRSTV_ERR_CUDA;
+  group_layout(&pl, 1, arena);
+  pl->arena = arena;
+  pl->arena_bytes = bytes;
+  pl->own_arena = 1;
+  if ((rc = arena_start(pl, arena, bytes)) != LRSTV_OK) {
+    cudaFree(arena);
+    plan_object_free(pl);
+    return rc;
   }
-  pl->mu = pl->prm.mu0;
   *plan = pl;
   return LRSTV_OK;
 }
@@ -747,7 +799,7 @@ int lrstv_plan_destroy(lrstv_plan *pl) {
   if (cudaEventDestroy(pl->ev_side) != cudaSuccess) rc = LRSTV_ERR_CUDA;
   if (cudaEventDestroy(pl->ev_sig) != cudaSuccess) rc = LRSTV_ERR_CUDA;
   if (cudaEventDestroy(pl->ev_ns) != cudaSuccess) rc = LRSTV_ERR_CUDA;
-  if (cudaFree(pl->arena) != cudaSuccess) rc = LRSTV_ERR_CUDA;
+  if (pl->own_arena && cudaFree(pl->arena) != cudaSuccess) rc = LRSTV_ERR_CUDA;
   if (pl->tk_mem && cudaFree(pl->tk_mem) != cudaSuccess) rc = LRSTV_ERR_CUDA;
   delete pl;
   return rc;
@@ -1100,17 +1152,33 @@ int lrstv_denoise(const float *Y, int n1, int n2, int n3, const lrstv_params *pa
 }  // extern "C"
 
 // ------------------------------------------------------------------ batches
+// A batch keeps its cubes in groups of one shape and one parameter set.  A
+// group's plans are carved from one arena by group_layout, so that its cubes
+// form a packed batch: each step of an iteration is one launch per kernel for
+// the whole group (the stencils, the mode-3 and spatial DFTs, the GEMMs and
+// the small per-slice kernels), and the Jacobi is one persistent launch over
+// the slices of every group.  A batched step's launches thus grow with the
+// number of distinct shapes, not with the number of cubes.  The arithmetic
+// of every cube is that of a plan of its own, so the results are the same
+// bit for bit.
+struct BatchGroup {
+  int m;              // cubes
+  lrstv_plan **pls;   // their plans, in batch order; pls[0] holds the group's block bases
+  void *arena;
+  int big;            // slices taller than the persistent kernel takes: one launch
+};
+
 struct lrstv_batch {
   int n;
   lrstv_plan **plans;
+  int ngroups;
+  BatchGroup *groups;
   void *arena;           // the slice work list and its counter
   SliceTask *d_tasks;
   int ntasks;
   int *d_counter;
   int grid;
   size_t smem;
-  int *big;              // cubes whose slices take their own Jacobi launch
-  int nbig;
   int max_nr;  // the tallest slice in the persistent work list
   cudaStream_t cap_stream;
   cudaGraphExec_t gexec;
@@ -1133,8 +1201,13 @@ void batch_free(lrstv_batch *b) {
   if (b->plans)
     for (int i = 0; i < b->n; ++i)
       if (b->plans[i]) lrstv_plan_destroy(b->plans[i]);
+  if (b->groups)
+    for (int k = 0; k < b->ngroups; ++k) {
+      if (b->groups[k].arena) cudaFree(b->groups[k].arena);
+      delete[] b->groups[k].pls;
+    }
+  delete[] b->groups;
   delete[] b->plans;
-  delete[] b->big;
   delete[] b->gY;
   delete[] b->gX;
   delete[] b->gS;
@@ -1150,17 +1223,70 @@ int task_cmp(const void *x, const void *y) {
   return a->W < b->W ? -1 : (a->W > b->W ? 1 : 0);  // a fixed order among equals
 }
 
+bool group_tucker(const BatchGroup &g) {
+  for (int i = 0; i < g.m; ++i)
+    if (g.pls[i]->tucker) return true;
+  return false;
+}
+
+// Steps 1 and 2 (L, T_z, Z-solve) of every cube of a group.  Cubes with the
+// Tucker L-update take their own launches.
+int group_l_tz_z(const BatchGroup &g, cudaStream_t st) {
+  int rc;
+  if (group_tucker(g)) {
+    for (int i = 0; i < g.m; ++i) {
+      if ((rc = lrstv_step_l_tz(g.pls[i], st)) != LRSTV_OK) return rc;
+      if ((rc = lrstv_step_z(g.pls[i], st)) != LRSTV_OK) return rc;
+    }
+    return LRSTV_OK;
+  }
+  lrstv_plan *p = g.pls[0];
+  const float mu = (float)p->mu;
+  {
+    Span sp(&p->prof, LRSTV_K_L_TZ, st);
+    CK(launch_l_tz(p->d, p->Y, p->S, p->Z, p->G1, p->G2, p->F, p->G3, mu, p->prm.w, p->L, p->T,
+                   st, g.m));
+  }
+  CK(zsolve_core(p->d, g.m, p->tb, p->T, mu, p->Z, p->specA, p->specB, st, &p->prof,
+                 plan_gemm(p)));
+  return LRSTV_OK;
+}
+
+// Steps 3, 5, 6 (F, S, Gamma1..3) of every cube of a group; each cube's
+// residual maxima go to its own ring slot.
+int group_fs_dual(const BatchGroup &g, cudaStream_t st) {
+  lrstv_plan *p = g.pls[0];
+  const double mu = p->mu;
+  const double thr_f = (p->prm.flags & LRSTV_FLAG_F_THRESH_EXACT) ? p->prm.tau / (2.0 * mu)
+                                                                   : p->prm.tau / mu;
+  const double thr_s = p->prm.lambda / mu;
+  const size_t rs = 2 * (size_t)kResRing;  // words between consecutive cubes' rings
+  unsigned *slot = p->res + 2 * (size_t)(p->iter % kResRing);
+  CK(cudaMemset2DAsync(slot, rs * sizeof(unsigned), 0, 2 * sizeof(unsigned), (size_t)g.m, st));
+  Span sp(&p->prof, LRSTV_K_FS_DUAL, st);
+  CK(launch_fs_dual(p->d, p->Y, p->L, p->Z, p->S, p->G1, p->G2, p->F, p->E, p->G3, p->G4,
+                    (float)mu, (float)thr_f, (float)thr_s, p->prm.w, slot, st,
+                    (p->prm.flags & LRSTV_FLAG_ISO_TV) ? 1 : 0, g.m, rs));
+  return LRSTV_OK;
+}
+
+// Step 4 (E) of every cube: per group the mode-3 DFT, the warm start's
+// products and the RMS norms; one persistent Jacobi launch over the slices of
+// all groups (taller slices: one launch per group); per group sigma and
+// V diag g, the reconstruction and the inverse DFT with Gamma4.
 int batch_e_step(lrstv_batch *b, cudaStream_t st) {
   const double mu = b->plans[0]->mu;
   const bool wflag = (b->plans[0]->prm.flags & LRSTV_FLAG_WARM_START) != 0;
   const int warm = wflag && b->plans[0]->vwarm;
   // the Jacobi always works on specA: a warm start transforms into it from specB
-  for (int i = 0; i < b->n; ++i) {
-    lrstv_plan *pl = b->plans[i];
-    CK(tsvt_pre(pl->d, 3, pl->F, pl->G4, (float)(1.0 / pl->mu), pl->tb.tw3,
-                warm ? pl->specB : pl->specA, st, &pl->prof, plan_gemm(pl)));
-    if (warm) CK(warm_basis(pl, pl->specB, pl->specA, pl->specA, st));
-    CK(launch_group_ms2(pl->d, 3 * pl->d.h, pl->specA, pl->d.h, pl->ms2, st));
+  for (int k = 0; k < b->ngroups; ++k) {
+    const BatchGroup &g = b->groups[k];
+    lrstv_plan *p = g.pls[0];
+    const Dims &d = p->d;
+    CK(tsvt_pre(d, 3 * g.m, p->F, p->G4, (float)(1.0 / mu), p->tb.tw3,
+                warm ? p->specB : p->specA, st, &p->prof, plan_gemm(p)));
+    if (warm) CK(warm_basis(p, p->specB, p->specA, p->specA, st, g.m));
+    CK(launch_group_ms2(d, 3 * d.h * g.m, p->specA, d.h, p->ms2, st));
   }
   if (b->ntasks > 0) {
     CK(cudaMemsetAsync(b->d_counter, 0, sizeof(int), st));
@@ -1170,26 +1296,31 @@ int batch_e_step(lrstv_batch *b, cudaStream_t st) {
                            prof->on ? prof->d_work : nullptr, b->grid, b->smem, st, warm,
                            wflag ? 1 : 0, b->max_nr));
   }
-  for (int k = 0; k < b->nbig; ++k) {
-    lrstv_plan *pl = b->plans[b->big[k]];
-    Span sp(&pl->prof, LRSTV_K_JACOBI, st);
+  for (int k = 0; k < b->ngroups; ++k) {
+    const BatchGroup &g = b->groups[k];
+    if (!g.big) continue;
+    lrstv_plan *p = g.pls[0];
+    Span sp(&p->prof, LRSTV_K_JACOBI, st);
     JacOpt o;
     o.warm = warm;
-    o.t_svt = (float)(pl->prm.alpha / pl->mu);
-    o.ms2 = pl->ms2;
-    o.group = pl->d.h;
-    CK(launch_jacobi(pl->d, 3 * pl->d.h, pl->specA, pl->V, wflag ? -1.0f : o.t_svt, kMaxSweeps,
-                     pl->sweeps, pl->prof.on ? pl->prof.d_work : nullptr, st, o));
+    o.t_svt = (float)(p->prm.alpha / mu);
+    o.ms2 = p->ms2;
+    o.group = p->d.h;
+    CK(launch_jacobi(p->d, 3 * p->d.h * g.m, p->specA, p->V, wflag ? -1.0f : o.t_svt,
+                     kMaxSweeps, p->sweeps, p->prof.on ? p->prof.d_work : nullptr, st, o));
   }
-  for (int i = 0; i < b->n; ++i) {
-    lrstv_plan *pl = b->plans[i];
-    const int gamma4 = (pl->prm.flags & LRSTV_FLAG_NO_GAMMA4) ? 0 : 1;
+  for (int k = 0; k < b->ngroups; ++k) {
+    const BatchGroup &g = b->groups[k];
+    lrstv_plan *p = g.pls[0];
+    const Dims &d = p->d;
+    const int gamma4 = (p->prm.flags & LRSTV_FLAG_NO_GAMMA4) ? 0 : 1;
     if (wflag)
-      CK(launch_sigma_scale(pl->d, 3 * pl->d.h, pl->specA, pl->V,
-                            (float)(pl->prm.alpha / pl->mu), nullptr, pl->Vs, st));
-    CK(tsvt_post(pl->d, 3, pl->E, 1, pl->G4, pl->F, (float)pl->mu, gamma4, pl->tb.tw3, pl->specA,
-                 pl->specB, wflag ? pl->Vs : pl->V, st, &pl->prof, plan_gemm(pl)));
-    if (wflag) pl->vwarm = 1;
+      CK(launch_sigma_scale(d, 3 * d.h * g.m, p->specA, p->V, (float)(p->prm.alpha / mu),
+                            nullptr, p->Vs, st));
+    CK(tsvt_post(d, 3 * g.m, p->E, 1, p->G4, p->F, (float)mu, gamma4, p->tb.tw3, p->specA,
+                 p->specB, wflag ? p->Vs : p->V, st, &p->prof, plan_gemm(p)));
+    if (wflag)
+      for (int i = 0; i < g.m; ++i) g.pls[i]->vwarm = 1;
   }
   return LRSTV_OK;
 }
@@ -1197,11 +1328,10 @@ int batch_e_step(lrstv_batch *b, cudaStream_t st) {
 int batch_iterate_async(lrstv_batch *b, int iters, cudaStream_t st) {
   for (int it = 0; it < iters; ++it) {
     int rc;
-    for (int i = 0; i < b->n; ++i) {
-      if ((rc = lrstv_step_l_tz(b->plans[i], st)) != LRSTV_OK) return rc;
-      if ((rc = lrstv_step_z(b->plans[i], st)) != LRSTV_OK) return rc;
-      if ((rc = lrstv_step_fs_dual(b->plans[i], st)) != LRSTV_OK) return rc;
-    }
+    for (int k = 0; k < b->ngroups; ++k)
+      if ((rc = group_l_tz_z(b->groups[k], st)) != LRSTV_OK) return rc;
+    for (int k = 0; k < b->ngroups; ++k)
+      if ((rc = group_fs_dual(b->groups[k], st)) != LRSTV_OK) return rc;
     if ((rc = batch_e_step(b, st)) != LRSTV_OK) return rc;
     for (int i = 0; i < b->n; ++i)
       if ((rc = lrstv_step_mu(b->plans[i])) != LRSTV_OK) return rc;
@@ -1227,6 +1357,76 @@ int batch_copy_out(lrstv_batch *b, float *const *X, float *const *S, cudaStream_
   return LRSTV_OK;
 }
 
+bool same_group(const lrstv_plan *p, const int *dims, const lrstv_params *prm) {
+  return p->d.n1 == dims[0] && p->d.n2 == dims[1] && p->d.n3 == dims[2] &&
+         memcmp(&p->prm, prm, sizeof(lrstv_params)) == 0;
+}
+
+// The groups' plans and memory (see BatchGroup); b->plans[i] is cube i's plan.
+int batch_groups(lrstv_batch *b, const int *dims, const lrstv_params *params) {
+  int *gid = new (std::nothrow) int[b->n];
+  int *cnt = new (std::nothrow) int[b->n]();
+  if (!gid || !cnt) {
+    delete[] gid;
+    delete[] cnt;
+    return LRSTV_ERR_ALLOC;
+  }
+  int rc = LRSTV_OK;
+  // plan objects, and each cube's group (the first cube of each group leads it)
+  int *lead = new (std::nothrow) int[b->n];
+  if (!lead) rc = LRSTV_ERR_ALLOC;
+  for (int i = 0; rc == LRSTV_OK && i < b->n; ++i) {
+    rc = plan_object(dims[3 * i], dims[3 * i + 1], dims[3 * i + 2], &params[i], &b->plans[i]);
+    if (rc != LRSTV_OK) break;
+    gid[i] = -1;
+    for (int k = 0; k < b->ngroups; ++k)
+      if (same_group(b->plans[lead[k]], dims + 3 * i, &params[i])) {
+        gid[i] = k;
+        break;
+      }
+    if (gid[i] < 0) {
+      gid[i] = b->ngroups;
+      lead[b->ngroups++] = i;
+    }
+    cnt[gid[i]] += 1;
+  }
+  if (rc == LRSTV_OK) {
+    b->groups = new (std::nothrow) BatchGroup[b->ngroups]();
+    if (!b->groups) rc = LRSTV_ERR_ALLOC;
+  }
+  for (int k = 0; rc == LRSTV_OK && k < b->ngroups; ++k) {
+    BatchGroup &g = b->groups[k];
+    g.pls = new (std::nothrow) lrstv_plan *[cnt[k]];
+    if (!g.pls) rc = LRSTV_ERR_ALLOC;
+  }
+  for (int i = 0; rc == LRSTV_OK && i < b->n; ++i) {
+    BatchGroup &g = b->groups[gid[i]];
+    g.pls[g.m++] = b->plans[i];
+  }
+  for (int k = 0; rc == LRSTV_OK && k < b->ngroups; ++k) {
+    BatchGroup &g = b->groups[k];
+    const size_t bytes = group_layout(g.pls, g.m, nullptr);
+    if (cudaMalloc(&g.arena, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      g.arena = nullptr;
+      rc = LRSTV_ERR_ALLOC;
+      break;
+    }
+    group_layout(g.pls, g.m, g.arena);
+    for (int i = 0; i < g.m; ++i) {
+      g.pls[i]->arena = g.arena;
+      g.pls[i]->arena_bytes = bytes / (size_t)g.m;
+      g.pls[i]->own_arena = 0;
+    }
+    rc = arena_start(g.pls[0], g.arena, bytes);
+    g.big = g.pls[0]->d.nr > kBatchMaxNr;
+  }
+  delete[] gid;
+  delete[] cnt;
+  delete[] lead;
+  return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1249,28 +1449,24 @@ int lrstv_batch_create(int ncubes, const int *dims, const lrstv_params *params,
   b->giters = -1;
   b->n = ncubes;
   b->plans = new (std::nothrow) lrstv_plan *[ncubes]();
-  b->big = new (std::nothrow) int[ncubes];
   b->gY = new (std::nothrow) const float *[ncubes]();
   b->gX = new (std::nothrow) float *[ncubes]();
   b->gS = new (std::nothrow) float *[ncubes]();
-  if (!b->plans || !b->big || !b->gY || !b->gX || !b->gS) {
+  if (!b->plans || !b->gY || !b->gX || !b->gS) {
     batch_free(b);
     return LRSTV_ERR_ALLOC;
   }
+  int rc = batch_groups(b, dims, params);
+  if (rc != LRSTV_OK) {
+    batch_free(b);
+    return rc;
+  }
   int ntasks = 0, maxnr = 1;
   for (int i = 0; i < ncubes; ++i) {
-    int rc = lrstv_plan_create(dims[3 * i], dims[3 * i + 1], dims[3 * i + 2], &params[i],
-                               &b->plans[i]);
-    if (rc != LRSTV_OK) {
-      batch_free(b);
-      return rc;
-    }
     const Dims &d = b->plans[i]->d;
     if (d.nr <= kBatchMaxNr) {
       ntasks += 3 * d.h;
       if (d.nr > maxnr) maxnr = d.nr;
-    } else {
-      b->big[b->nbig++] = i;
     }
   }
   b->ntasks = ntasks;
@@ -1339,6 +1535,17 @@ int lrstv_batch_destroy(lrstv_batch *b) {
 int lrstv_batch_size(const lrstv_batch *b, int *ncubes) {
   if (!b || !ncubes) return LRSTV_ERR_ARG;
   *ncubes = b->n;
+  return LRSTV_OK;
+}
+
+int lrstv_batch_groups(const lrstv_batch *b, int *ngroups, int *group_of) {
+  if (!b || !ngroups) return LRSTV_ERR_ARG;
+  *ngroups = b->ngroups;
+  if (group_of)
+    for (int i = 0; i < b->n; ++i)
+      for (int k = 0; k < b->ngroups; ++k)
+        for (int j = 0; j < b->groups[k].m; ++j)
+          if (b->groups[k].pls[j] == b->plans[i]) group_of[i] = k;
   return LRSTV_OK;
 }
 

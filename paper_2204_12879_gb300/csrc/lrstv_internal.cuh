@@ -26,16 +26,21 @@ constexpr int kMaxBands = 4096;
 
 // ---------------------------------------------------------------- stencil.cu
 // Step 1 + T_z: L = (Y - S + Z + (G1 - G2)/mu)/2, T = mu L + G2 + D_w^*(mu F - G3).
+// nb cubes packed back to back (cube b's single blocks at b N floats, its
+// three-component blocks F, G3 at 3 b N), one launch.
 cudaError_t launch_l_tz(const Dims &d, const float *Y, const float *S, const float *Z,
                         const float *G1, const float *G2, const float *F, const float *G3,
-                        float mu, const float w[3], float *L, float *T, cudaStream_t st);
+                        float mu, const float w[3], float *L, float *T, cudaStream_t st,
+                        int nb = 1);
 // Steps 3, 5, 6: F, S, Gamma1..3; res2 receives atomic maxima of |Y-L-S|, |L-Z|
 // as float bits (may be null).  iso: the F threshold acts on each voxel's
 // 3-vector (F_1, F_2, F_3) by its 2-norm (isotropic LRSTV, eq. CRSSTV_iso).
+// nb cubes packed as for launch_l_tz; cube b's maxima at res2 + b rs.
 cudaError_t launch_fs_dual(const Dims &d, const float *Y, const float *L, const float *Z,
                            float *S, float *G1, float *G2, float *F, const float *E, float *G3,
                            const float *G4, float mu, float thr_f, float thr_s, const float w[3],
-                           unsigned *res2, cudaStream_t st, int iso = 0);
+                           unsigned *res2, cudaStream_t st, int iso = 0, int nb = 1,
+                           size_t rs = 0);
 cudaError_t launch_diff(const Dims &d, const float *x, const float w[3], float *g, cudaStream_t st);
 cudaError_t launch_diff_adjoint(const Dims &d, const float *g, const float w[3], float *x,
                                 cudaStream_t st);

@@ -59,14 +59,19 @@ Chunking chunking(const Dims &d) {
 }
 
 __global__ void __launch_bounds__(kBX *kBY)
-    k_l_tz(int n1, int n2, int n3, size_t N, int kchunk, const float *__restrict__ Y,
-           const float *__restrict__ S, const float *__restrict__ Z, const float *__restrict__ G1,
-           const float *__restrict__ G2, const float *__restrict__ F, const float *__restrict__ G3,
-           float mu, float w0, float w1, float w2, float *__restrict__ L, float *__restrict__ T) {
+    k_l_tz(int n1, int n2, int n3, size_t N, int kchunk, int cchunks,
+           const float *__restrict__ Y, const float *__restrict__ S, const float *__restrict__ Z,
+           const float *__restrict__ G1, const float *__restrict__ G2,
+           const float *__restrict__ F, const float *__restrict__ G3, float mu, float w0,
+           float w1, float w2, float *__restrict__ L, float *__restrict__ T) {
   const int i = blockIdx.x * kBX + threadIdx.x;
   const int j = blockIdx.y * kBY + threadIdx.y;
   if (i >= n1 || j >= n2) return;
-  const int k0 = blockIdx.z * kchunk;
+  // cube of a packed multi-cube launch (cchunks band chunks a cube)
+  const size_t cb = blockIdx.z / cchunks;
+  Y += cb * N; S += cb * N; Z += cb * N; G1 += cb * N; G2 += cb * N; L += cb * N; T += cb * N;
+  F += 3 * cb * N; G3 += 3 * cb * N;
+  const int k0 = (blockIdx.z % cchunks) * kchunk;
   const int k1 = min(n3, k0 + kchunk);
   const size_t P = (size_t)n1 * n2;
   const size_t col = (size_t)i + (size_t)n1 * j;
@@ -95,17 +100,24 @@ __global__ void __launch_bounds__(kBX *kBY)
 
 template <int ISO>
 __global__ void __launch_bounds__(kBX *kBY)
-    k_fs_dual(int n1, int n2, int n3, size_t N, int kchunk, const float *__restrict__ Y,
-              const float *__restrict__ L, const float *__restrict__ Z, float *__restrict__ S,
-              float *__restrict__ G1, float *__restrict__ G2, float *__restrict__ F,
-              const float *__restrict__ E, float *__restrict__ G3, const float *__restrict__ G4,
-              float mu, float thr_f, float thr_s, float w0, float w1, float w2,
-              unsigned *__restrict__ res2) {
+    k_fs_dual(int n1, int n2, int n3, size_t N, int kchunk, int cchunks,
+              const float *__restrict__ Y, const float *__restrict__ L,
+              const float *__restrict__ Z, float *__restrict__ S, float *__restrict__ G1,
+              float *__restrict__ G2, float *__restrict__ F, const float *__restrict__ E,
+              float *__restrict__ G3, const float *__restrict__ G4, float mu, float thr_f,
+              float thr_s, float w0, float w1, float w2, unsigned *__restrict__ res2,
+              size_t rs) {
   const int i = blockIdx.x * kBX + threadIdx.x;
   const int j = blockIdx.y * kBY + threadIdx.y;
   float r1max = 0.0f, r2max = 0.0f;
+  // cube of a packed multi-cube launch (cchunks band chunks a cube); its
+  // residual maxima go rs words after the previous cube's
+  const size_t cb = blockIdx.z / cchunks;
+  Y += cb * N; L += cb * N; Z += cb * N; S += cb * N; G1 += cb * N; G2 += cb * N;
+  F += 3 * cb * N; E += 3 * cb * N; G3 += 3 * cb * N; G4 += 3 * cb * N;
+  if (res2) res2 += cb * rs;
   if (i < n1 && j < n2) {
-    const int k0 = blockIdx.z * kchunk;
+    const int k0 = (blockIdx.z % cchunks) * kchunk;
     const int k1 = min(n3, k0 + kchunk);
     const size_t P = (size_t)n1 * n2;
     const size_t col = (size_t)i + (size_t)n1 * j;
@@ -269,6 +281,9 @@ __global__ void __launch_bounds__(256)
             float mu, float w0, float w1, float w2, float *__restrict__ L, float *__restrict__ T) {
   Vox4 o;
   if (!vox4(n1, n2, n3, blockIdx.x * (size_t)blockDim.x + threadIdx.x, o)) return;
+  const size_t cb = blockIdx.y;  // cube of a packed multi-cube launch
+  Y += cb * N; S += cb * N; Z += cb * N; G1 += cb * N; G2 += cb * N; L += cb * N; T += cb * N;
+  F += 3 * cb * N; G3 += 3 * cb * N;
   const float *F1 = F, *F2 = F + N, *F3 = F + 2 * N;
   const float *H1 = G3, *H2 = G3 + N, *H3 = G3 + 2 * N;
   const float4 y = ld4(Y + o.v), s = ld4(S + o.v), z = ld4(Z + o.v), g1 = ld4(G1 + o.v),
@@ -309,8 +324,14 @@ __global__ void __launch_bounds__(256)
                float *__restrict__ G1, float *__restrict__ G2, float *__restrict__ F,
                const float *__restrict__ E, float *__restrict__ G3, const float *__restrict__ G4,
                float mu, float thr_f, float thr_s, float w0, float w1, float w2,
-               unsigned *__restrict__ res2) {
+               unsigned *__restrict__ res2, size_t rs) {
   float r1max = 0.0f, r2max = 0.0f;
+  // cube of a packed multi-cube launch; its residual maxima go rs words after
+  // the previous cube's
+  const size_t cb = blockIdx.y;
+  Y += cb * N; L += cb * N; Z += cb * N; S += cb * N; G1 += cb * N; G2 += cb * N;
+  F += 3 * cb * N; E += 3 * cb * N; G3 += 3 * cb * N; G4 += 3 * cb * N;
+  if (res2) res2 += cb * rs;
   Vox4 o;
   if (vox4(n1, n2, n3, blockIdx.x * (size_t)blockDim.x + threadIdx.x, o)) {
     const float4 z = ld4(Z + o.v), zp2 = ld4(Z + o.vp2), zp3 = ld4(Z + o.vp3);
@@ -415,35 +436,61 @@ unsigned vec4_blocks(const Dims &d) { return (unsigned)((d.N / 4 + 255) / 256); 
 
 }  // namespace
 
+// The chunked (scalar) form takes nb cubes in one launch while nb times its
+// band chunks fit the grid's z extent; beyond that one launch per cube.
+constexpr int kMaxGridZ = 65535;
+
 cudaError_t launch_l_tz(const Dims &d, const float *Y, const float *S, const float *Z,
                         const float *G1, const float *G2, const float *F, const float *G3,
-                        float mu, const float w[3], float *L, float *T, cudaStream_t st) {
+                        float mu, const float w[3], float *L, float *T, cudaStream_t st, int nb) {
+  if (nb < 1 || nb > kMaxGridZ) return cudaErrorInvalidValue;
   if (vec4_ok(d, {Y, S, Z, G1, G2, F, G3, L, T})) {
-    k_l_tz4<<<vec4_blocks(d), 256, 0, st>>>(d.n1, d.n2, d.n3, d.N, Y, S, Z, G1, G2, F, G3, mu, w[0],
-                                             w[1], w[2], L, T);
+    k_l_tz4<<<dim3(vec4_blocks(d), nb), 256, 0, st>>>(d.n1, d.n2, d.n3, d.N, Y, S, Z, G1, G2, F,
+                                                       G3, mu, w[0], w[1], w[2], L, T);
     return cudaGetLastError();
   }
   Chunking c = chunking(d);
-  k_l_tz<<<c.grid, dim3(kBX, kBY), 0, st>>>(d.n1, d.n2, d.n3, d.N, c.kchunk, Y, S, Z, G1, G2, F,
-                                            G3, mu, w[0], w[1], w[2], L, T);
-  return cudaGetLastError();
+  const int chunks = (int)c.grid.z;
+  const int per = (long long)nb * chunks <= kMaxGridZ ? nb : 1;
+  for (int b0 = 0; b0 < nb; b0 += per) {
+    const size_t o = (size_t)b0 * d.N;
+    c.grid.z = per * chunks;
+    k_l_tz<<<c.grid, dim3(kBX, kBY), 0, st>>>(d.n1, d.n2, d.n3, d.N, c.kchunk, chunks, Y + o,
+                                              S + o, Z + o, G1 + o, G2 + o, F + 3 * o,
+                                              G3 + 3 * o, mu, w[0], w[1], w[2], L + o, T + o);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_fs_dual(const Dims &d, const float *Y, const float *L, const float *Z,
                            float *S, float *G1, float *G2, float *F, const float *E, float *G3,
                            const float *G4, float mu, float thr_f, float thr_s, const float w[3],
-                           unsigned *res2, cudaStream_t st, int iso) {
+                           unsigned *res2, cudaStream_t st, int iso, int nb, size_t rs) {
+  if (nb < 1 || nb > kMaxGridZ) return cudaErrorInvalidValue;
   if (vec4_ok(d, {Y, L, Z, S, G1, G2, F, E, G3, G4})) {
     auto k = iso ? k_fs_dual4<1> : k_fs_dual4<0>;
-    k<<<vec4_blocks(d), 256, 0, st>>>(d.n1, d.n2, d.n3, d.N, Y, L, Z, S, G1, G2, F, E, G3, G4, mu,
-                                      thr_f, thr_s, w[0], w[1], w[2], res2);
+    k<<<dim3(vec4_blocks(d), nb), 256, 0, st>>>(d.n1, d.n2, d.n3, d.N, Y, L, Z, S, G1, G2, F, E,
+                                                G3, G4, mu, thr_f, thr_s, w[0], w[1], w[2], res2,
+                                                rs);
     return cudaGetLastError();
   }
   Chunking c = chunking(d);
+  const int chunks = (int)c.grid.z;
+  const int per = (long long)nb * chunks <= kMaxGridZ ? nb : 1;
   auto k = iso ? k_fs_dual<1> : k_fs_dual<0>;
-  k<<<c.grid, dim3(kBX, kBY), 0, st>>>(d.n1, d.n2, d.n3, d.N, c.kchunk, Y, L, Z, S, G1, G2, F, E,
-                                       G3, G4, mu, thr_f, thr_s, w[0], w[1], w[2], res2);
-  return cudaGetLastError();
+  for (int b0 = 0; b0 < nb; b0 += per) {
+    const size_t o = (size_t)b0 * d.N;
+    c.grid.z = per * chunks;
+    k<<<c.grid, dim3(kBX, kBY), 0, st>>>(d.n1, d.n2, d.n3, d.N, c.kchunk, chunks, Y + o, L + o,
+                                         Z + o, S + o, G1 + o, G2 + o, F + 3 * o, E + 3 * o,
+                                         G3 + 3 * o, G4 + 3 * o, mu, thr_f, thr_s, w[0], w[1],
+                                         w[2], res2 ? res2 + (size_t)b0 * rs : nullptr, rs);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_diff(const Dims &d, const float *x, const float w[3], float *g,

@@ -459,20 +459,13 @@ int unroll_forward(lrstv_unroll *u, cudaStream_t st) {
     UCK(cudaMemcpyAsync(dst, src, sizeof(float) * u->slot_floats, cudaMemcpyDeviceToDevice, st));
     const UnrollSlot s = slot_at(u, dst);
     const float muf = (float)mu;
-    // L and T_z, then Z (all cubes in one batched solve)
-    for (int b = 0; b < B; ++b) {
-      const size_t o = (size_t)b * N, o3 = 3 * o;
-      UCK(launch_l_tz(d, u->Y + o, s.S + o, s.Z + o, s.G1 + o, s.G2 + o, s.F + o3, s.G3 + o3, muf,
-                      u->w, s.L + o, u->T + o, st));
-    }
+    // L and T_z, then Z (all cubes in one launch each)
+    UCK(launch_l_tz(d, u->Y, s.S, s.Z, s.G1, s.G2, s.F, s.G3, muf, u->w, s.L, u->T, st, B));
     UCK(zsolve_core(d, B, u->tb, u->T, muf, s.Z, u->specA, u->specB, st, nullptr, gs));
     // F, S and Gamma1..3
     const float thr_f = (float)(tau / mu), thr_s = (float)(lam / mu);
-    for (int b = 0; b < B; ++b) {
-      const size_t o = (size_t)b * N, o3 = 3 * o;
-      UCK(launch_fs_dual(d, u->Y + o, s.L + o, s.Z + o, s.S + o, s.G1 + o, s.G2 + o, s.F + o3,
-                         s.E + o3, s.G3 + o3, s.G4 + o3, muf, thr_f, thr_s, u->w, nullptr, st));
-    }
+    UCK(launch_fs_dual(d, u->Y, s.L, s.Z, s.S, s.G1, s.G2, s.F, s.E, s.G3, s.G4, muf, thr_f, thr_s,
+                       u->w, nullptr, st, 0, B));
     // E: t-SVT of F - Gamma4/mu for all 3 B gradient cubes, factors kept
     float2 *Wk = u->W + (size_t)k * ns * d.P;
     float2 *Vk = u->V + (size_t)k * ns * d.nc * d.nc;

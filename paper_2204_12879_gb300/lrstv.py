@@ -140,6 +140,7 @@ _SIGS = {
     "lrstv_batch_create": [_I, ctypes.POINTER(_I), ctypes.POINTER(Params), ctypes.POINTER(_P)],
     "lrstv_batch_destroy": [_P],
     "lrstv_batch_size": [_P, ctypes.POINTER(_I)],
+    "lrstv_batch_groups": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "lrstv_batch_plan": [_P, _I, ctypes.POINTER(_P)],
     "lrstv_batch_init": [_P, ctypes.POINTER(_P), _P],
     "lrstv_batch_iterate": [_P, _I, _P],
@@ -393,8 +394,9 @@ class _BorrowedPlan(Plan):
 
 
 class Batch:
-    """An lrstv_batch: independent cubes of uneven shapes run in lockstep with
-    one persistent Jacobi launch per E-step."""
+    """An lrstv_batch: independent cubes of uneven shapes run in lockstep,
+    one launch per kernel and group of equal shapes and parameters, with one
+    persistent Jacobi launch per E-step."""
 
     def __init__(self, shapes, params):
         _torch()
@@ -426,6 +428,13 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+    def groups(self):
+        """(number of groups, list of each cube's group)."""
+        ng = ctypes.c_int()
+        gof = (ctypes.c_int * self.n)()
+        _call("lrstv_batch_groups", self._h, ctypes.byref(ng), gof)
+        return ng.value, list(gof)
 
     def plan(self, i) -> Plan:
         h = ctypes.c_void_p()

@@ -63,6 +63,80 @@ def test_batch_equals_single_plans(L, warm):
         assert torch.equal(S, Ss[i]), sh
 
 
+# repeated shapes with equal parameters share a group (packed state, one launch
+# per kernel for the group): three and two cubes of float4-stencil shapes, two
+# of a scalar-stencil shape (n1 % 4 != 0), two taller than the persistent
+# Jacobi takes; an equal shape with another alpha forms a group of its own
+GROUPED = [(24, 20, 9), (24, 20, 9), (70, 42, 6), (24, 20, 9), (70, 42, 6), (260, 12, 3),
+           (32, 32, 16), (260, 12, 3), (24, 20, 9)]
+GROUP_OF = [0, 0, 1, 0, 1, 2, 3, 2, 4]
+
+
+def _grouped_params(L, iters, flags):
+    out = []
+    for i, sh in enumerate(GROUPED):
+        alpha = 0.15 if i == len(GROUPED) - 1 else 0.1
+        out.append(L.Params.make(sh[0], sh[1], tau=0.002, alpha=alpha, max_iter=iters, flags=flags))
+    return out
+
+
+@pytest.mark.parametrize("warm", [False, True])
+def test_batch_groups_equal_single_plans(L, warm):
+    import torch
+    iters = 6
+    flags = L.FLAG_WARM_START if warm else 0
+    Ys = [dev(_cube(sh, 400 + i)) for i, sh in enumerate(GROUPED)]
+    params = _grouped_params(L, iters, flags)
+    with L.Batch(GROUPED, params) as b:
+        ng, gof = b.groups()
+        assert ng == 5 and gof == GROUP_OF
+        Xs, Ss = b.run(Ys)
+        torch.cuda.synchronize()
+        for i in range(len(GROUPED)):
+            st = b.plan(i).stats()
+            assert st.iters == iters and st.jacobi_unconverged == 0
+            assert st.res_inf[0] >= 0.0 and st.res_inf[1] >= 0.0
+        # every cube's own residuals, stats and state, not its group's
+        single = _grouped_params(L, iters, flags | L.FLAG_JACOBI_PER_SLICE)
+        for i, sh in enumerate(GROUPED):
+            with L.Plan(*sh, single[i]) as pl:
+                X, S = pl.run(Ys[i])
+                torch.cuda.synchronize()
+                st1, stb = pl.stats(), b.plan(i).stats()
+                assert torch.equal(pl.get("E"), b.plan(i).get("E")), sh
+            assert torch.equal(X, Xs[i]), (i, sh)
+            assert torch.equal(S, Ss[i]), (i, sh)
+            assert list(st1.res_inf) == list(stb.res_inf), (i, sh)
+            assert st1.jacobi_max_sweeps == stb.jacobi_max_sweeps, (i, sh)
+
+
+def _spans_per_iteration(L, shapes, iters):
+    import torch
+    Ys = [dev(_cube(sh, 500 + i)) for i, sh in enumerate(shapes)]
+    params = [L.Params.make(sh[0], sh[1], max_iter=iters, flags=L.FLAG_WARM_START)
+              for sh in shapes]
+    with L.Batch(shapes, params) as b:
+        b.init(Ys)
+        b.iterate(2)  # past the first E-step, which starts cold
+        plans = [b.plan(i) for i in range(len(shapes))]
+        for p in plans:
+            p.profile_enable(True)
+        b.iterate(iters)
+        torch.cuda.synchronize()
+        total = sum(sum(p.profile_read().launches) for p in plans)
+        for p in plans:
+            p.profile_enable(False)
+    return total / iters
+
+
+def test_batch_launches_independent_of_cube_count(L):
+    # the profiled kernel launches of a batched step depend on the groups
+    # (distinct shapes), not on how many cubes each group holds
+    two = _spans_per_iteration(L, [(24, 20, 9), (32, 32, 16)], 3)
+    many = _spans_per_iteration(L, [(24, 20, 9)] * 5 + [(32, 32, 16)] * 4, 3)
+    assert two == many and two > 0
+
+
 def test_batch_graph_replay(L):
     import torch
     iters = 4
