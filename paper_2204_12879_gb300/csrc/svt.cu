@@ -442,6 +442,28 @@ struct PkShape {
   static constexpr int LD2 = (16 * KP > 32 * KPF) ? 16 * KP : 32 * KPF;  // row pairs per column
 };
 
+// This thread's share of sum |x_e|^2 over n complex values (e = thread,
+// thread + blockDim.x, ...), in four chains so that four loads are in flight.
+template <bool CG>
+__device__ __forceinline__ float sumsq4(const float2 *x, size_t n) {
+  const size_t T = blockDim.x;
+  float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;
+  size_t e = threadIdx.x;
+  for (; e + 3 * T < n; e += 4 * T) {
+    const float2 a = ldw<CG>(x + e), b = ldw<CG>(x + e + T), c = ldw<CG>(x + e + 2 * T),
+                 d = ldw<CG>(x + e + 3 * T);
+    p0 = fmaf(a.x, a.x, fmaf(a.y, a.y, p0));
+    p1 = fmaf(b.x, b.x, fmaf(b.y, b.y, p1));
+    p2 = fmaf(c.x, c.x, fmaf(c.y, c.y, p2));
+    p3 = fmaf(d.x, d.x, fmaf(d.y, d.y, p3));
+  }
+  for (; e < n; e += T) {
+    const float2 a = ldw<CG>(x + e);
+    p0 = fmaf(a.x, a.x, fmaf(a.y, a.y, p0));
+  }
+  return (p0 + p1) + (p2 + p3);
+}
+
 // Per-slice set-up of a packed Jacobi run by the whole CTA: V := I unless warm
 // (warm: V holds the basis W was multiplied by), then ||W||_F^2, returned to
 // every thread (s_red: 32 floats of shared memory).
@@ -452,11 +474,7 @@ __device__ __forceinline__ float pk_setup(int nr, int nc, const float2 *W, float
   if (!warm)
     for (int e = tid; e < nc * nc; e += blockDim.x)
       V[e] = make_float2((e % nc) == (e / nc) ? 1.0f : 0.0f, 0.0f);
-  float part = 0.0f;
-  for (size_t e = tid; e < (size_t)nr * nc; e += blockDim.x) {
-    const float2 x = ldw<CG>(W + e);
-    part = fmaf(x.x, x.x, fmaf(x.y, x.y, part));
-  }
+  float part = sumsq4<CG>(W, (size_t)nr * nc);
   part = warp_sum(part);
   if (lane == 0) s_red[warp] = part;
   __syncthreads();
@@ -1126,13 +1144,17 @@ __global__ void __launch_bounds__(512)
     k_sigma_scale(int nr, int nc, size_t wstride, const float2 *__restrict__ W,
                   const float2 *__restrict__ V, float t, double *__restrict__ sig,
                   float2 *__restrict__ Vs) {
+  // slice blockIdx.x, one column a warp: blockIdx.y takes columns
+  // blockDim.x / 32 blockIdx.y .. + blockDim.x / 32 - 1
   const int s = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
   const float2 *Ws = W + (size_t)s * wstride;
   const size_t vs = (size_t)nc * nc;
-  for (int i = warp; i < nc; i += nwarps) {
+  const int i = blockIdx.y * nwarps + warp;
+  if (i < nc) {
     const float2 *wi = Ws + (size_t)nr * i;
     float n2 = 0.f;
+#pragma unroll 4
     for (int row = lane; row < nr; row += 32)
       n2 = fmaf(wi[row].x, wi[row].x, fmaf(wi[row].y, wi[row].y, n2));
     n2 = warp_sum(n2);
@@ -1141,6 +1163,7 @@ __global__ void __launch_bounds__(512)
     if (sig && lane == 0) sig[(size_t)s * nc + i] = sigma;
     const float2 *vi = V + s * vs + (size_t)nc * i;
     float2 *oi = Vs + s * vs + (size_t)nc * i;
+#pragma unroll 4
     for (int row = lane; row < nc; row += 32) oi[row] = make_float2(vi[row].x * g, vi[row].y * g);
   }
 }
@@ -1148,16 +1171,12 @@ __global__ void __launch_bounds__(512)
 // Mean-square column norm ||W_s||_F^2 / nc of every slice, reduced to the
 // largest over each group of `group` consecutive slices (atomic max on the
 // bits of non-negative floats; the group slots start at zero).
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(1024)
     k_group_ms2(int nr, int nc, size_t wstride, const float2 *__restrict__ W, int group,
                 unsigned *__restrict__ gmax) {
-  __shared__ float s_red[8];
+  __shared__ float s_red[32];
   const float2 *Ws = W + (size_t)blockIdx.x * wstride;
-  float part = 0.0f;
-  for (size_t e = threadIdx.x; e < (size_t)nr * nc; e += blockDim.x) {
-    const float2 x = Ws[e];
-    part = fmaf(x.x, x.x, fmaf(x.y, x.y, part));
-  }
+  float part = sumsq4<false>(Ws, (size_t)nr * nc);
   part = warp_sum(part);
   if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = part;
   __syncthreads();
@@ -1186,7 +1205,9 @@ __global__ void k_ns_update(int nc, int nslices, size_t dstride, float2 *__restr
 cudaError_t launch_sigma_scale(const Dims &d, int nslices, const float2 *W, const float2 *V,
                                float t, double *sig, float2 *Vs, cudaStream_t st) {
   if (nslices <= 0) return cudaSuccess;
-  k_sigma_scale<<<nslices, 512, 0, st>>>(d.nr, d.nc, d.P, W, V, t, sig, Vs);
+  // 16 columns a CTA: about a dozen CTAs a slice, so every SM streams
+  k_sigma_scale<<<dim3(nslices, (d.nc + 15) / 16), 512, 0, st>>>(d.nr, d.nc, d.P, W, V, t, sig,
+                                                                   Vs);
   return cudaGetLastError();
 }
 
@@ -1196,7 +1217,7 @@ cudaError_t launch_group_ms2(const Dims &d, int nslices, const float2 *W, int gr
   const int ngroups = (nslices + group - 1) / group;
   cudaError_t e = cudaMemsetAsync(ms2, 0, sizeof(float) * ngroups, st);
   if (e != cudaSuccess) return e;
-  k_group_ms2<<<nslices, 256, 0, st>>>(d.nr, d.nc, d.P, W, group, (unsigned *)ms2);
+  k_group_ms2<<<nslices, 1024, 0, st>>>(d.nr, d.nc, d.P, W, group, (unsigned *)ms2);
   return cudaGetLastError();
 }
 

@@ -24,8 +24,9 @@
 // 2^-17 relative error per term, half the shared-memory bytes and half the
 // MMA instructions of 3xTF32 (K = 16 per instruction instead of 8).
 //
-// Tile: 128 rows of C (M = 128 MMA), 64 complex columns (two N = 64 MMAs
-// into 128 TMEM columns), 8 (3xTF32) or 16 (3xBF16) complex K per chunk: two
+// Tile: 128 rows of C (M = 128 MMA), 64 complex columns (one N = 128 MMA over
+// the adjacent Re and Im B tiles into 128 TMEM columns, which reads the A tile
+// once for both parts), 8 (3xTF32) or 16 (3xBF16) complex K per chunk: two
 // K = 8 TF32 or two K = 16 BF16 MMA steps per product, a 32 KB stage either
 // way.  Operands are staged by the CTA's threads into shared memory in the
 // canonical K-major layout without swizzle: 8-row x 16-byte core matrices,
@@ -233,6 +234,8 @@ __global__ void __launch_bounds__(kThreads, KIND == 1 ? 1 : 2) k_cgemm_tc(CGemm 
   // D format F32, A and B in the precision's format, both K-major, N, M
   const uint32_t idesc = (1u << 4) | (P::kFmt << 7) | (P::kFmt << 10) |
                          ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+  const uint32_t idesc2 = (1u << 4) | (P::kFmt << 7) | (P::kFmt << 10) |
+                          ((uint32_t)((2 * TN) >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
   const uint32_t bar0 = smem_u32(&mbar[0]), bar1 = smem_u32(&mbar[1]);
   // per stage: the parity of its next MMA commit, and whether a commit is
   // outstanding (issued, not yet seen complete)
@@ -354,8 +357,9 @@ __global__ void __launch_bounds__(kThreads, KIND == 1 ? 1 : 2) k_cgemm_tc(CGemm 
   // split the registers' chunk into the hi / lo tiles of stage `st`
   auto store_chunk = [&](int st, int k0) {
     char *aHi = smem + st * kStageBytes, *aLo = aHi + P::kTileA;
-    char *bReHi = aLo + P::kTileA, *bReLo = bReHi + P::kTileB;
-    char *bImHi = bReLo + P::kTileB, *bImLo = bImHi + P::kTileB;
+    // [Re | Im] B tiles of each split adjacent: one 128-row B operand
+    char *bReHi = aLo + P::kTileA, *bImHi = bReHi + P::kTileB;
+    char *bReLo = bImHi + P::kTileB, *bImLo = bReLo + P::kTileB;
     // the A values as the MMAs take them: KIND 1 x - ycoef y, KIND 2 the
     // conjugate on transposed slices
     auto aval = [&](int i) -> float2 {
@@ -431,21 +435,19 @@ __global__ void __launch_bounds__(kThreads, KIND == 1 ? 1 : 2) k_cgemm_tc(CGemm 
   auto issue = [&](int st) {
     const char *base = smem + st * kStageBytes;
     const uint32_t a_hi = smem_u32(base), a_lo = a_hi + (uint32_t)P::kTileA;
-    const uint32_t br_hi = a_lo + (uint32_t)P::kTileA, br_lo = br_hi + (uint32_t)P::kTileB;
-    const uint32_t bi_hi = br_lo + (uint32_t)P::kTileB, bi_lo = bi_hi + (uint32_t)P::kTileB;
+    const uint32_t b_hi = a_lo + (uint32_t)P::kTileA, b_lo = b_hi + 2 * (uint32_t)P::kTileB;
     const uint32_t dt = tmem + (uint32_t)st * (2 * TN);
 #pragma unroll
     for (int j = 0; j < KR / P::kMmaK; ++j) {  // one instruction spans two core matrices
       const uint32_t ko = (uint32_t)j * 2 * kLBO;
       const uint32_t acc0 = j > 0 ? 1u : 0u;  // a fresh tile per chunk
-      // Re C (tile columns 0..63), Im C (64..127); three split products each
-      mma<PREC>(dt, sdesc<PREC>(a_hi + ko), sdesc<PREC>(br_hi + ko), idesc, acc0);
-      mma<PREC>(dt, sdesc<PREC>(a_hi + ko), sdesc<PREC>(br_lo + ko), idesc, 1u);
-      mma<PREC>(dt, sdesc<PREC>(a_lo + ko), sdesc<PREC>(br_hi + ko), idesc, 1u);
-      if (KIND == 2) continue;  // the real part is the whole result
-      mma<PREC>(dt + TN, sdesc<PREC>(a_hi + ko), sdesc<PREC>(bi_hi + ko), idesc, acc0);
-      mma<PREC>(dt + TN, sdesc<PREC>(a_hi + ko), sdesc<PREC>(bi_lo + ko), idesc, 1u);
-      mma<PREC>(dt + TN, sdesc<PREC>(a_lo + ko), sdesc<PREC>(bi_hi + ko), idesc, 1u);
+      // Re C (tile columns 0..63) and Im C (64..127) from one N = 128 MMA over
+      // the adjacent [Re | Im] B tiles, so that A is read once for both; the
+      // real part alone (KIND 2) from N = 64.  Three split products each.
+      const uint32_t id = KIND == 2 ? idesc : idesc2;
+      mma<PREC>(dt, sdesc<PREC>(a_hi + ko), sdesc<PREC>(b_hi + ko), id, acc0);
+      mma<PREC>(dt, sdesc<PREC>(a_hi + ko), sdesc<PREC>(b_lo + ko), id, 1u);
+      mma<PREC>(dt, sdesc<PREC>(a_lo + ko), sdesc<PREC>(b_hi + ko), id, 1u);
     }
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
