@@ -294,13 +294,14 @@ int lrstv_plan_run_host(lrstv_plan *plan, const float *Y_host, float *X_host, fl
 /* Autotuner (no counterpart in the paper): times `iters` iterations
  * (params.max_iter when 0) of the plan from the device cube Y for every
  * combination of the flags in `allowed` (a subset of LRSTV_FLAG_SIMT_GEMM |
- * LRSTV_FLAG_SIMT_DFT | LRSTV_FLAG_JACOBI_PER_SLICE | LRSTV_FLAG_WARM_START;
- * combinations params rejects, and SIMT_DFT together with SIMT_GEMM, are
- * skipped), each after
+ * LRSTV_FLAG_SIMT_DFT | LRSTV_FLAG_JACOBI_PER_SLICE | LRSTV_FLAG_WARM_START |
+ * LRSTV_FLAG_BF16X3; combinations params rejects, and SIMT_DFT together with
+ * SIMT_GEMM, are skipped), each after
  * one untimed pass, with CUDA events on `stream`, and keeps the fastest in
  * the plan's params.flags.  These choices change the work (GEMM and DFT
  * engines, the Jacobi's schedule and starting basis), not the result beyond
- * the FP32 bound.  *chosen and
+ * the FP32 bound; allowing LRSTV_FLAG_BF16X3 lets the tuner trade that bound
+ * for the 3xBF16 one (see the flag).  *chosen and
  * *ms_out (may be NULL) receive the flags kept and their time in ms.  Leaves
  * the plan initialised from Y (lrstv_init) and synchronises `stream`.
  * ERR_ARG for a NULL plan or Y, iters < 0 or other bits in `allowed`; on any

@@ -1068,13 +1068,13 @@ int lrstv_plan_autotune(lrstv_plan *pl, const float *Y, int iters, unsigned allo
                         unsigned *chosen, float *ms_out, void *stream) {
   if (!pl || !Y || iters < 0) return LRSTV_ERR_ARG;
   if (allowed & ~(unsigned)(LRSTV_FLAG_SIMT_GEMM | LRSTV_FLAG_WARM_START | LRSTV_FLAG_SIMT_DFT |
-                            LRSTV_FLAG_JACOBI_PER_SLICE))
+                            LRSTV_FLAG_JACOBI_PER_SLICE | LRSTV_FLAG_BF16X3))
     return LRSTV_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   const int n = iters > 0 ? iters : pl->prm.max_iter;
   const unsigned base = pl->prm.flags & ~allowed;
   // candidates: every subset of `allowed` that check_params accepts
-  unsigned cands[16];
+  unsigned cands[32];
   int nc = 0;
   for (unsigned sub = 0; sub <= allowed; ++sub) {
     if ((sub & ~allowed) != 0) continue;
@@ -1082,7 +1082,7 @@ int lrstv_plan_autotune(lrstv_plan *pl, const float *Y, int iters, unsigned allo
     if ((sub & LRSTV_FLAG_SIMT_GEMM) && (sub & LRSTV_FLAG_SIMT_DFT)) continue;
     lrstv_params trial = pl->prm;
     trial.flags = base | sub;
-    if (check_params(&trial) == LRSTV_OK && nc < 16) cands[nc++] = base | sub;
+    if (check_params(&trial) == LRSTV_OK && nc < 32) cands[nc++] = base | sub;
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {

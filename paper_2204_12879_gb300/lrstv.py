@@ -355,8 +355,9 @@ class Plan:
 
     def autotune(self, Y, iters=0, allowed=None, stream=None):
         """lrstv_plan_autotune: keeps the fastest combination of the allowed
-        flags (default: SIMT_GEMM, SIMT_DFT, JACOBI_PER_SLICE and WARM_START)
-        for this plan and cube.
+        flags (default: SIMT_GEMM, SIMT_DFT, JACOBI_PER_SLICE and WARM_START;
+        FLAG_BF16X3 may be added, which trades the FP32 bound for the 3xBF16
+        one) for this plan and cube.
         Returns (flags kept, their time in ms); leaves the plan initialised
         from Y."""
         if allowed is None:

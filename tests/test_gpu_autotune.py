@@ -61,11 +61,29 @@ def test_autotune_skips_rejected_combinations(L):
         assert flags & L.FLAG_BF16X3 and not flags & L.FLAG_SIMT_GEMM
 
 
+def test_autotune_may_choose_the_bf16_split(L, orc):
+    """With LRSTV_FLAG_BF16X3 allowed the tuner times both splits (never with
+    the SIMT GEMMs), and the plan it leaves meets the 3xBF16 bound (1e-3
+    against the FP64 oracle, as the mixed-precision tests hold it)."""
+    shape = (24, 20, 9)
+    clean, Y = _noisy(shape, 7)
+    allowed = L.FLAG_BF16X3 | L.FLAG_SIMT_GEMM | L.FLAG_WARM_START
+    with L.Plan(*shape, L.Params.make(24, 20, max_iter=6)) as pl:
+        flags, ms = pl.autotune(dev(Y), allowed=allowed)
+        assert ms > 0.0 and (flags & ~allowed) == 0
+        assert not (flags & L.FLAG_BF16X3 and flags & L.FLAG_SIMT_GEMM)
+        X, _ = pl.run(dev(Y))
+        X = host(X, shape)
+    ost = orc.State(Y, orc.Params(n1=24, n2=20))
+    ost.iterate(6)
+    assert maxabs(X, ost.X) <= 1e-3
+
+
 def test_autotune_argument_errors(L):
     shape = (8, 8, 4)
     _, Y = _noisy(shape, 6)
     with L.Plan(*shape, L.Params.make(8, 8)) as pl:
         with pytest.raises(L.LrstvError, match="status 1"):
-            pl.autotune(dev(Y), allowed=L.FLAG_BF16X3)
+            pl.autotune(dev(Y), allowed=L.FLAG_GRAPH)
         with pytest.raises(L.LrstvError, match="status 1"):
             pl.autotune(dev(Y), iters=-1)
