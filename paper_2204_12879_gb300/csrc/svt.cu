@@ -399,6 +399,10 @@ __device__ __forceinline__ float2 ldw(const float2 *p) {
 // wcols interleaved columns of n rows; warp w copies columns w, w + 16, ...
 // With nrm (kPW floats), also each staged column's squared norm (0 for the
 // padding columns).
+// A lane's row pairs of one column: ld2 <= kStageIt * 32 for every packed
+// shape (PkShape: at most 128 row pairs).
+constexpr int kStageIt = 4;
+
 template <bool CG = false>
 __device__ __forceinline__ void pk_stage_in(float4 *dst, int ld2, const float2 *src, int n,
                                             int wcols, float *nrm = nullptr) {
@@ -407,13 +411,24 @@ __device__ __forceinline__ void pk_stage_in(float4 *dst, int ld2, const float2 *
     const float2 *s = src + (size_t)n * c;
     float4 *d = dst + ld2 * c;
     const bool real = c < wcols;
+    // every load of the lane's row pairs is issued before the first store
+    float2 x0[kStageIt], x1[kStageIt];
+#pragma unroll
+    for (int it = 0; it < kStageIt; ++it) {
+      const int m = lane + 32 * it, r0 = 2 * m, r1 = 2 * m + 1;
+      x0[it] = (real && m < ld2 && r0 < n) ? ldw<CG>(s + r0) : make_float2(0.f, 0.f);
+      x1[it] = (real && m < ld2 && r1 < n) ? ldw<CG>(s + r1) : make_float2(0.f, 0.f);
+    }
     float part = 0.0f;
-    for (int m = lane; m < ld2; m += 32) {
-      const int r0 = 2 * m, r1 = 2 * m + 1;
-      const float2 x0 = (real && r0 < n) ? ldw<CG>(s + r0) : make_float2(0.f, 0.f);
-      const float2 x1 = (real && r1 < n) ? ldw<CG>(s + r1) : make_float2(0.f, 0.f);
-      d[m] = make_float4(x0.x, x1.x, x0.y, x1.y);
-      if (nrm) part = fmaf(x0.x, x0.x, fmaf(x0.y, x0.y, fmaf(x1.x, x1.x, fmaf(x1.y, x1.y, part))));
+#pragma unroll
+    for (int it = 0; it < kStageIt; ++it) {
+      const int m = lane + 32 * it;
+      if (m < ld2) {
+        d[m] = make_float4(x0[it].x, x1[it].x, x0[it].y, x1[it].y);
+        if (nrm)
+          part = fmaf(x0[it].x, x0[it].x,
+                      fmaf(x0[it].y, x0[it].y, fmaf(x1[it].x, x1[it].x, fmaf(x1[it].y, x1[it].y, part))));
+      }
     }
     if (nrm) {
       part = warp_sum(part);
@@ -440,6 +455,7 @@ template <int KP>
 struct PkShape {
   static constexpr int KPF = (KP + 1) / 2;  // row pairs per lane, full warp
   static constexpr int LD2 = (16 * KP > 32 * KPF) ? 16 * KP : 32 * KPF;  // row pairs per column
+  static_assert(LD2 <= 32 * kStageIt, "pk_stage_in covers a column in kStageIt loads a lane");
 };
 
 // This thread's share of sum |x_e|^2 over n complex values (e = thread,
