@@ -412,6 +412,8 @@ def run_ours(args, wl_name):
         flags |= lrstv.FLAG_SIMT_DFT
     if args.jacobi_schedule == "slice":
         flags |= lrstv.FLAG_JACOBI_PER_SLICE
+    if args.jacobi_panel == 16:
+        flags |= lrstv.FLAG_JACOBI_PANEL16
     params = lrstv.Params.make(n1, n2, max_iter=iters, flags=flags)
     plan = lrstv.Plan(n1, n2, n3, params)
     ranks = tucker_ranks(args, (n1, n2, n3))
@@ -566,6 +568,7 @@ def run_ours(args, wl_name):
                    "mode3_dft": "tensor cores" if args.dft == "tc" else "SIMT direct sums",
                    "jacobi_schedule": ("task graph: panel-pair tasks of every slice on all SMs"
                                        if args.jacobi_schedule == "tasks" else "one CTA per slice"),
+                   "jacobi_panel": args.jacobi_panel,
                    "l_update": ("Tucker projection, one HOOI sweep per iteration, ranks %s" % (ranks,)
                                 if ranks else "plain (full Tucker ranks)"),
                    "l2": "working set (18 state cubes + spectra, ~330 MB) exceeds the 129 MB L2",
@@ -1010,6 +1013,9 @@ def build_parser():
     ap.add_argument("--jacobi-schedule", choices=["tasks", "slice"], default="tasks",
                     help="the Jacobi's task-graph schedule over all SMs, or one CTA per slice "
                          "(LRSTV_FLAG_JACOBI_PER_SLICE)")
+    ap.add_argument("--jacobi-panel", type=int, choices=[32, 16], default=32,
+                    help="the Jacobi's column panel width: 32 (16-warp CTAs) or 16 (8-warp CTAs, "
+                         "two to an SM; LRSTV_FLAG_JACOBI_PANEL16)")
     ap.add_argument("--micro", choices=["tsvt"], default=None,
                     help="time one standalone operator instead of the iteration")
     ap.add_argument("--shape", default="200,200,16", help="n1,n2,n3 for --micro")

@@ -79,6 +79,11 @@ typedef enum lrstv_status {
                                         sums with twiddle tables) instead of the tensor-core
                                         pipeline (3xTF32, or 3xBF16 with LRSTV_FLAG_BF16X3);
                                         LRSTV_FLAG_SIMT_GEMM puts them there too */
+#define LRSTV_FLAG_JACOBI_PANEL16 1024u /* the Jacobi's column panels 16 wide, each CTA 8 warps
+                                        and two CTAs to an SM, instead of 32 wide with 16-warp
+                                        CTAs (slices up to 256 rows; the same t-SVT to
+                                        rounding, the pairs visited in another order).
+                                        Batches run 32-column panels whatever the flag. */
 
 /* Scalars of Algorithm 1 (Section III-C; parameter roles in Section IV-D).
  *  tau     weight of ||D_w L||_1 (gradient sparsity)
@@ -294,12 +299,13 @@ int lrstv_plan_run_host(lrstv_plan *plan, const float *Y_host, float *X_host, fl
 /* Autotuner (no counterpart in the paper): times `iters` iterations
  * (params.max_iter when 0) of the plan from the device cube Y for every
  * combination of the flags in `allowed` (a subset of LRSTV_FLAG_SIMT_GEMM |
- * LRSTV_FLAG_SIMT_DFT | LRSTV_FLAG_JACOBI_PER_SLICE | LRSTV_FLAG_WARM_START |
- * LRSTV_FLAG_BF16X3; combinations params rejects, and SIMT_DFT together with
- * SIMT_GEMM, are skipped), each after
+ * LRSTV_FLAG_SIMT_DFT | LRSTV_FLAG_JACOBI_PER_SLICE | LRSTV_FLAG_JACOBI_PANEL16 |
+ * LRSTV_FLAG_WARM_START | LRSTV_FLAG_BF16X3; combinations params rejects, and
+ * SIMT_DFT together with SIMT_GEMM, are skipped), each after
  * one untimed pass, with CUDA events on `stream`, and keeps the fastest in
  * the plan's params.flags.  These choices change the work (GEMM and DFT
- * engines, the Jacobi's schedule and starting basis), not the result beyond
+ * engines, the Jacobi's schedule, panel width and starting basis), not the
+ * result beyond
  * the FP32 bound; allowing LRSTV_FLAG_BF16X3 lets the tuner trade that bound
  * for the 3xBF16 one (see the flag).  *chosen and
  * *ms_out (may be NULL) receive the flags kept and their time in ms.  Leaves
@@ -438,7 +444,7 @@ int lrstv_tsvt_noalloc(const float *A, int n1, int n2, int n3, float t, float *o
  *   of every E-update (K x 3 B (n3/2+1) slices) and the scratch of both
  *   passes; lrstv_unroll_bytes reports its size.  w: weights of D_w (NULL =
  *   1, 1, 1).  flags: any of LRSTV_FLAG_SIMT_GEMM, LRSTV_FLAG_SIMT_DFT,
- *   LRSTV_FLAG_JACOBI_PER_SLICE, LRSTV_FLAG_WARM_START (iteration
+ *   LRSTV_FLAG_JACOBI_PER_SLICE, LRSTV_FLAG_JACOBI_PANEL16, LRSTV_FLAG_WARM_START (iteration
  *   k > 0 starts its Jacobi SVDs from iteration k-1's singular vectors, as a
  *   plan does).  iters in 1..4096.
  * lrstv_unroll_forward  Y: device, B cubes back to back (B N floats).

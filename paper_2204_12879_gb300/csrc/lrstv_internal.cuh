@@ -165,6 +165,9 @@ struct JacOpt {
   // SMs the task-graph grid leaves free for concurrent work (another stream's
   // kernels cannot share an SM with a worker CTA, which takes its shared memory)
   int spare_sms = 0;
+  // panel width of the packed kernels (slices of up to 256 rows): 32 columns
+  // with 16-warp CTAs, or 16 with 8-warp CTAs, two to an SM
+  int pw = 32;
 };
 // ints of task-graph scratch for nslices working matrices
 size_t jacobi_task_ints(int nslices);

@@ -195,7 +195,10 @@ __global__ void __launch_bounds__(R <= 8 ? 1024 : 512)
 
 // ---------------------------------------------------------------------------
 // Shared pieces of the packed kernel: panel width, rotation formula.
-constexpr int kPW = 32;  // panel width (columns)
+// Panel width (columns) of the packed kernels: 32 with 16-warp CTAs, or 16
+// with 8-warp CTAs, two of which share an SM (a warp per pair of columns of
+// a panel: PW / 2 warps, PW half-warps).
+constexpr int kPW = 32;
 
 struct Rot {
   float c, s, er, ei;
@@ -235,7 +238,7 @@ __device__ __forceinline__ bool make_rot(float al, float be, float gr, float gi,
 }
 
 
-constexpr int kHW = 16;  // warps per CTA of the packed kernel (32 half-warps)
+constexpr int kHW = kPW / 2;  // warps per CTA of the 32-column packed kernel
 
 __device__ __forceinline__ float half_sum(float v) {
 #pragma unroll
@@ -397,17 +400,17 @@ __device__ __forceinline__ float2 ldw(const float2 *p) {
 
 // shared panel (ld2 row pairs per column, split layout, zero padded) <-
 // wcols interleaved columns of n rows; warp w copies columns w, w + 16, ...
-// With nrm (kPW floats), also each staged column's squared norm (0 for the
+// With nrm (PW floats), also each staged column's squared norm (0 for the
 // padding columns).
 // A lane's row pairs of one column: ld2 <= kStageIt * 32 for every packed
 // shape (PkShape: at most 128 row pairs).
 constexpr int kStageIt = 4;
 
-template <bool CG = false>
+template <int PW, bool CG = false>
 __device__ __forceinline__ void pk_stage_in(float4 *dst, int ld2, const float2 *src, int n,
                                             int wcols, float *nrm = nullptr) {
   const int lane = threadIdx.x & 31;
-  for (int c = threadIdx.x >> 5; c < kPW; c += kHW) {
+  for (int c = threadIdx.x >> 5; c < PW; c += PW / 2) {
     const float2 *s = src + (size_t)n * c;
     float4 *d = dst + ld2 * c;
     const bool real = c < wcols;
@@ -437,10 +440,11 @@ __device__ __forceinline__ void pk_stage_in(float4 *dst, int ld2, const float2 *
   }
 }
 
+template <int PW>
 __device__ __forceinline__ void pk_stage_out(float2 *dst, const float4 *src, int ld2, int n,
                                              int wcols) {
   const int lane = threadIdx.x & 31;
-  for (int c = threadIdx.x >> 5; c < wcols; c += kHW) {
+  for (int c = threadIdx.x >> 5; c < wcols; c += PW / 2) {
     float2 *d = dst + (size_t)n * c;
     const float4 *s = src + ld2 * c;
     for (int m = lane; 2 * m < n; m += 32) {
@@ -495,7 +499,7 @@ __device__ __forceinline__ float pk_setup(int nr, int nc, const float2 *W, float
   if (lane == 0) s_red[warp] = part;
   __syncthreads();
   if (warp == 0) {
-    float v = lane < kHW ? s_red[lane] : 0.0f;
+    float v = lane < (int)(blockDim.x >> 5) ? s_red[lane] : 0.0f;
     v = warp_sum(v);
     if (lane == 0) s_red[0] = v;
   }
@@ -524,16 +528,16 @@ __device__ __forceinline__ float pk_tolerance(float tol, float fro2, int nc, flo
 
 // The pairs inside one staged panel (W in sW with squared norms s_na, V in
 // sVa; wa real columns): 31 rounds of 16 disjoint pairs, one per warp.
-template <int KP>
+template <int KP, int PW>
 __device__ __forceinline__ void pk_intra(float4 *sW, float4 *sVa, float *s_na, int wa, float tol,
                                          float negl, unsigned &n_pairs, unsigned &n_rot,
                                          int &rotated) {
   constexpr int KPF = PkShape<KP>::KPF;
   constexpr int LD2 = PkShape<KP>::LD2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int r = 0; r < kPW - 1; ++r) {
+  for (int r = 0; r < PW - 1; ++r) {
     int p, q;
-    pair_of(r, warp, kPW, p, q);
+    pair_of(r, warp, PW, p, q);
     if (p < wa && q < wa) {
       float4 xa[KPF], xb[KPF];
 #pragma unroll
@@ -580,7 +584,7 @@ __device__ __forceinline__ void pk_intra(float4 *sW, float4 *sVa, float *s_na, i
 // which warp w owns streamed columns 2c, 2c+1 (c = (w + R) mod 16) and its
 // half-warps rotate them in swapped order, so only the warp synchronises
 // between the two sub-steps and the block once per double round.
-template <int KP>
+template <int KP, int PW>
 __device__ __forceinline__ void pk_cross_pass(float4 (&aW)[KP], float4 (&aV)[KP], bool mine,
                                               float4 *sW, float4 *sVb, float *s_nb, int wb,
                                               float tol, float negl, unsigned &n_pairs,
@@ -593,9 +597,9 @@ __device__ __forceinline__ void pk_cross_pass(float4 (&aW)[KP], float4 (&aV)[KP]
   // panel (the whole warp shuffles: both halves compute theirs)
   float al_reg = half_sum(pk_norm<KP>(aW));
   __syncthreads();
-  for (int r = 0; r < kPW; ++r) {
+  for (int r = 0; r < PW; ++r) {
     const int sub = r & 1;
-    const int cpi = (warp + (r >> 1)) & (kPW / 2 - 1);
+    const int cpi = (warp + (r >> 1)) & (PW / 2 - 1);
     const int j = 2 * cpi + ((unit & 1) ^ sub);
     const bool real = mine && j < wb;
 #pragma unroll
@@ -665,7 +669,7 @@ __device__ __forceinline__ void pk_to_registers(const float4 *sW, const float4 *
 }
 
 // Panel a back to global memory from the registers (W) and, through sVa, V.
-template <int KP>
+template <int KP, int PW>
 __device__ __forceinline__ void pk_from_registers(const float4 (&aW)[KP], const float4 (&aV)[KP],
                                                   bool mine, float4 *sVa, float2 *Wa,
                                                   float2 *Va, int nr, int nc, int wa) {
@@ -683,7 +687,7 @@ __device__ __forceinline__ void pk_from_registers(const float4 (&aW)[KP], const 
       if (2 * m + 1 < nr) wcol[2 * m + 1] = make_float2(aW[k].y, aW[k].w);
     }
   }
-  pk_stage_out(Va, sVa, LD2, nc, wa);
+  pk_stage_out<PW>(Va, sVa, LD2, nc, wa);
 }
 
 // g_i = max(1 - t / sigma_i, 0) applied to V's columns (t < 0: V unscaled),
@@ -692,7 +696,7 @@ template <bool CG>
 __device__ __forceinline__ void pk_epilogue(int nr, int nc, const float2 *W, float2 *V, float t) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (t < 0.0f) return;
-  for (int i = warp; i < nc; i += kHW) {
+  for (int i = warp; i < nc; i += (int)(blockDim.x >> 5)) {
     const float2 *wi = W + (size_t)nr * i;
     float n2 = 0.f;
     for (int row = lane; row < nr; row += 32) {
@@ -717,27 +721,27 @@ __device__ __forceinline__ void pk_epilogue(int nr, int nc, const float2 *W, flo
 // Writes the sweep count (negative at the cap) to *sweeps_slot.  Shared by the
 // one-slice-per-CTA kernel and the persistent batch kernel, so both compute
 // bit-identical results.
-template <int KP>
+template <int KP, int PW>
 __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float2 *V, float t,
                                                 int max_sweeps, float tol, float negl_rel,
                                                 int *sweeps_slot, unsigned long long *work,
                                                 float4 *smem, int warm, float skip_t,
                                                 float gms2) {
   constexpr int LD2 = PkShape<KP>::LD2;
-  float4 *sW = smem;               // panel a (own pairs), then panel b: W
-  float4 *sVa = sW + kPW * LD2;    // panel a: V
-  float4 *sVb = sVa + kPW * LD2;   // panel b: V
+  float4 *sW = smem;              // panel a (own pairs), then panel b: W
+  float4 *sVa = sW + PW * LD2;    // panel a: V
+  float4 *sVb = sVa + PW * LD2;   // panel b: V
   const int tid = threadIdx.x, ul = tid & 15, unit = tid >> 4;
   __shared__ float s_red[32];
   __shared__ int s_rot;
   // squared column norms of panel a and of the streamed panel b: exact when
   // a panel is staged, then carried through each rotation by the 2x2 update
   // (|a|^2 - d, |b|^2 + d), so that a pair's test needs only its inner product
-  __shared__ float s_na[kPW], s_nb[kPW];
+  __shared__ float s_na[PW], s_nb[PW];
 
   const float fro2 = pk_setup<false>(nr, nc, W, V, warm, s_red);
   const float negl = negl_rel * fro2;
-  const int npan = (nc + kPW - 1) / kPW;
+  const int npan = (nc + PW - 1) / PW;
   unsigned n_pairs = 0, n_rot = 0;  // lane 0 (own pairs) and ul 0 (cross pairs) count
   int sweeps = (nc < 2) ? 1 : 0;
   bool converged = (nc < 2);
@@ -753,25 +757,25 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
     if (tid == 0) s_rot = 0;
     int rotated = 0;
     for (int a = 0; a < npan; ++a) {
-      const int ca = a * kPW, wa = min(kPW, nc - ca);
+      const int ca = a * PW, wa = min(PW, nc - ca);
       __syncthreads();
-      pk_stage_in(sW, LD2, W + (size_t)nr * ca, nr, wa, s_na);
-      pk_stage_in(sVa, LD2, V + (size_t)nc * ca, nc, wa);
+      pk_stage_in<PW>(sW, LD2, W + (size_t)nr * ca, nr, wa, s_na);
+      pk_stage_in<PW>(sVa, LD2, V + (size_t)nc * ca, nc, wa);
       __syncthreads();
-      pk_intra<KP>(sW, sVa, s_na, wa, tol, negl, n_pairs, n_rot, rotated);
+      pk_intra<KP, PW>(sW, sVa, s_na, wa, tol, negl, n_pairs, n_rot, rotated);
       const bool mine = unit < wa;
       pk_to_registers<KP>(sW, sVa, aW, aV);
       for (int b = a + 1; b < npan; ++b) {
-        const int cb = b * kPW, wb = min(kPW, nc - cb);
+        const int cb = b * PW, wb = min(PW, nc - cb);
         __syncthreads();
-        pk_stage_in(sW, LD2, W + (size_t)nr * cb, nr, wb, s_nb);
-        pk_stage_in(sVb, LD2, V + (size_t)nc * cb, nc, wb);
-        pk_cross_pass<KP>(aW, aV, mine, sW, sVb, s_nb, wb, tol, negl, n_pairs, n_rot, rotated);
-        pk_stage_out(W + (size_t)nr * cb, sW, LD2, nr, wb);
-        pk_stage_out(V + (size_t)nc * cb, sVb, LD2, nc, wb);
+        pk_stage_in<PW>(sW, LD2, W + (size_t)nr * cb, nr, wb, s_nb);
+        pk_stage_in<PW>(sVb, LD2, V + (size_t)nc * cb, nc, wb);
+        pk_cross_pass<KP, PW>(aW, aV, mine, sW, sVb, s_nb, wb, tol, negl, n_pairs, n_rot, rotated);
+        pk_stage_out<PW>(W + (size_t)nr * cb, sW, LD2, nr, wb);
+        pk_stage_out<PW>(V + (size_t)nc * cb, sVb, LD2, nc, wb);
       }
-      pk_from_registers<KP>(aW, aV, mine, sVa, W + (size_t)nr * ca, V + (size_t)nc * ca, nr, nc,
-                            wa);
+      pk_from_registers<KP, PW>(aW, aV, mine, sVa, W + (size_t)nr * ca, V + (size_t)nc * ca, nr,
+                                nc, wa);
     }
     if (rotated) s_rot = 1;
     __syncthreads();
@@ -787,14 +791,15 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
   }
 }
 
-// Slices of up to 64 rows fit in 64 registers a thread: two CTAs share an SM.
-template <int KP>
-__global__ void __launch_bounds__(kHW * 32, KP <= 2 ? 2 : 1)
+// Slices of up to 64 rows fit in 64 registers a thread, and 16-column panels
+// take 8-warp CTAs: two CTAs share an SM.
+template <int KP, int PW>
+__global__ void __launch_bounds__(PW * 16, (KP <= 2 || PW == 16) ? 2 : 1)
     k_jacobi_pk(int nr, int nc, size_t wstride, size_t vstride, float2 *W_all, float2 *V_all,
                 float t, int max_sweeps, float tol, float negl_rel, int *__restrict__ sweeps_out,
                 unsigned long long *__restrict__ work, JacOpt o) {
   extern __shared__ float4 smem_f4[];
-  jacobi_pk_slice<KP>(nr, nc, W_all + (size_t)blockIdx.x * wstride,
+  jacobi_pk_slice<KP, PW>(nr, nc, W_all + (size_t)blockIdx.x * wstride,
                       V_all + (size_t)blockIdx.x * vstride, t, max_sweeps, tol, negl_rel,
                       sweeps_out + blockIdx.x, work, smem_f4, o.warm, o.t_svt,
                       o.ms2 ? o.ms2[blockIdx.x / o.group] : -1.0f);
@@ -862,6 +867,8 @@ __device__ __forceinline__ bool tour_pair(int npan, int r, int i, int &p, int &q
 }
 // tasks per round at most: npan (even npan, round 0) or (npan + 1) / 2
 __device__ __forceinline__ int tour_width(int npan) { return (npan & 1) ? (npan + 1) / 2 : npan; }
+// task ids per slice: tour_width of 512 columns in 16-column panels (32)
+constexpr int kTaskIds = 32;
 
 struct TaskView {
   int *head, *tail, *finished, *err;
@@ -883,9 +890,10 @@ struct TaskView {
     qtask = (int *)(negl + ns);
     qready = qtask + cap;
   }
-  // queues the tasks of round r of slice s (one thread)
+  // queues the tasks of round r of slice s (one thread); a task is
+  // s * kTaskIds + its pair index in the round
   __device__ void push_round(int s, int r, int npan) {
-    int ids[16], c = 0;
+    int ids[kTaskIds], c = 0;
     for (int i = 0; i < tour_width(npan); ++i) {
       int p, q;
       if (tour_pair(npan, r, i, p, q)) ids[c++] = i;
@@ -895,7 +903,7 @@ struct TaskView {
     __threadfence();
     for (int k = 0; k < c; ++k) {
       const int idx = atomicAdd(tail, 1);
-      qtask[idx & (cap - 1)] = s * 16 + ids[k];
+      qtask[idx & (cap - 1)] = s * kTaskIds + ids[k];
       __threadfence();
       atomicExch(qready + (idx & (cap - 1)), idx + 1);
     }
@@ -910,7 +918,7 @@ __global__ void __launch_bounds__(kHW * 32)
     k_jacobi_task_setup(int nr, int nc, int nslices, size_t wstride, size_t vstride,
                         float2 *W_all, float2 *V_all, float t, int max_sweeps, float tol0,
                         float negl_rel, int *__restrict__ sweeps_out, JacOpt o, int *sched,
-                        int cap) {
+                        int cap, int pw) {
   __shared__ float s_red[32];
   const int s = blockIdx.x;
   TaskView tv(sched, nslices, cap);
@@ -932,7 +940,7 @@ __global__ void __launch_bounds__(kHW * 32)
       atomicAdd(tv.finished, 1);
     } else {
       sweeps_out[s] = -max_sweeps;  // until the slice ends: a run that stops early reports it
-      tv.push_round(s, 0, (nc + kPW - 1) / kPW);
+      tv.push_round(s, 0, (nc + pw - 1) / pw);
     }
   }
 }
@@ -940,19 +948,19 @@ __global__ void __launch_bounds__(kHW * 32)
 // The persistent worker grid: every CTA takes tasks until every slice has
 // ended (or a wait for work runs out, after kTaskWaitNs; the slices still
 // open then stay reported as capped).
-template <int KP>
-__global__ void __launch_bounds__(kHW * 32, KP <= 2 ? 2 : 1)
+template <int KP, int PW>
+__global__ void __launch_bounds__(PW * 16, (KP <= 2 || PW == 16) ? 2 : 1)
     k_jacobi_tasks(int nr, int nc, int nslices, size_t wstride, size_t vstride, float2 *W_all,
                    float2 *V_all, float t, int max_sweeps, int *__restrict__ sweeps_out,
                    unsigned long long *__restrict__ work, int *sched, int cap) {
   extern __shared__ float4 smem_f4[];
   constexpr int LD2 = PkShape<KP>::LD2;
-  float4 *sW = smem_f4, *sVa = sW + kPW * LD2, *sVb = sVa + kPW * LD2;
-  __shared__ float s_na[kPW], s_nb[kPW];
+  float4 *sW = smem_f4, *sVa = sW + PW * LD2, *sVb = sVa + PW * LD2;
+  __shared__ float s_na[PW], s_nb[PW];
   __shared__ int s_task, s_last, s_end;
   const int tid = threadIdx.x, ul = tid & 15, unit = tid >> 4;
   TaskView tv(sched, nslices, cap);
-  const int npan = (nc + kPW - 1) / kPW, nrounds = tour_rounds(npan);
+  const int npan = (nc + PW - 1) / PW, nrounds = tour_rounds(npan);
   unsigned n_pairs = 0, n_rot = 0;
   float4 aW[KP], aV[KP];
   for (;;) {
@@ -981,7 +989,7 @@ __global__ void __launch_bounds__(kHW * 32, KP <= 2 ? 2 : 1)
     __syncthreads();
     const int task = s_task;
     if (task < 0) break;
-    const int s = task >> 4, pi = task & 15;
+    const int s = task / kTaskIds, pi = task % kTaskIds;
     float2 *W = W_all + (size_t)s * wstride, *V = V_all + (size_t)s * vstride;
     const int r = ld_relaxed(tv.round + s);
     const float tol = ((const volatile float *)tv.tol)[s];
@@ -989,26 +997,26 @@ __global__ void __launch_bounds__(kHW * 32, KP <= 2 ? 2 : 1)
     int pa, pb;
     tour_pair(npan, r, pi, pa, pb);  // pa is a real panel; pb >= npan: pa's own pairs
     int rotated = 0;
-    const int ca = pa * kPW, wa = min(kPW, nc - ca);
-    pk_stage_in<true>(sW, LD2, W + (size_t)nr * ca, nr, wa, s_na);
-    pk_stage_in<true>(sVa, LD2, V + (size_t)nc * ca, nc, wa);
+    const int ca = pa * PW, wa = min(PW, nc - ca);
+    pk_stage_in<PW, true>(sW, LD2, W + (size_t)nr * ca, nr, wa, s_na);
+    pk_stage_in<PW, true>(sVa, LD2, V + (size_t)nc * ca, nc, wa);
     __syncthreads();
     if (pb >= npan) {  // panel pa's own pairs
-      pk_intra<KP>(sW, sVa, s_na, wa, tol, negl, n_pairs, n_rot, rotated);
-      pk_stage_out(W + (size_t)nr * ca, sW, LD2, nr, wa);
-      pk_stage_out(V + (size_t)nc * ca, sVa, LD2, nc, wa);
+      pk_intra<KP, PW>(sW, sVa, s_na, wa, tol, negl, n_pairs, n_rot, rotated);
+      pk_stage_out<PW>(W + (size_t)nr * ca, sW, LD2, nr, wa);
+      pk_stage_out<PW>(V + (size_t)nc * ca, sVa, LD2, nc, wa);
     } else {  // panel pa (registers) against panel pb (streamed)
-      const int cb = pb * kPW, wb = min(kPW, nc - cb);
+      const int cb = pb * PW, wb = min(PW, nc - cb);
       const bool mine = unit < wa;
       pk_to_registers<KP>(sW, sVa, aW, aV);
       __syncthreads();
-      pk_stage_in<true>(sW, LD2, W + (size_t)nr * cb, nr, wb, s_nb);
-      pk_stage_in<true>(sVb, LD2, V + (size_t)nc * cb, nc, wb);
-      pk_cross_pass<KP>(aW, aV, mine, sW, sVb, s_nb, wb, tol, negl, n_pairs, n_rot, rotated);
-      pk_stage_out(W + (size_t)nr * cb, sW, LD2, nr, wb);
-      pk_stage_out(V + (size_t)nc * cb, sVb, LD2, nc, wb);
-      pk_from_registers<KP>(aW, aV, mine, sVa, W + (size_t)nr * ca, V + (size_t)nc * ca, nr, nc,
-                            wa);
+      pk_stage_in<PW, true>(sW, LD2, W + (size_t)nr * cb, nr, wb, s_nb);
+      pk_stage_in<PW, true>(sVb, LD2, V + (size_t)nc * cb, nc, wb);
+      pk_cross_pass<KP, PW>(aW, aV, mine, sW, sVb, s_nb, wb, tol, negl, n_pairs, n_rot, rotated);
+      pk_stage_out<PW>(W + (size_t)nr * cb, sW, LD2, nr, wb);
+      pk_stage_out<PW>(V + (size_t)nc * cb, sVb, LD2, nc, wb);
+      pk_from_registers<KP, PW>(aW, aV, mine, sVa, W + (size_t)nr * ca, V + (size_t)nc * ca, nr,
+                                nc, wa);
     }
     // the panels are written (every thread fences its own stores); then the
     // task counts off its slice's round
@@ -1084,42 +1092,43 @@ __global__ void __launch_bounds__(kHW * 32, 1)
     const float negl = ((float)tk.nr * eps) * ((float)tk.nr * eps);
     const int KP = (tk.nr + 31) / 32;
     if (KP <= 1)
-      jacobi_pk_slice<1>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
+      jacobi_pk_slice<1, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
     else if (KP <= 2)
-      jacobi_pk_slice<2>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
+      jacobi_pk_slice<2, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
     else if (KP <= 4)
-      jacobi_pk_slice<4>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
+      jacobi_pk_slice<4, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
     else if (KPMAX <= 7 || KP <= 7)
-      jacobi_pk_slice<7>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
+      jacobi_pk_slice<7, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
     else
-      jacobi_pk_slice<KPMAX>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
+      jacobi_pk_slice<KPMAX, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
   }
 }
 
 int task_cap(int nslices) {
   // a slot is reused only after the ring has wrapped: queued-but-untaken
-  // tasks stay below 5 per live slice and claimed-but-unfilled slots below one
-  // per worker CTA, far under the capacity
+  // tasks stay below one round (at most kTaskIds) per live slice and
+  // claimed-but-unfilled slots below one per worker CTA, under the capacity
   int cap = 4096;
-  while (cap < 16 * nslices + 4096) cap <<= 1;
+  while (cap < kTaskIds * nslices + 4096) cap <<= 1;
   return cap;
 }
 
-template <int KP>
+template <int KP, int PW>
 cudaError_t launch_tasks(int nslices, int nr, int nc, size_t ws, size_t vs, float2 *W, float2 *V,
                          float t, int max_sweeps, float tol, float negl, int *sweeps,
                          unsigned long long *work, const JacOpt &o, cudaStream_t st) {
-  const size_t smem = sizeof(float4) * 3 * (size_t)kPW * PkShape<KP>::LD2;
-  cudaError_t e = cudaFuncSetAttribute(k_jacobi_tasks<KP>,
+  const size_t smem = sizeof(float4) * 3 * (size_t)PW * PkShape<KP>::LD2;
+  cudaError_t e = cudaFuncSetAttribute(k_jacobi_tasks<KP, PW>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int dev = 0, nsm = 0, occ = 0;
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jacobi_tasks<KP>, kHW * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jacobi_tasks<KP, PW>, PW * 16,
+                                                      smem);
   if (e != cudaSuccess) return e;
   const int cap = task_cap(nslices);
-  const int npan = (nc + kPW - 1) / kPW;
+  const int npan = (nc + PW - 1) / PW;
   const int width = (npan & 1) ? (npan + 1) / 2 : npan;
   // workers: the resident CTAs of every SM but the spare ones, and no more
   // than the tasks a round offers
@@ -1131,26 +1140,46 @@ cudaError_t launch_tasks(int nslices, int nr, int nc, size_t ws, size_t vs, floa
   e = cudaMemsetAsync(o.sched, 0, sizeof(int) * jacobi_task_ints(nslices), st);
   if (e != cudaSuccess) return e;
   k_jacobi_task_setup<<<nslices, kHW * 32, 0, st>>>(nr, nc, nslices, ws, vs, W, V, t, max_sweeps,
-                                                     tol, negl, sweeps, o, o.sched, cap);
+                                                     tol, negl, sweeps, o, o.sched, cap, PW);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_jacobi_tasks<KP><<<(unsigned)grid, kHW * 32, smem, st>>>(nr, nc, nslices, ws, vs, W, V, t,
-                                                               max_sweeps, sweeps, work, o.sched,
-                                                               cap);
+  k_jacobi_tasks<KP, PW><<<(unsigned)grid, PW * 16, smem, st>>>(nr, nc, nslices, ws, vs, W, V, t,
+                                                                  max_sweeps, sweeps, work,
+                                                                  o.sched, cap);
   return cudaGetLastError();
 }
 
-template <int KP>
+template <int KP, int PW>
 cudaError_t launch_pk(int nslices, int nr, int nc, size_t ws, size_t vs, float2 *W, float2 *V,
                       float t, int max_sweeps, float tol, float negl, int *sweeps,
                       unsigned long long *work, const JacOpt &o, cudaStream_t st) {
-  const size_t smem = sizeof(float4) * 3 * (size_t)kPW * PkShape<KP>::LD2;
-  cudaError_t e = cudaFuncSetAttribute(k_jacobi_pk<KP>,
+  const size_t smem = sizeof(float4) * 3 * (size_t)PW * PkShape<KP>::LD2;
+  cudaError_t e = cudaFuncSetAttribute(k_jacobi_pk<KP, PW>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_jacobi_pk<KP><<<nslices, kHW * 32, smem, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl,
-                                                   sweeps, work, o);
+  k_jacobi_pk<KP, PW><<<nslices, PW * 16, smem, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol,
+                                                      negl, sweeps, work, o);
   return cudaGetLastError();
+}
+
+// the packed kernel of a slice height (KP row pairs per lane) and panel width
+template <int PW>
+cudaError_t launch_packed(bool tasks, int nslices, int nr, int nc, size_t ws, size_t vs,
+                          float2 *W, float2 *V, float t, int max_sweeps, float tol, float negl,
+                          int *sweeps, unsigned long long *work, const JacOpt &o,
+                          cudaStream_t st) {
+  const int KP = (nr + 31) / 32;
+#define LRSTV_PK(K)                                                                            \
+  return tasks ? launch_tasks<K, PW>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl,  \
+                                     sweeps, work, o, st)                                      \
+               : launch_pk<K, PW>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl,     \
+                                  sweeps, work, o, st)
+  if (KP <= 1) LRSTV_PK(1);
+  if (KP <= 2) LRSTV_PK(2);
+  if (KP <= 4) LRSTV_PK(4);
+  if (KP <= 7) LRSTV_PK(7);
+  LRSTV_PK(8);
+#undef LRSTV_PK
 }
 
 // sigma_i = |w_i| and V_s = V diag(g), g = max(1 - t / sigma, 0), with the same
@@ -1253,14 +1282,14 @@ cudaError_t launch_ns_update(int nc, int nslices, size_t dstride, float2 *V, con
 // panel in registers across the streamed panels and reads each slice's data
 // fewer times, and the task graph's extra panel traffic costs more than its
 // balance gains (measured at 256 x 256 x 191: 288 slices, 17.1 against 13.3 ms).
-bool tasks_pay(int nslices, int nr) {
+bool tasks_pay(int nslices, int nr, int pw) {
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  const int per_sm = nr <= 64 ? 2 : 1;  // the packed kernel's CTAs per SM
+  const int per_sm = (nr <= 64 || pw == 16) ? 2 : 1;  // the packed kernel's CTAs per SM
   return nslices < nsm * per_sm;
 }
 
@@ -1309,21 +1338,14 @@ cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, floa
   const float tol = 8.0f * sqrtf((float)nr) * eps;
   const float negl = o.negl_rel >= 0.0f ? o.negl_rel : ((float)nr * eps) * ((float)nr * eps);
   const size_t ws = d.P, vs = (size_t)nc * nc;
-  if (nr <= 256 && nc >= 2 && o.sched && tasks_pay(nslices, nr)) {
-    const int KP = (nr + 31) / 32;
-    if (KP <= 1) return launch_tasks<1>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
-    if (KP <= 2) return launch_tasks<2>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
-    if (KP <= 4) return launch_tasks<4>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
-    if (KP <= 7) return launch_tasks<7>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
-    return launch_tasks<8>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
-  }
   if (nr <= 256 && nc >= 2) {
-    const int KP = (nr + 31) / 32;  // row pairs per lane of a half-warp
-    if (KP <= 1) return launch_pk<1>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
-    if (KP <= 2) return launch_pk<2>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
-    if (KP <= 4) return launch_pk<4>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
-    if (KP <= 7) return launch_pk<7>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
-    return launch_pk<8>(nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o, st);
+    // the task graph when one CTA per slice would leave SMs idle
+    const bool tasks = o.sched && tasks_pay(nslices, nr, o.pw);
+    if (o.pw == 16)
+      return launch_packed<16>(tasks, nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl,
+                               sweeps, work, o, st);
+    return launch_packed<32>(tasks, nslices, nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl,
+                             sweeps, work, o, st);
   }
   dim3 grid(nslices), block(32 * nw);
   if (R <= 1) k_jacobi<1><<<grid, block, 0, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol, negl, sweeps, work, o);

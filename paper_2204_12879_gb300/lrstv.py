@@ -22,7 +22,7 @@ __all__ = [
     "lrstv_tsvt_noalloc", "lrstv_peak_probe", "PEAK_UNITS",
     "lrstv_denoise", "BLOCK", "FLAG_F_THRESH_EXACT", "FLAG_NO_GAMMA4", "FLAG_GRAPH",
     "FLAG_STRICT", "FLAG_SIMT_GEMM", "FLAG_WARM_START", "FLAG_ISO_TV", "FLAG_BF16X3",
-    "FLAG_SIMT_DFT", "FLAG_JACOBI_PER_SLICE",
+    "FLAG_SIMT_DFT", "FLAG_JACOBI_PER_SLICE", "FLAG_JACOBI_PANEL16",
     "EXPORTED",
 ]
 
@@ -36,6 +36,7 @@ FLAG_ISO_TV = 64
 FLAG_BF16X3 = 128
 FLAG_SIMT_DFT = 256
 FLAG_JACOBI_PER_SLICE = 512
+FLAG_JACOBI_PANEL16 = 1024
 
 BLOCK = {"Y": 0, "L": 1, "Z": 2, "S": 3, "G1": 4, "G2": 5, "F": 6, "E": 7, "G3": 8, "G4": 9,
          "TZ": 10}
@@ -355,13 +356,15 @@ class Plan:
 
     def autotune(self, Y, iters=0, allowed=None, stream=None):
         """lrstv_plan_autotune: keeps the fastest combination of the allowed
-        flags (default: SIMT_GEMM, SIMT_DFT, JACOBI_PER_SLICE and WARM_START;
+        flags (default: SIMT_GEMM, SIMT_DFT, JACOBI_PER_SLICE, JACOBI_PANEL16
+        and WARM_START;
         FLAG_BF16X3 may be added, which trades the FP32 bound for the 3xBF16
         one) for this plan and cube.
         Returns (flags kept, their time in ms); leaves the plan initialised
         from Y."""
         if allowed is None:
-            allowed = FLAG_SIMT_GEMM | FLAG_SIMT_DFT | FLAG_JACOBI_PER_SLICE | FLAG_WARM_START
+            allowed = (FLAG_SIMT_GEMM | FLAG_SIMT_DFT | FLAG_JACOBI_PER_SLICE |
+                       FLAG_JACOBI_PANEL16 | FLAG_WARM_START)
         chosen = ctypes.c_uint()
         ms = _F()
         _call("lrstv_plan_autotune", self._h, _dev(Y, self.N), int(iters), int(allowed),

@@ -71,7 +71,7 @@ def test_argument_errors_before_any_cuda_call(lib):
     assert lib.lrstv_plan_create(8, 8, 8, None, ctypes.byref(h)) == 1
     bad = lrstv.Params.make(8, 8, mu0=-1.0)
     assert lib.lrstv_plan_create(8, 8, 8, ctypes.byref(bad), ctypes.byref(h)) == 1
-    bad = lrstv.Params.make(8, 8, flags=1 << 10)
+    bad = lrstv.Params.make(8, 8, flags=1 << 11)
     assert lib.lrstv_plan_create(8, 8, 8, ctypes.byref(bad), ctypes.byref(h)) == 1
     # the split-BF16 GEMMs exist on the tensor-core path only
     bad = lrstv.Params.make(8, 8, flags=lrstv.FLAG_BF16X3 | lrstv.FLAG_SIMT_GEMM)

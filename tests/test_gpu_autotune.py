@@ -30,8 +30,10 @@ def _noisy(shape, seed):
 def test_autotune_keeps_a_candidate_and_parity(L, orc, shape):
     clean, Y = _noisy(shape, 3)
     n1, n2, _ = shape
-    # the default search: GEMM engine, mode-3 DFT engine, Jacobi schedule, warm start
-    allowed = L.FLAG_SIMT_GEMM | L.FLAG_SIMT_DFT | L.FLAG_JACOBI_PER_SLICE | L.FLAG_WARM_START
+    # the default search: GEMM engine, mode-3 DFT engine, Jacobi schedule and
+    # panel width, warm start
+    allowed = (L.FLAG_SIMT_GEMM | L.FLAG_SIMT_DFT | L.FLAG_JACOBI_PER_SLICE |
+               L.FLAG_JACOBI_PANEL16 | L.FLAG_WARM_START)
     with L.Plan(*shape, L.Params.make(n1, n2, max_iter=20, flags=L.FLAG_GRAPH)) as pl:
         flags, ms = pl.autotune(dev(Y), iters=10)
         assert (flags & ~allowed) == L.FLAG_GRAPH  # only the allowed bits move

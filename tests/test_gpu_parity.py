@@ -510,16 +510,19 @@ def test_dft_engines_agree(L, orc):
 @pytest.mark.parametrize("shape", [(32, 32, 16), (70, 65, 9), (29, 37, 10), (200, 64, 4)])
 def test_jacobi_schedules_agree(L, orc, shape):
     """The task-graph Jacobi (the default: every SM takes panel-pair tasks of
-    any slice) and one CTA per slice (LRSTV_FLAG_JACOBI_PER_SLICE) visit every
-    column pair once per sweep in different orders: whole warm-started runs of
-    both are within the run bound of the oracle.  Shapes with one, three and
+    any slice) and one CTA per slice (LRSTV_FLAG_JACOBI_PER_SLICE), each with
+    32- and 16-column panels (LRSTV_FLAG_JACOBI_PANEL16), visit every column
+    pair once per sweep in different orders: whole warm-started runs of all
+    four are within the run bound of the oracle.  Shapes with one, three and
     two column panels (odd and even counts: the tournament's one or two empty
     players) and a transposed slice."""
     n1, n2, n3 = shape
     _, Y = _noisy(shape, 23)
     iters = 10
     outs = []
-    for flags in (L.FLAG_WARM_START, L.FLAG_WARM_START | L.FLAG_JACOBI_PER_SLICE):
+    for flags in (L.FLAG_WARM_START, L.FLAG_WARM_START | L.FLAG_JACOBI_PER_SLICE,
+                  L.FLAG_WARM_START | L.FLAG_JACOBI_PANEL16,
+                  L.FLAG_WARM_START | L.FLAG_JACOBI_PER_SLICE | L.FLAG_JACOBI_PANEL16):
         with _plan(L, shape, max_iter=iters, flags=flags) as pl:
             X, S, st = pl.run(dev(Y), stats=True)
             assert st.jacobi_unconverged == 0
