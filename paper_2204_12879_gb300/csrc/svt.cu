@@ -398,44 +398,71 @@ __device__ __forceinline__ float2 ldw(const float2 *p) {
   return CG ? __ldcg(p) : *p;
 }
 
-// shared panel (ld2 row pairs per column, split layout, zero padded) <-
-// wcols interleaved columns of n rows; warp w copies columns w, w + 16, ...
-// With nrm (PW floats), also each staged column's squared norm (0 for the
-// padding columns).
-// A lane's row pairs of one column: ld2 <= kStageIt * 32 for every packed
-// shape (PkShape: at most 128 row pairs).
+// Staging of panels into shared memory: a shared panel holds ld2 row pairs
+// per column in the split layout, zero padded, of wcols columns of n rows;
+// warp w copies columns w, w + PW / 2.  A lane's row pairs of one column:
+// ld2 <= kStageIt * 32 for every packed shape (PkShape: at most 128).
 constexpr int kStageIt = 4;
 
-template <int PW, bool CG = false>
-__device__ __forceinline__ void pk_stage_in(float4 *dst, int ld2, const float2 *src, int n,
-                                            int wcols, float *nrm = nullptr) {
+// One column of n rows into registers (the lane's row pairs m = lane + 32 it,
+// zeros past n or for a padding column), and from there into a shared panel
+// column in the split row-pair layout, returning the lane's part of its
+// squared norm.
+template <bool CG>
+__device__ __forceinline__ void col_load(float2 (&x0)[kStageIt], float2 (&x1)[kStageIt],
+                                         const float2 *s, int n, int ld2, bool real) {
   const int lane = threadIdx.x & 31;
-  for (int c = threadIdx.x >> 5; c < PW; c += PW / 2) {
-    const float2 *s = src + (size_t)n * c;
-    float4 *d = dst + ld2 * c;
-    const bool real = c < wcols;
-    // every load of the lane's row pairs is issued before the first store
-    float2 x0[kStageIt], x1[kStageIt];
 #pragma unroll
-    for (int it = 0; it < kStageIt; ++it) {
-      const int m = lane + 32 * it, r0 = 2 * m, r1 = 2 * m + 1;
-      x0[it] = (real && m < ld2 && r0 < n) ? ldw<CG>(s + r0) : make_float2(0.f, 0.f);
-      x1[it] = (real && m < ld2 && r1 < n) ? ldw<CG>(s + r1) : make_float2(0.f, 0.f);
-    }
-    float part = 0.0f;
+  for (int it = 0; it < kStageIt; ++it) {
+    const int m = lane + 32 * it, r0 = 2 * m, r1 = 2 * m + 1;
+    x0[it] = (real && m < ld2 && r0 < n) ? ldw<CG>(s + r0) : make_float2(0.f, 0.f);
+    x1[it] = (real && m < ld2 && r1 < n) ? ldw<CG>(s + r1) : make_float2(0.f, 0.f);
+  }
+}
+
+__device__ __forceinline__ float col_store(float4 *d, const float2 (&x0)[kStageIt],
+                                           const float2 (&x1)[kStageIt], int ld2) {
+  const int lane = threadIdx.x & 31;
+  float part = 0.0f;
 #pragma unroll
-    for (int it = 0; it < kStageIt; ++it) {
-      const int m = lane + 32 * it;
-      if (m < ld2) {
-        d[m] = make_float4(x0[it].x, x1[it].x, x0[it].y, x1[it].y);
-        if (nrm)
-          part = fmaf(x0[it].x, x0[it].x,
-                      fmaf(x0[it].y, x0[it].y, fmaf(x1[it].x, x1[it].x, fmaf(x1[it].y, x1[it].y, part))));
-      }
+  for (int it = 0; it < kStageIt; ++it) {
+    const int m = lane + 32 * it;
+    if (m < ld2) {
+      d[m] = make_float4(x0[it].x, x1[it].x, x0[it].y, x1[it].y);
+      part = fmaf(x0[it].x, x0[it].x,
+                  fmaf(x0[it].y, x0[it].y, fmaf(x1[it].x, x1[it].x, fmaf(x1[it].y, x1[it].y, part))));
     }
-    if (nrm) {
-      part = warp_sum(part);
+  }
+  return part;
+}
+
+// A panel's W (nr rows, squared column norms into nrm) and V (nc rows)
+// staged together: a warp issues the loads of its W and V columns (NCOL of
+// each) before its first shared store, so that 16 NCOL loads a lane are in
+// flight.  NCOL = 2 holds 32 float2 a lane, for stagings with no register
+// panel live.
+template <int PW, bool CG, int NCOL>
+__device__ __forceinline__ void pk_stage_wv(float4 *dW, const float2 *sW, int nr, float *nrm,
+                                            float4 *dV, const float2 *sV, int nc, int ld2,
+                                            int wcols) {
+  constexpr int HW = PW / 2;
+  const int lane = threadIdx.x & 31;
+  for (int c0 = threadIdx.x >> 5; c0 < PW; c0 += NCOL * HW) {
+    float2 w0[NCOL][kStageIt], w1[NCOL][kStageIt], v0[NCOL][kStageIt], v1[NCOL][kStageIt];
+#pragma unroll
+    for (int k = 0; k < NCOL; ++k) {
+      const int c = c0 + k * HW;
+      const bool real = c < PW && c < wcols;
+      col_load<CG>(w0[k], w1[k], sW + (size_t)nr * c, nr, ld2, real);
+      col_load<CG>(v0[k], v1[k], sV + (size_t)nc * c, nc, ld2, real);
+    }
+#pragma unroll
+    for (int k = 0; k < NCOL; ++k) {
+      const int c = c0 + k * HW;
+      if (c >= PW) break;
+      const float part = warp_sum(col_store(dW + ld2 * c, w0[k], w1[k], ld2));
       if (lane == 0) nrm[c] = part;
+      col_store(dV + ld2 * c, v0[k], v1[k], ld2);
     }
   }
 }
@@ -459,7 +486,7 @@ template <int KP>
 struct PkShape {
   static constexpr int KPF = (KP + 1) / 2;  // row pairs per lane, full warp
   static constexpr int LD2 = (16 * KP > 32 * KPF) ? 16 * KP : 32 * KPF;  // row pairs per column
-  static_assert(LD2 <= 32 * kStageIt, "pk_stage_in covers a column in kStageIt loads a lane");
+  static_assert(LD2 <= 32 * kStageIt, "col_load covers a column in kStageIt loads a lane");
 };
 
 // This thread's share of sum |x_e|^2 over n complex values (e = thread,
@@ -759,8 +786,8 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
     for (int a = 0; a < npan; ++a) {
       const int ca = a * PW, wa = min(PW, nc - ca);
       __syncthreads();
-      pk_stage_in<PW>(sW, LD2, W + (size_t)nr * ca, nr, wa, s_na);
-      pk_stage_in<PW>(sVa, LD2, V + (size_t)nc * ca, nc, wa);
+      pk_stage_wv<PW, false, 2>(sW, W + (size_t)nr * ca, nr, s_na, sVa, V + (size_t)nc * ca, nc,
+                                LD2, wa);
       __syncthreads();
       pk_intra<KP, PW>(sW, sVa, s_na, wa, tol, negl, n_pairs, n_rot, rotated);
       const bool mine = unit < wa;
@@ -768,8 +795,8 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
       for (int b = a + 1; b < npan; ++b) {
         const int cb = b * PW, wb = min(PW, nc - cb);
         __syncthreads();
-        pk_stage_in<PW>(sW, LD2, W + (size_t)nr * cb, nr, wb, s_nb);
-        pk_stage_in<PW>(sVb, LD2, V + (size_t)nc * cb, nc, wb);
+        pk_stage_wv<PW, false, 1>(sW, W + (size_t)nr * cb, nr, s_nb, sVb, V + (size_t)nc * cb,
+                                  nc, LD2, wb);
         pk_cross_pass<KP, PW>(aW, aV, mine, sW, sVb, s_nb, wb, tol, negl, n_pairs, n_rot, rotated);
         pk_stage_out<PW>(W + (size_t)nr * cb, sW, LD2, nr, wb);
         pk_stage_out<PW>(V + (size_t)nc * cb, sVb, LD2, nc, wb);
@@ -998,8 +1025,8 @@ __global__ void __launch_bounds__(PW * 16, (KP <= 2 || PW == 16) ? 2 : 1)
     tour_pair(npan, r, pi, pa, pb);  // pa is a real panel; pb >= npan: pa's own pairs
     int rotated = 0;
     const int ca = pa * PW, wa = min(PW, nc - ca);
-    pk_stage_in<PW, true>(sW, LD2, W + (size_t)nr * ca, nr, wa, s_na);
-    pk_stage_in<PW, true>(sVa, LD2, V + (size_t)nc * ca, nc, wa);
+    pk_stage_wv<PW, true, 2>(sW, W + (size_t)nr * ca, nr, s_na, sVa, V + (size_t)nc * ca, nc,
+                             LD2, wa);
     __syncthreads();
     if (pb >= npan) {  // panel pa's own pairs
       pk_intra<KP, PW>(sW, sVa, s_na, wa, tol, negl, n_pairs, n_rot, rotated);
@@ -1010,8 +1037,8 @@ __global__ void __launch_bounds__(PW * 16, (KP <= 2 || PW == 16) ? 2 : 1)
       const bool mine = unit < wa;
       pk_to_registers<KP>(sW, sVa, aW, aV);
       __syncthreads();
-      pk_stage_in<PW, true>(sW, LD2, W + (size_t)nr * cb, nr, wb, s_nb);
-      pk_stage_in<PW, true>(sVb, LD2, V + (size_t)nc * cb, nc, wb);
+      pk_stage_wv<PW, true, 1>(sW, W + (size_t)nr * cb, nr, s_nb, sVb, V + (size_t)nc * cb, nc,
+                               LD2, wb);
       pk_cross_pass<KP, PW>(aW, aV, mine, sW, sVb, s_nb, wb, tol, negl, n_pairs, n_rot, rotated);
       pk_stage_out<PW>(W + (size_t)nr * cb, sW, LD2, nr, wb);
       pk_stage_out<PW>(V + (size_t)nc * cb, sVb, LD2, nc, wb);
