@@ -175,7 +175,7 @@ cudaError_t tsvt_pre(const Dims &d, int nb, const float *x, const float *y, floa
 // norms, which then set the threshold-aware tolerance tensor by tensor.
 cudaError_t tsvt_jac(const Dims &d, int nb, float t, float2 *specA, float2 *V, int *sweeps,
                      cudaStream_t st, Prof *prof, float *ms2 = nullptr, int *sched = nullptr,
-                     int pw = 32) {
+                     int pw = 32, int *order = nullptr) {
   if (ms2) {
     cudaError_t e = launch_group_ms2(d, nb * d.h, specA, d.h, ms2, st);
     if (e != cudaSuccess) return e;
@@ -187,6 +187,7 @@ cudaError_t tsvt_jac(const Dims &d, int nb, float t, float2 *specA, float2 *V, i
   o.sched = sched;
   o.spare_sms = sched ? kJacobiSpareSMs : 0;
   o.pw = pw;
+  o.order = order;
   Span sp(prof, LRSTV_K_JACOBI, st);
   return launch_jacobi(d, nb * d.h, specA, V, t, kMaxSweeps, sweeps, prof ? prof->d_work : nullptr,
                        st, o);
@@ -215,10 +216,11 @@ cudaError_t tsvt_core(const Dims &d, int nb, const float *x, const float *y, flo
                       float *out, int mode, float *G4, const float *F, float mu, int gamma4,
                       const float2 *tw3, float2 *specA, float2 *specB, float2 *V, int *sweeps,
                       cudaStream_t st, Prof *prof = nullptr, GemmSel gs = kSimt,
-                      float *ms2 = nullptr, int *sched = nullptr, int pw = 32) {
+                      float *ms2 = nullptr, int *sched = nullptr, int pw = 32,
+                      int *order = nullptr) {
   cudaError_t e = tsvt_pre(d, nb, x, y, ycoef, tw3, specA, st, prof, gs);
   if (e != cudaSuccess) return e;
-  if ((e = tsvt_jac(d, nb, t, specA, V, sweeps, st, prof, ms2, sched, pw)) != cudaSuccess)
+  if ((e = tsvt_jac(d, nb, t, specA, V, sweeps, st, prof, ms2, sched, pw, order)) != cudaSuccess)
     return e;
   return tsvt_post(d, nb, out, mode, G4, F, mu, gamma4, tw3, specA, specB, V, st, prof, gs);
 }
@@ -255,6 +257,7 @@ struct lrstv_plan {
   Tables tb;
   unsigned *res;  // kResRing x 2 residual maxima (float bits)
   int *sweeps;    // 3h
+  int *order;     // 3h: the one-CTA-per-slice Jacobi's slice order
   int *jsched;    // task-graph Jacobi scratch (jacobi_task_ints(3h))
   int *gemm_err;  // tensor-core GEMM wait timeouts
   // graph cache for lrstv_plan_run
@@ -389,6 +392,7 @@ cudaError_t tsvt_warm(lrstv_plan *pl, float ycoef, float t, float mu, int gamma4
     o.sched = plan_sched(pl);
     o.spare_sms = kJacobiSpareSMs;
     o.pw = plan_pw(pl);
+    o.order = pl->order;
     Span sp(&pl->prof, LRSTV_K_JACOBI, st);
     e = launch_jacobi(d, ns, Wm, pl->V, -1.0f, kMaxSweeps, pl->sweeps,
                       pl->prof.on ? pl->prof.d_work : nullptr, st, o);
@@ -463,6 +467,7 @@ size_t group_layout(lrstv_plan *const *pls, int m, void *base) {
   for (int i = 0; i < m; ++i) pls[i]->tb = tb;
   take_each(c, pls, m, 2 * (size_t)kResRing, &lrstv_plan::res);
   take_each(c, pls, m, 3 * h, &lrstv_plan::sweeps);
+  take_each(c, pls, m, 3 * h, &lrstv_plan::order);
   take_each(c, pls, m, (size_t)jacobi_task_ints(3 * d.h), &lrstv_plan::jsched);
   take_each(c, pls, m, 1, &lrstv_plan::gemm_err);
   unsigned long long *work = c.take<unsigned long long>(2 * (size_t)m);
@@ -914,7 +919,7 @@ int lrstv_step_e(lrstv_plan *pl, void *stream) {
   CK(tsvt_core(pl->d, 3, pl->F, pl->G4, (float)(1.0 / mu), (float)(pl->prm.alpha / mu), pl->E, 1,
                pl->G4, pl->F, (float)mu, gamma4, pl->tb.tw3, pl->specA, pl->specB, pl->V,
                pl->sweeps, (cudaStream_t)stream, &pl->prof, plan_gemm(pl), pl->ms2,
-               plan_sched(pl), plan_pw(pl)));
+               plan_sched(pl), plan_pw(pl), pl->order));
   return LRSTV_OK;
 }
 
@@ -1314,6 +1319,7 @@ int batch_e_step(lrstv_batch *b, cudaStream_t st) {
     o.t_svt = (float)(p->prm.alpha / mu);
     o.ms2 = p->ms2;
     o.group = p->d.h;
+    o.order = p->order;
     CK(launch_jacobi(p->d, 3 * p->d.h * g.m, p->specA, p->V, wflag ? -1.0f : o.t_svt,
                      kMaxSweeps, p->sweeps, p->prof.on ? p->prof.d_work : nullptr, st, o));
   }

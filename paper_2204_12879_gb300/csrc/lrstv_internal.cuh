@@ -168,6 +168,10 @@ struct JacOpt {
   // panel width of the packed kernels (slices of up to 256 rows): 32 columns
   // with 16-warp CTAs, or 16 with 8-warp CTAs, two to an SM
   int pw = 32;
+  // scratch of nslices ints: with it, the one-CTA-per-slice kernel starts the
+  // slices in the order of their sweeps in the previous run (the sweeps array
+  // as passed in), most first, so that long slices do not end a wave alone
+  int *order = nullptr;
 };
 // ints of task-graph scratch for nslices working matrices
 size_t jacobi_task_ints(int nslices);

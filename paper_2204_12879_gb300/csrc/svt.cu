@@ -24,6 +24,9 @@
 
 namespace lrstv {
 
+// fewer slices than resident CTAs (defined with the launchers below)
+bool tasks_pay(int nslices, int nr, int pw);
+
 namespace {
 
 __device__ __forceinline__ void pair_of(int r, int i, int np, int &p, int &q) {
@@ -824,12 +827,59 @@ template <int KP, int PW>
 __global__ void __launch_bounds__(PW * 16, (KP <= 2 || PW == 16) ? 2 : 1)
     k_jacobi_pk(int nr, int nc, size_t wstride, size_t vstride, float2 *W_all, float2 *V_all,
                 float t, int max_sweeps, float tol, float negl_rel, int *__restrict__ sweeps_out,
-                unsigned long long *__restrict__ work, JacOpt o) {
+                unsigned long long *__restrict__ work, JacOpt o, const int *__restrict__ order) {
   extern __shared__ float4 smem_f4[];
-  jacobi_pk_slice<KP, PW>(nr, nc, W_all + (size_t)blockIdx.x * wstride,
-                      V_all + (size_t)blockIdx.x * vstride, t, max_sweeps, tol, negl_rel,
-                      sweeps_out + blockIdx.x, work, smem_f4, o.warm, o.t_svt,
-                      o.ms2 ? o.ms2[blockIdx.x / o.group] : -1.0f);
+  // CTAs start in launch order: with `order`, the slices that took the most
+  // sweeps in the previous E-step come first
+  const int s = order ? order[blockIdx.x] : (int)blockIdx.x;
+  jacobi_pk_slice<KP, PW>(nr, nc, W_all + (size_t)s * wstride, V_all + (size_t)s * vstride, t,
+                          max_sweeps, tol, negl_rel, sweeps_out + s, work, smem_f4, o.warm,
+                          o.t_svt, o.ms2 ? o.ms2[s / o.group] : -1.0f);
+}
+
+// order[0..n) = the slices by the sweeps |sweeps[s]| of their previous run,
+// most first, equal counts in slice order (a stable counting sort by one
+// CTA; counts above 63 share the first bucket).
+__global__ void __launch_bounds__(1024) k_slice_order(const int *__restrict__ sweeps, int n,
+                                                      int *__restrict__ order) {
+  __shared__ int s_cnt[64], s_start[64];
+  const int tid = threadIdx.x;
+  if (tid < 64) s_cnt[tid] = 0;
+  __syncthreads();
+  auto key = [&](int i) {
+    const int a = abs(sweeps[i]);
+    return 63 - (a < 63 ? a : 63);  // bucket 0: the most sweeps
+  };
+  for (int i = tid; i < n; i += blockDim.x) atomicAdd(&s_cnt[key(i)], 1);
+  __syncthreads();
+  if (tid == 0) {
+    int run = 0;
+    for (int k = 0; k < 64; ++k) {
+      s_start[k] = run;
+      run += s_cnt[k];
+    }
+  }
+  __syncthreads();
+  // stable placement: warp 0 walks the slices in order, a 32-slice chunk at
+  // a time, ranking each lane within its bucket by the lanes before it
+  if (tid < 32) {
+    for (int base = 0; base < n; base += 32) {
+      const int i = base + tid;
+      const int k = i < n ? key(i) : -1;
+      int rank = 0;
+      for (int j = 0; j < 32; ++j) {
+        const int kj = __shfl_sync(0xffffffffu, k, j);
+        if (j < tid && kj == k) ++rank;
+      }
+      if (i < n) order[s_start[k] + rank] = i;
+      __syncwarp();
+      for (int j = 0; j < 32; ++j) {
+        const int kj = __shfl_sync(0xffffffffu, k, j);
+        if (tid == 0 && kj >= 0) s_start[kj] += 1;
+      }
+      __syncwarp();
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1184,8 +1234,14 @@ cudaError_t launch_pk(int nslices, int nr, int nc, size_t ws, size_t vs, float2 
   cudaError_t e = cudaFuncSetAttribute(k_jacobi_pk<KP, PW>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  // the order matters only when the slices take more than one wave of CTAs
+  const int *order = (o.order && !tasks_pay(nslices, nr, PW)) ? o.order : nullptr;
+  if (order) {
+    k_slice_order<<<1, 1024, 0, st>>>(sweeps, nslices, o.order);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   k_jacobi_pk<KP, PW><<<nslices, PW * 16, smem, st>>>(nr, nc, ws, vs, W, V, t, max_sweeps, tol,
-                                                      negl, sweeps, work, o);
+                                                      negl, sweeps, work, o, order);
   return cudaGetLastError();
 }
 
