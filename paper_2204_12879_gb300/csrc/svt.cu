@@ -902,9 +902,10 @@ __global__ void __launch_bounds__(1024) k_slice_order(const int *__restrict__ sw
 //
 // Scratch (ints, zeroed by the host before each launch; jacobi_task_ints):
 // [0] queue head, [1] queue tail, [2] finished slices, [3] error flag;
-// per slice: sweep, round, tasks left in the round, rotated-in-this-sweep;
-// per slice (floats): tolerance, negligible squared norm;
-// the queue: cap task ids and cap ready marks (the mark of slot i is i + 1).
+// per slice: sweep, round in progress, tasks left in the round,
+// rotated-in-this-sweep; per slice (floats): tolerance, negligible squared
+// norm; the queue: cap 64-bit slots, each a task (its slice, round and pair)
+// and the mark of its position (slot i's mark is i + 1).
 constexpr unsigned long long kTaskWaitNs = 2000000000ull;  // a wait for work gives up after 2 s
 
 __device__ __forceinline__ int ld_relaxed(const int *p) { return *(const volatile int *)p; }
@@ -944,14 +945,23 @@ __device__ __forceinline__ bool tour_pair(int npan, int r, int i, int &p, int &q
 }
 // tasks per round at most: npan (even npan, round 0) or (npan + 1) / 2
 __device__ __forceinline__ int tour_width(int npan) { return (npan & 1) ? (npan + 1) / 2 : npan; }
-// task ids per slice: tour_width of 512 columns in 16-column panels (32)
+// task ids per slice: tour_width of 512 columns in 16-column panels (32);
+// rounds of a sweep: tour_rounds of up to 32 panels
 constexpr int kTaskIds = 32;
+constexpr int kTaskRounds = 32;
+
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long *p) {
+  return *(const volatile unsigned long long *)p;
+}
 
 struct TaskView {
   int *head, *tail, *finished, *err;
   int *sweep, *round, *left, *rot;
   float *tol, *negl;
-  int *qtask, *qready;
+  // the queue: slot i holds (mark << 32) | task, the mark of the i-th task
+  // queued being i + 1, written in one 64-bit exchange so that a reader sees
+  // the task and its mark together
+  unsigned long long *qslot;
   int cap;
   __device__ TaskView(int *sched, int ns, int cap_) : cap(cap_) {
     head = sched;
@@ -964,11 +974,10 @@ struct TaskView {
     rot = left + ns;
     tol = (float *)(rot + ns);
     negl = tol + ns;
-    qtask = (int *)(negl + ns);
-    qready = qtask + cap;
+    qslot = (unsigned long long *)(negl + ns);  // 4 + 6 ns ints before it: 8-byte aligned
   }
   // queues the tasks of round r of slice s (one thread); a task is
-  // s * kTaskIds + its pair index in the round
+  // (s kTaskRounds + r) kTaskIds + its pair index in the round
   __device__ void push_round(int s, int r, int npan) {
     int ids[kTaskIds], c = 0;
     for (int i = 0; i < tour_width(npan); ++i) {
@@ -980,9 +989,9 @@ struct TaskView {
     __threadfence();
     for (int k = 0; k < c; ++k) {
       const int idx = atomicAdd(tail, 1);
-      qtask[idx & (cap - 1)] = s * kTaskIds + ids[k];
-      __threadfence();
-      atomicExch(qready + (idx & (cap - 1)), idx + 1);
+      const unsigned task = (unsigned)((s * kTaskRounds + r) * kTaskIds + ids[k]);
+      atomicExch(qslot + (idx & (cap - 1)),
+                 ((unsigned long long)(unsigned)(idx + 1) << 32) | task);
     }
   }
 };
@@ -1049,9 +1058,10 @@ __global__ void __launch_bounds__(PW * 16, (KP <= 2 || PW == 16) ? 2 : 1)
       const unsigned long long t0 = gtimer();
       int task = -1;
       for (;;) {
-        if (ld_relaxed(tv.qready + slot) == idx + 1) {
+        const unsigned long long v = ld_relaxed64(tv.qslot + slot);
+        if ((unsigned)(v >> 32) == (unsigned)(idx + 1)) {
           __threadfence();
-          task = ld_relaxed(tv.qtask + slot);
+          task = (int)(unsigned)v;
           break;
         }
         if (ld_relaxed(tv.finished) >= nslices) break;
@@ -1066,9 +1076,9 @@ __global__ void __launch_bounds__(PW * 16, (KP <= 2 || PW == 16) ? 2 : 1)
     __syncthreads();
     const int task = s_task;
     if (task < 0) break;
-    const int s = task / kTaskIds, pi = task % kTaskIds;
+    const int s = task / (kTaskIds * kTaskRounds), pi = task % kTaskIds;
+    const int r = (task / kTaskIds) % kTaskRounds;
     float2 *W = W_all + (size_t)s * wstride, *V = V_all + (size_t)s * vstride;
-    const int r = ld_relaxed(tv.round + s);
     const float tol = ((const volatile float *)tv.tol)[s];
     const float negl = ((const volatile float *)tv.negl)[s];
     int pa, pb;
