@@ -1049,11 +1049,14 @@ __global__ void __launch_bounds__(PW * 16, (KP <= 2 || PW == 16) ? 2 : 1)
   const int npan = (nc + PW - 1) / PW, nrounds = tour_rounds(npan);
   unsigned n_pairs = 0, n_rot = 0;
   float4 aW[KP], aV[KP];
+  int claim = -1;  // thread 0: a queue slot claimed ahead
   for (;;) {
-    // one thread claims the next queue slot and waits (bounded) until it is
+    // one thread claims the next queue slot (unless it claimed it while the
+    // previous task wrote its panels back) and waits (bounded) until it is
     // filled or every slice has ended
     if (tid == 0) {
-      const int idx = atomicAdd(tv.head, 1);
+      const int idx = claim >= 0 ? claim : atomicAdd(tv.head, 1);
+      claim = -1;
       const int slot = idx & (cap - 1);
       const unsigned long long t0 = gtimer();
       int task = -1;
@@ -1090,6 +1093,7 @@ __global__ void __launch_bounds__(PW * 16, (KP <= 2 || PW == 16) ? 2 : 1)
     __syncthreads();
     if (pb >= npan) {  // panel pa's own pairs
       pk_intra<KP, PW>(sW, sVa, s_na, wa, tol, negl, n_pairs, n_rot, rotated);
+      if (tid == 0) claim = atomicAdd(tv.head, 1);  // its latency hides behind the write-back
       pk_stage_out<PW>(W + (size_t)nr * ca, sW, LD2, nr, wa);
       pk_stage_out<PW>(V + (size_t)nc * ca, sVa, LD2, nc, wa);
     } else {  // panel pa (registers) against panel pb (streamed)
@@ -1100,6 +1104,7 @@ __global__ void __launch_bounds__(PW * 16, (KP <= 2 || PW == 16) ? 2 : 1)
       pk_stage_wv<PW, true, 1>(sW, W + (size_t)nr * cb, nr, s_nb, sVb, V + (size_t)nc * cb, nc,
                                LD2, wb);
       pk_cross_pass<KP, PW>(aW, aV, mine, sW, sVb, s_nb, wb, tol, negl, n_pairs, n_rot, rotated);
+      if (tid == 0) claim = atomicAdd(tv.head, 1);  // its latency hides behind the write-back
       pk_stage_out<PW>(W + (size_t)nr * cb, sW, LD2, nr, wb);
       pk_stage_out<PW>(V + (size_t)nc * cb, sVb, LD2, nc, wb);
       pk_from_registers<KP, PW>(aW, aV, mine, sVa, W + (size_t)nr * ca, V + (size_t)nc * ca, nr,
