@@ -258,6 +258,7 @@ struct lrstv_plan {
   unsigned *res;  // kResRing x 2 residual maxima (float bits)
   int *sweeps;    // 3h
   int *order;     // 3h: the one-CTA-per-slice Jacobi's slice order
+  int *gcand, *gconv;  // 3h each: the tensor-core Gram check's candidates and flags
   int *jsched;    // task-graph Jacobi scratch (jacobi_task_ints(3h))
   int *gemm_err;  // tensor-core GEMM wait timeouts
   // graph cache for lrstv_plan_run
@@ -383,8 +384,18 @@ cudaError_t tsvt_warm(lrstv_plan *pl, float ycoef, float t, float mu, int gamma4
     R = pl->specA;
   }
   if ((e = launch_group_ms2(d, ns, Wm, d.h, pl->ms2, st)) != cudaSuccess) return e;
+  // slices whose previous run took one sweep: the Gram check on the tensor
+  // cores (into the free spectrum buffer R) shows which would rotate nothing
+  const bool gram = gs.tc;
+  if (gram) {
+    Span sp(&pl->prof, LRSTV_K_WARM_E, st);
+    if ((e = launch_gram_check(d, ns, Wm, R, pl->sweeps, pl->gcand, pl->gconv, t, pl->ms2, d.h,
+                               pl->gemm_err, st)) != cudaSuccess)
+      return e;
+  }
   {
     JacOpt o;
+    o.conv = gram ? pl->gconv : nullptr;
     o.warm = pl->vwarm;
     o.t_svt = t;
     o.ms2 = pl->ms2;
@@ -468,6 +479,8 @@ size_t group_layout(lrstv_plan *const *pls, int m, void *base) {
   take_each(c, pls, m, 2 * (size_t)kResRing, &lrstv_plan::res);
   take_each(c, pls, m, 3 * h, &lrstv_plan::sweeps);
   take_each(c, pls, m, 3 * h, &lrstv_plan::order);
+  take_each(c, pls, m, 3 * h, &lrstv_plan::gcand);
+  take_each(c, pls, m, 3 * h, &lrstv_plan::gconv);
   take_each(c, pls, m, (size_t)jacobi_task_ints(3 * d.h), &lrstv_plan::jsched);
   take_each(c, pls, m, 1, &lrstv_plan::gemm_err);
   unsigned long long *work = c.take<unsigned long long>(2 * (size_t)m);
@@ -1300,6 +1313,11 @@ int batch_e_step(lrstv_batch *b, cudaStream_t st) {
                 warm ? p->specB : p->specA, st, &p->prof, plan_gemm(p)));
     if (warm) CK(warm_basis(p, p->specB, p->specA, p->specA, st, g.m));
     CK(launch_group_ms2(d, 3 * d.h * g.m, p->specA, d.h, p->ms2, st));
+    if (wflag && plan_gemm(p).tc) {
+      Span sp(&p->prof, LRSTV_K_WARM_E, st);
+      CK(launch_gram_check(d, 3 * d.h * g.m, p->specA, p->specB, p->sweeps, p->gcand, p->gconv,
+                           (float)(p->prm.alpha / mu), p->ms2, d.h, p->gemm_err, st));
+    }
   }
   if (b->ntasks > 0) {
     CK(cudaMemsetAsync(b->d_counter, 0, sizeof(int), st));
@@ -1503,6 +1521,9 @@ int lrstv_batch_create(int ncubes, const int *dims, const lrstv_params *params,
         h[k].nr = d.nr;
         h[k].nc = d.nc;
         h[k].ms2 = pl->ms2 + s / d.h;
+        // the Gram check runs with the warm start on the tensor-core engine
+        h[k].conv = ((pl->prm.flags & LRSTV_FLAG_WARM_START) && plan_gemm(pl).tc)
+                        ? pl->gconv + s : nullptr;
         ++k;
       }
     }

@@ -87,6 +87,9 @@ struct CGemm {
   int M, N, K, batch;
   int epi; const float *lam1, *lam2, *lam3; float mu, scale;
   int lam3_period;
+  // tensor-core kernel only (may be null): batch entry b is computed only
+  // where gate[b] != 0 (the other entries' C is left as it is)
+  const int *gate;
 };
 cudaError_t launch_cgemm(const CGemm &g, cudaStream_t st);
 
@@ -172,7 +175,26 @@ struct JacOpt {
   // slices in the order of their sweeps in the previous run (the sweeps array
   // as passed in), most first, so that long slices do not end a wave alone
   int *order = nullptr;
+  // nslices flags of launch_gram_check (may be null): a slice whose flag is
+  // set ends after one sweep without running it (that sweep would rotate
+  // no pair)
+  const int *conv = nullptr;
 };
+// The Jacobi's base tolerance for slices of nr rows: a pair is rotated when
+// |w_p^H w_q| > tol ||w_p|| ||w_q|| (FP32 inner products of nr terms carry
+// about sqrt(nr) eps of relative rounding; the tolerance is a few times that).
+float jacobi_tol0(int nr);
+// Tensor-core pre-check of a warm-started Jacobi run (no counterpart in the
+// paper): for every slice s whose previous run took at most one sweep
+// (|sweeps[s]| <= 1; those flags go to cand), G_s = W_s^H W_s on the tensor
+// cores (3xTF32, into G: nslices nc x nc complex), then conv[s] = 1 when every
+// column pair passes the sweep's rotation test with a margin that covers the
+// rounding of G and of the sweep's own FP32 inner products, so that the
+// sweep would rotate no pair; conv[s] = 0 otherwise.  t_svt, ms2 and group
+// as JacOpt (the threshold-aware tolerance); gemm_err as GemmSel.
+cudaError_t launch_gram_check(const Dims &d, int nslices, const float2 *W, float2 *G,
+                              const int *sweeps, int *cand, int *conv, float t_svt,
+                              const float *ms2, int group, int *gemm_err, cudaStream_t st);
 // ints of task-graph scratch for nslices working matrices
 size_t jacobi_task_ints(int nslices);
 cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, float t,
@@ -201,6 +223,7 @@ struct SliceTask {
   float alpha;
   int nr, nc;
   const float *ms2;  // the slice's group value of launch_group_ms2 (may be null)
+  const int *conv;   // the slice's launch_gram_check flag (may be null)
 };
 // Largest slice height the persistent batch kernel takes.
 constexpr int kBatchMaxNr = 256;  // the packed kernel's tallest slice

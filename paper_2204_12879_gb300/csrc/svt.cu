@@ -756,7 +756,7 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
                                                 int max_sweeps, float tol, float negl_rel,
                                                 int *sweeps_slot, unsigned long long *work,
                                                 float4 *smem, int warm, float skip_t,
-                                                float gms2) {
+                                                float gms2, bool preconv = false) {
   constexpr int LD2 = PkShape<KP>::LD2;
   float4 *sW = smem;              // panel a (own pairs), then panel b: W
   float4 *sVa = sW + PW * LD2;    // panel a: V
@@ -779,6 +779,12 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
   // is zero whatever the sweeps would find, so none is run
   if (skip_t >= 0.0f && fro2 <= skip_t * skip_t) {
     sweeps = 0;
+    converged = true;
+  }
+  // the tensor-core Gram check showed that a sweep would rotate no pair: the
+  // one sweep it would take changes nothing
+  if (!converged && preconv) {
+    sweeps = 1;
     converged = true;
   }
   tol = pk_tolerance(tol, fro2, nc, skip_t, gms2);
@@ -834,7 +840,8 @@ __global__ void __launch_bounds__(PW * 16, (KP <= 2 || PW == 16) ? 2 : 1)
   const int s = order ? order[blockIdx.x] : (int)blockIdx.x;
   jacobi_pk_slice<KP, PW>(nr, nc, W_all + (size_t)s * wstride, V_all + (size_t)s * vstride, t,
                           max_sweeps, tol, negl_rel, sweeps_out + s, work, smem_f4, o.warm,
-                          o.t_svt, o.ms2 ? o.ms2[s / o.group] : -1.0f);
+                          o.t_svt, o.ms2 ? o.ms2[s / o.group] : -1.0f,
+                          o.conv ? o.conv[s] != 0 : false);
 }
 
 // order[0..n) = the slices by the sweeps |sweeps[s]| of their previous run,
@@ -1012,7 +1019,9 @@ __global__ void __launch_bounds__(kHW * 32)
   const float fro2 = pk_setup<false>(nr, nc, W, V, o.warm, s_red);
   const float skip_t = o.t_svt;
   const bool cut = skip_t >= 0.0f && fro2 <= skip_t * skip_t;
-  if (cut) pk_epilogue<false>(nr, nc, W, V, t);  // every g_i is 0 (t >= 0), or V is kept
+  // the tensor-core Gram check showed that a sweep would rotate no pair
+  const bool pre = !cut && o.conv && o.conv[s];
+  if (cut || pre) pk_epilogue<false>(nr, nc, W, V, t);  // cut: every g_i is 0 (t >= 0), or V is kept
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1020,8 +1029,8 @@ __global__ void __launch_bounds__(kHW * 32)
     tv.negl[s] = negl_rel * fro2;
     tv.sweep[s] = 0;
     tv.rot[s] = 0;
-    if (cut) {
-      sweeps_out[s] = 0;
+    if (cut || pre) {
+      sweeps_out[s] = cut ? 0 : 1;
       __threadfence();
       atomicAdd(tv.finished, 1);
     } else {
@@ -1184,15 +1193,15 @@ __global__ void __launch_bounds__(kHW * 32, 1)
     const float negl = ((float)tk.nr * eps) * ((float)tk.nr * eps);
     const int KP = (tk.nr + 31) / 32;
     if (KP <= 1)
-      jacobi_pk_slice<1, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
+      jacobi_pk_slice<1, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f, tk.conv ? *tk.conv != 0 : false);
     else if (KP <= 2)
-      jacobi_pk_slice<2, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
+      jacobi_pk_slice<2, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f, tk.conv ? *tk.conv != 0 : false);
     else if (KP <= 4)
-      jacobi_pk_slice<4, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
+      jacobi_pk_slice<4, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f, tk.conv ? *tk.conv != 0 : false);
     else if (KPMAX <= 7 || KP <= 7)
-      jacobi_pk_slice<7, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
+      jacobi_pk_slice<7, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f, tk.conv ? *tk.conv != 0 : false);
     else
-      jacobi_pk_slice<KPMAX, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f);
+      jacobi_pk_slice<KPMAX, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f, tk.conv ? *tk.conv != 0 : false);
   }
 }
 
@@ -1330,6 +1339,59 @@ __global__ void __launch_bounds__(1024)
   }
 }
 
+// cand[s] = 1 when slice s's previous Jacobi run took at most one sweep.
+__global__ void k_gram_gate(const int *__restrict__ sweeps, int n, int *__restrict__ cand) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) cand[s] = abs(sweeps[s]) <= 1 ? 1 : 0;
+}
+
+// conv[s] for the Gram matrix G_s (nc x nc, column-major) of a candidate slice:
+// 1 when every pair p < q passes |G_pq| <= (tol (1 - 1e-3) - kappa) sqrt(G_pp G_qq).
+// The sweep rotates a pair when |g|^2 > tol^2 |w_p|^2 |w_q|^2 with g its own FP32
+// inner product; G_pq carries at most about (nr eps + 2^-20) |w_p| |w_q| of
+// rounding (3xTF32 products, FP32 sums) and g about nr eps |w_p| |w_q|, so
+// kappa = 4 nr eps + 4e-6 keeps every passing pair below the sweep's test, and
+// the (1 - 1e-3) covers the sweep's own squared norms and this test's FP32
+// squares.  tol: the Jacobi's threshold-aware tolerance (pk_tolerance with the
+// tensor's ms2).  One CTA a slice.
+__global__ void __launch_bounds__(256)
+    k_gram_check(const float2 *__restrict__ G, int nr, int nc, const int *__restrict__ cand,
+                 float tol0, float skip_t, const float *__restrict__ ms2, int group,
+                 int *__restrict__ conv) {
+  const int s = blockIdx.x;
+  if (!cand[s]) {
+    if (threadIdx.x == 0) conv[s] = 0;
+    return;
+  }
+  const float2 *Gs = G + (size_t)s * nc * nc;
+  __shared__ float s_d[512];
+  __shared__ float s_red[8];
+  float part = 0.0f;
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+    const float di = Gs[(size_t)i * nc + i].x;
+    s_d[i] = fmaxf(di, 0.0f);
+    part += di;
+  }
+  part = warp_sum(part);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  float fro2 = 0.0f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) fro2 += s_red[w];
+  const float tol = pk_tolerance(tol0, fro2, nc, skip_t, ms2 ? ms2[s / group] : -1.0f);
+  const double eps = (double)FLT_EPSILON * 0.5;
+  const double lim = (double)tol * (1.0 - 1e-3) - (4.0 * nr * eps + 4e-6);
+  const float lim2 = (float)(lim * lim);
+  int ok = lim > 0.0;
+  for (size_t e = threadIdx.x; ok && e < (size_t)nc * nc; e += blockDim.x) {
+    const int p = (int)(e % nc), q = (int)(e / nc);
+    if (p >= q) continue;
+    const float2 g = Gs[e];
+    if (!(fmaf(g.x, g.x, g.y * g.y) <= lim2 * (s_d[p] * s_d[q]))) ok = 0;
+  }
+  ok = __syncthreads_and(ok);
+  if (threadIdx.x == 0) conv[s] = ok;
+}
+
 // One Newton-Schulz step towards the nearest unitary matrix:
 // V := V (3 I - V^H V) / 2 = 1.5 V - 0.5 D with D = (V V^H) V given.
 __global__ void k_ns_update(int nc, int nslices, size_t dstride, float2 *__restrict__ V,
@@ -1361,6 +1423,28 @@ cudaError_t launch_group_ms2(const Dims &d, int nslices, const float2 *W, int gr
   cudaError_t e = cudaMemsetAsync(ms2, 0, sizeof(float) * ngroups, st);
   if (e != cudaSuccess) return e;
   k_group_ms2<<<nslices, 1024, 0, st>>>(d.nr, d.nc, d.P, W, group, (unsigned *)ms2);
+  return cudaGetLastError();
+}
+
+float jacobi_tol0(int nr) { return 8.0f * sqrtf((float)nr) * (FLT_EPSILON * 0.5f); }
+
+cudaError_t launch_gram_check(const Dims &d, int nslices, const float2 *W, float2 *G,
+                              const int *sweeps, int *cand, int *conv, float t_svt,
+                              const float *ms2, int group, int *gemm_err, cudaStream_t st) {
+  if (nslices <= 0) return cudaSuccess;
+  if (d.nc > 512) return cudaErrorInvalidValue;  // s_d holds the diagonal
+  k_gram_gate<<<(nslices + 255) / 256, 256, 0, st>>>(sweeps, nslices, cand);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  CGemm g{};
+  g.A = W; g.sA = (long long)d.P; g.lda = d.nr; g.opA = 1;
+  g.B = W; g.sB = (long long)d.P; g.ldb = d.nr; g.opB = 0;
+  g.C = G; g.sC = (long long)d.nc * d.nc; g.ldc = d.nc;
+  g.M = d.nc; g.N = d.nc; g.K = d.nr; g.batch = nslices;
+  g.gate = cand;
+  if ((e = launch_cgemm_tc(g, gemm_err, st, 0)) != cudaSuccess) return e;
+  k_gram_check<<<nslices, 256, 0, st>>>(G, d.nr, d.nc, cand, jacobi_tol0(d.nr), t_svt, ms2, group,
+                                        conv);
   return cudaGetLastError();
 }
 
@@ -1433,7 +1517,7 @@ cudaError_t launch_jacobi(const Dims &d, int nslices, float2 *W, float2 *V, floa
   // FP32 dot products of nr terms carry about sqrt(nr) eps relative noise;
   // pairs are rotated only above a few times that.
   const float eps = FLT_EPSILON * 0.5f;
-  const float tol = 8.0f * sqrtf((float)nr) * eps;
+  const float tol = jacobi_tol0(nr);
   const float negl = o.negl_rel >= 0.0f ? o.negl_rel : ((float)nr * eps) * ((float)nr * eps);
   const size_t ws = d.P, vs = (size_t)nc * nc;
   if (nr <= 256 && nc >= 2) {

@@ -155,7 +155,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
   return done != 0;
 }
 
-// KIND 0: the complex GEMM C = A op(B) of CGemm.  KIND 1 and 2: the mode-3
+// KIND 0: the complex GEMM C = A op(B) of CGemm (OPB 0: B, 1: B^H), or, with
+// OPB 2, C = A^H B (the Gram products W^H W).  KIND 1 and 2: the mode-3
 // DFTs of the cubes of Dft3 as GEMMs over the pixels (M = n1 n2):
 //  KIND 1 (real -> half spectrum): C(p, k) = sum_c x(p, c) exp(-2 pi i k c / n3),
 //    k < h, a real A (x, or x - ycoef y) against the twiddles; a K chunk holds
@@ -186,6 +187,7 @@ __global__ void __launch_bounds__(kThreads, KIND == 1 ? 1 : 2) k_cgemm_tc(CGemm 
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int b = blockIdx.z;
+  if (KIND == 0 && g.gate && !g.gate[b]) return;  // a gated-off batch entry (CTA-uniform)
   const float2 *A = g.A + (size_t)b * g.sA;
   const float2 *B = g.B + (size_t)b * g.sB;
   float2 *C = g.C + (size_t)b * g.sC;
@@ -313,6 +315,13 @@ __global__ void __launch_bounds__(kThreads, KIND == 1 ? 1 : 2) k_cgemm_tc(CGemm 
         const int gm = m0 + r, gk = k0 + kc;
         if (KIND == 2) {  // raw; conjugated (transposed slices) when stored
           ra[i] = (gm < gM && gk < gK) ? specb[wpos(gm) + f.P * gk] : make_float2(0.f, 0.f);
+        } else if (OPB == 2) {  // A^H(m, k) = conj A(k, m)
+          float2 v = make_float2(0.f, 0.f);
+          if (gm < g.M && gk < g.K) {
+            v = A[gk + (size_t)g.lda * gm];
+            v.y = -v.y;
+          }
+          ra[i] = v;
         } else {
           ra[i] = (gm < g.M && gk < g.K) ? A[gm + (size_t)g.lda * gk] : make_float2(0.f, 0.f);
         }
@@ -325,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, KIND == 1 ? 1 : 2) k_cgemm_tc(CGemm 
           const int gn = n0 + n, gk = k0 + kc;
           float2 v = make_float2(0.f, 0.f);
           if (gn < g.N && gk < g.K) {
-            v = OPB == 0 ? B[gk + (size_t)g.ldb * gn] : B[gn + (size_t)g.ldb * gk];
+            v = OPB != 1 ? B[gk + (size_t)g.ldb * gn] : B[gn + (size_t)g.ldb * gk];
             if (OPB == 1) v.y = -v.y;
           }
           rb[i] = v;
@@ -735,6 +744,10 @@ cudaError_t launch_dft(const Dft3 &f, int nb, int *err, cudaStream_t st) {
 
 template <int PREC>
 cudaError_t launch_prec(const CGemm &g, int *err, cudaStream_t st) {
+  if (g.opA == 1) {  // A^H B only
+    if (g.opB == 0 && g.epi == 0) return launch_one<2, 0, PREC>(g, err, st);
+    return cudaErrorInvalidValue;
+  }
   if (g.opB == 0 && g.epi == 0) return launch_one<0, 0, PREC>(g, err, st);
   if (g.opB == 0 && g.epi == 1) return launch_one<0, 1, PREC>(g, err, st);
   if (g.opB == 1 && g.epi == 0) return launch_one<1, 0, PREC>(g, err, st);
@@ -780,7 +793,7 @@ cudaError_t launch_dft3_tc(int kind, const Dft3 &f, int nb, int *err, cudaStream
 
 cudaError_t launch_cgemm_tc(const CGemm &g, int *err, cudaStream_t st, int prec) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
-  if (g.opA != 0 || g.epi == 2) return cudaErrorInvalidValue;  // SIMT kernel only
+  if (g.epi == 2) return cudaErrorInvalidValue;  // SIMT kernel only
   if (prec == 0) return launch_prec<0>(g, err, st);
   if (prec == 1) return launch_prec<1>(g, err, st);
   return cudaErrorInvalidValue;

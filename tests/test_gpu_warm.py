@@ -119,3 +119,34 @@ def test_all_cut_slices_skip_sweeps(L, orc):
     out = host(L.lrstv_tsvt(dev(A), shape, t), shape)
     ref, _ = orc.tsvt(A, t)
     assert maxabs(out, ref) <= 2e-5 * np.max(np.abs(A))
+
+
+@pytest.mark.parametrize("schedule", ["tasks", "per_slice"])
+def test_gram_check_skips_only_idle_sweeps(L, orc, schedule):
+    """The tensor-core Gram check (late warm-started E-steps): once a slice's
+    previous run took one sweep, G = W^H W on the tensor cores shows whether a
+    sweep would rotate any of its column pairs, and a slice that it would not
+    ends without one.  The late E-steps then examine no column pair on the
+    FP32 units yet report one sweep, and the run keeps the oracle's bound;
+    with the SIMT GEMM engine (no check) the same E-steps examine every pair."""
+    shape = (64, 64, 31)
+    clean, Y = _noisy(shape, 13)
+    f = L.FLAG_WARM_START | (L.FLAG_JACOBI_PER_SLICE if schedule == "per_slice" else 0)
+    ost = orc.State(Y, orc.Params(n1=64, n2=64))
+    ost.iterate(50)
+    pairs = {}
+    for name, extra in (("tc", 0), ("simt", L.FLAG_SIMT_GEMM)):
+        with L.Plan(*shape, L.Params.make(64, 64, max_iter=50, flags=f | extra)) as pl:
+            pl.init(dev(Y))
+            pl.iterate(45)
+            pl.profile_enable(True)
+            pl.iterate(5)
+            st = pl.stats()
+            prof = pl.profile_read()
+            pl.profile_enable(False)
+            X = host(pl.get("L"), shape)
+        assert st.iters == 50 and st.jacobi_unconverged == 0 and st.jacobi_max_sweeps == 1
+        pairs[name] = prof.jacobi_pairs
+        assert maxabs(X, ost.X) <= 1e-4, name
+    print("pairs examined in iterations 45-49:", pairs)
+    assert pairs["tc"] == 0 and pairs["simt"] > 0
