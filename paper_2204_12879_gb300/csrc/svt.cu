@@ -1198,6 +1198,8 @@ __global__ void __launch_bounds__(kHW * 32, 1)
       jacobi_pk_slice<2, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f, tk.conv ? *tk.conv != 0 : false);
     else if (KP <= 4)
       jacobi_pk_slice<4, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f, tk.conv ? *tk.conv != 0 : false);
+    else if (KP <= 5)
+      jacobi_pk_slice<5, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f, tk.conv ? *tk.conv != 0 : false);
     else if (KPMAX <= 7 || KP <= 7)
       jacobi_pk_slice<7, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f, tk.conv ? *tk.conv != 0 : false);
     else
@@ -1284,6 +1286,7 @@ cudaError_t launch_packed(bool tasks, int nslices, int nr, int nc, size_t ws, si
   if (KP <= 1) LRSTV_PK(1);
   if (KP <= 2) LRSTV_PK(2);
   if (KP <= 4) LRSTV_PK(4);
+  if (KP <= 5) LRSTV_PK(5);  // 129-160 rows (the 145-pixel Indian Pines shape)
   if (KP <= 7) LRSTV_PK(7);
   LRSTV_PK(8);
 #undef LRSTV_PK
@@ -1482,6 +1485,7 @@ size_t jacobi_batch_smem(int max_nr) {
   const int LD2 = KP <= 1 ? PkShape<1>::LD2
                   : KP <= 2 ? PkShape<2>::LD2
                   : KP <= 4 ? PkShape<4>::LD2
+                  : KP <= 5 ? PkShape<5>::LD2
                   : KP <= 7 ? PkShape<7>::LD2
                             : PkShape<8>::LD2;
   return sizeof(float4) * 3 * (size_t)kPW * LD2;
