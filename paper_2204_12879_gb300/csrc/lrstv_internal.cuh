@@ -185,8 +185,8 @@ struct JacOpt {
 // about sqrt(nr) eps of relative rounding; the tolerance is a few times that).
 float jacobi_tol0(int nr);
 // Tensor-core pre-check of a warm-started Jacobi run (no counterpart in the
-// paper): for every slice s whose previous run took at most one sweep
-// (|sweeps[s]| <= 1; those flags go to cand), G_s = W_s^H W_s on the tensor
+// paper): for every slice s whose previous run took one sweep
+// (sweeps[s] == 1; those flags go to cand), G_s = W_s^H W_s on the tensor
 // cores (3xTF32, into G: nslices nc x nc complex), then conv[s] = 1 when every
 // column pair passes the sweep's rotation test with a margin that covers the
 // rounding of G and of the sweep's own FP32 inner products, so that the

@@ -1342,10 +1342,12 @@ __global__ void __launch_bounds__(1024)
   }
 }
 
-// cand[s] = 1 when slice s's previous Jacobi run took at most one sweep.
+// cand[s] = 1 when slice s's previous Jacobi run took one sweep (not none:
+// a slice whose singular values were all cut, or that has not run yet, is
+// left to the Jacobi's own cheap all-cut test or to its sweeps).
 __global__ void k_gram_gate(const int *__restrict__ sweeps, int n, int *__restrict__ cand) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < n) cand[s] = abs(sweeps[s]) <= 1 ? 1 : 0;
+  if (s < n) cand[s] = sweeps[s] == 1 ? 1 : 0;
 }
 
 // conv[s] for the Gram matrix G_s (nc x nc, column-major) of a candidate slice:
