@@ -66,10 +66,11 @@ def test_batch_equals_single_plans(L, warm):
 # repeated shapes with equal parameters share a group (packed state, one launch
 # per kernel for the group): three and two cubes of float4-stencil shapes, two
 # of a scalar-stencil shape (n1 % 4 != 0), two taller than the persistent
-# Jacobi takes; an equal shape with another alpha forms a group of its own
+# Jacobi takes, two of 145 rows (its 160-row variant); an equal shape with
+# another alpha forms a group of its own
 GROUPED = [(24, 20, 9), (24, 20, 9), (70, 42, 6), (24, 20, 9), (70, 42, 6), (260, 12, 3),
-           (32, 32, 16), (260, 12, 3), (24, 20, 9)]
-GROUP_OF = [0, 0, 1, 0, 1, 2, 3, 2, 4]
+           (32, 32, 16), (260, 12, 3), (145, 20, 4), (145, 20, 4), (24, 20, 9)]
+GROUP_OF = [0, 0, 1, 0, 1, 2, 3, 2, 4, 4, 5]
 
 
 def _grouped_params(L, iters, flags):
@@ -89,7 +90,7 @@ def test_batch_groups_equal_single_plans(L, warm):
     params = _grouped_params(L, iters, flags)
     with L.Batch(GROUPED, params) as b:
         ng, gof = b.groups()
-        assert ng == 5 and gof == GROUP_OF
+        assert ng == 6 and gof == GROUP_OF
         Xs, Ss = b.run(Ys)
         torch.cuda.synchronize()
         for i in range(len(GROUPED)):

@@ -507,7 +507,8 @@ def test_dft_engines_agree(L, orc):
     assert maxabs(outs[0], outs[1]) <= 2e-6 * max(1.0, np.abs(outs[1]).max())
 
 
-@pytest.mark.parametrize("shape", [(32, 32, 16), (70, 65, 9), (29, 37, 10), (200, 64, 4)])
+@pytest.mark.parametrize("shape", [(32, 32, 16), (70, 65, 9), (29, 37, 10), (200, 64, 4),
+                                   (150, 48, 6)])
 def test_jacobi_schedules_agree(L, orc, shape):
     """The task-graph Jacobi (the default: every SM takes panel-pair tasks of
     any slice) and one CTA per slice (LRSTV_FLAG_JACOBI_PER_SLICE), each with
@@ -515,7 +516,8 @@ def test_jacobi_schedules_agree(L, orc, shape):
     pair once per sweep in different orders: whole warm-started runs of all
     four are within the run bound of the oracle.  Shapes with one, three and
     two column panels (odd and even counts: the tournament's one or two empty
-    players) and a transposed slice."""
+    players), a transposed slice, and slices of 129-160 rows (the 160-row
+    variant)."""
     n1, n2, n3 = shape
     _, Y = _noisy(shape, 23)
     iters = 10
