@@ -717,7 +717,8 @@ UNROLL = {"batch": 8, "iters": 10, "pool": 2000, "seed": 5,
 
 def run_unroll(args):
     """The differentiable unrolled form: one step = forward (10 iterations,
-    iterates and SVD factors kept) + backward (hand-written adjoint) + an Adam
+    iterates kept; SVD factors kept, or recomputed in the backward pass with
+    --unroll-factors recompute) + backward (hand-written adjoint) + an Adam
     update of the 40 log-scalars, on the next batch of 8 pairs from a pool
     resident in HBM.  value = training steps per second."""
     import numpy as np
@@ -738,7 +739,9 @@ def run_unroll(args):
     noisy = to_dev([y for _, y in pairs])
     nb = UNROLL["pool"] // B
     from paper_2204_12879_gb300 import lrstv
-    model = UnrolledLRSTV(n1, n2, n3, batch=B, iters=K, flags=lrstv.FLAG_WARM_START)
+    recompute = args.unroll_factors == "recompute"
+    model = UnrolledLRSTV(n1, n2, n3, batch=B, iters=K, flags=lrstv.FLAG_WARM_START | (
+        lrstv.FLAG_UNROLL_RECOMPUTE if recompute else 0))
     opt = torch.optim.Adam(model.parameters(), lr=0.02)
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)
@@ -785,6 +788,8 @@ def run_unroll(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": UNROLL["desc"], "shape": [n1, n2, n3], "batch": B,
                    "unrolled_iters": K, "learnable_scalars": 4 * K,
+                   "svd_factors": ("recomputed in the backward pass" if recompute
+                                   else "kept from the forward pass"),
                    "pool": f"{UNROLL['pool']} pairs resident in HBM, cycled",
                    "cubes_per_s": value * B, "cube_iterations_per_s": value * B * K},
         "phases": {"forward_ms": fwd, "backward_and_update_ms": bwd,
@@ -1016,6 +1021,9 @@ def build_parser():
     ap.add_argument("--jacobi-panel", type=int, choices=[32, 16], default=32,
                     help="the Jacobi's column panel width: 32 (16-warp CTAs) or 16 (8-warp CTAs, "
                          "two to an SM; LRSTV_FLAG_JACOBI_PANEL16)")
+    ap.add_argument("--unroll-factors", choices=["keep", "recompute"], default="keep",
+                    help="c5: keep every iteration's SVD factors from the forward pass, or "
+                         "recompute them in the backward pass (LRSTV_FLAG_UNROLL_RECOMPUTE)")
     ap.add_argument("--micro", choices=["tsvt"], default=None,
                     help="time one standalone operator instead of the iteration")
     ap.add_argument("--shape", default="200,200,16", help="n1,n2,n3 for --micro")

@@ -84,6 +84,13 @@ typedef enum lrstv_status {
                                         CTAs (slices up to 256 rows; the same t-SVT to
                                         rounding, the pairs visited in another order).
                                         Batches run 32-column panels whatever the flag. */
+#define LRSTV_FLAG_UNROLL_RECOMPUTE 2048u /* unrolled iteration only: the forward pass keeps one
+                                        slot of SVD factors instead of one per iteration, and
+                                        the backward pass recomputes iteration k's factors
+                                        from its checkpointed states (the same kernels on the
+                                        same inputs: bit-identical gradients) before its t-SVT
+                                        adjoint; a warm start still keeps every iteration's V,
+                                        the next iteration's starting point */
 
 /* Scalars of Algorithm 1 (Section III-C; parameter roles in Section IV-D).
  *  tau     weight of ||D_w L||_1 (gradient sparsity)
@@ -440,13 +447,15 @@ int lrstv_tsvt_noalloc(const float *A, int n1, int n2, int n3, float t, float *o
  * The start is the plan's: L = Z = Y, everything else zero.
  *
  * lrstv_unroll_create   allocates one device arena holding every iterate
- *   (K + 1 states of 17 B N floats), the SVD factors of every Fourier slice
- *   of every E-update (K x 3 B (n3/2+1) slices) and the scratch of both
+ *   (K + 1 states of 17 B N floats, the per-iteration checkpoints), the SVD
+ *   factors of every Fourier slice of every E-update (K x 3 B (n3/2+1)
+ *   slices; one iteration's with LRSTV_FLAG_UNROLL_RECOMPUTE, which reruns
+ *   each E-update's SVDs in the backward pass) and the scratch of both
  *   passes; lrstv_unroll_bytes reports its size.  w: weights of D_w (NULL =
  *   1, 1, 1).  flags: any of LRSTV_FLAG_SIMT_GEMM, LRSTV_FLAG_SIMT_DFT,
  *   LRSTV_FLAG_JACOBI_PER_SLICE, LRSTV_FLAG_JACOBI_PANEL16, LRSTV_FLAG_WARM_START (iteration
  *   k > 0 starts its Jacobi SVDs from iteration k-1's singular vectors, as a
- *   plan does).  iters in 1..4096.
+ *   plan does), LRSTV_FLAG_UNROLL_RECOMPUTE.  iters in 1..4096.
  * lrstv_unroll_forward  Y: device, B cubes back to back (B N floats).
  *   theta: HOST array of K x 4 doubles (tau, alpha, lambda, mu per
  *   iteration; all finite and >= 0, mu > 0), copied during the call.

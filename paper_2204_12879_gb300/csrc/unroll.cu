@@ -5,11 +5,14 @@
 // and to the noisy input Y.
 //
 // Forward: iteration k reads state slot k and writes slot k+1 (every slot is
-// kept: 17 B N floats each), and keeps the SVD factors W_k, V_k and the
-// singular values of every Fourier slice of the E-update, so the backward
-// pass recomputes nothing.  The kernels are those of the plain iteration
-// (the Jacobi with a negative threshold keeps V unscaled; a separate kernel
-// forms sigma and the thresholded V exactly as the Jacobi epilogue does).
+// kept: 17 B N floats each, the per-iteration checkpoints), and keeps the SVD
+// factors W_k, V_k and the singular values of every Fourier slice of the
+// E-update.  With LRSTV_FLAG_UNROLL_RECOMPUTE it keeps one slot of W and
+// sigma (and of V without a warm start) and the backward pass reruns
+// iteration k's factorisation from the checkpoints before its t-SVT adjoint.
+// The kernels are those of the plain iteration (the Jacobi with a negative
+// threshold keeps V unscaled; a separate kernel forms sigma and the
+// thresholded V exactly as the Jacobi epilogue does).
 //
 // Backward, per iteration in reverse, with adjoint buffers a* in the layout of
 // a state slot (the adjoint of the new state on entry, of the old on exit):
@@ -378,8 +381,13 @@ struct lrstv_unroll {
   float *adj;          // one slot-shaped adjoint state
   float *aY, *T, *X3, *bT;
   float2 *specA, *specB;
-  float2 *W, *V;       // K x (3 B h) factor slices: P and nc^2 complex each
-  double *sig;         // K x (3 B h) x nc
+  // SVD factors of the E-updates, in slots of 3 B h Fourier slices (P and
+  // nc^2 complex each, nc doubles of sigma): one slot per iteration, or, for a
+  // handle that recomputes them in the backward pass, one slot of W and sigma
+  // and one of V (K of V with a warm start: iteration k starts from V_{k-1})
+  int nw, nv;          // slots of W and sigma, of V
+  float2 *W, *V;
+  double *sig;
   float2 *Hs;          // 3 B h nc^2 complex: thresholded V, then H / K'
   int *sweeps;         // K x 3 B h
   int *jsched;         // task-graph Jacobi scratch (jacobi_task_ints(3 B h))
@@ -409,6 +417,17 @@ UnrollSlot slot_at(const lrstv_unroll *u, float *base) {
 
 UnrollSlot slot_k(const lrstv_unroll *u, int k) { return slot_at(u, u->slots + (size_t)k * u->slot_floats); }
 
+// iteration k's factor slots (a single slot is shared by every iteration)
+float2 *w_slot(const lrstv_unroll *u, int k) {
+  return u->W + (size_t)(k % u->nw) * 3 * u->B * u->d.h * u->d.P;
+}
+float2 *v_slot(const lrstv_unroll *u, int k) {
+  return u->V + (size_t)(k % u->nv) * 3 * u->B * u->d.h * u->d.nc * u->d.nc;
+}
+double *sig_slot(const lrstv_unroll *u, int k) {
+  return u->sig + (size_t)(k % u->nw) * 3 * u->B * u->d.h * u->d.nc;
+}
+
 size_t unroll_layout(lrstv_unroll *u, void *base) {
   const Dims &d = u->d;
   const size_t BN = (size_t)u->B * d.N;
@@ -423,9 +442,9 @@ size_t unroll_layout(lrstv_unroll *u, void *base) {
   u->bT = c.take<float>(BN);
   u->specA = c.take<float2>(ns * d.P);
   u->specB = c.take<float2>(ns * d.P);
-  u->W = c.take<float2>((size_t)u->K * ns * d.P);
-  u->V = c.take<float2>((size_t)u->K * ns * d.nc * d.nc);
-  u->sig = c.take<double>((size_t)u->K * ns * d.nc);
+  u->W = c.take<float2>((size_t)u->nw * ns * d.P);
+  u->V = c.take<float2>((size_t)u->nv * ns * d.nc * d.nc);
+  u->sig = c.take<double>((size_t)u->nw * ns * d.nc);
   u->Hs = c.take<float2>(ns * d.nc * d.nc);
   u->sweeps = c.take<int>((size_t)u->K * ns);
   u->jsched = c.take<int>(jacobi_task_ints((int)ns));
@@ -445,6 +464,63 @@ GemmSel unroll_gemm(const lrstv_unroll *u) {
   do {                                          \
     if ((x) != cudaSuccess) return LRSTV_ERR_CUDA; \
   } while (0)
+
+// The factor half of iteration k's E-update: the SVDs of the Fourier slices of
+// F - Gamma4_k/mu (F the iteration's new F, Gamma4_k the multiplier it started
+// from), into W_k, V_k and sigma_k, and the thresholded V into Hs.  The same
+// call in the backward pass of a recomputing handle reproduces the forward's
+// factors bit for bit: every kernel here is deterministic, and a warm start
+// reads V_{k-1}, which such a handle keeps.
+int e_factor(lrstv_unroll *u, int k, const float *F, const float *G4, double mu, double alpha,
+             cudaStream_t st) {
+  const Dims &d = u->d;
+  const int B = u->B;
+  const size_t ns = (size_t)3 * B * d.h;
+  const GemmSel gs = unroll_gemm(u);
+  float2 *Wk = w_slot(u, k);
+  float2 *Vk = v_slot(u, k);
+  double *sk = sig_slot(u, k);
+  const int warm = (u->flags & LRSTV_FLAG_WARM_START) && k > 0;
+  if (warm) {
+    // start from the previous iteration's right singular vectors, made
+    // unitary again by one Newton-Schulz step, exactly as a plan does
+    const long long nc2 = (long long)d.nc * d.nc, P = (long long)d.P;
+    UCK(launch_r2c3(d, 3 * B, F, G4, (float)(1.0 / mu), u->specA, 1, u->tb.tw3, st, gs));
+    UCK(cudaMemcpyAsync(Vk, v_slot(u, k - 1), sizeof(float2) * ns * d.nc * d.nc,
+                        cudaMemcpyDeviceToDevice, st));
+    CGemm g{};
+    g.batch = (int)ns;
+    g.A = Vk; g.sA = nc2; g.lda = d.nc;
+    g.B = Vk; g.sB = nc2; g.ldb = d.nc; g.opB = 1;
+    g.C = u->Hs; g.sC = nc2; g.ldc = d.nc;
+    g.M = d.nc; g.N = d.nc; g.K = d.nc;
+    UCK(gemm(g, gs, st));
+    g.A = u->Hs; g.B = Vk; g.opB = 0;
+    g.C = u->specB; g.sC = P; g.ldc = d.nc;
+    UCK(gemm(g, gs, st));
+    UCK(launch_ns_update(d.nc, (int)ns, (size_t)P, Vk, u->specB, st));
+    g.A = u->specA; g.sA = P; g.lda = d.nr;
+    g.B = Vk; g.sB = nc2; g.ldb = d.nc; g.opB = 0;
+    g.C = Wk; g.sC = P; g.ldc = d.nr;
+    g.M = d.nr; g.N = d.nc; g.K = d.nc;
+    UCK(gemm(g, gs, st));
+  } else {
+    UCK(launch_r2c3(d, 3 * B, F, G4, (float)(1.0 / mu), Wk, 1, u->tb.tw3, st, gs));
+  }
+  const float t = (float)(alpha / mu);
+  UCK(launch_group_ms2(d, (int)ns, Wk, d.h, u->ms2, st));
+  JacOpt o;
+  o.warm = warm;
+  o.t_svt = t;
+  o.ms2 = u->ms2;
+  o.group = d.h;
+  o.sched = (u->flags & LRSTV_FLAG_JACOBI_PER_SLICE) ? nullptr : u->jsched;
+  o.pw = (u->flags & LRSTV_FLAG_JACOBI_PANEL16) ? 16 : 32;
+  UCK(launch_jacobi(d, (int)ns, Wk, Vk, -1.0f, kMaxSweeps, u->sweeps + (size_t)k * ns, nullptr,
+                    st, o));
+  UCK(launch_sigma_scale(d, (int)ns, Wk, Vk, t, sk, u->Hs, st));
+  return LRSTV_OK;
+}
 
 int unroll_forward(lrstv_unroll *u, cudaStream_t st) {
   const Dims &d = u->d;
@@ -466,49 +542,9 @@ int unroll_forward(lrstv_unroll *u, cudaStream_t st) {
     const float thr_f = (float)(tau / mu), thr_s = (float)(lam / mu);
     UCK(launch_fs_dual(d, u->Y, s.L, s.Z, s.S, s.G1, s.G2, s.F, s.E, s.G3, s.G4, muf, thr_f, thr_s,
                        u->w, nullptr, st, 0, B));
-    // E: t-SVT of F - Gamma4/mu for all 3 B gradient cubes, factors kept
-    float2 *Wk = u->W + (size_t)k * ns * d.P;
-    float2 *Vk = u->V + (size_t)k * ns * d.nc * d.nc;
-    double *sk = u->sig + (size_t)k * ns * d.nc;
-    const int warm = (u->flags & LRSTV_FLAG_WARM_START) && k > 0;
-    if (warm) {
-      // start from the previous iteration's right singular vectors, made
-      // unitary again by one Newton-Schulz step, exactly as a plan does
-      const long long nc2 = (long long)d.nc * d.nc, P = (long long)d.P;
-      UCK(launch_r2c3(d, 3 * B, s.F, s.G4, (float)(1.0 / mu), u->specA, 1, u->tb.tw3, st, gs));
-      UCK(cudaMemcpyAsync(Vk, Vk - ns * d.nc * d.nc, sizeof(float2) * ns * d.nc * d.nc,
-                          cudaMemcpyDeviceToDevice, st));
-      CGemm g{};
-      g.batch = (int)ns;
-      g.A = Vk; g.sA = nc2; g.lda = d.nc;
-      g.B = Vk; g.sB = nc2; g.ldb = d.nc; g.opB = 1;
-      g.C = u->Hs; g.sC = nc2; g.ldc = d.nc;
-      g.M = d.nc; g.N = d.nc; g.K = d.nc;
-      UCK(gemm(g, gs, st));
-      g.A = u->Hs; g.B = Vk; g.opB = 0;
-      g.C = u->specB; g.sC = P; g.ldc = d.nc;
-      UCK(gemm(g, gs, st));
-      UCK(launch_ns_update(d.nc, (int)ns, (size_t)P, Vk, u->specB, st));
-      g.A = u->specA; g.sA = P; g.lda = d.nr;
-      g.B = Vk; g.sB = nc2; g.ldb = d.nc; g.opB = 0;
-      g.C = Wk; g.sC = P; g.ldc = d.nr;
-      g.M = d.nr; g.N = d.nc; g.K = d.nc;
-      UCK(gemm(g, gs, st));
-    } else {
-      UCK(launch_r2c3(d, 3 * B, s.F, s.G4, (float)(1.0 / mu), Wk, 1, u->tb.tw3, st, gs));
-    }
-    const float t = (float)(alpha / mu);
-    UCK(launch_group_ms2(d, (int)ns, Wk, d.h, u->ms2, st));
-    JacOpt o;
-    o.warm = warm;
-    o.t_svt = t;
-    o.ms2 = u->ms2;
-    o.group = d.h;
-    o.sched = (u->flags & LRSTV_FLAG_JACOBI_PER_SLICE) ? nullptr : u->jsched;
-    o.pw = (u->flags & LRSTV_FLAG_JACOBI_PANEL16) ? 16 : 32;
-    UCK(launch_jacobi(d, (int)ns, Wk, Vk, -1.0f, kMaxSweeps, u->sweeps + (size_t)k * ns, nullptr,
-                      st, o));
-    UCK(launch_sigma_scale(d, (int)ns, Wk, Vk, t, sk, u->Hs, st));
+    // E: t-SVT of F - Gamma4/mu for all 3 B gradient cubes
+    UCK(e_factor(u, k, s.F, s.G4, mu, alpha, st));
+    float2 *Wk = w_slot(u, k);
     CGemm g{};
     g.A = Wk; g.sA = (long long)d.P; g.lda = d.nr;
     g.B = u->Hs; g.sB = (long long)d.nc * d.nc; g.ldb = d.nc; g.opB = 1;
@@ -549,9 +585,15 @@ int unroll_backward(lrstv_unroll *u, double *dtheta, cudaStream_t st) {
                                    ls);
     UCK(cudaGetLastError());
     // t-SVT adjoint of the three gradient tensors of every cube
-    float2 *Wk = u->W + (size_t)k * ns * d.P;
-    float2 *Vk = u->V + (size_t)k * ns * d.nc * d.nc;
-    const double *sk = u->sig + (size_t)k * ns * d.nc;
+    if (u->nw < u->K) {
+      // recompute iteration k's factors from its checkpoints: the new F
+      // (slot k + 1) and the Gamma4 the iteration started from (slot k)
+      const int rc = e_factor(u, k, n.F, o.G4, mu, alpha, st);
+      if (rc != LRSTV_OK) return rc;
+    }
+    float2 *Wk = w_slot(u, k);
+    float2 *Vk = v_slot(u, k);
+    const double *sk = sig_slot(u, k);
     UCK(launch_r2c3(d, 3 * B, a.E, nullptr, 0.0f, u->specA, 1, u->tb.tw3, st, gs));
     CGemm g{};
     g.batch = (int)ns;
@@ -623,7 +665,8 @@ int lrstv_unroll_create(int n1, int n2, int n3, int batch, int iters, const floa
   if (rc) return rc;
   if (batch < 1 || iters < 1 || iters > 4096) return LRSTV_ERR_ARG;
   if (flags & ~(unsigned)(LRSTV_FLAG_SIMT_GEMM | LRSTV_FLAG_WARM_START | LRSTV_FLAG_SIMT_DFT |
-                          LRSTV_FLAG_JACOBI_PER_SLICE | LRSTV_FLAG_JACOBI_PANEL16))
+                          LRSTV_FLAG_JACOBI_PER_SLICE | LRSTV_FLAG_JACOBI_PANEL16 |
+                          LRSTV_FLAG_UNROLL_RECOMPUTE))
     return LRSTV_ERR_ARG;
   float wl[3] = {1.0f, 1.0f, 1.0f};
   if (w)
@@ -639,6 +682,9 @@ int lrstv_unroll_create(int n1, int n2, int n3, int batch, int iters, const floa
   memcpy(u->w, wl, sizeof(wl));
   u->flags = flags;
   u->slot_floats = 17 * (size_t)batch * u->d.N;
+  const bool recompute = (flags & LRSTV_FLAG_UNROLL_RECOMPUTE) != 0;
+  u->nw = recompute ? 1 : iters;
+  u->nv = recompute && !(flags & LRSTV_FLAG_WARM_START) ? 1 : iters;
   u->theta = (double *)calloc(4 * (size_t)iters, sizeof(double));
   if (!u->theta) {
     unroll_free(u);

@@ -98,3 +98,14 @@ def test_argument_errors_before_any_cuda_call(lib):
     assert lib.lrstv_peak_probe(0, 10, None, ctypes.byref(d)) == 1
     # one band above the largest n3 a plan takes
     assert lib.lrstv_plan_create(2, 2, 4097, ctypes.byref(p), ctypes.byref(h)) == 2
+
+
+def test_flag_constants_match_header():
+    """The binding's FLAG_* constants are the header's LRSTV_FLAG_* values."""
+    import re
+    from paper_2204_12879_gb300 import lrstv
+    with open(os.path.join(ROOT, "include", "lrstv.h")) as f:
+        flags = dict(re.findall(r"#define LRSTV_FLAG_(\w+) (\d+)u", f.read()))
+    assert len(flags) >= 12
+    for name, val in flags.items():
+        assert getattr(lrstv, "FLAG_" + name) == int(val), name

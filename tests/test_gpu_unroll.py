@@ -169,6 +169,52 @@ def test_unroll_simt_gemm_agrees(L):
     assert np.max(np.abs(y0 - y1)) <= 1e-3 * np.max(np.abs(y1))
 
 
+@pytest.mark.parametrize("flags", ["cold", "warm", "warm_per_slice"])
+def test_unroll_recompute_bitwise(L, flags):
+    """LRSTV_FLAG_UNROLL_RECOMPUTE keeps one slot of SVD factors and reruns each
+    E-update's SVDs from the checkpointed states in the backward pass: the
+    same kernels on the same inputs, so the iterate and dY equal the storing
+    handle's bit for bit, twice in a row (a warm start rewrites the kept V
+    slots with the same bits), and the scalars' gradients up to the order of
+    their FP64 atomic sums, in a smaller arena."""
+    import torch
+    fl = {"cold": 0, "warm": L.FLAG_WARM_START,
+          "warm_per_slice": L.FLAG_WARM_START | L.FLAG_JACOBI_PER_SLICE}[flags]
+    shape, K, B = (24, 20, 9), 5, 2
+    cubes = _cubes(shape, B, 80)
+    Y = _to_dev([c[1] for c in cubes])
+    theta = _free_theta(K)
+    rng = np.random.default_rng(5)
+    dX = _to_dev([f32(rng.standard_normal(shape) / np.prod(shape)) for _ in range(B)])
+    res, sizes = [], []
+    for extra in (0, L.FLAG_UNROLL_RECOMPUTE):
+        with L.Unroll(shape, B, K, flags=fl | extra) as u:
+            sizes.append(u.nbytes)
+            X = u.forward(Y, theta)
+            runs = []
+            for _ in range(2):
+                dth, dY = u.backward(dX)
+                runs.append((dth.cpu().numpy(), dY.cpu().numpy()))
+            assert u.stats() == (0, 0)
+            res.append((X.cpu().numpy(), runs))
+    (X0, r0), (X1, r1) = res
+    assert np.array_equal(X0, X1)
+    # dY is bitwise; the scalars' gradients are FP64 sums whose block partials
+    # arrive by atomics in no fixed order, so two runs of one handle already
+    # differ in the last bits: they are held to 1e-12 of each column's largest
+    top = np.max(np.abs(r0[0][0]), axis=0) + 1e-300
+    for t, y in r0[1:] + r1:
+        assert np.array_equal(y, r0[0][1])
+        assert np.all(np.abs(t - r0[0][0]) <= 1e-12 * top)
+    assert np.count_nonzero(r0[0][0]) >= 8
+    # factor slots: W and sigma for K - 1 iterations, V too without a warm start
+    n1, n2, n3 = shape
+    ns, nc = 3 * B * (n3 // 2 + 1), min(n1, n2)
+    saved = (K - 1) * ns * (n1 * n2 * 8 + nc * 8) + (0 if fl else (K - 1) * ns * nc * nc * 8)
+    assert sizes[0] - sizes[1] >= saved - 3 * 256  # up to 256 bytes of alignment a field
+    torch.cuda.synchronize()
+
+
 def test_unroll_argument_checks(L):
     import ctypes
     import torch
