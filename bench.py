@@ -414,6 +414,8 @@ def run_ours(args, wl_name):
         flags |= lrstv.FLAG_JACOBI_PER_SLICE
     if args.jacobi_panel == 16:
         flags |= lrstv.FLAG_JACOBI_PANEL16
+    if args.jacobi_order == "fixed":
+        flags |= lrstv.FLAG_JACOBI_FIXED_ORDER
     params = lrstv.Params.make(n1, n2, max_iter=iters, flags=flags)
     plan = lrstv.Plan(n1, n2, n3, params)
     ranks = tucker_ranks(args, (n1, n2, n3))
@@ -569,6 +571,8 @@ def run_ours(args, wl_name):
                    "jacobi_schedule": ("task graph: panel-pair tasks of every slice on all SMs"
                                        if args.jacobi_schedule == "tasks" else "one CTA per slice"),
                    "jacobi_panel": args.jacobi_panel,
+                   "jacobi_order": ("columns by norm, largest first, each sweep (task graph)"
+                                    if args.jacobi_order == "sorted" else "stored order"),
                    "l_update": ("Tucker projection, one HOOI sweep per iteration, ranks %s" % (ranks,)
                                 if ranks else "plain (full Tucker ranks)"),
                    "l2": "working set (18 state cubes + spectra, ~330 MB) exceeds the 129 MB L2",
@@ -1021,6 +1025,9 @@ def build_parser():
     ap.add_argument("--jacobi-panel", type=int, choices=[32, 16], default=32,
                     help="the Jacobi's column panel width: 32 (16-warp CTAs) or 16 (8-warp CTAs, "
                          "two to an SM; LRSTV_FLAG_JACOBI_PANEL16)")
+    ap.add_argument("--jacobi-order", choices=["sorted", "fixed"], default="sorted",
+                    help="task-graph Jacobi: order each sweep's columns by norm, largest first, "
+                         "or keep their stored order (LRSTV_FLAG_JACOBI_FIXED_ORDER)")
     ap.add_argument("--unroll-factors", choices=["keep", "recompute"], default="keep",
                     help="c5: keep every iteration's SVD factors from the forward pass, or "
                          "recompute them in the backward pass (LRSTV_FLAG_UNROLL_RECOMPUTE)")

@@ -84,6 +84,12 @@ typedef enum lrstv_status {
                                         CTAs (slices up to 256 rows; the same t-SVT to
                                         rounding, the pairs visited in another order).
                                         Batches run 32-column panels whatever the flag. */
+#define LRSTV_FLAG_JACOBI_FIXED_ORDER 4096u /* the task-graph Jacobi pairs a slice's columns in
+                                        their stored order in every sweep, instead of ordering
+                                        them by squared norm, largest first, at the start of
+                                        each sweep (de Rijk's ordering: fewer sweeps; the same
+                                        t-SVT to rounding).  The one-CTA-per-slice schedule
+                                        keeps the stored order either way. */
 #define LRSTV_FLAG_UNROLL_RECOMPUTE 2048u /* unrolled iteration only: the forward pass keeps one
                                         slot of SVD factors instead of one per iteration, and
                                         the backward pass recomputes iteration k's factors
@@ -307,7 +313,7 @@ int lrstv_plan_run_host(lrstv_plan *plan, const float *Y_host, float *X_host, fl
  * (params.max_iter when 0) of the plan from the device cube Y for every
  * combination of the flags in `allowed` (a subset of LRSTV_FLAG_SIMT_GEMM |
  * LRSTV_FLAG_SIMT_DFT | LRSTV_FLAG_JACOBI_PER_SLICE | LRSTV_FLAG_JACOBI_PANEL16 |
- * LRSTV_FLAG_WARM_START | LRSTV_FLAG_BF16X3; combinations params rejects, and
+ * LRSTV_FLAG_JACOBI_FIXED_ORDER | LRSTV_FLAG_WARM_START | LRSTV_FLAG_BF16X3; combinations params rejects, and
  * SIMT_DFT together with SIMT_GEMM, are skipped), each after
  * one untimed pass, with CUDA events on `stream`, and keeps the fastest in
  * the plan's params.flags.  These choices change the work (GEMM and DFT

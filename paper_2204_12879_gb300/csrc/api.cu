@@ -66,7 +66,8 @@ int check_params(const lrstv_params *p) {
   if (p->flags & ~(unsigned)(LRSTV_FLAG_F_THRESH_EXACT | LRSTV_FLAG_NO_GAMMA4 | LRSTV_FLAG_GRAPH |
                              LRSTV_FLAG_STRICT | LRSTV_FLAG_SIMT_GEMM | LRSTV_FLAG_WARM_START |
                              LRSTV_FLAG_SIMT_DFT | LRSTV_FLAG_JACOBI_PER_SLICE |
-                             LRSTV_FLAG_ISO_TV | LRSTV_FLAG_BF16X3 | LRSTV_FLAG_JACOBI_PANEL16))
+                             LRSTV_FLAG_ISO_TV | LRSTV_FLAG_BF16X3 | LRSTV_FLAG_JACOBI_PANEL16 |
+                             LRSTV_FLAG_JACOBI_FIXED_ORDER))
     return LRSTV_ERR_ARG;
   // the split-BF16 products exist on the tensor-core path only
   if ((p->flags & LRSTV_FLAG_BF16X3) && (p->flags & LRSTV_FLAG_SIMT_GEMM)) return LRSTV_ERR_ARG;
@@ -175,7 +176,7 @@ cudaError_t tsvt_pre(const Dims &d, int nb, const float *x, const float *y, floa
 // norms, which then set the threshold-aware tolerance tensor by tensor.
 cudaError_t tsvt_jac(const Dims &d, int nb, float t, float2 *specA, float2 *V, int *sweeps,
                      cudaStream_t st, Prof *prof, float *ms2 = nullptr, int *sched = nullptr,
-                     int pw = 32, int *order = nullptr) {
+                     int pw = 32, int *order = nullptr, int sort = 1) {
   if (ms2) {
     cudaError_t e = launch_group_ms2(d, nb * d.h, specA, d.h, ms2, st);
     if (e != cudaSuccess) return e;
@@ -188,6 +189,7 @@ cudaError_t tsvt_jac(const Dims &d, int nb, float t, float2 *specA, float2 *V, i
   o.spare_sms = sched ? kJacobiSpareSMs : 0;
   o.pw = pw;
   o.order = order;
+  o.sort = sort;
   Span sp(prof, LRSTV_K_JACOBI, st);
   return launch_jacobi(d, nb * d.h, specA, V, t, kMaxSweeps, sweeps, prof ? prof->d_work : nullptr,
                        st, o);
@@ -217,10 +219,11 @@ cudaError_t tsvt_core(const Dims &d, int nb, const float *x, const float *y, flo
                       const float2 *tw3, float2 *specA, float2 *specB, float2 *V, int *sweeps,
                       cudaStream_t st, Prof *prof = nullptr, GemmSel gs = kSimt,
                       float *ms2 = nullptr, int *sched = nullptr, int pw = 32,
-                      int *order = nullptr) {
+                      int *order = nullptr, int sort = 1) {
   cudaError_t e = tsvt_pre(d, nb, x, y, ycoef, tw3, specA, st, prof, gs);
   if (e != cudaSuccess) return e;
-  if ((e = tsvt_jac(d, nb, t, specA, V, sweeps, st, prof, ms2, sched, pw, order)) != cudaSuccess)
+  if ((e = tsvt_jac(d, nb, t, specA, V, sweeps, st, prof, ms2, sched, pw, order, sort)) !=
+      cudaSuccess)
     return e;
   return tsvt_post(d, nb, out, mode, G4, F, mu, gamma4, tw3, specA, specB, V, st, prof, gs);
 }
@@ -299,6 +302,11 @@ int *plan_sched(const lrstv_plan *pl) {
 
 // The packed Jacobi's panel width for a plan's flags.
 int plan_pw(const lrstv_plan *pl) { return (pl->prm.flags & LRSTV_FLAG_JACOBI_PANEL16) ? 16 : 32; }
+
+// Whether the task-graph Jacobi orders each sweep's columns by norm.
+int plan_sort(const lrstv_plan *pl) {
+  return (pl->prm.flags & LRSTV_FLAG_JACOBI_FIXED_ORDER) ? 0 : 1;
+}
 
 GemmSel plan_gemm(const lrstv_plan *pl) {
   if (pl->prm.flags & LRSTV_FLAG_SIMT_GEMM) return kSimt;
@@ -404,6 +412,7 @@ cudaError_t tsvt_warm(lrstv_plan *pl, float ycoef, float t, float mu, int gamma4
     o.spare_sms = kJacobiSpareSMs;
     o.pw = plan_pw(pl);
     o.order = pl->order;
+    o.sort = plan_sort(pl);
     Span sp(&pl->prof, LRSTV_K_JACOBI, st);
     e = launch_jacobi(d, ns, Wm, pl->V, -1.0f, kMaxSweeps, pl->sweeps,
                       pl->prof.on ? pl->prof.d_work : nullptr, st, o);
@@ -932,7 +941,7 @@ int lrstv_step_e(lrstv_plan *pl, void *stream) {
   CK(tsvt_core(pl->d, 3, pl->F, pl->G4, (float)(1.0 / mu), (float)(pl->prm.alpha / mu), pl->E, 1,
                pl->G4, pl->F, (float)mu, gamma4, pl->tb.tw3, pl->specA, pl->specB, pl->V,
                pl->sweeps, (cudaStream_t)stream, &pl->prof, plan_gemm(pl), pl->ms2,
-               plan_sched(pl), plan_pw(pl), pl->order));
+               plan_sched(pl), plan_pw(pl), pl->order, plan_sort(pl)));
   return LRSTV_OK;
 }
 
@@ -1094,7 +1103,7 @@ int lrstv_plan_autotune(lrstv_plan *pl, const float *Y, int iters, unsigned allo
   if (!pl || !Y || iters < 0) return LRSTV_ERR_ARG;
   if (allowed & ~(unsigned)(LRSTV_FLAG_SIMT_GEMM | LRSTV_FLAG_WARM_START | LRSTV_FLAG_SIMT_DFT |
                             LRSTV_FLAG_JACOBI_PER_SLICE | LRSTV_FLAG_JACOBI_PANEL16 |
-                            LRSTV_FLAG_BF16X3))
+                            LRSTV_FLAG_JACOBI_FIXED_ORDER | LRSTV_FLAG_BF16X3))
     return LRSTV_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   const int n = iters > 0 ? iters : pl->prm.max_iter;

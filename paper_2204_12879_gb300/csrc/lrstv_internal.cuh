@@ -179,6 +179,9 @@ struct JacOpt {
   // set ends after one sweep without running it (that sweep would rotate
   // no pair)
   const int *conv = nullptr;
+  // task-graph schedule: each sweep pairs the slice's columns in the order of
+  // their squared norms, largest first (0: in the stored order)
+  int sort = 1;
 };
 // The Jacobi's base tolerance for slices of nr rows: a pair is rotated when
 // |w_p^H w_q| > tol ||w_p|| ||w_q|| (FP32 inner products of nr terms carry

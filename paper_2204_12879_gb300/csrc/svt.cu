@@ -444,10 +444,13 @@ __device__ __forceinline__ float col_store(float4 *d, const float2 (&x0)[kStageI
 // each) before its first shared store, so that 16 NCOL loads a lane are in
 // flight.  NCOL = 2 holds 32 float2 a lane, for stagings with no register
 // panel live.
+// With a column map (cols, shared memory: the panel's wcols column indices),
+// sW and sV are the slice's first columns and panel column c is column
+// cols[c]; without one the panel's columns are contiguous from sW and sV.
 template <int PW, bool CG, int NCOL>
 __device__ __forceinline__ void pk_stage_wv(float4 *dW, const float2 *sW, int nr, float *nrm,
                                             float4 *dV, const float2 *sV, int nc, int ld2,
-                                            int wcols) {
+                                            int wcols, const int *cols = nullptr) {
   constexpr int HW = PW / 2;
   const int lane = threadIdx.x & 31;
   for (int c0 = threadIdx.x >> 5; c0 < PW; c0 += NCOL * HW) {
@@ -456,8 +459,9 @@ __device__ __forceinline__ void pk_stage_wv(float4 *dW, const float2 *sW, int nr
     for (int k = 0; k < NCOL; ++k) {
       const int c = c0 + k * HW;
       const bool real = c < PW && c < wcols;
-      col_load<CG>(w0[k], w1[k], sW + (size_t)nr * c, nr, ld2, real);
-      col_load<CG>(v0[k], v1[k], sV + (size_t)nc * c, nc, ld2, real);
+      const int g = cols ? (real ? cols[c] : 0) : c;
+      col_load<CG>(w0[k], w1[k], sW + (size_t)nr * g, nr, ld2, real);
+      col_load<CG>(v0[k], v1[k], sV + (size_t)nc * g, nc, ld2, real);
     }
 #pragma unroll
     for (int k = 0; k < NCOL; ++k) {
@@ -472,10 +476,10 @@ __device__ __forceinline__ void pk_stage_wv(float4 *dW, const float2 *sW, int nr
 
 template <int PW>
 __device__ __forceinline__ void pk_stage_out(float2 *dst, const float4 *src, int ld2, int n,
-                                             int wcols) {
+                                             int wcols, const int *cols = nullptr) {
   const int lane = threadIdx.x & 31;
   for (int c = threadIdx.x >> 5; c < wcols; c += PW / 2) {
-    float2 *d = dst + (size_t)n * c;
+    float2 *d = dst + (size_t)n * (cols ? cols[c] : c);
     const float4 *s = src + ld2 * c;
     for (int m = lane; 2 * m < n; m += 32) {
       const float4 v = s[m];
@@ -618,7 +622,8 @@ template <int KP, int PW>
 __device__ __forceinline__ void pk_cross_pass(float4 (&aW)[KP], float4 (&aV)[KP], bool mine,
                                               float4 *sW, float4 *sVb, float *s_nb, int wb,
                                               float tol, float negl, unsigned &n_pairs,
-                                              unsigned &n_rot, int &rotated) {
+                                              unsigned &n_rot, int &rotated,
+                                              float *al_out = nullptr) {
   constexpr int LD2 = PkShape<KP>::LD2;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int unit = tid >> 4, ul = tid & 15;
@@ -683,6 +688,7 @@ __device__ __forceinline__ void pk_cross_pass(float4 (&aW)[KP], float4 (&aV)[KP]
     else
       __syncthreads();
   }
+  if (al_out) *al_out = al_reg;
 }
 
 // Panel a's W column `unit` of the staged panel moves to registers, with its V.
@@ -702,14 +708,15 @@ __device__ __forceinline__ void pk_to_registers(const float4 *sW, const float4 *
 template <int KP, int PW>
 __device__ __forceinline__ void pk_from_registers(const float4 (&aW)[KP], const float4 (&aV)[KP],
                                                   bool mine, float4 *sVa, float2 *Wa,
-                                                  float2 *Va, int nr, int nc, int wa) {
+                                                  float2 *Va, int nr, int nc, int wa,
+                                                  const int *cols = nullptr) {
   constexpr int LD2 = PkShape<KP>::LD2;
   const int unit = threadIdx.x >> 4, ul = threadIdx.x & 15;
 #pragma unroll
   for (int k = 0; k < KP; ++k) sVa[LD2 * unit + ul + 16 * k] = aV[k];
   __syncthreads();
   if (mine) {
-    float2 *wcol = Wa + (size_t)nr * unit;
+    float2 *wcol = Wa + (size_t)nr * (cols ? cols[unit] : unit);
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
       const int m = ul + 16 * k;
@@ -717,7 +724,7 @@ __device__ __forceinline__ void pk_from_registers(const float4 (&aW)[KP], const 
       if (2 * m + 1 < nr) wcol[2 * m + 1] = make_float2(aW[k].y, aW[k].w);
     }
   }
-  pk_stage_out<PW>(Va, sVa, LD2, nc, wa);
+  pk_stage_out<PW>(Va, sVa, LD2, nc, wa, cols);
 }
 
 // g_i = max(1 - t / sigma_i, 0) applied to V's columns (t < 0: V unscaled),
@@ -912,8 +919,12 @@ __global__ void __launch_bounds__(1024) k_slice_order(const int *__restrict__ sw
 // per slice: sweep, round in progress, tasks left in the round,
 // rotated-in-this-sweep; per slice (floats): tolerance, negligible squared
 // norm; the queue: cap 64-bit slots, each a task (its slice, round and pair)
-// and the mark of its position (slot i's mark is i + 1).
+// and the mark of its position (slot i's mark is i + 1); per slice,
+// kSortCols ints (the column order of its current sweep: panel p holds the
+// columns at positions p PW ...) and kSortCols floats (each column's squared
+// norm as the last task that rotated it left it).
 constexpr unsigned long long kTaskWaitNs = 2000000000ull;  // a wait for work gives up after 2 s
+constexpr int kSortCols = 256;  // columns of a task-graph slice at most (nc <= nr <= 256)
 
 __device__ __forceinline__ int ld_relaxed(const int *p) { return *(const volatile int *)p; }
 
@@ -969,6 +980,8 @@ struct TaskView {
   // queued being i + 1, written in one 64-bit exchange so that a reader sees
   // the task and its mark together
   unsigned long long *qslot;
+  int *perm;     // per slice, kSortCols: position -> column
+  float *norm;   // per slice, kSortCols: column -> squared norm
   int cap;
   __device__ TaskView(int *sched, int ns, int cap_) : cap(cap_) {
     head = sched;
@@ -982,6 +995,8 @@ struct TaskView {
     tol = (float *)(rot + ns);
     negl = tol + ns;
     qslot = (unsigned long long *)(negl + ns);  // 4 + 6 ns ints before it: 8-byte aligned
+    perm = (int *)(qslot + cap);
+    norm = (float *)(perm + (size_t)kSortCols * ns);
   }
   // queues the tasks of round r of slice s (one thread); a task is
   // (s kTaskRounds + r) kTaskIds + its pair index in the round
@@ -1003,6 +1018,29 @@ struct TaskView {
   }
 };
 
+// The order of a slice's columns for its next sweep, by the whole CTA: by
+// decreasing squared norm, ties by index (the norm-sorted ordering that de
+// Rijk proposed for one-sided Jacobi, 1989: sweeps that pair the large
+// columns first converge in fewer sweeps).  key: nc squared norms in shared
+// memory (a NaN or a negative value sorts as 0); perm[rank] = column.  The
+// ranks are counted, not sorted, so ties and the result are deterministic.
+__device__ void order_columns(int nc, float *key, int *perm) {
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+    const float v = key[i];
+    key[i] = v > 0.0f ? v : 0.0f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+    const float ki = key[i];
+    int rank = 0;
+    for (int j = 0; j < nc; ++j) {
+      const float kj = key[j];
+      rank += (kj > ki) || (kj == ki && j < i);
+    }
+    perm[rank] = i;
+  }
+}
+
 // Set-up of the task-graph run, one CTA per slice: V := I unless warm,
 // ||W||_F^2, the slice's tolerance and negligible squared norm; a slice whose
 // singular values are all cut (||W||_F <= t) ends here with 0 sweeps, the
@@ -1013,6 +1051,7 @@ __global__ void __launch_bounds__(kHW * 32)
                         float negl_rel, int *__restrict__ sweeps_out, JacOpt o, int *sched,
                         int cap, int pw) {
   __shared__ float s_red[32];
+  __shared__ float s_key[kSortCols];
   const int s = blockIdx.x;
   TaskView tv(sched, nslices, cap);
   float2 *W = W_all + (size_t)s * wstride, *V = V_all + (size_t)s * vstride;
@@ -1022,6 +1061,41 @@ __global__ void __launch_bounds__(kHW * 32)
   // the tensor-core Gram check showed that a sweep would rotate no pair
   const bool pre = !cut && o.conv && o.conv[s];
   if (cut || pre) pk_epilogue<false>(nr, nc, W, V, t);  // cut: every g_i is 0 (t >= 0), or V is kept
+  // the first sweep's column order: by the columns' squared norms, or as stored
+  int *perm = tv.perm + (size_t)kSortCols * s;
+  if (!(cut || pre)) {
+    if (o.sort) {
+      const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+      // two columns a warp at a time, every lane's loads of both issued together
+      for (int c = threadIdx.x >> 5; c < nc; c += 2 * nwarp) {
+        const int c2 = c + nwarp;
+        const float2 *w0 = W + (size_t)nr * c, *w1 = W + (size_t)nr * (c2 < nc ? c2 : c);
+        float2 x[8], y[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int r = lane + 32 * k;
+          x[k] = r < nr ? w0[r] : make_float2(0.f, 0.f);
+          y[k] = r < nr ? w1[r] : make_float2(0.f, 0.f);
+        }
+        float a = 0.f, b = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          a = fmaf(x[k].x, x[k].x, fmaf(x[k].y, x[k].y, a));
+          b = fmaf(y[k].x, y[k].x, fmaf(y[k].y, y[k].y, b));
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        if (lane == 0) {
+          s_key[c] = a;
+          if (c2 < nc) s_key[c2] = b;
+        }
+      }
+      __syncthreads();
+      order_columns(nc, s_key, perm);
+    } else {
+      for (int c = threadIdx.x; c < nc; c += blockDim.x) perm[c] = c;
+    }
+  }
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1047,12 +1121,13 @@ template <int KP, int PW>
 __global__ void __launch_bounds__(PW * 16, (KP <= 2 || PW == 16) ? 2 : 1)
     k_jacobi_tasks(int nr, int nc, int nslices, size_t wstride, size_t vstride, float2 *W_all,
                    float2 *V_all, float t, int max_sweeps, int *__restrict__ sweeps_out,
-                   unsigned long long *__restrict__ work, int *sched, int cap) {
+                   unsigned long long *__restrict__ work, int *sched, int cap, int sort) {
   extern __shared__ float4 smem_f4[];
   constexpr int LD2 = PkShape<KP>::LD2;
   float4 *sW = smem_f4, *sVa = sW + PW * LD2, *sVb = sVa + PW * LD2;
   __shared__ float s_na[PW], s_nb[PW];
-  __shared__ int s_task, s_last, s_end;
+  __shared__ int s_cola[PW], s_colb[PW];  // the panels' columns (the sweep's column order)
+  __shared__ int s_task, s_last, s_end, s_next;
   const int tid = threadIdx.x, ul = tid & 15, unit = tid >> 4;
   TaskView tv(sched, nslices, cap);
   const int npan = (nc + PW - 1) / PW, nrounds = tour_rounds(npan);
@@ -1097,27 +1172,38 @@ __global__ void __launch_bounds__(PW * 16, (KP <= 2 || PW == 16) ? 2 : 1)
     tour_pair(npan, r, pi, pa, pb);  // pa is a real panel; pb >= npan: pa's own pairs
     int rotated = 0;
     const int ca = pa * PW, wa = min(PW, nc - ca);
-    pk_stage_wv<PW, true, 2>(sW, W + (size_t)nr * ca, nr, s_na, sVa, V + (size_t)nc * ca, nc,
-                             LD2, wa);
+    const int cb = pb < npan ? pb * PW : 0, wb = pb < npan ? min(PW, nc - cb) : 0;
+    // the panels' columns in this sweep's order (written by the task that
+    // started the sweep, on another SM: read past L1)
+    int *perm = tv.perm + (size_t)kSortCols * s;
+    float *gnorm = tv.norm + (size_t)kSortCols * s;
+    if (tid < wa) s_cola[tid] = __ldcg(perm + ca + tid);
+    if (tid >= PW && tid - PW < wb) s_colb[tid - PW] = __ldcg(perm + cb + tid - PW);
+    __syncthreads();
+    pk_stage_wv<PW, true, 2>(sW, W, nr, s_na, sVa, V, nc, LD2, wa, s_cola);
     __syncthreads();
     if (pb >= npan) {  // panel pa's own pairs
       pk_intra<KP, PW>(sW, sVa, s_na, wa, tol, negl, n_pairs, n_rot, rotated);
       if (tid == 0) claim = atomicAdd(tv.head, 1);  // its latency hides behind the write-back
-      pk_stage_out<PW>(W + (size_t)nr * ca, sW, LD2, nr, wa);
-      pk_stage_out<PW>(V + (size_t)nc * ca, sVa, LD2, nc, wa);
+      if (sort && tid < wa) gnorm[s_cola[tid]] = s_na[tid];
+      pk_stage_out<PW>(W, sW, LD2, nr, wa, s_cola);
+      pk_stage_out<PW>(V, sVa, LD2, nc, wa, s_cola);
     } else {  // panel pa (registers) against panel pb (streamed)
-      const int cb = pb * PW, wb = min(PW, nc - cb);
       const bool mine = unit < wa;
       pk_to_registers<KP>(sW, sVa, aW, aV);
       __syncthreads();
-      pk_stage_wv<PW, true, 1>(sW, W + (size_t)nr * cb, nr, s_nb, sVb, V + (size_t)nc * cb, nc,
-                               LD2, wb);
-      pk_cross_pass<KP, PW>(aW, aV, mine, sW, sVb, s_nb, wb, tol, negl, n_pairs, n_rot, rotated);
+      pk_stage_wv<PW, true, 1>(sW, W, nr, s_nb, sVb, V, nc, LD2, wb, s_colb);
+      float al = 0.0f;
+      pk_cross_pass<KP, PW>(aW, aV, mine, sW, sVb, s_nb, wb, tol, negl, n_pairs, n_rot, rotated,
+                            &al);
       if (tid == 0) claim = atomicAdd(tv.head, 1);  // its latency hides behind the write-back
-      pk_stage_out<PW>(W + (size_t)nr * cb, sW, LD2, nr, wb);
-      pk_stage_out<PW>(V + (size_t)nc * cb, sVb, LD2, nc, wb);
-      pk_from_registers<KP, PW>(aW, aV, mine, sVa, W + (size_t)nr * ca, V + (size_t)nc * ca, nr,
-                                nc, wa);
+      if (sort) {
+        if (mine && ul == 0) gnorm[s_cola[unit]] = al;
+        if (tid < wb) gnorm[s_colb[tid]] = s_nb[tid];
+      }
+      pk_stage_out<PW>(W, sW, LD2, nr, wb, s_colb);
+      pk_stage_out<PW>(V, sVb, LD2, nc, wb, s_colb);
+      pk_from_registers<KP, PW>(aW, aV, mine, sVa, W, V, nr, nc, wa, s_cola);
     }
     // the panels are written (every thread fences its own stores); then the
     // task counts off its slice's round
@@ -1128,6 +1214,7 @@ __global__ void __launch_bounds__(PW * 16, (KP <= 2 || PW == 16) ? 2 : 1)
       __threadfence();
       s_last = atomicSub(tv.left + s, 1) == 1;
       s_end = 0;
+      s_next = -1;
       if (s_last) {  // this task completed the round: queue the next, or end the slice
         __threadfence();
         int next = r + 1;
@@ -1143,10 +1230,21 @@ __global__ void __launch_bounds__(PW * 16, (KP <= 2 || PW == 16) ? 2 : 1)
             next = 0;
           }
         }
-        if (!s_end) tv.push_round(s, next, npan);
+        if (!s_end) s_next = next;
       }
     }
     __syncthreads();
+    if (s_next == 0 && sort) {
+      // a new sweep: its column order from the norms the sweep's tasks left
+      // (every one of them fenced its stores before counting off its round)
+      float *key = (float *)smem_f4;
+      for (int c = tid; c < nc; c += blockDim.x) key[c] = __ldcg(gnorm + c);
+      __syncthreads();
+      order_columns(nc, key, perm);
+      __threadfence();
+      __syncthreads();
+    }
+    if (tid == 0 && s_next >= 0) tv.push_round(s, s_next, npan);
     if (s_end) {  // the slice ended: this CTA applies its epilogue and counts it
       pk_epilogue<true>(nr, nc, W, V, t);
       __threadfence();
@@ -1248,7 +1346,7 @@ cudaError_t launch_tasks(int nslices, int nr, int nc, size_t ws, size_t vs, floa
   if (e != cudaSuccess) return e;
   k_jacobi_tasks<KP, PW><<<(unsigned)grid, PW * 16, smem, st>>>(nr, nc, nslices, ws, vs, W, V, t,
                                                                   max_sweeps, sweeps, work,
-                                                                  o.sched, cap);
+                                                                  o.sched, cap, o.sort ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -1480,7 +1578,10 @@ bool tasks_pay(int nslices, int nr, int pw) {
   return nslices < nsm * per_sm;
 }
 
-size_t jacobi_task_ints(int nslices) { return 4 + 6 * (size_t)nslices + 2 * (size_t)task_cap(nslices); }
+size_t jacobi_task_ints(int nslices) {
+  return 4 + 6 * (size_t)nslices + 2 * (size_t)task_cap(nslices) +
+         2 * (size_t)kSortCols * nslices;
+}
 
 size_t jacobi_batch_smem(int max_nr) {
   const int KP = (max_nr + 31) / 32;

@@ -516,6 +516,7 @@ int e_factor(lrstv_unroll *u, int k, const float *F, const float *G4, double mu,
   o.group = d.h;
   o.sched = (u->flags & LRSTV_FLAG_JACOBI_PER_SLICE) ? nullptr : u->jsched;
   o.pw = (u->flags & LRSTV_FLAG_JACOBI_PANEL16) ? 16 : 32;
+  o.sort = (u->flags & LRSTV_FLAG_JACOBI_FIXED_ORDER) ? 0 : 1;
   UCK(launch_jacobi(d, (int)ns, Wk, Vk, -1.0f, kMaxSweeps, u->sweeps + (size_t)k * ns, nullptr,
                     st, o));
   UCK(launch_sigma_scale(d, (int)ns, Wk, Vk, t, sk, u->Hs, st));
@@ -666,7 +667,7 @@ int lrstv_unroll_create(int n1, int n2, int n3, int batch, int iters, const floa
   if (batch < 1 || iters < 1 || iters > 4096) return LRSTV_ERR_ARG;
   if (flags & ~(unsigned)(LRSTV_FLAG_SIMT_GEMM | LRSTV_FLAG_WARM_START | LRSTV_FLAG_SIMT_DFT |
                           LRSTV_FLAG_JACOBI_PER_SLICE | LRSTV_FLAG_JACOBI_PANEL16 |
-                          LRSTV_FLAG_UNROLL_RECOMPUTE))
+                          LRSTV_FLAG_JACOBI_FIXED_ORDER | LRSTV_FLAG_UNROLL_RECOMPUTE))
     return LRSTV_ERR_ARG;
   float wl[3] = {1.0f, 1.0f, 1.0f};
   if (w)

@@ -23,6 +23,7 @@ __all__ = [
     "lrstv_denoise", "BLOCK", "FLAG_F_THRESH_EXACT", "FLAG_NO_GAMMA4", "FLAG_GRAPH",
     "FLAG_STRICT", "FLAG_SIMT_GEMM", "FLAG_WARM_START", "FLAG_ISO_TV", "FLAG_BF16X3",
     "FLAG_SIMT_DFT", "FLAG_JACOBI_PER_SLICE", "FLAG_JACOBI_PANEL16", "FLAG_UNROLL_RECOMPUTE",
+    "FLAG_JACOBI_FIXED_ORDER",
     "EXPORTED",
 ]
 
@@ -38,6 +39,7 @@ FLAG_SIMT_DFT = 256
 FLAG_JACOBI_PER_SLICE = 512
 FLAG_JACOBI_PANEL16 = 1024
 FLAG_UNROLL_RECOMPUTE = 2048
+FLAG_JACOBI_FIXED_ORDER = 4096
 
 BLOCK = {"Y": 0, "L": 1, "Z": 2, "S": 3, "G1": 4, "G2": 5, "F": 6, "E": 7, "G3": 8, "G4": 9,
          "TZ": 10}
