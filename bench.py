@@ -571,7 +571,7 @@ def run_ours(args, wl_name):
                    "jacobi_schedule": ("task graph: panel-pair tasks of every slice on all SMs"
                                        if args.jacobi_schedule == "tasks" else "one CTA per slice"),
                    "jacobi_panel": args.jacobi_panel,
-                   "jacobi_order": ("columns by norm, largest first, each sweep (task graph)"
+                   "jacobi_order": ("columns by norm, largest first, each sweep"
                                     if args.jacobi_order == "sorted" else "stored order"),
                    "l_update": ("Tucker projection, one HOOI sweep per iteration, ranks %s" % (ranks,)
                                 if ranks else "plain (full Tucker ranks)"),
@@ -617,6 +617,8 @@ def run_batch(args):
     shapes = [r.shape for r in recs]
     Ys = [torch.from_numpy(flat(make_cube(r, 5000 + i)[1])).cuda() for i, r in enumerate(recs)]
     flags = lrstv.FLAG_WARM_START if args.jacobi_start == "warm" else 0
+    if args.jacobi_order == "fixed":
+        flags |= lrstv.FLAG_JACOBI_FIXED_ORDER
     params = [lrstv.Params.make(sh[0], sh[1], max_iter=BATCH["iters"], flags=flags)
               for sh in shapes]
     stream = torch.cuda.current_stream()
@@ -979,6 +981,8 @@ def run_sweep_profile(args):
     n1, n2, n3 = shape
     y = torch.from_numpy(flat(Y)).cuda()
     flags = lrstv.FLAG_WARM_START if args.jacobi_start == "warm" else 0
+    if args.jacobi_order == "fixed":
+        flags |= lrstv.FLAG_JACOBI_FIXED_ORDER
     with lrstv.Plan(n1, n2, n3, lrstv.Params.make(n1, n2, max_iter=wl["iters"], flags=flags)) as pl:
         if args.tucker:
             pl.set_tucker((max(1, round(0.8 * n1)), max(1, round(0.8 * n2)), min(args.tucker, n3)))
@@ -1026,8 +1030,8 @@ def build_parser():
                     help="the Jacobi's column panel width: 32 (16-warp CTAs) or 16 (8-warp CTAs, "
                          "two to an SM; LRSTV_FLAG_JACOBI_PANEL16)")
     ap.add_argument("--jacobi-order", choices=["sorted", "fixed"], default="sorted",
-                    help="task-graph Jacobi: order each sweep's columns by norm, largest first, "
-                         "or keep their stored order (LRSTV_FLAG_JACOBI_FIXED_ORDER)")
+                    help="the Jacobi orders each sweep's columns by norm, largest first, or "
+                         "keeps their stored order (LRSTV_FLAG_JACOBI_FIXED_ORDER)")
     ap.add_argument("--unroll-factors", choices=["keep", "recompute"], default="keep",
                     help="c5: keep every iteration's SVD factors from the forward pass, or "
                          "recompute them in the backward pass (LRSTV_FLAG_UNROLL_RECOMPUTE)")

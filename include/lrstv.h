@@ -84,12 +84,12 @@ typedef enum lrstv_status {
                                         CTAs (slices up to 256 rows; the same t-SVT to
                                         rounding, the pairs visited in another order).
                                         Batches run 32-column panels whatever the flag. */
-#define LRSTV_FLAG_JACOBI_FIXED_ORDER 4096u /* the task-graph Jacobi pairs a slice's columns in
-                                        their stored order in every sweep, instead of ordering
-                                        them by squared norm, largest first, at the start of
-                                        each sweep (de Rijk's ordering: fewer sweeps; the same
-                                        t-SVT to rounding).  The one-CTA-per-slice schedule
-                                        keeps the stored order either way. */
+#define LRSTV_FLAG_JACOBI_FIXED_ORDER 4096u /* the Jacobi pairs a slice's columns in their
+                                        stored order in every sweep, instead of ordering them
+                                        by squared norm, largest first, at the start of each
+                                        sweep (de Rijk's ordering: fewer sweeps; the same t-SVT
+                                        to rounding).  Slices of up to 256 rows, either
+                                        schedule; a batch follows its first cube's flag. */
 #define LRSTV_FLAG_UNROLL_RECOMPUTE 2048u /* unrolled iteration only: the forward pass keeps one
                                         slot of SVD factors instead of one per iteration, and
                                         the backward pass recomputes iteration k's factors

@@ -1334,7 +1334,7 @@ int batch_e_step(lrstv_batch *b, cudaStream_t st) {
     Span sp(prof, LRSTV_K_JACOBI, st);
     CK(launch_jacobi_batch(b->d_tasks, b->ntasks, b->d_counter, mu, kMaxSweeps,
                            prof->on ? prof->d_work : nullptr, b->grid, b->smem, st, warm,
-                           wflag ? 1 : 0, b->max_nr));
+                           wflag ? 1 : 0, b->max_nr, plan_sort(b->plans[0])));
   }
   for (int k = 0; k < b->ngroups; ++k) {
     const BatchGroup &g = b->groups[k];
@@ -1347,6 +1347,7 @@ int batch_e_step(lrstv_batch *b, cudaStream_t st) {
     o.ms2 = p->ms2;
     o.group = p->d.h;
     o.order = p->order;
+    o.sort = plan_sort(p);
     CK(launch_jacobi(p->d, 3 * p->d.h * g.m, p->specA, p->V, wflag ? -1.0f : o.t_svt,
                      kMaxSweeps, p->sweeps, p->prof.on ? p->prof.d_work : nullptr, st, o));
   }

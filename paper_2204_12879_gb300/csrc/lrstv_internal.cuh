@@ -179,8 +179,9 @@ struct JacOpt {
   // set ends after one sweep without running it (that sweep would rotate
   // no pair)
   const int *conv = nullptr;
-  // task-graph schedule: each sweep pairs the slice's columns in the order of
-  // their squared norms, largest first (0: in the stored order)
+  // packed kernels (slices of up to 256 rows, either schedule): each sweep
+  // pairs the slice's columns in the order of their squared norms, largest
+  // first (0: in the stored order)
   int sort = 1;
 };
 // The Jacobi's base tolerance for slices of nr rows: a pair is rotated when
@@ -233,10 +234,10 @@ constexpr int kBatchMaxNr = 256;  // the packed kernel's tallest slice
 size_t jacobi_batch_smem(int max_nr);
 // Persistent work-list Jacobi over `ntasks` slices; *counter must be 0.  warm:
 // as launch_jacobi; keep: V left unscaled (threshold taken as negative).
-// max_nr: the tallest slice (up to 256 rows).
+// max_nr: the tallest slice (up to 256 rows).  sort: as JacOpt::sort.
 cudaError_t launch_jacobi_batch(const SliceTask *tasks, int ntasks, int *counter, double mu,
                                 int max_sweeps, unsigned long long *work, int grid, size_t smem,
-                                cudaStream_t st, int warm, int keep, int max_nr);
+                                cudaStream_t st, int warm, int keep, int max_nr, int sort);
 
 // ------------------------------------------------------------------- api.cu
 constexpr size_t kAlign = 256;

@@ -751,6 +751,62 @@ __device__ __forceinline__ void pk_epilogue(int nr, int nc, const float2 *W, flo
   }
 }
 
+// Columns of a slice of the packed kernels at most (nc <= nr <= 256).
+constexpr int kSortCols = 256;
+
+// Squared norms of a slice's nc columns of nr <= 256 rows into key (shared
+// memory), by the whole CTA: two columns a warp at a time, every lane's loads
+// of both issued together.  W was written by an earlier launch.
+__device__ void col_norms(int nr, int nc, const float2 *W, float *key) {
+  const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int c = threadIdx.x >> 5; c < nc; c += 2 * nwarp) {
+    const int c2 = c + nwarp;
+    const float2 *w0 = W + (size_t)nr * c, *w1 = W + (size_t)nr * (c2 < nc ? c2 : c);
+    float2 x[8], y[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int r = lane + 32 * k;
+      x[k] = r < nr ? w0[r] : make_float2(0.f, 0.f);
+      y[k] = r < nr ? w1[r] : make_float2(0.f, 0.f);
+    }
+    float a = 0.f, b = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      a = fmaf(x[k].x, x[k].x, fmaf(x[k].y, x[k].y, a));
+      b = fmaf(y[k].x, y[k].x, fmaf(y[k].y, y[k].y, b));
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (lane == 0) {
+      key[c] = a;
+      if (c2 < nc) key[c2] = b;
+    }
+  }
+}
+
+// The order of a slice's columns for its next sweep, by the whole CTA: by
+// decreasing squared norm, ties by index (the norm-sorted ordering that de
+// Rijk proposed for one-sided Jacobi, 1989: sweeps that pair the large
+// columns first converge in fewer sweeps).  key: nc squared norms in shared
+// memory (a NaN or a negative value sorts as 0); perm[rank] = column.  The
+// ranks are counted, not sorted, so ties and the result are deterministic.
+__device__ void order_columns(int nc, float *key, int *perm) {
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+    const float v = key[i];
+    key[i] = v > 0.0f ? v : 0.0f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+    const float ki = key[i];
+    int rank = 0;
+    for (int j = 0; j < nc; ++j) {
+      const float kj = key[j];
+      rank += (kj > ki) || (kj == ki && j < i);
+    }
+    perm[rank] = i;
+  }
+}
+
 // The packed Jacobi SVT of one slice by the whole CTA (kHW warps): W (nr x nc)
 // and V (nc x nc) in global memory, `smem` the CTA's dynamic shared memory
 // (3 kPW LD2 float4).  Panel by panel: panel a's own pairs, then panel a (in
@@ -763,7 +819,8 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
                                                 int max_sweeps, float tol, float negl_rel,
                                                 int *sweeps_slot, unsigned long long *work,
                                                 float4 *smem, int warm, float skip_t,
-                                                float gms2, bool preconv = false) {
+                                                float gms2, bool preconv = false,
+                                                bool sort = false) {
   constexpr int LD2 = PkShape<KP>::LD2;
   float4 *sW = smem;              // panel a (own pairs), then panel b: W
   float4 *sVa = sW + PW * LD2;    // panel a: V
@@ -775,6 +832,10 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
   // a panel is staged, then carried through each rotation by the 2x2 update
   // (|a|^2 - d, |b|^2 + d), so that a pair's test needs only its inner product
   __shared__ float s_na[PW], s_nb[PW];
+  // with `sort`: the sweep's column order (position -> column; panel a holds
+  // positions a PW ...) and each column's squared norm as the sweep left it
+  __shared__ int s_perm[kSortCols];
+  __shared__ float s_key[kSortCols];
 
   const float fro2 = pk_setup<false>(nr, nc, W, V, warm, s_red);
   const float negl = negl_rel * fro2;
@@ -796,34 +857,51 @@ __device__ __forceinline__ void jacobi_pk_slice(int nr, int nc, float2 *W, float
   }
   tol = pk_tolerance(tol, fro2, nc, skip_t, gms2);
   float4 aW[KP], aV[KP];
+  if (!converged) {  // the first sweep's order: by the columns' norms, or as stored
+    if (sort) {
+      col_norms(nr, nc, W, s_key);
+      __syncthreads();
+      order_columns(nc, s_key, s_perm);
+    } else {
+      for (int c = tid; c < nc; c += blockDim.x) s_perm[c] = c;
+    }
+  }
   for (int sweep = 1; sweep <= max_sweeps && !converged; ++sweep) {
     if (tid == 0) s_rot = 0;
     int rotated = 0;
     for (int a = 0; a < npan; ++a) {
       const int ca = a * PW, wa = min(PW, nc - ca);
+      const int *cola = s_perm + ca;  // panel a: positions ca ... of the sweep's order
       __syncthreads();
-      pk_stage_wv<PW, false, 2>(sW, W + (size_t)nr * ca, nr, s_na, sVa, V + (size_t)nc * ca, nc,
-                                LD2, wa);
+      pk_stage_wv<PW, false, 2>(sW, W, nr, s_na, sVa, V, nc, LD2, wa, cola);
       __syncthreads();
       pk_intra<KP, PW>(sW, sVa, s_na, wa, tol, negl, n_pairs, n_rot, rotated);
+      if (sort && tid < wa) s_key[cola[tid]] = s_na[tid];
       const bool mine = unit < wa;
       pk_to_registers<KP>(sW, sVa, aW, aV);
       for (int b = a + 1; b < npan; ++b) {
         const int cb = b * PW, wb = min(PW, nc - cb);
+        const int *colb = s_perm + cb;
         __syncthreads();
-        pk_stage_wv<PW, false, 1>(sW, W + (size_t)nr * cb, nr, s_nb, sVb, V + (size_t)nc * cb,
-                                  nc, LD2, wb);
-        pk_cross_pass<KP, PW>(aW, aV, mine, sW, sVb, s_nb, wb, tol, negl, n_pairs, n_rot, rotated);
-        pk_stage_out<PW>(W + (size_t)nr * cb, sW, LD2, nr, wb);
-        pk_stage_out<PW>(V + (size_t)nc * cb, sVb, LD2, nc, wb);
+        pk_stage_wv<PW, false, 1>(sW, W, nr, s_nb, sVb, V, nc, LD2, wb, colb);
+        float al = 0.0f;
+        pk_cross_pass<KP, PW>(aW, aV, mine, sW, sVb, s_nb, wb, tol, negl, n_pairs, n_rot, rotated,
+                              &al);
+        if (sort) {
+          if (mine && ul == 0) s_key[cola[unit]] = al;
+          if (tid < wb) s_key[colb[tid]] = s_nb[tid];
+        }
+        pk_stage_out<PW>(W, sW, LD2, nr, wb, colb);
+        pk_stage_out<PW>(V, sVb, LD2, nc, wb, colb);
       }
-      pk_from_registers<KP, PW>(aW, aV, mine, sVa, W + (size_t)nr * ca, V + (size_t)nc * ca, nr,
-                                nc, wa);
+      pk_from_registers<KP, PW>(aW, aV, mine, sVa, W, V, nr, nc, wa, cola);
     }
     if (rotated) s_rot = 1;
     __syncthreads();
     sweeps = sweep;
     converged = (s_rot == 0);
+    // the next sweep's order, from the norms this one left
+    if (sort && !converged) order_columns(nc, s_key, s_perm);
     __syncthreads();
   }
   pk_epilogue<false>(nr, nc, W, V, t);
@@ -848,7 +926,7 @@ __global__ void __launch_bounds__(PW * 16, (KP <= 2 || PW == 16) ? 2 : 1)
   jacobi_pk_slice<KP, PW>(nr, nc, W_all + (size_t)s * wstride, V_all + (size_t)s * vstride, t,
                           max_sweeps, tol, negl_rel, sweeps_out + s, work, smem_f4, o.warm,
                           o.t_svt, o.ms2 ? o.ms2[s / o.group] : -1.0f,
-                          o.conv ? o.conv[s] != 0 : false);
+                          o.conv ? o.conv[s] != 0 : false, o.sort != 0);
 }
 
 // order[0..n) = the slices by the sweeps |sweeps[s]| of their previous run,
@@ -924,7 +1002,6 @@ __global__ void __launch_bounds__(1024) k_slice_order(const int *__restrict__ sw
 // columns at positions p PW ...) and kSortCols floats (each column's squared
 // norm as the last task that rotated it left it).
 constexpr unsigned long long kTaskWaitNs = 2000000000ull;  // a wait for work gives up after 2 s
-constexpr int kSortCols = 256;  // columns of a task-graph slice at most (nc <= nr <= 256)
 
 __device__ __forceinline__ int ld_relaxed(const int *p) { return *(const volatile int *)p; }
 
@@ -1018,29 +1095,6 @@ struct TaskView {
   }
 };
 
-// The order of a slice's columns for its next sweep, by the whole CTA: by
-// decreasing squared norm, ties by index (the norm-sorted ordering that de
-// Rijk proposed for one-sided Jacobi, 1989: sweeps that pair the large
-// columns first converge in fewer sweeps).  key: nc squared norms in shared
-// memory (a NaN or a negative value sorts as 0); perm[rank] = column.  The
-// ranks are counted, not sorted, so ties and the result are deterministic.
-__device__ void order_columns(int nc, float *key, int *perm) {
-  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-    const float v = key[i];
-    key[i] = v > 0.0f ? v : 0.0f;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-    const float ki = key[i];
-    int rank = 0;
-    for (int j = 0; j < nc; ++j) {
-      const float kj = key[j];
-      rank += (kj > ki) || (kj == ki && j < i);
-    }
-    perm[rank] = i;
-  }
-}
-
 // Set-up of the task-graph run, one CTA per slice: V := I unless warm,
 // ||W||_F^2, the slice's tolerance and negligible squared norm; a slice whose
 // singular values are all cut (||W||_F <= t) ends here with 0 sweeps, the
@@ -1065,31 +1119,7 @@ __global__ void __launch_bounds__(kHW * 32)
   int *perm = tv.perm + (size_t)kSortCols * s;
   if (!(cut || pre)) {
     if (o.sort) {
-      const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-      // two columns a warp at a time, every lane's loads of both issued together
-      for (int c = threadIdx.x >> 5; c < nc; c += 2 * nwarp) {
-        const int c2 = c + nwarp;
-        const float2 *w0 = W + (size_t)nr * c, *w1 = W + (size_t)nr * (c2 < nc ? c2 : c);
-        float2 x[8], y[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int r = lane + 32 * k;
-          x[k] = r < nr ? w0[r] : make_float2(0.f, 0.f);
-          y[k] = r < nr ? w1[r] : make_float2(0.f, 0.f);
-        }
-        float a = 0.f, b = 0.f;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          a = fmaf(x[k].x, x[k].x, fmaf(x[k].y, x[k].y, a));
-          b = fmaf(y[k].x, y[k].x, fmaf(y[k].y, y[k].y, b));
-        }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        if (lane == 0) {
-          s_key[c] = a;
-          if (c2 < nc) s_key[c2] = b;
-        }
-      }
+      col_norms(nr, nc, W, s_key);
       __syncthreads();
       order_columns(nc, s_key, perm);
     } else {
@@ -1274,7 +1304,7 @@ __global__ void __launch_bounds__(PW * 16, (KP <= 2 || PW == 16) ? 2 : 1)
 template <int KPMAX>
 __global__ void __launch_bounds__(kHW * 32, 1)
     k_jacobi_batch(const SliceTask *__restrict__ tasks, int ntasks, int *counter, double mu,
-                   int max_sweeps, unsigned long long *work, int warm, int keep) {
+                   int max_sweeps, unsigned long long *work, int warm, int keep, int sort) {
   extern __shared__ float4 smem_f4[];
   __shared__ int s_item;
   const float eps = FLT_EPSILON * 0.5f;
@@ -1291,17 +1321,17 @@ __global__ void __launch_bounds__(kHW * 32, 1)
     const float negl = ((float)tk.nr * eps) * ((float)tk.nr * eps);
     const int KP = (tk.nr + 31) / 32;
     if (KP <= 1)
-      jacobi_pk_slice<1, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f, tk.conv ? *tk.conv != 0 : false);
+      jacobi_pk_slice<1, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f, tk.conv ? *tk.conv != 0 : false, sort != 0);
     else if (KP <= 2)
-      jacobi_pk_slice<2, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f, tk.conv ? *tk.conv != 0 : false);
+      jacobi_pk_slice<2, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f, tk.conv ? *tk.conv != 0 : false, sort != 0);
     else if (KP <= 4)
-      jacobi_pk_slice<4, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f, tk.conv ? *tk.conv != 0 : false);
+      jacobi_pk_slice<4, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f, tk.conv ? *tk.conv != 0 : false, sort != 0);
     else if (KP <= 5)
-      jacobi_pk_slice<5, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f, tk.conv ? *tk.conv != 0 : false);
+      jacobi_pk_slice<5, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f, tk.conv ? *tk.conv != 0 : false, sort != 0);
     else if (KPMAX <= 7 || KP <= 7)
-      jacobi_pk_slice<7, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f, tk.conv ? *tk.conv != 0 : false);
+      jacobi_pk_slice<7, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f, tk.conv ? *tk.conv != 0 : false, sort != 0);
     else
-      jacobi_pk_slice<KPMAX, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f, tk.conv ? *tk.conv != 0 : false);
+      jacobi_pk_slice<KPMAX, kPW>(tk.nr, tk.nc, tk.W, tk.V, t, max_sweeps, tol, negl, tk.sweeps, work, smem_f4, warm, tt, tk.ms2 ? *tk.ms2 : -1.0f, tk.conv ? *tk.conv != 0 : false, sort != 0);
   }
 }
 
@@ -1596,7 +1626,7 @@ size_t jacobi_batch_smem(int max_nr) {
 
 cudaError_t launch_jacobi_batch(const SliceTask *tasks, int ntasks, int *counter, double mu,
                                 int max_sweeps, unsigned long long *work, int grid, size_t smem,
-                                cudaStream_t st, int warm, int keep, int max_nr) {
+                                cudaStream_t st, int warm, int keep, int max_nr, int sort) {
   if (ntasks <= 0) return cudaSuccess;
   const bool tall = max_nr > 224;
   cudaError_t e = cudaFuncSetAttribute(tall ? k_jacobi_batch<8> : k_jacobi_batch<7>,
@@ -1604,10 +1634,10 @@ cudaError_t launch_jacobi_batch(const SliceTask *tasks, int ntasks, int *counter
   if (e != cudaSuccess) return e;
   if (tall)
     k_jacobi_batch<8><<<grid, kHW * 32, smem, st>>>(tasks, ntasks, counter, mu, max_sweeps, work,
-                                                     warm, keep);
+                                                     warm, keep, sort);
   else
     k_jacobi_batch<7><<<grid, kHW * 32, smem, st>>>(tasks, ntasks, counter, mu, max_sweeps, work,
-                                                     warm, keep);
+                                                     warm, keep, sort);
   return cudaGetLastError();
 }
 
