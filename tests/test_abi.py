@@ -71,8 +71,14 @@ def test_argument_errors_before_any_cuda_call(lib):
     assert lib.lrstv_plan_create(8, 8, 8, None, ctypes.byref(h)) == 1
     bad = lrstv.Params.make(8, 8, mu0=-1.0)
     assert lib.lrstv_plan_create(8, 8, 8, ctypes.byref(bad), ctypes.byref(h)) == 1
-    bad = lrstv.Params.make(8, 8, flags=1 << 11)
-    assert lib.lrstv_plan_create(8, 8, 8, ctypes.byref(bad), ctypes.byref(h)) == 1
+    # LRSTV_FLAG_UNROLL_RECOMPUTE belongs to the unrolled form; 1 << 13 is no flag
+    for f in (lrstv.FLAG_UNROLL_RECOMPUTE, 1 << 13):
+        bad = lrstv.Params.make(8, 8, flags=f)
+        assert lib.lrstv_plan_create(8, 8, 8, ctypes.byref(bad), ctypes.byref(h)) == 1
+    # the unrolled form refuses the plan-only flags and unknown bits before any CUDA call
+    w = (ctypes.c_float * 3)(1, 1, 1)
+    for f in (lrstv.FLAG_ISO_TV, lrstv.FLAG_BF16X3, lrstv.FLAG_GRAPH, 1 << 13):
+        assert lib.lrstv_unroll_create(8, 8, 4, 1, 2, w, f, ctypes.byref(h)) == 1, f
     # the split-BF16 GEMMs exist on the tensor-core path only
     bad = lrstv.Params.make(8, 8, flags=lrstv.FLAG_BF16X3 | lrstv.FLAG_SIMT_GEMM)
     assert lib.lrstv_plan_create(8, 8, 8, ctypes.byref(bad), ctypes.byref(h)) == 1
